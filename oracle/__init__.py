@@ -1,0 +1,249 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+use this package.  The product library never imports it.  It wraps the plain C
+in ``tomo_oracle.c`` (built with gcc, ``-ffp-contract=off``, OpenMP) through
+ctypes and promotes every float32 input to float64.
+
+Function map (paper: "Sparse Matrix-Based HPC Tomography"):
+  build_matrix      Sec. 2 projection integral, discretised as chord lengths;
+                    Sec. 3.1 CSR sorted by row and column, transpose stored apart
+  project / backproject   y = A x, x' = A^T y per slice (Sec. 3, SpMV / SpMM)
+  project_mf / backproject_mf   the same without storing A
+  sirt / cgls       Sec. 2.1 iterative solvers (classical SIRT, textbook CGLS)
+  loss_grad         Sec. 2.1 model-based objective with a TV prior
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tomo_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lib = None
+
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_ptr = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (idempotent)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.oracle_threads.restype = _i32
+        lib.oracle_count.restype = _i64
+        lib.oracle_row.restype = _i64
+        lib.oracle_weight.restype = _i32
+        lib.oracle_loss_grad.restype = _dbl
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_ptr)
+
+
+def threads() -> int:
+    return int(_load().oracle_threads())
+
+
+@dataclasses.dataclass
+class Geometry:
+    nx: int
+    ny: int
+    n_p: int
+    n_theta: int
+    angles: Optional[np.ndarray] = None   # radians; None -> m*pi/n_theta
+    center: Optional[float] = None         # None -> n_p/2
+
+    def theta(self) -> np.ndarray:
+        if self.angles is not None:
+            return np.ascontiguousarray(self.angles, dtype=np.float64)
+        t = np.empty(self.n_theta)
+        _load().oracle_default_angles(_i32(self.n_theta), _p(t))
+        return t
+
+    def c(self) -> float:
+        return self.n_p / 2.0 if self.center is None else float(self.center)
+
+    def trig(self):
+        th = self.theta()
+        cs = np.empty(self.n_theta)
+        sn = np.empty(self.n_theta)
+        _load().oracle_trig(_i32(self.n_theta), _p(th), _p(cs), _p(sn))
+        return cs, sn
+
+    @property
+    def rows(self) -> int:
+        return self.n_theta * self.n_p
+
+    @property
+    def cols(self) -> int:
+        return self.nx * self.ny
+
+
+@dataclasses.dataclass
+class CSR:
+    rows: int
+    cols: int
+    row_ptr: np.ndarray   # int64 [rows+1]
+    col: np.ndarray       # int32 [nnz]
+    val: np.ndarray       # float64 [nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def transpose(self) -> "CSR":
+        lib = _load()
+        trp = np.empty(self.cols + 1, np.int64)
+        tci = np.empty(self.nnz, np.int32)
+        tv = np.empty(self.nnz, np.float64)
+        lib.oracle_transpose(_i64(self.rows), _i64(self.cols), _p(self.row_ptr), _p(self.col),
+                             _p(self.val), _p(trp), _p(tci), _p(tv))
+        return CSR(self.cols, self.rows, trp, tci, tv)
+
+    def dense(self) -> np.ndarray:
+        d = np.zeros((self.rows, self.cols))
+        for i in range(self.rows):
+            for e in range(self.row_ptr[i], self.row_ptr[i + 1]):
+                d[i, self.col[e]] += self.val[e]
+        return d
+
+    def apply(self, x: np.ndarray) -> np.ndarray:
+        """Row-wise SpMV of every slice: x (nz, cols) -> (nz, rows), float64."""
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, self.cols))
+        nz = x.shape[0]
+        y = np.empty((nz, self.rows))
+        _load().oracle_spmv(_i64(self.rows), _i64(self.cols), _p(self.row_ptr), _p(self.col),
+                            _p(self.val), _i32(nz), _p(x), _p(y))
+        return y
+
+
+def weight(g: Geometry, m: int, k: int, ix: int, iy: int) -> Optional[float]:
+    cs, sn = g.trig()
+    L = _dbl(0.0)
+    hit = _load().oracle_weight(_i32(g.nx), _i32(g.ny), _dbl(g.c()), _dbl(cs[m]), _dbl(sn[m]),
+                                _i32(k), _i32(ix), _i32(iy), ctypes.byref(L))
+    return L.value if hit else None
+
+
+def build_matrix(g: Geometry) -> CSR:
+    """A as CSR (int64 row_ptr, int32 col ascending per row, float64 values)."""
+    lib = _load()
+    cs, sn = g.trig()
+    counts = np.empty(g.rows, np.int64)
+    nnz = lib.oracle_count(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()),
+                           _p(cs), _p(sn), _p(counts))
+    rp = np.zeros(g.rows + 1, np.int64)
+    np.cumsum(counts, out=rp[1:])
+    col = np.empty(nnz, np.int32)
+    val = np.empty(nnz, np.float64)
+    lib.oracle_fill(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()),
+                    _p(cs), _p(sn), _p(rp), _p(col), _p(val))
+    return CSR(g.rows, g.cols, rp, col, val)
+
+
+def row(g: Geometry, i: int):
+    """Row i of A by brute force over all pixels: (cols int32, vals float64)."""
+    cs, sn = g.trig()
+    m, k = divmod(int(i), g.n_p)
+    cap = 2 * (g.nx + g.ny) + 8
+    col = np.empty(cap, np.int32)
+    val = np.empty(cap, np.float64)
+    n = _load().oracle_row(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _dbl(g.c()), _dbl(cs[m]),
+                           _dbl(sn[m]), _i32(k), _p(col), _p(val), _i64(cap))
+    assert n <= cap
+    return col[:n].copy(), val[:n].copy()
+
+
+def project(A: CSR, x) -> np.ndarray:
+    return A.apply(x)
+
+
+def backproject(AT: CSR, y) -> np.ndarray:
+    return AT.apply(y)
+
+
+def project_mf(g: Geometry, x) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, g.cols))
+    nz = x.shape[0]
+    cs, sn = g.trig()
+    y = np.empty((nz, g.rows))
+    _load().oracle_project_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()),
+                              _p(cs), _p(sn), _i32(nz), _p(x), _p(y))
+    return y
+
+
+def backproject_mf(g: Geometry, y) -> np.ndarray:
+    y = np.ascontiguousarray(np.asarray(y, np.float64).reshape(-1, g.rows))
+    nz = y.shape[0]
+    cs, sn = g.trig()
+    x = np.empty((nz, g.cols))
+    _load().oracle_backproject_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta),
+                                  _dbl(g.c()), _p(cs), _p(sn), _i32(nz), _p(y), _p(x))
+    return x
+
+
+def inv_row_sums(M: CSR) -> np.ndarray:
+    out = np.empty(M.rows)
+    _load().oracle_inv_row_sums(_i64(M.rows), _p(M.row_ptr), _p(M.val), _p(out))
+    return out
+
+
+def sirt(A: CSR, AT: CSR, b, iters: int, lam: float = 1.0, x0=None) -> np.ndarray:
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1, A.rows))
+    nz = b.shape[0]
+    x = np.zeros((nz, A.cols)) if x0 is None else np.array(x0, np.float64).reshape(nz, A.cols)
+    x = np.ascontiguousarray(x)
+    _load().oracle_sirt(_i64(A.rows), _i64(A.cols), _p(A.row_ptr), _p(A.col), _p(A.val),
+                        _p(AT.row_ptr), _p(AT.col), _p(AT.val), _i32(nz), _p(b), _p(x),
+                        _i32(iters), _dbl(lam))
+    return x
+
+
+def cgls(A: CSR, AT: CSR, b, iters: int):
+    """Returns (x (nz, cols), hist (iters, nz) of ||r|| after each iteration)."""
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1, A.rows))
+    nz = b.shape[0]
+    x = np.zeros((nz, A.cols))
+    hist = np.zeros((max(iters, 1), nz))
+    _load().oracle_cgls(_i64(A.rows), _i64(A.cols), _p(A.row_ptr), _p(A.col), _p(A.val),
+                        _p(AT.row_ptr), _p(AT.col), _p(AT.val), _i32(nz), _p(b), _p(x),
+                        _i32(iters), _p(hist))
+    return x, hist[:iters]
+
+
+def loss_grad(A: CSR, AT: CSR, nx: int, ny: int, x, b, mu: float = 1e-3, eps: float = 1e-3):
+    """(f, grad) of sum ||A x - b||^2 + mu * TV_eps(x); x (nz, ny*nx), b (nz, rows)."""
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, A.cols))
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1, A.rows))
+    nz = x.shape[0]
+    g = np.empty_like(x)
+    f = _load().oracle_loss_grad(_i64(A.rows), _i64(A.cols), _p(A.row_ptr), _p(A.col), _p(A.val),
+                                 _p(AT.row_ptr), _p(AT.col), _p(AT.val), _i32(nx), _i32(ny),
+                                 _i32(nz), _p(x), _p(b), _dbl(mu), _dbl(eps), _p(g))
+    return float(f), g

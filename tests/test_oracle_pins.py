@@ -1,0 +1,351 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test states what fixes the expected value: a special angle where the chord
+lengths are known exactly, an independent clipping algorithm, a closed-form
+projection, a conservation law, the definition of the transpose, a spectral
+closed form of the SIRT recurrence, the Krylov-subspace minimiser that CGLS
+must reproduce, or finite differences of the objective.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.sparse
+
+import oracle
+from paper_2003_12677_b300 import inputs
+
+
+# ---------------------------------------------------------------------------
+# independent chord-length reference: Liang-Barsky clipping of the ray
+# ---------------------------------------------------------------------------
+
+def clip_length(theta, p, xc, yc):
+    """Length of {x cos t + y sin t = p} inside the unit square centred (xc, yc).
+
+    The line is parametrised as p*(cos, sin) + s*(-sin, cos) and the s-range
+    clipped against the four slabs (Liang & Barsky, 1984)."""
+    c, s_ = math.cos(theta), math.sin(theta)
+    x0, y0 = p * c, p * s_
+    dx, dy = -s_, c
+    lo, hi = -1e300, 1e300
+    for d, o, a, b in ((dx, x0, xc - 0.5, xc + 0.5), (dy, y0, yc - 0.5, yc + 0.5)):
+        if abs(d) < 1e-300:
+            if o < a or o > b:
+                return 0.0
+            continue
+        t1, t2 = (a - o) / d, (b - o) / d
+        lo, hi = max(lo, min(t1, t2)), min(hi, max(t1, t2))
+    return max(0.0, hi - lo)
+
+
+@pytest.mark.parametrize("nx,ny,n_p,center,angles", [
+    (8, 8, 8, None, [0.0, math.pi / 4, math.pi / 2, 0.3, 1.1, 2.0, 2.9, 3.0]),
+    (8, 8, 11, 5.3, [0.05, 0.7, 1.5707, 1.6, 2.356194490192345, 3.1]),
+    (7, 9, 12, None, list(np.random.default_rng(3).uniform(0, math.pi, 10))),
+])
+def test_weights_match_clipping(nx, ny, n_p, center, angles):
+    g = oracle.Geometry(nx, ny, n_p, len(angles), np.array(angles), center)
+    A = oracle.build_matrix(g)
+    cs, sn = g.trig()
+    c = g.c()
+    dense = A.dense()
+    checked = 0
+    for m, th in enumerate(g.theta()):
+        a = max(abs(cs[m]), abs(sn[m]))
+        e = min(abs(cs[m]), abs(sn[m]))
+        h = 0.5 * (a + e)
+        for k in range(n_p):
+            p = k + 0.5 - c
+            for iy in range(ny):
+                for ix in range(nx):
+                    xc, yc = ix + 0.5 - nx / 2, iy + 0.5 - ny / 2
+                    delta = abs(p - (xc * cs[m] + yc * sn[m]))
+                    if abs(delta - h) < 1e-9:
+                        continue  # line through a corner / along an edge
+                    ref = clip_length(th, p, xc, yc)
+                    got = dense[m * n_p + k, iy * nx + ix]
+                    assert abs(got - ref) < 1e-12, (m, k, ix, iy, got, ref)
+                    checked += 1
+    assert checked > 0.9 * A.rows * A.cols
+
+
+def test_structure_invariants():
+    g = oracle.Geometry(32, 32, 40, 17, center=19.25)
+    A = oracle.build_matrix(g)
+    rp, col, val = A.row_ptr, A.col, A.val
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0)
+    for i in range(A.rows):
+        cc = col[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(cc) > 0)  # strictly ascending, no duplicates
+    assert np.all(val > 0) and np.all(val <= math.sqrt(2) + 1e-15)
+    assert col.min() >= 0 and col.max() < A.cols
+    # the brute-force row walk over every pixel gives the same rows
+    for i in list(range(0, A.rows, 37)) + [A.rows - 1]:
+        c2, v2 = oracle.row(g, i)
+        np.testing.assert_array_equal(c2, col[rp[i]:rp[i + 1]])
+        np.testing.assert_array_equal(v2, val[rp[i]:rp[i + 1]])
+
+
+def test_theta_zero_is_column_sum():
+    """theta = 0: ray k is the pixel column ix = k; every chord is exactly 1."""
+    n = 16
+    g = oracle.Geometry(n, n, n, 4)
+    A = oracle.build_matrix(g)
+    for k in range(n):
+        cc = A.col[A.row_ptr[k]:A.row_ptr[k + 1]]
+        vv = A.val[A.row_ptr[k]:A.row_ptr[k + 1]]
+        np.testing.assert_array_equal(cc, np.arange(n) * n + k)
+        assert np.all(vv == 1.0)
+
+
+def test_theta_half_pi_is_row_sum():
+    """theta = pi/2 (m = 1 of 2 angles): ray k is the pixel row iy = k, chord 1."""
+    n = 16
+    g = oracle.Geometry(n, n, n, 2)
+    A = oracle.build_matrix(g)
+    for k in range(n):
+        i = n + k
+        cc = A.col[A.row_ptr[i]:A.row_ptr[i + 1]]
+        vv = A.val[A.row_ptr[i]:A.row_ptr[i + 1]]
+        np.testing.assert_array_equal(cc, k * n + np.arange(n))
+        assert np.all(vv == 1.0)
+
+
+def _disk_error(n, n_theta=24):
+    r = 0.3 * n
+    g = oracle.Geometry(n, n, n, n_theta)
+    A = oracle.build_matrix(g)
+    x = (np.arange(n) + 0.5 - n / 2)
+    X, Y = np.meshgrid(x, x)
+    img = (X * X + Y * Y <= r * r).astype(np.float64)
+    y = A.apply(img.reshape(1, -1)).reshape(n_theta, n)
+    s = np.arange(n) + 0.5 - n / 2
+    ref = np.where(np.abs(s) < r, 2 * np.sqrt(np.maximum(r * r - s * s, 0)), 0.0)
+    ref = np.broadcast_to(ref, y.shape)
+    return np.linalg.norm(y - ref) / np.linalg.norm(ref)
+
+
+def test_uniform_disk_closed_form():
+    """Centred disk of radius r: every projection is 2 sqrt(r^2 - s^2)."""
+    e64, e128, e256 = _disk_error(64), _disk_error(128), _disk_error(256)
+    assert e128 < 3e-2
+    assert e256 < e128 < e64          # pixelisation error falls as n doubles
+
+
+def test_gaussian_blob_closed_form():
+    """exp(-r^2/2 sigma^2) projects to sqrt(2 pi) sigma exp(-s^2/2 sigma^2)."""
+    n, sig, nt = 96, 6.0, 12
+    g = oracle.Geometry(n, n, n, nt)
+    A = oracle.build_matrix(g)
+    x = np.arange(n) + 0.5 - n / 2
+    X, Y = np.meshgrid(x, x)
+    img = np.exp(-(X * X + Y * Y) / (2 * sig * sig))
+    y = A.apply(img.reshape(1, -1)).reshape(nt, n)
+    ref = math.sqrt(2 * math.pi) * sig * np.exp(-x * x / (2 * sig * sig))
+    err = np.linalg.norm(y - ref[None, :]) / np.linalg.norm(np.broadcast_to(ref, y.shape))
+    assert err < 1e-3
+
+
+def test_ellipse_closed_form():
+    """Random ellipses: the discrete projection approaches the analytic one."""
+    errs = []
+    for n in (64, 128, 256):
+        rng = np.random.default_rng(7)
+        ell = inputs.random_ellipses(n, rng, 6)
+        g = oracle.Geometry(n, n, n, 16)
+        A = oracle.build_matrix(g)
+        y = A.apply(inputs.rasterize(ell, n, n).reshape(1, -1)).reshape(16, n)
+        ref = inputs.project_ellipses(ell, g.theta(), n)
+        errs.append(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    assert errs[2] < errs[0] and errs[1] < 5e-2
+
+
+def test_mass_conservation():
+    """sum_k (A x)_{m,k} = sum_j x_j: exact at theta = 0 and pi/2 (unit chords),
+    within the unit-spacing sampling error of the chord trapezoid elsewhere."""
+    n = 128
+    nt = 8
+    g = oracle.Geometry(n, n, n, nt)
+    A = oracle.build_matrix(g)
+    ell = inputs.random_ellipses(n, np.random.default_rng(11))
+    img = inputs.rasterize(ell, n, n)
+    y = A.apply(img.reshape(1, -1)).reshape(nt, n)
+    tot = img.sum()
+    rel = np.abs(y.sum(axis=1) - tot) / tot
+    assert rel[0] < 1e-13 and rel[nt // 2] < 1e-13
+    assert rel.max() < 1e-3
+
+
+def test_transpose_is_exact_transpose():
+    g = oracle.Geometry(24, 20, 30, 13, center=14.6)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    S = scipy.sparse.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.rows, A.cols))
+    T = S.T.tocsr()
+    T.sort_indices()
+    np.testing.assert_array_equal(AT.row_ptr, T.indptr)
+    np.testing.assert_array_equal(AT.col, T.indices)
+    np.testing.assert_array_equal(AT.val, T.data)
+
+
+def test_adjoint_identity_fp64():
+    g = oracle.Geometry(40, 40, 44, 31)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((3, A.cols))
+    y = rng.standard_normal((3, A.rows))
+    lhs = np.sum(A.apply(x) * y)
+    rhs = np.sum(x * AT.apply(y))
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs) * 10
+
+
+def test_matrix_free_equals_stored():
+    g = oracle.Geometry(33, 33, 35, 21, center=17.2)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    rng = np.random.default_rng(9)
+    x = rng.random((2, A.cols))
+    y = rng.random((2, A.rows))
+    np.testing.assert_array_equal(oracle.project_mf(g, x), A.apply(x))
+    np.testing.assert_array_equal(oracle.backproject_mf(g, y), AT.apply(y))
+
+
+# ---------------------------------------------------------------------------
+# SIRT: spectral closed form of the preconditioned Landweber recurrence
+# ---------------------------------------------------------------------------
+
+def _inv(v):
+    """Reciprocal with 1/0 -> 0 (rays that miss the image carry no weight)."""
+    out = np.zeros_like(v)
+    out[v != 0] = 1.0 / v[v != 0]
+    return out
+
+
+def _small_system(n=8, nt=16, n_p=12, seed=0):
+    g = oracle.Geometry(n, n, n_p, nt)
+    A = oracle.build_matrix(g)
+    return g, A, A.transpose()
+
+
+def test_sirt_spectral_closed_form():
+    """x_k = C^1/2 V f_k(mu) V^T lam C^1/2 A^T R b, with C^1/2 H C^1/2 = V mu V^T,
+    H = A^T R A and f_k(mu) = (1 - (1 - lam mu)^k)/(lam mu) (k when mu = 0)."""
+    g, A, AT = _small_system()
+    D = A.dense()
+    R = _inv(D.sum(axis=1))
+    C = _inv(D.sum(axis=0))
+    rng = np.random.default_rng(1)
+    b = rng.random(A.rows)
+    lam = 0.9
+    H = D.T @ (R[:, None] * D)
+    Ch = np.sqrt(C)
+    S = Ch[:, None] * H * Ch[None, :]
+    mu, V = scipy.linalg.eigh(S)
+    gvec = lam * Ch * (D.T @ (R * b))
+    for k in (1, 2, 7, 40):
+        lm = lam * mu
+        fk = np.where(np.abs(lm) > 1e-14, (1 - (1 - lm) ** k) / np.where(lm == 0, 1, lm), k)
+        ref = Ch * (V @ (fk * (V.T @ gvec)))
+        got = oracle.sirt(A, AT, b[None], k, lam)[0]
+        assert np.max(np.abs(got - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_sirt_limit_is_weighted_least_squares():
+    """The SIRT fixed point solves min ||R^1/2 (A x - b)|| (unique: full rank)."""
+    g, A, AT = _small_system()
+    D = A.dense()
+    assert np.linalg.matrix_rank(D) == A.cols
+    R = _inv(D.sum(axis=1))
+    rng = np.random.default_rng(2)
+    b = rng.random(A.rows)
+    ref = np.linalg.lstsq(np.sqrt(R)[:, None] * D, np.sqrt(R) * b, rcond=None)[0]
+    got = oracle.sirt(A, AT, b[None], 100000, 1.0)[0]
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# CGLS: the k-th iterate minimises ||A x - b|| over the Krylov space
+# ---------------------------------------------------------------------------
+
+def _krylov_min(D, b, k):
+    H = D.T @ D
+    q = D.T @ b
+    Q = np.zeros((D.shape[1], k))
+    v = q / np.linalg.norm(q)
+    for j in range(k):
+        for _ in range(2):  # Gram-Schmidt twice
+            v = v - Q[:, :j] @ (Q[:, :j].T @ v)
+        v = v / np.linalg.norm(v)
+        Q[:, j] = v
+        v = H @ v
+    y = np.linalg.lstsq(D @ Q, b, rcond=None)[0]
+    return Q @ y
+
+
+def test_cgls_krylov_minimiser():
+    g, A, AT = _small_system()
+    D = A.dense()
+    rng = np.random.default_rng(4)
+    b = rng.random((2, A.rows))
+    for k in (1, 2, 3, 5, 8, 10):
+        x, hist = oracle.cgls(A, AT, b, k)
+        for s in range(2):
+            ref = _krylov_min(D, b[s], k)
+            assert np.linalg.norm(x[s] - ref) <= 1e-9 * np.linalg.norm(ref)
+            assert abs(hist[-1, s] - np.linalg.norm(D @ ref - b[s])) <= 1e-9 * np.linalg.norm(b[s])
+
+
+def test_cgls_reaches_lstsq():
+    g, A, AT = _small_system()
+    D = A.dense()
+    b = np.random.default_rng(6).random(A.rows)
+    ref = np.linalg.lstsq(D, b, rcond=None)[0]
+    x, _ = oracle.cgls(A, AT, b[None], 200)
+    assert np.linalg.norm(x[0] - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_cgls_zero_rhs_freezes():
+    g, A, AT = _small_system()
+    x, hist = oracle.cgls(A, AT, np.zeros((1, A.rows)), 5)
+    assert np.all(x == 0) and np.all(hist == 0)
+
+
+# ---------------------------------------------------------------------------
+# loss / gradient of ||A x - b||^2 + mu TV_eps(x)
+# ---------------------------------------------------------------------------
+
+def test_tv_value_hand_computed():
+    """2x2 image [[0,1],[2,3]] with data term 0: TV = sqrt(5+e^2) + sqrt(4+e^2)
+    + sqrt(1+e^2) + e (forward differences, zero on the last row / column)."""
+    g = oracle.Geometry(2, 2, 3, 3)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    x = np.array([[0.0, 1.0, 2.0, 3.0]])
+    b = A.apply(x)
+    mu, eps = 0.5, 0.1
+    f, grad = oracle.loss_grad(A, AT, 2, 2, x, b, mu, eps)
+    ref = mu * (math.sqrt(5 + eps ** 2) + math.sqrt(4 + eps ** 2) + math.sqrt(1 + eps ** 2) + eps)
+    assert abs(f - ref) < 1e-14
+
+
+def test_gradient_finite_differences():
+    n = 12
+    g = oracle.Geometry(n, n, 14, 10)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    rng = np.random.default_rng(8)
+    x = rng.random((2, A.cols))
+    b = rng.random((2, A.rows))
+    f0, grad = oracle.loss_grad(A, AT, n, n, x, b, 1e-3, 1e-3)
+    h = 1e-3
+    for _ in range(64):
+        v = rng.standard_normal(x.shape)
+        v /= np.linalg.norm(v)
+        fp, _ = oracle.loss_grad(A, AT, n, n, x + h * v, b, 1e-3, 1e-3)
+        fm, _ = oracle.loss_grad(A, AT, n, n, x - h * v, b, 1e-3, 1e-3)
+        fd = (fp - fm) / (2 * h)
+        an = float(np.sum(grad * v))
+        assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
