@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Throughput of batched projection + backprojection inside SIRT.
+
+Workload (default): 64 slices of 512x512 pixels, 360 angles over [0, pi), 512
+detector bins; seeded random-ellipsoid phantom with analytic projections and
+Poisson noise at 1e4 photons/ray; SIRT, 100 iterations per solve.  One step is
+one full SIRT solve of the 64-slice batch (interleave, 100 iterations of the
+fused A / A^T passes replayed from a CUDA graph, de-interleave).  The matrix is
+built once before timing (its build time is reported separately).
+
+Metric: slice-iterations per second (one slice-iteration = one application of
+A and of A^T to one slice plus the SIRT update), summed over all ranks.
+
+Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU: one process per GPU (torchrun); every rank solves its own batch
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "proj+backproj slice-iters/s"
+UNIT = "slice-iters/s"
+DATA = ("synthetic: seeded random ellipsoids (16 per volume), analytic line integrals, "
+        "Poisson noise at 1e4 photons/ray")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="sirt_512x360_b64")
+    p.add_argument("--batch-width", type=int, default=0, help="0 = library default")
+    p.add_argument("--precision", type=int, default=0, help="1 = 16-bit matrix encoding")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e / plain-CSR legs")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.bus_id:
+                cmd += ["-i", self.bus_id]
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = max(mx, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bus_id_of(dev):
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) leg: the FP64 reference timed on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(w, slices=1, iters=1, steps=1, warmup=0):
+    """Time oracle SIRT on a bounded sample of the workload; returns a dict."""
+    import oracle
+    from paper_2003_12677_b300 import inputs
+    g = oracle.Geometry(w.n, w.n, w.n, w.n_theta)
+    t0 = time.perf_counter()
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    build_s = time.perf_counter() - t0
+    case = inputs.workload_case(w.name, slices=list(range(slices)))
+    b = case.sino.reshape(slices, -1)
+    for _ in range(warmup):
+        oracle.sirt(A, AT, b, iters)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.sirt(A, AT, b, iters)
+    dt = time.perf_counter() - t0
+    return {"value": slices * iters * steps / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d slice(s) x %d SIRT iteration(s) x %d step(s) of the %s workload, FP64, matrix "
+                      "stored (oracle build %.1f s untimed)" % (slices, iters, steps, w.name, build_s),
+            "seconds": dt}
+
+
+def workload_config(w, B, precision):
+    return {"workload": w.name, "n": w.n, "n_theta": w.n_theta, "n_p": w.n, "slices": w.n_z,
+            "solver": w.solver, "iters": w.iters, "batch_width": B,
+            "values": "f32" if precision == 0 else w.values,
+            "l2": "working set larger than L2: A and A^T are streamed from HBM every iteration"}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    res = oracle_sample(w, slices=1, iters=1, steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * res["seconds"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": DATA, "config": workload_config(w, 0, 0),
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2003_12677_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    from paper_2003_12677_b300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2003_12677_b300 as tomo
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    B = args.batch_width or 16
+    prec = args.precision
+    values = w.values if prec == 1 else "f32"
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    M = tomo.Matrix(w.n, w.n_theta, values=values)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+
+    case = inputs.workload_case(w.name)
+    sino = torch.from_numpy(case.sino).cuda()
+    x = torch.zeros((w.n_z, w.n, w.n), device="cuda")
+    wsb = torch.empty(M.workspace_size(2, w.n_z, B, prec), dtype=torch.uint8, device="cuda")
+
+    def step():
+        tomo.sirt(M, sino, w.iters, batch_width=B, precision=prec, out=x, workspace=wsb)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(bus_id_of(local))
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units_per_step = world * w.n_z * w.iters
+    value = units_per_step / (ms / 1000.0)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == 0 else "f32-accumulate/%s-values" % values,
+            "data": DATA, "config": workload_config(w, B, prec), "clocks": clk,
+            "build_s": build_s, "nnz": M.nnz}
+
+    # per-kernel device time of one extra solve (CUDA events around every launch)
+    tm = tomo.new_timing()
+    tomo.sirt(M, sino, w.iters, batch_width=B, precision=prec, out=x, workspace=wsb, timing=tm)
+    launches = int(sum(tm.launches[k] for k in range(3)))
+    line["gpu_launches"] = launches * args.steps
+    kind = 0 if tm.ms[0] >= tm.ms[1] else 1
+    avg_ms = tm.ms[kind] / max(tm.launches[kind], 1)
+    rows, cols, nnz = M.rows, M.cols, M.nnz
+    bnnz = 8 if prec == 0 else 4.25
+    mat_bytes = (rows + 1 if kind == 0 else cols + 1) * 8 + nnz * bnnz
+    if kind == 0:   # r = R o (b - A x): matrix, x gathered once, b, R, r
+        vec_bytes = cols * B * 4 + 2 * rows * B * 4 + rows * 4
+        kname = "k_spmm_%s<%d, EpiSirtResidual> (A pass)" % ("f32" if prec == 0 else "lp", B)
+    else:           # x += lambda C o A^T r: matrix, r gathered once, x read+write, C
+        vec_bytes = rows * B * 4 + 2 * cols * B * 4 + cols * 4
+        kname = "k_spmm_%s<%d, EpiSirtUpdate> (A^T pass)" % ("f32" if prec == 0 else "lp", B)
+    alg = mat_bytes + vec_bytes
+    peak, src = measured_peaks()
+    achieved = alg / (avg_ms / 1000.0) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        key = "%s/B%d/p%d/k%d" % (w.name, B, prec, kind)
+        if tj.get("kernel_hash") == kernel_hash() and key in tj.get("per_launch_bytes", {}):
+            traffic = tj["per_launch_bytes"][key]
+    line["roofline"] = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": traffic, "peak_source": src + " (burst copy)",
+                        "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
+                        "kernel_share": tm.ms[kind] / max(sum(tm.ms[k] for k in range(3)), 1e-12)}
+    step_bytes = w.iters * ((rows + cols + 2) * 8 + 2 * nnz * bnnz
+                            + (3 * rows + 3 * cols) * B * 4) * math.ceil(w.n_z / B)
+    line["hbm_gbs_step"] = step_bytes / (ms / 1000.0) / 1e9
+
+    if not args.no_extras:
+        # end to end through the public API: pinned host sinogram in, tomogram out
+        sino_h = torch.from_numpy(case.sino).pin_memory()
+        x_h = torch.empty((w.n_z, w.n, w.n), pin_memory=True)
+        sd = torch.empty_like(sino)
+
+        def e2e_step():
+            sd.copy_(sino_h, non_blocking=True)
+            tomo.sirt(M, sd, w.iters, batch_width=B, precision=prec, out=x, workspace=wsb)
+            x_h.copy_(x, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / args.steps
+        line["e2e"] = {"value": units_per_step / (ems / 1000.0), "unit": UNIT,
+                       "h2d_bytes_per_step": sino_h.numel() * 4, "d2h_bytes_per_step": x_h.numel() * 4,
+                       "ms_per_step": ems}
+
+        # the plain FP32 CSR SpMV form (one slice per pass) on the same GPU
+        nzp, itp = 4, 10
+        xp = torch.zeros((nzp, w.n, w.n), device="cuda")
+        wsp = torch.empty(M.workspace_size(2, nzp, 1, 0), dtype=torch.uint8, device="cuda")
+        sp = sino[:nzp].contiguous()
+        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp)
+        torch.cuda.synchronize()
+        e0.record()
+        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp)
+        e1.record()
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        line["plain_f32_csr"] = {"value": world * nzp * itp / (pms / 1000.0), "unit": UNIT,
+                                 "form": "FP32 CSR SpMV (batch width 1, warp per row)",
+                                 "sample": "%d slices x %d SIRT iterations" % (nzp, itp)}
+        line["speedup_vs_plain_f32_csr"] = value / line["plain_f32_csr"]["value"]
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = oracle_sample(w, slices=1, iters=2, steps=1)
+        except Exception as e:  # reported, never fatal for the GPU number
+            line["cpu_baseline"] = {"error": str(e)}
+
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * tomo.h -- C ABI of the B300 sparse-matrix tomography library (libtomo.so).
+ *
+ * The library builds the parallel-beam projector A of Sec. 2 ("Tomography":
+ * the projection P_theta(p) is the integral of u along the line
+ * x cos(theta) + y sin(theta) = p) as a sparse ray-by-pixel matrix, stores its
+ * transpose explicitly (Sec. 3.1: matrix and transpose are kept as two separate
+ * sparse matrices), and applies both to batches of slices (Sec. 3: SpMV /
+ * SpMM over a stack of sinograms or tomograms) inside SIRT and CGLS (Sec. 2.1).
+ *
+ * Conventions shared by every call
+ *   - Pixel (ix, iy) is the unit square centred at x = ix + 1/2 - n_x/2,
+ *     y = iy + 1/2 - n_y/2; column j = iy*n_x + ix.  A tomogram batch is
+ *     (n_z, n_y, n_x) floats, x fastest.
+ *   - Row i = m*n_p + k is the ray of angle theta_m through the centre of
+ *     detector bin k, p_k = k + 1/2 - c.  A sinogram batch is
+ *     (n_z, n_theta, n_p) floats.
+ *   - A[i, j] is the chord length of ray i through pixel j: with
+ *     a = max(|cos|,|sin|), e = min(|cos|,|sin|), h = (a+e)/2 and
+ *     delta = |p_k - (x cos + y sin)|, the pixel is hit iff delta < h and the
+ *     length is 1/a when delta <= (a-e)/2, else (h - delta)/(a e).  Membership
+ *     and lengths are decided in IEEE FP64 (no fused multiply-add), so the
+ *     structure is reproducible bit for bit on any IEEE machine.
+ *   - Every float pointer passed to a compute call is a DEVICE pointer on the
+ *     current CUDA device, 16-byte aligned, owned by the caller and never
+ *     freed by the library.  Host pointers are only used where stated.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Compute calls are asynchronous on that stream unless stated.
+ *   - Errors are return codes; nothing throws across this boundary.  Invalid
+ *     arguments are rejected before any work is queued.  CUDA launch errors
+ *     are reported as TOMO_ERR_CUDA.
+ */
+#ifndef TOMO_H
+#define TOMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TOMO_API __attribute__((visibility("default")))
+#else
+#define TOMO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TOMO_OK = 0,
+  TOMO_ERR_INVALID_ARG = 1,
+  TOMO_ERR_OOM = 2,
+  TOMO_ERR_CUDA = 3,
+  TOMO_ERR_TIMEOUT = 4,
+  TOMO_ERR_UNSUPPORTED = 5,
+  TOMO_ERR_NUMERIC = 6,
+  TOMO_ERR_IO = 7
+} tomo_status;
+
+typedef enum { TOMO_F32 = 0, TOMO_BF16 = 1, TOMO_F16 = 2 } tomo_dtype;
+
+typedef enum {
+  TOMO_SLICE_MAJOR = 0, /* (n_z, rows): one contiguous slice after another      */
+  TOMO_INTERLEAVED = 1  /* (rows, n_z): the n_z values of one row are adjacent */
+} tomo_layout;
+
+/* Acquisition geometry (Sec. 2).  `angles` is a HOST array of n_theta radians
+ * (copied during the call; NULL selects theta_m = m*pi/n_theta).  `center` is
+ * the detector coordinate of the rotation axis in bins (Sec. 3: c = n_p/2 when
+ * the axis projects onto the central detector column); NaN selects n_p/2. */
+typedef struct {
+  int32_t n_x, n_y, n_p, n_theta;
+  const double *angles;
+  double center;
+} tomo_geometry;
+
+/* Build options.  values: TOMO_F32 builds only the FP32 CSR pair.  TOMO_BF16 /
+ * TOMO_F16 also build the 16-bit encoding (16-bit values scaled per angle so a
+ * full chord is exactly 1.0, uint16 column offsets against a 32-bit base per
+ * 16-entry chunk) that compute calls use when exec opts select it. */
+typedef struct {
+  int32_t values;   /* tomo_dtype */
+  int32_t reserved[7];
+} tomo_matrix_opts;
+
+/* Device time of the kernels one call launched, filled when a call is given
+ * a tomo_exec_opts with `timing` set.  Kinds: [0] SpMM with A (projection
+ * passes), [1] SpMM with A^T (backprojection passes), [2] every other kernel
+ * (layout changes, solver vector and scalar updates), [3] unused. */
+typedef struct {
+  double ms[4];         /* summed device milliseconds per kind */
+  int64_t launches[4];  /* kernels launched per kind */
+} tomo_timing;
+
+/* Per-call execution options (pointer may be NULL = defaults). */
+typedef struct {
+  int32_t batch_width; /* slices per SpMM pass: 0 = library default, else one of 1,2,4,8,16,32,64 */
+  int32_t use_graph;   /* SIRT/CGLS: replay one captured iteration as a CUDA graph (default 1) */
+  int32_t precision;   /* 0 = FP32 CSR, 1 = the 16-bit encoding built with the matrix */
+  int32_t reserved0;
+  tomo_timing *timing; /* non-NULL: bracket every launch with CUDA events on the call's stream,
+                          launch without graphs, synchronise the stream before returning and
+                          ADD the measured times and counts into *timing */
+  int32_t reserved[4];
+} tomo_exec_opts;
+
+typedef struct tomo_matrix tomo_matrix; /* opaque, immutable after build */
+
+typedef struct {
+  int64_t rows, cols, nnz;
+  int64_t bytes_f32;   /* device bytes of the FP32 CSR pair (A and A^T) */
+  int64_t bytes_lp;    /* device bytes of the 16-bit pair (0 if not built) */
+  int64_t max_row_len, max_col_len;
+  int32_t lp_dtype;    /* tomo_dtype of the 16-bit values (TOMO_F32 if none) */
+  int32_t reserved;
+} tomo_matrix_info_t;
+
+/* Operations that need scratch memory; see tomo_workspace_size. */
+typedef enum { TOMO_OP_PROJECT = 0, TOMO_OP_BACKPROJECT = 1, TOMO_OP_SIRT = 2, TOMO_OP_CGLS = 3 } tomo_op;
+
+/* Build A and A^T on the current device (Sec. 3.1: entries generated from the
+ * geometry, zero / out-of-range entries dropped, CSR sorted by row and by
+ * column; the transpose is stored separately).  A is rows = n_theta*n_p by
+ * cols = n_x*n_y with int64 row pointers, int32 columns ascending within each
+ * row and FP32 values (FP64 chord lengths rounded to nearest).  Also computes
+ * the SIRT normalisers R_i = 1/sum_j A_ij and C_j = 1/sum_i A_ij (0 where the
+ * sum is 0).  Synchronises `stream` (nnz must be known to allocate).
+ * Errors: INVALID_ARG for non-positive sizes, non-finite angles or center,
+ * or sizes beyond int32 columns; OOM if the device cannot hold the matrices
+ * (nothing is left allocated); CUDA on launch failures. */
+TOMO_API tomo_status tomo_build_matrix(const tomo_geometry *geom, const tomo_matrix_opts *opts,
+                                       void *stream, tomo_matrix **out);
+
+/* Free every device buffer of the handle.  NULL is accepted. */
+TOMO_API tomo_status tomo_matrix_destroy(tomo_matrix *A);
+
+/* Sizes of the handle (host struct filled synchronously). */
+TOMO_API tomo_status tomo_matrix_info(const tomo_matrix *A, tomo_matrix_info_t *info);
+
+/* Copy rows [row_begin, row_end) of A (transpose = 0) or of A^T (transpose = 1)
+ * to HOST buffers: row_ptr gets row_end-row_begin+1 offsets relative to the
+ * first exported row, col / val the entries (capacity `cap` entries; the call
+ * fails with INVALID_ARG when the range holds more, after filling row_ptr).
+ * Synchronous.  For parity checks of the stored structure. */
+TOMO_API tomo_status tomo_matrix_export_rows(const tomo_matrix *A, int32_t transpose, int64_t row_begin,
+                                             int64_t row_end, int64_t *row_ptr, int32_t *col, float *val,
+                                             int64_t cap);
+
+/* Copy the SIRT normalisers to HOST buffers (R: rows floats, C: cols floats;
+ * either may be NULL).  Synchronous. */
+TOMO_API tomo_status tomo_matrix_export_norms(const tomo_matrix *A, float *R, float *C);
+
+/* Bytes of scratch a call needs for n_z slices with the given options.  A call
+ * given workspace = NULL allocates this much itself (stream-ordered) and frees
+ * it before returning. */
+TOMO_API tomo_status tomo_workspace_size(const tomo_matrix *A, int32_t op, int32_t n_z,
+                                         const tomo_exec_opts *opts, size_t *bytes);
+
+/* Forward projection y = A x for n_z slices (Sec. 2 Radon transform, applied as
+ * SpMM with the slices as right-hand sides; Sec. 3).  x: n_z tomograms, y: n_z
+ * sinograms, both in `layout`.  TOMO_INTERLEAVED requires n_z to be one of
+ * 1,2,4,8,16,32,64.  Errors: INVALID_ARG (NULL / unaligned pointers, n_z < 1),
+ * UNSUPPORTED (interleaved n_z not a supported width, or precision = 1 on a
+ * matrix built without the 16-bit encoding). */
+TOMO_API tomo_status tomo_project(const tomo_matrix *A, const float *x, float *y, int32_t n_z, int32_t layout,
+                                  const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes,
+                                  void *stream);
+
+/* Backprojection x = A^T y with the stored transpose (no atomics). */
+TOMO_API tomo_status tomo_backproject(const tomo_matrix *A, const float *y, float *x, int32_t n_z,
+                                      int32_t layout, const tomo_exec_opts *opts, void *workspace,
+                                      size_t workspace_bytes, void *stream);
+
+/* SIRT (Sec. 2.1), classical form: x <- x + lambda * C o A^T (R o (b - A x)),
+ * `iters` times, for n_z independent slices.  sino: (n_z, n_theta, n_p);
+ * x: (n_z, n_y, n_x), holds the start on entry and the result on return. */
+TOMO_API tomo_status tomo_sirt(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
+                               float lambda, const tomo_exec_opts *opts, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
+/* CGLS (Sec. 2.1) for min ||A x - b|| per slice from x0 = 0: vectors FP32,
+ * inner products, norms and the step scalars alpha / beta in FP64 on the
+ * device.  Every `recompute_every` iterations (0 = never) the residual is
+ * recomputed as r = b - A x.  A slice whose ||s||^2 or ||q||^2 reaches 0 stops
+ * changing.  resnorm_hist (DEVICE, nullable) receives ||r|| per iteration and
+ * slice, laid out (iters, n_z).  x: (n_z, n_y, n_x) output. */
+TOMO_API tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
+                               int32_t recompute_every, double *resnorm_hist, const tomo_exec_opts *opts,
+                               void *workspace, size_t workspace_bytes, void *stream);
+
+/* Human-readable name of a status code (static string). */
+TOMO_API const char *tomo_status_string(tomo_status s);
+
+/* Message of the last failure on the calling thread (static per-thread buffer). */
+TOMO_API const char *tomo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOMO_H */

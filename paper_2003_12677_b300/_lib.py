@@ -1,0 +1,99 @@
+"""ctypes binding of libtomo.so: signatures and status checking only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtomo.so")
+
+TOMO_OK = 0
+STATUS = {0: "TOMO_OK", 1: "TOMO_ERR_INVALID_ARG", 2: "TOMO_ERR_OOM", 3: "TOMO_ERR_CUDA",
+          4: "TOMO_ERR_TIMEOUT", 5: "TOMO_ERR_UNSUPPORTED", 6: "TOMO_ERR_NUMERIC", 7: "TOMO_ERR_IO"}
+DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+OP_PROJECT, OP_BACKPROJECT, OP_SIRT, OP_CGLS = 0, 1, 2, 3
+SLICE_MAJOR, INTERLEAVED = 0, 1
+
+# every entry point include/tomo.h declares
+EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
+           "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
+           "tomo_sirt", "tomo_cgls", "tomo_status_string", "tomo_last_error"]
+
+
+class TomoError(RuntimeError):
+    def __init__(self, code: int, func: str, msg: str):
+        self.code = code
+        super().__init__("%s failed with %s: %s" % (func, STATUS.get(code, str(code)), msg))
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_x", ctypes.c_int32), ("n_y", ctypes.c_int32), ("n_p", ctypes.c_int32),
+                ("n_theta", ctypes.c_int32), ("angles", ctypes.c_void_p), ("center", ctypes.c_double)]
+
+
+class MatrixOpts(ctypes.Structure):
+    _fields_ = [("values", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4)]
+
+
+class ExecOpts(ctypes.Structure):
+    _fields_ = [("batch_width", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("timing", ctypes.POINTER(Timing)), ("reserved", ctypes.c_int32 * 4)]
+
+
+class MatrixInfo(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("bytes_f32", ctypes.c_int64), ("bytes_lp", ctypes.c_int64),
+                ("max_row_len", ctypes.c_int64), ("max_col_len", ctypes.c_int64),
+                ("lp_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtomo.so; raises (never falls back) when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libtomo.so is not built (%s); run `python -m paper_2003_12677_b300.build`" % path)
+    lib = ctypes.CDLL(path)
+    P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sigs = {
+        "tomo_build_matrix": [ctypes.POINTER(Geometry), ctypes.POINTER(MatrixOpts), P, ctypes.POINTER(P)],
+        "tomo_matrix_destroy": [P],
+        "tomo_matrix_info": [P, ctypes.POINTER(MatrixInfo)],
+        "tomo_matrix_export_rows": [P, I32, I64, I64, P, P, P, I64],
+        "tomo_matrix_export_norms": [P, P, P],
+        "tomo_workspace_size": [P, I32, I32, ctypes.POINTER(ExecOpts), ctypes.POINTER(SZ)],
+        "tomo_project": [P, P, P, I32, I32, ctypes.POINTER(ExecOpts), P, SZ, P],
+        "tomo_backproject": [P, P, P, I32, I32, ctypes.POINTER(ExecOpts), P, SZ, P],
+        "tomo_sirt": [P, P, P, I32, I32, ctypes.c_float, ctypes.POINTER(ExecOpts), P, SZ, P],
+        "tomo_cgls": [P, P, P, I32, I32, I32, P, ctypes.POINTER(ExecOpts), P, SZ, P],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.tomo_status_string.argtypes = [ctypes.c_int]
+    lib.tomo_status_string.restype = ctypes.c_char_p
+    lib.tomo_last_error.argtypes = []
+    lib.tomo_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(code: int, func: str):
+    if code != TOMO_OK:
+        msg = _lib.tomo_last_error().decode() if _lib is not None else ""
+        raise TomoError(code, func, msg)
+
+
+def call(name: str, *args):
+    lib = load()
+    check(getattr(lib, name)(*args), name)

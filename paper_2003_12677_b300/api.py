@@ -1,0 +1,253 @@
+"""PyTorch-facing binding of libtomo (argument marshalling only).
+
+Every step runs in the CUDA library; this module checks tensor properties,
+passes device pointers and the current CUDA stream, and allocates workspaces
+through torch's caching allocator.  There is no CPU path: without a CUDA
+device or without libtomo.so every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check_tensor(t: torch.Tensor, name: str, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float32:
+        raise TypeError("%s must be float32" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+
+
+def _exec(batch_width: int = 0, use_graph: bool = True, precision: int = 0, timing=None) -> _lib.ExecOpts:
+    o = _lib.ExecOpts()
+    o.batch_width = batch_width
+    o.use_graph = 1 if use_graph else 0
+    o.precision = precision
+    if timing is not None:
+        o.timing = ctypes.pointer(timing)
+    return o
+
+
+def new_timing() -> _lib.Timing:
+    """A zeroed tomo_timing to pass as `timing=` (per-kind device ms and launch counts)."""
+    return _lib.Timing()
+
+
+class Matrix:
+    """A and A^T for one parallel-beam geometry, resident on the current device.
+
+    n_x = n_y = n unless given; n_p defaults to n; angles (radians) default to
+    m*pi/n_theta; center defaults to n_p/2.  values in {"f32", "bf16", "f16"}
+    also builds the 16-bit encoding used with precision=1.
+    """
+
+    def __init__(self, n: int, n_theta: int, n_p: Optional[int] = None, n_y: Optional[int] = None,
+                 angles=None, center: Optional[float] = None, values: str = "f32"):
+        self._h = None
+        lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtomo needs a CUDA device")
+        self.n_x = int(n)
+        self.n_y = int(n if n_y is None else n_y)
+        self.n_p = int(n if n_p is None else n_p)
+        self.n_theta = int(n_theta)
+        self._angles = None
+        g = _lib.Geometry()
+        g.n_x, g.n_y, g.n_p, g.n_theta = self.n_x, self.n_y, self.n_p, self.n_theta
+        if angles is not None:
+            self._angles = np.ascontiguousarray(np.asarray(angles, np.float64))
+            if self._angles.shape != (self.n_theta,):
+                raise ValueError("angles must have n_theta entries")
+            g.angles = self._angles.ctypes.data
+        else:
+            g.angles = None
+        g.center = float("nan") if center is None else float(center)
+        o = _lib.MatrixOpts()
+        o.values = _lib.DTYPES[values]
+        h = ctypes.c_void_p()
+        _lib.check(lib.tomo_build_matrix(ctypes.byref(g), ctypes.byref(o), _stream(), ctypes.byref(h)),
+                   "tomo_build_matrix")
+        self._h = h
+        self.values = values
+        info = _lib.MatrixInfo()
+        _lib.check(lib.tomo_matrix_info(self._h, ctypes.byref(info)), "tomo_matrix_info")
+        self.rows, self.cols, self.nnz = info.rows, info.cols, info.nnz
+        self.bytes_f32, self.bytes_lp = info.bytes_f32, info.bytes_lp
+        self.max_row_len, self.max_col_len = info.max_row_len, info.max_col_len
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("matrix was closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.load().tomo_matrix_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def export_rows(self, begin: int, end: int, transpose: bool = False) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """Rows [begin, end) of A (or A^T) as host (row_ptr int64, col int32, val float32)."""
+        lib = _lib.load()
+        rp = np.empty(end - begin + 1, np.int64)
+        # a first call with capacity 0 fills the row pointers and so the size
+        st = lib.tomo_matrix_export_rows(self.handle, int(transpose), begin, end, rp.ctypes.data, None, None, 0)
+        if st not in (0, 1):
+            _lib.check(st, "tomo_matrix_export_rows")
+        need = int(rp[-1])
+        col = np.empty(max(need, 1), np.int32)
+        val = np.empty(max(need, 1), np.float32)
+        _lib.check(lib.tomo_matrix_export_rows(self.handle, int(transpose), begin, end, rp.ctypes.data,
+                                               col.ctypes.data, val.ctypes.data, need), "tomo_matrix_export_rows")
+        return rp, col[:need], val[:need]
+
+    def export_csr(self, transpose: bool = False):
+        n = self.cols if transpose else self.rows
+        return self.export_rows(0, n, transpose)
+
+    def export_norms(self) -> Tuple[np.ndarray, np.ndarray]:
+        R = np.empty(self.rows, np.float32)
+        C = np.empty(self.cols, np.float32)
+        _lib.call("tomo_matrix_export_norms", self.handle, R.ctypes.data, C.ctypes.data)
+        return R, C
+
+    def workspace_size(self, op: int, n_z: int, batch_width: int = 0, precision: int = 0) -> int:
+        b = ctypes.c_size_t()
+        o = _exec(batch_width, True, precision)
+        _lib.call("tomo_workspace_size", self.handle, op, n_z, ctypes.byref(o), ctypes.byref(b))
+        return b.value
+
+    def _workspace(self, op, n_z, batch_width, precision) -> Optional[torch.Tensor]:
+        nb = self.workspace_size(op, n_z, batch_width, precision)
+        if nb == 0:
+            return None
+        return torch.empty(nb, dtype=torch.uint8, device="cuda")
+
+
+def _nz(t: torch.Tensor, per: int, name: str) -> int:
+    if t.numel() % per != 0:
+        raise ValueError("%s has %d elements, not a multiple of %d" % (name, t.numel(), per))
+    return t.numel() // per
+
+
+def project(M: Matrix, x: torch.Tensor, out: Optional[torch.Tensor] = None, batch_width: int = 0,
+            precision: int = 0, interleaved: bool = False, timing=None) -> torch.Tensor:
+    """y = A x for a stack of tomograms x (n_z, n_y, n_x) -> sinograms (n_z, n_theta, n_p).
+
+    interleaved=True takes x as (cols, n_z) and returns (rows, n_z)."""
+    _check_tensor(x, "x")
+    nz = x.shape[-1] if interleaved else _nz(x, M.cols, "x")
+    if out is None:
+        out = torch.empty((M.rows, nz) if interleaved else (nz, M.n_theta, M.n_p), device=x.device,
+                          dtype=torch.float32)
+    _check_tensor(out, "out")
+    ws = None if interleaved else M._workspace(_lib.OP_PROJECT, nz, batch_width, precision)
+    o = _exec(batch_width, True, precision, timing)
+    _lib.call("tomo_project", M.handle, _ptr(x), _ptr(out), nz, _lib.INTERLEAVED if interleaved else 0,
+              ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
+    return out
+
+
+def backproject(M: Matrix, y: torch.Tensor, out: Optional[torch.Tensor] = None, batch_width: int = 0,
+                precision: int = 0, interleaved: bool = False, timing=None) -> torch.Tensor:
+    """x = A^T y for a stack of sinograms y (n_z, n_theta, n_p) -> (n_z, n_y, n_x)."""
+    _check_tensor(y, "y")
+    nz = y.shape[-1] if interleaved else _nz(y, M.rows, "y")
+    if out is None:
+        out = torch.empty((M.cols, nz) if interleaved else (nz, M.n_y, M.n_x), device=y.device,
+                          dtype=torch.float32)
+    _check_tensor(out, "out")
+    ws = None if interleaved else M._workspace(_lib.OP_BACKPROJECT, nz, batch_width, precision)
+    o = _exec(batch_width, True, precision, timing)
+    _lib.call("tomo_backproject", M.handle, _ptr(y), _ptr(out), nz, _lib.INTERLEAVED if interleaved else 0,
+              ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
+    return out
+
+
+def sirt(M: Matrix, sino: torch.Tensor, iters: int, lam: float = 1.0, x0: Optional[torch.Tensor] = None,
+         batch_width: int = 0, precision: int = 0, use_graph: bool = True,
+         workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None, timing=None) -> torch.Tensor:
+    """SIRT from x0 (zeros by default): x <- x + lam * C o A^T (R o (b - A x))."""
+    _check_tensor(sino, "sino")
+    nz = _nz(sino, M.rows, "sino")
+    if out is not None:
+        x = out
+        if x0 is None:
+            x.zero_()
+        else:
+            x.copy_(x0)
+    else:
+        x = torch.zeros((nz, M.n_y, M.n_x), device=sino.device) if x0 is None else x0.clone()
+    _check_tensor(x, "x0", (nz, M.n_y, M.n_x))
+    ws = workspace if workspace is not None else M._workspace(_lib.OP_SIRT, nz, batch_width, precision)
+    o = _exec(batch_width, use_graph, precision, timing)
+    _lib.call("tomo_sirt", M.handle, _ptr(sino), _ptr(x), nz, iters, ctypes.c_float(lam), ctypes.byref(o),
+              _ptr(ws), 0 if ws is None else ws.numel(), _stream())
+    return x
+
+
+def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, history: bool = False,
+         batch_width: int = 0, precision: int = 0, use_graph: bool = True, out: Optional[torch.Tensor] = None,
+         workspace: Optional[torch.Tensor] = None, timing=None):
+    """CGLS from x0 = 0 per slice.  Returns x, or (x, ||r|| history (iters, n_z) float64)."""
+    _check_tensor(sino, "sino")
+    nz = _nz(sino, M.rows, "sino")
+    x = torch.empty((nz, M.n_y, M.n_x), device=sino.device) if out is None else out
+    _check_tensor(x, "out", (nz, M.n_y, M.n_x))
+    hist = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
+    ws = workspace if workspace is not None else M._workspace(_lib.OP_CGLS, nz, batch_width, precision)
+    o = _exec(batch_width, use_graph, precision, timing)
+    _lib.call("tomo_cgls", M.handle, _ptr(sino), _ptr(x), nz, iters, recompute_every, _ptr(hist),
+              ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
+    return (x, hist[:iters]) if history else x
+
+
+class TomoProject(torch.autograd.Function):
+    """y = A x with the stored transpose as the backward: dL/dx = A^T dL/dy."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, M: Matrix, batch_width: int = 0, precision: int = 0):
+        ctx.M, ctx.bw, ctx.prec = M, batch_width, precision
+        return project(M, x.contiguous(), batch_width=batch_width, precision=precision)
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        gx = backproject(ctx.M, g.contiguous(), batch_width=ctx.bw, precision=ctx.prec)
+        return gx, None, None, None
+
+
+def radon(x: torch.Tensor, M: Matrix, batch_width: int = 0, precision: int = 0) -> torch.Tensor:
+    """Differentiable forward projection."""
+    return TomoProject.apply(x, M, batch_width, precision)
+
+
+def tv_loss(x: torch.Tensor, eps: float = 1e-3) -> torch.Tensor:
+    """Isotropic TV with forward differences (0 on the last row / column), per slice."""
+    dx = torch.zeros_like(x)
+    dy = torch.zeros_like(x)
+    dx[..., :, :-1] = x[..., :, 1:] - x[..., :, :-1]
+    dy[..., :-1, :] = x[..., 1:, :] - x[..., :-1, :]
+    return torch.sqrt(dx * dx + dy * dy + eps * eps).sum()

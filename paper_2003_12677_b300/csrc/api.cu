@@ -1,0 +1,206 @@
+// api.cu -- the extern "C" boundary of libtomo (declared in include/tomo.h).
+// Argument checking, device selection and error strings live here; every
+// computation is queued by build.cu / ops.cu.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+namespace tomo {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+tomo_status fail(tomo_status s, const std::string &msg) {
+  set_error(msg);
+  return s;
+}
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+      cudaSetDevice(dev);
+    else
+      prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static tomo_status check_vec(const void *p, const char *name) {
+  if (!p) return fail(TOMO_ERR_INVALID_ARG, std::string(name) + " must be non-NULL");
+  if (!aligned16(p)) return fail(TOMO_ERR_INVALID_ARG, std::string(name) + " must be 16-byte aligned");
+  return TOMO_OK;
+}
+
+static bool pow2_width(int b) { return b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32 || b == 64; }
+
+static tomo_status check_ws(const tomo_matrix *A, int op, int32_t n_z, const Exec &ex, void *ws, size_t bytes) {
+  size_t need = workspace_bytes(A, op, n_z, ex);
+  if (ws && bytes < need) return fail(TOMO_ERR_INVALID_ARG, "workspace too small: need " + std::to_string(need));
+  if (ws && !aligned16(ws)) return fail(TOMO_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+  return TOMO_OK;
+}
+
+}  // namespace tomo
+
+using namespace tomo;
+
+extern "C" {
+
+tomo_status tomo_build_matrix(const tomo_geometry *geom, const tomo_matrix_opts *opts, void *stream,
+                              tomo_matrix **out) {
+  return build_matrix(geom, opts, (cudaStream_t)stream, out);
+}
+
+tomo_status tomo_matrix_destroy(tomo_matrix *A) {
+  if (!A) return TOMO_OK;
+  DeviceGuard dg(A->device);
+  free_matrix(A);
+  return TOMO_OK;
+}
+
+tomo_status tomo_matrix_info(const tomo_matrix *A, tomo_matrix_info_t *info) {
+  if (!A || !info) return fail(TOMO_ERR_INVALID_ARG, "matrix and info must be non-NULL");
+  std::memset(info, 0, sizeof(*info));
+  info->rows = A->A.rows;
+  info->cols = A->A.cols;
+  info->nnz = A->A.nnz;
+  info->bytes_f32 = A->bytes_f32;
+  info->bytes_lp = A->bytes_lp;
+  info->max_row_len = A->A.max_len;
+  info->max_col_len = A->AT.max_len;
+  info->lp_dtype = A->lp_dtype;
+  return TOMO_OK;
+}
+
+tomo_status tomo_matrix_export_rows(const tomo_matrix *A, int32_t transpose, int64_t row_begin, int64_t row_end,
+                                    int64_t *row_ptr, int32_t *col, float *val, int64_t cap) {
+  if (!A || !row_ptr) return fail(TOMO_ERR_INVALID_ARG, "matrix and row_ptr must be non-NULL");
+  const Csr &M = transpose ? A->AT : A->A;
+  if (row_begin < 0 || row_end < row_begin || row_end > M.rows)
+    return fail(TOMO_ERR_INVALID_ARG, "row range out of bounds");
+  DeviceGuard dg(A->device);
+  const int64_t n = row_end - row_begin;
+  if (cudaMemcpy(row_ptr, M.rp + row_begin, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(TOMO_ERR_CUDA, "copy of row pointers failed");
+  const int64_t first = row_ptr[0], cnt = row_ptr[n] - first;
+  for (int64_t i = 0; i <= n; ++i) row_ptr[i] -= first;
+  if (cnt > cap) return fail(TOMO_ERR_INVALID_ARG, "export capacity too small: need " + std::to_string(cnt));
+  if (cnt > 0) {
+    if (!col || !val) return fail(TOMO_ERR_INVALID_ARG, "col and val must be non-NULL");
+    if (cudaMemcpy(col, M.ci + first, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(val, M.v + first, sizeof(float) * cnt, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(TOMO_ERR_CUDA, "copy of entries failed");
+  }
+  return TOMO_OK;
+}
+
+tomo_status tomo_matrix_export_norms(const tomo_matrix *A, float *R, float *C) {
+  if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
+  DeviceGuard dg(A->device);
+  if (R && cudaMemcpy(R, A->R, sizeof(float) * A->A.rows, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(TOMO_ERR_CUDA, "copy of R failed");
+  if (C && cudaMemcpy(C, A->C, sizeof(float) * A->A.cols, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(TOMO_ERR_CUDA, "copy of C failed");
+  return TOMO_OK;
+}
+
+tomo_status tomo_workspace_size(const tomo_matrix *A, int32_t op, int32_t n_z, const tomo_exec_opts *opts,
+                                size_t *bytes) {
+  if (!A || !bytes) return fail(TOMO_ERR_INVALID_ARG, "matrix and bytes must be non-NULL");
+  if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
+  if (op < TOMO_OP_PROJECT || op > TOMO_OP_CGLS) return fail(TOMO_ERR_INVALID_ARG, "unknown op");
+  Exec ex;
+  TOMO_TRY(resolve_exec(A, opts, n_z, &ex));
+  *bytes = workspace_bytes(A, op, n_z, ex);
+  return TOMO_OK;
+}
+
+static tomo_status project_common(const tomo_matrix *A, bool trans, const float *in, float *out, int32_t n_z,
+                                  int32_t layout, const tomo_exec_opts *opts, void *ws, size_t ws_bytes,
+                                  void *stream) {
+  if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
+  TOMO_TRY(check_vec(in, trans ? "y" : "x"));
+  TOMO_TRY(check_vec(out, trans ? "x" : "y"));
+  if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
+  if (layout != TOMO_SLICE_MAJOR && layout != TOMO_INTERLEAVED)
+    return fail(TOMO_ERR_INVALID_ARG, "layout must be TOMO_SLICE_MAJOR or TOMO_INTERLEAVED");
+  DeviceGuard dg(A->device);
+  Exec ex;
+  tomo_exec_opts o = opts ? *opts : tomo_exec_opts{};
+  if (!opts) o.use_graph = 1;
+  if (layout == TOMO_INTERLEAVED) {
+    if (!pow2_width(n_z)) return fail(TOMO_ERR_UNSUPPORTED, "interleaved layout needs n_z in {1,2,4,8,16,32,64}");
+    o.batch_width = n_z;
+  }
+  TOMO_TRY(resolve_exec(A, &o, n_z, &ex));
+  TOMO_TRY(check_ws(A, trans ? TOMO_OP_BACKPROJECT : TOMO_OP_PROJECT, n_z, ex, ws, ws_bytes));
+  return run_project(A, trans, in, out, n_z, layout, ex, ws, (cudaStream_t)stream);
+}
+
+tomo_status tomo_project(const tomo_matrix *A, const float *x, float *y, int32_t n_z, int32_t layout,
+                         const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes, void *stream) {
+  return project_common(A, false, x, y, n_z, layout, opts, workspace, workspace_bytes, stream);
+}
+
+tomo_status tomo_backproject(const tomo_matrix *A, const float *y, float *x, int32_t n_z, int32_t layout,
+                             const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes, void *stream) {
+  return project_common(A, true, y, x, n_z, layout, opts, workspace, workspace_bytes, stream);
+}
+
+tomo_status tomo_sirt(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters, float lambda,
+                      const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes, void *stream) {
+  if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
+  TOMO_TRY(check_vec(sino, "sino"));
+  TOMO_TRY(check_vec(x, "x"));
+  if (n_z < 1 || iters < 0) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1 and iters >= 0");
+  if (!std::isfinite(lambda)) return fail(TOMO_ERR_INVALID_ARG, "lambda must be finite");
+  DeviceGuard dg(A->device);
+  Exec ex;
+  TOMO_TRY(resolve_exec(A, opts, n_z, &ex));
+  TOMO_TRY(check_ws(A, TOMO_OP_SIRT, n_z, ex, workspace, workspace_bytes));
+  if (iters == 0) return TOMO_OK;
+  return run_sirt(A, sino, x, n_z, iters, lambda, ex, workspace, (cudaStream_t)stream);
+}
+
+tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
+                      int32_t recompute_every, double *resnorm_hist, const tomo_exec_opts *opts, void *workspace,
+                      size_t workspace_bytes, void *stream) {
+  if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
+  TOMO_TRY(check_vec(sino, "sino"));
+  TOMO_TRY(check_vec(x, "x"));
+  if (n_z < 1 || iters < 0 || recompute_every < 0)
+    return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1, iters >= 0 and recompute_every >= 0");
+  DeviceGuard dg(A->device);
+  Exec ex;
+  TOMO_TRY(resolve_exec(A, opts, n_z, &ex));
+  TOMO_TRY(check_ws(A, TOMO_OP_CGLS, n_z, ex, workspace, workspace_bytes));
+  return run_cgls(A, sino, x, n_z, iters, recompute_every, resnorm_hist, ex, workspace, (cudaStream_t)stream);
+}
+
+const char *tomo_status_string(tomo_status s) {
+  switch (s) {
+    case TOMO_OK: return "TOMO_OK";
+    case TOMO_ERR_INVALID_ARG: return "TOMO_ERR_INVALID_ARG";
+    case TOMO_ERR_OOM: return "TOMO_ERR_OOM";
+    case TOMO_ERR_CUDA: return "TOMO_ERR_CUDA";
+    case TOMO_ERR_TIMEOUT: return "TOMO_ERR_TIMEOUT";
+    case TOMO_ERR_UNSUPPORTED: return "TOMO_ERR_UNSUPPORTED";
+    case TOMO_ERR_NUMERIC: return "TOMO_ERR_NUMERIC";
+    case TOMO_ERR_IO: return "TOMO_ERR_IO";
+  }
+  return "TOMO_ERR_UNKNOWN";
+}
+
+const char *tomo_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,576 @@
+// build.cu -- construction of the projector A, its explicit transpose A^T, the
+// SIRT normalisers and the 16-bit encoding, all on the device.
+//
+// Sec. 2 defines the projection as the line integral of u along
+// x cos(theta) + y sin(theta) = p; for a piecewise-constant pixel image that
+// integral is sum_j u_j * chord(ray, pixel j), which is what A stores.  Sec. 3.1
+// builds the entries, drops zero / out-of-range ones and keeps CSR sorted by
+// row and column, with the transpose stored separately.  Here both A and A^T
+// are generated directly from the geometry by the same FP64 predicate, so A^T
+// is the exact transpose of A bit for bit and no sort is needed:
+//   * A, row-driven: for ray (m,k) and pixel row iy the hit pixels form one
+//     run of consecutive ix (the rounded predicate is monotone in x), so a warp
+//     per ray finds each run's ends and writes the columns in ascending order;
+//   * A^T, pixel-driven: for pixel (ix,iy) and angle m at most two bins k are
+//     hit, so a warp per pixel tests the candidates of 32 angles at a time and
+//     compacts the hits in (m, k) order.
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <type_traits>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace tomo {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// The chord rule in IEEE FP64 without contraction:
+//   t = fl(fl(x cs) + fl(y sn)), delta = |fl(p - t)|, hit iff delta < h,
+//   length = 1/a if delta <= hm else fl(fl(h - delta) / (a e)).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double coord(int i, int n) {
+  return __dsub_rn(__dadd_rn((double)i, 0.5), 0.5 * (double)n);  // exact
+}
+
+__device__ __forceinline__ double chord_delta(const AngleC &A, double pk, double x, double y) {
+  double t = __dadd_rn(__dmul_rn(x, A.cs), __dmul_rn(y, A.sn));
+  return fabs(__dsub_rn(pk, t));
+}
+
+__device__ __forceinline__ bool chord_hit(const AngleC &A, double pk, double x, double y) {
+  return chord_delta(A, pk, x, y) < A.h;
+}
+
+__device__ __forceinline__ double chord_len(const AngleC &A, double pk, double x, double y) {
+  double del = chord_delta(A, pk, x, y);
+  return del <= A.hm ? A.inv_a : __ddiv_rn(__dsub_rn(A.h, del), A.ae);
+}
+
+// Run [lo, hi] of hit pixels of ray (A, pk) in pixel row y (hi < lo: none).
+// A cheap estimate of the run's ends seeds the search; the exact predicate then
+// walks to the true ends, so the estimate only has to land near the run.
+__device__ void row_run(const AngleC &A, double pk, int nx, double y, int &lo, int &hi) {
+  lo = 0;
+  hi = -1;
+  auto pred = [&](int ix) { return chord_hit(A, pk, coord(ix, nx), y); };
+  if (A.cs == 0.0) {
+    // x drops out of the predicate: the whole row or nothing
+    if (pred(0)) {
+      lo = 0;
+      hi = nx - 1;
+    }
+    return;
+  }
+  double r = pk - y * A.sn;
+  double xa = (r - A.h) * A.inv_cs, xb = (r + A.h) * A.inv_cs;
+  double off = 0.5 * nx - 0.5;
+  double xl = fmin(xa, xb) + off, xh = fmax(xa, xb) + off;
+  xl = fmin(fmax(xl, -16.0), nx + 16.0);
+  xh = fmin(fmax(xh, -16.0), nx + 16.0);
+  int s0 = max(0, (int)floor(xl) - 4);
+  int s1 = min(nx - 1, (int)ceil(xh) + 4);
+  if (s0 > s1) return;
+  int a = s0;
+  while (a <= s1 && !pred(a)) ++a;
+  if (a > s1) return;
+  int b = s1;
+  while (b > a && !pred(b)) --b;
+  while (a > 0 && pred(a - 1)) --a;
+  while (b < nx - 1 && pred(b + 1)) ++b;
+  lo = a;
+  hi = b;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// A: count and fill, one warp per ray
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_count_rays(const AngleC *__restrict__ ang, int nx, int ny,
+                                                         int np, int nt, double c,
+                                                         int32_t *__restrict__ cnt) {
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= (int64_t)nt * np) return;
+  int m = (int)(w / np), k = (int)(w % np);
+  AngleC A = ang[m];
+  double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
+  int total = 0;
+  for (int iy = lane; iy < ny; iy += 32) {
+    int lo, hi;
+    row_run(A, pk, nx, coord(iy, ny), lo, hi);
+    total += max(0, hi - lo + 1);
+  }
+  total = warp_sum_i(total);
+  if (lane == 0) cnt[w] = total;
+}
+
+__global__ void __launch_bounds__(kThreads) k_fill_rays(const AngleC *__restrict__ ang, int nx, int ny,
+                                                        int np, int nt, double c,
+                                                        const int64_t *__restrict__ rp,
+                                                        int32_t *__restrict__ ci, float *__restrict__ v,
+                                                        float *__restrict__ R) {
+  __shared__ int s_off[kThreads / 32][33];
+  __shared__ int s_lo[kThreads / 32][32];
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  if (w >= (int64_t)nt * np) return;
+  int m = (int)(w / np), k = (int)(w % np);
+  AngleC A = ang[m];
+  double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
+  int64_t pos = rp[w];
+  double sum = 0.0;
+  for (int iy0 = 0; iy0 < ny; iy0 += 32) {
+    int iy = iy0 + lane;
+    int lo = 0, hi = -1;
+    if (iy < ny) row_run(A, pk, nx, coord(iy, ny), lo, hi);
+    int len = max(0, hi - lo + 1);
+    int incl = warp_incl_scan(len, lane);
+    s_off[wl][lane + 1] = incl;
+    if (lane == 0) s_off[wl][0] = 0;
+    s_lo[wl][lane] = lo;
+    __syncwarp();
+    int T = __shfl_sync(0xffffffffu, incl, 31);
+    for (int e = lane; e < T; e += 32) {
+      int q = 0;  // largest q with s_off[q] <= e
+#pragma unroll
+      for (int step = 16; step; step >>= 1)
+        if (q + step < 32 && s_off[wl][q + step] <= e) q += step;
+      int ix = s_lo[wl][q] + (e - s_off[wl][q]);
+      int yy = iy0 + q;
+      double L = chord_len(A, pk, coord(ix, nx), coord(yy, ny));
+      sum += L;
+      ci[pos + e] = yy * nx + ix;
+      v[pos + e] = __double2float_rn(L);
+    }
+    pos += T;
+    __syncwarp();
+  }
+  sum = warp_sum_d(sum);
+  if (lane == 0) R[w] = sum != 0.0 ? __double2float_rn(1.0 / sum) : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// A^T: count and fill, one warp per pixel, lanes over angles
+// ---------------------------------------------------------------------------
+template <bool kFill>
+__global__ void __launch_bounds__(kThreads) k_pixels(const AngleC *__restrict__ ang, int nx, int ny,
+                                                     int np, int nt, double c,
+                                                     int32_t *__restrict__ cnt,
+                                                     const int64_t *__restrict__ rp,
+                                                     int32_t *__restrict__ ci, float *__restrict__ v,
+                                                     float *__restrict__ C, int *__restrict__ err) {
+  int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= (int64_t)nx * ny) return;
+  int ix = (int)(w % nx), iy = (int)(w / nx);
+  double x = coord(ix, nx), y = coord(iy, ny);
+  int total = 0;
+  int64_t pos = kFill ? rp[w] : 0;
+  double sum = 0.0;
+  for (int m0 = 0; m0 < nt; m0 += 32) {
+    int m = m0 + lane;
+    int nh = 0;
+    int kh[2] = {0, 0};
+    double Lh[2] = {0.0, 0.0};
+    if (m < nt) {
+      AngleC A = ang[m];
+      // |p_k - t| < h <= 0.7072 puts k within 0.71 of u = t + c - 1/2
+      double u = x * A.cs + y * A.sn + (c - 0.5);
+      long long kf = (long long)floor(u);
+      for (long long k = kf - 2; k <= kf + 2; ++k) {
+        if (k < 0 || k >= np) continue;
+        double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
+        if (chord_hit(A, pk, x, y)) {
+          if (nh < 2) {
+            kh[nh] = (int)k;
+            if (kFill) Lh[nh] = chord_len(A, pk, x, y);
+          } else if (err) {
+            atomicExch(err, 1);  // impossible by the bound above; reported, never written
+          }
+          ++nh;
+        }
+      }
+      nh = min(nh, 2);
+    }
+    if (!kFill) {
+      total += nh;
+    } else {
+      int incl = warp_incl_scan(nh, lane);
+      int base = incl - nh;
+      for (int q = 0; q < nh; ++q) {
+        ci[pos + base + q] = m * np + kh[q];
+        v[pos + base + q] = __double2float_rn(Lh[q]);
+        sum += Lh[q];
+      }
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  if (!kFill) {
+    total = warp_sum_i(total);
+    if (lane == 0) cnt[w] = total;
+  } else {
+    sum = warp_sum_d(sum);
+    if (lane == 0) C[w] = sum != 0.0 ? __double2float_rn(1.0 / sum) : 0.0f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 counts into int64 offsets (three passes) + max.
+// ---------------------------------------------------------------------------
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;
+
+__device__ int64_t block_excl_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t s_w[kThreads / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_w[wid] = incl;
+  __syncthreads();
+  int64_t woff = 0, tot = 0;
+  for (int i = 0; i < kThreads / 32; ++i) {
+    if (i < wid) woff += s_w[i];
+    tot += s_w[i];
+  }
+  __syncthreads();
+  *total = tot;
+  return woff + incl - v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const int32_t *__restrict__ in, int64_t n,
+                                                          int64_t *__restrict__ part,
+                                                          int *__restrict__ maxv) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t s = 0;
+  int mx = 0;
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) {
+      s += in[base + i];
+      mx = max(mx, in[base + i]);
+    }
+  int64_t tot;
+  block_excl_scan(s, &tot);
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxv, mx);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_parts(int64_t *part, int64_t nparts) {
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < nparts; b0 += kThreads) {
+    int64_t i = b0 + threadIdx.x;
+    int64_t v = i < nparts ? part[i] : 0;
+    int64_t tot;
+    int64_t ex = block_excl_scan(v, &tot);
+    if (i < nparts) part[i] = carry + ex;
+    carry += tot;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_apply(const int32_t *__restrict__ in, int64_t n,
+                                                         const int64_t *__restrict__ part,
+                                                         int64_t *__restrict__ out) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t s = 0;
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) s += in[base + i];
+  int64_t tot;
+  int64_t ex = block_excl_scan(s, &tot) + part[blockIdx.x];
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) {
+      out[base + i] = ex;
+      ex += in[base + i];
+    }
+  if (base + kScanItems >= n && base < n) out[n] = ex;  // thread owning the last item
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit encoding: one warp per row; lane q handles entries q, q+32, ...
+// ---------------------------------------------------------------------------
+__global__ void k_lp_chunks(const int64_t *__restrict__ rp, int64_t rows, int32_t *__restrict__ cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < rows) cnt[i] = (int32_t)((rp[i + 1] - rp[i] + 15) / 16);
+}
+
+template <bool kTranspose, typename W>
+__global__ void __launch_bounds__(kThreads) k_lp_encode(const AngleC *__restrict__ ang, int nx, int ny,
+                                                        int np, double c, const int64_t *__restrict__ rp,
+                                                        const int32_t *__restrict__ ci, int64_t rows,
+                                                        const int64_t *__restrict__ cp,
+                                                        int32_t *__restrict__ base,
+                                                        uint32_t *__restrict__ ow, int *__restrict__ err) {
+  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  int64_t b = rp[r], len = rp[r + 1] - b;
+  int64_t c0 = cp[r], nch = cp[r + 1] - c0;
+  for (int64_t e = lane; e < nch * 16; e += 32) {
+    int64_t ch = e >> 4;
+    int32_t cb = ci[b + ch * 16];
+    if ((e & 15) == 0) base[c0 + ch] = cb;
+    uint16_t o = 0, wbits = 0;
+    if (e < len) {
+      int32_t col = ci[b + e];
+      int64_t d = (int64_t)col - cb;
+      if (d < 0 || d > 65535) {
+        atomicExch(err, 2);
+      } else {
+        o = (uint16_t)d;
+      }
+      int ray = kTranspose ? col : (int)r;
+      int pix = kTranspose ? (int)r : col;
+      int m = ray / np, k = ray % np;
+      int ix = pix % nx, iy = pix / nx;
+      AngleC A = ang[m];
+      double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
+      double w = __dmul_rn(chord_len(A, pk, coord(ix, nx), coord(iy, ny)), A.a);
+      if constexpr (std::is_same<W, __nv_bfloat16>::value) {
+        __nv_bfloat16 hv = __double2bfloat16(w);
+        wbits = __bfloat16_as_ushort(hv);
+      } else {
+        __half hv = __double2half(w);
+        wbits = __half_as_ushort(hv);
+      }
+    }
+    ow[c0 * 16 + e] = (uint32_t)o | ((uint32_t)wbits << 16);
+  }
+}
+
+int grid_for_warps(int64_t warps) { return (int)((warps * 32 + kThreads - 1) / kThreads); }
+
+tomo_status scan_counts(const int32_t *cnt, int64_t n, int64_t *out, int64_t *part, int *maxv,
+                        cudaStream_t st) {
+  int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  k_scan_reduce<<<(unsigned)tiles, kThreads, 0, st>>>(cnt, n, part, maxv);
+  k_scan_parts<<<1, kThreads, 0, st>>>(part, tiles);
+  k_scan_apply<<<(unsigned)tiles, kThreads, 0, st>>>(cnt, n, part, out);
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
+}
+
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+template <typename T>
+tomo_status dmalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(TOMO_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  return TOMO_OK;
+}
+
+template <typename W>
+void launch_encode(tomo_matrix *h, bool transpose, const Csr &M, Lp &L, int *scratch, cudaStream_t st) {
+  int g = grid_for_warps(M.rows);
+  if (transpose)
+    k_lp_encode<true, W><<<g, kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, h->center, M.rp, M.ci, M.rows,
+                                                 L.cp, L.base, L.ow, scratch);
+  else
+    k_lp_encode<false, W><<<g, kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, h->center, M.rp, M.ci, M.rows,
+                                                  L.cp, L.base, L.ow, scratch);
+}
+
+tomo_status build_lp(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t *cnt, int64_t *part,
+                     int *scratch) {
+  const Csr &M = transpose ? h->AT : h->A;
+  Lp &L = transpose ? h->lpAT : h->lpA;
+  L.rows = M.rows;
+  TOMO_TRY(dmalloc(&L.cp, M.rows + 1));
+  k_lp_chunks<<<(unsigned)((M.rows + 255) / 256), 256, 0, st>>>(M.rp, M.rows, cnt);
+  TOMO_TRY(scan_counts(cnt, M.rows, L.cp, part, scratch + 3, st));
+  TOMO_CUDA(cudaMemcpyAsync(&L.chunks, L.cp + M.rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  TOMO_TRY(dmalloc(&L.base, L.chunks));
+  TOMO_TRY(dmalloc(&L.ow, L.chunks * 16));
+  if (h->lp_dtype == TOMO_BF16)
+    launch_encode<__nv_bfloat16>(h, transpose, M, L, scratch, st);
+  else
+    launch_encode<__half>(h, transpose, M, L, scratch, st);
+  TOMO_CUDA(cudaGetLastError());
+  h->bytes_lp += (M.rows + 1) * 8 + L.chunks * (4 + 16 * 4);
+  return TOMO_OK;
+}
+
+}  // namespace
+
+void free_matrix(tomo_matrix *h) {
+  if (!h) return;
+  void *ptrs[] = {h->ang,    h->ang_scale, h->A.rp,   h->A.ci,    h->A.v,       h->AT.rp,
+                  h->AT.ci,  h->AT.v,      h->R,      h->C,       h->lpA.cp,    h->lpA.base,
+                  h->lpA.ow, h->lpAT.cp,   h->lpAT.base, h->lpAT.ow};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cudaStream_t st,
+                         tomo_matrix **out) {
+  if (!g || !out) return fail(TOMO_ERR_INVALID_ARG, "geometry and out must be non-NULL");
+  *out = nullptr;
+  if (g->n_x <= 0 || g->n_y <= 0 || g->n_p <= 0 || g->n_theta <= 0)
+    return fail(TOMO_ERR_INVALID_ARG, "n_x, n_y, n_p and n_theta must be positive");
+  if ((int64_t)g->n_x * g->n_y >= (int64_t)INT32_MAX || (int64_t)g->n_p * g->n_theta >= (int64_t)INT32_MAX)
+    return fail(TOMO_ERR_INVALID_ARG, "n_x*n_y and n_theta*n_p must fit in int32 column indices");
+  int32_t lp = o ? o->values : TOMO_F32;
+  if (lp != TOMO_F32 && lp != TOMO_BF16 && lp != TOMO_F16)
+    return fail(TOMO_ERR_INVALID_ARG, "opts.values must be TOMO_F32, TOMO_BF16 or TOMO_F16");
+  double c = std::isnan(g->center) ? 0.5 * (double)g->n_p : g->center;
+  if (!std::isfinite(c)) return fail(TOMO_ERR_INVALID_ARG, "center must be finite or NaN");
+  const int nt = g->n_theta;
+  std::vector<AngleC> ang(nt);
+  std::vector<float> scale(nt);
+  for (int m = 0; m < nt; ++m) {
+    double th = g->angles ? g->angles[m] : (double)m * M_PI / (double)nt;
+    if (!std::isfinite(th)) return fail(TOMO_ERR_INVALID_ARG, "angles must be finite");
+    AngleC &A = ang[m];
+    A.cs = std::cos(th);
+    A.sn = std::sin(th);
+    double acs = std::fabs(A.cs), asn = std::fabs(A.sn);
+    A.a = acs > asn ? acs : asn;
+    A.e = acs > asn ? asn : acs;
+    A.h = 0.5 * (A.a + A.e);
+    A.hm = 0.5 * (A.a - A.e);
+    A.inv_a = 1.0 / A.a;
+    A.ae = A.a * A.e;
+    A.inv_cs = A.cs != 0.0 ? 1.0 / A.cs : 0.0;
+    A.inv_sn = A.sn != 0.0 ? 1.0 / A.sn : 0.0;
+    scale[m] = (float)(1.0 / A.a);
+  }
+
+  tomo_matrix *h = new tomo_matrix();
+  struct Guard {
+    tomo_matrix *h;
+    bool keep = false;
+    ~Guard() {
+      if (!keep) free_matrix(h);
+    }
+  } guard{h};
+  cudaGetDevice(&h->device);
+  h->nx = g->n_x;
+  h->ny = g->n_y;
+  h->np = g->n_p;
+  h->nt = nt;
+  h->center = c;
+  h->lp_dtype = lp;
+  const int64_t rows = (int64_t)nt * g->n_p, cols = (int64_t)g->n_x * g->n_y;
+  h->A.rows = rows;
+  h->A.cols = cols;
+  h->AT.rows = cols;
+  h->AT.cols = rows;
+
+  TOMO_TRY(dmalloc(&h->ang, nt));
+  TOMO_TRY(dmalloc(&h->ang_scale, nt));
+  TOMO_CUDA(cudaMemcpyAsync(h->ang, ang.data(), sizeof(AngleC) * nt, cudaMemcpyHostToDevice, st));
+  TOMO_CUDA(cudaMemcpyAsync(h->ang_scale, scale.data(), sizeof(float) * nt, cudaMemcpyHostToDevice, st));
+
+  int64_t nmax = rows > cols ? rows : cols;
+  int32_t *cnt = nullptr;
+  int64_t *part = nullptr;
+  int *scratch = nullptr;  // [0] error flag, [1] max row length, [2] max column length, [3] unused max
+  TOMO_TRY(dmalloc(&cnt, nmax));
+  DevBuf cnt_guard{cnt};
+  TOMO_TRY(dmalloc(&part, nmax / kScanTile + 2));
+  DevBuf part_guard{part};
+  TOMO_TRY(dmalloc(&scratch, 4));
+  DevBuf scratch_guard{scratch};
+  TOMO_CUDA(cudaMemsetAsync(scratch, 0, 4 * sizeof(int), st));
+
+  TOMO_TRY(dmalloc(&h->A.rp, rows + 1));
+  TOMO_TRY(dmalloc(&h->AT.rp, cols + 1));
+  TOMO_TRY(dmalloc(&h->R, rows));
+  TOMO_TRY(dmalloc(&h->C, cols));
+
+  k_count_rays<<<grid_for_warps(rows), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, cnt);
+  TOMO_CUDA(cudaGetLastError());
+  TOMO_TRY(scan_counts(cnt, rows, h->A.rp, part, scratch + 1, st));
+  k_pixels<false><<<grid_for_warps(cols), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, cnt,
+                                                               nullptr, nullptr, nullptr, nullptr, scratch);
+  TOMO_CUDA(cudaGetLastError());
+  TOMO_TRY(scan_counts(cnt, cols, h->AT.rp, part, scratch + 2, st));
+
+  int64_t nnz_a = 0, nnz_t = 0;
+  int hs[4] = {0, 0, 0, 0};
+  TOMO_CUDA(cudaMemcpyAsync(&nnz_a, h->A.rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaMemcpyAsync(&nnz_t, h->AT.rp + cols, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaMemcpyAsync(hs, scratch, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  if (hs[0] != 0) return fail(TOMO_ERR_NUMERIC, "pixel enumeration found more than two bins per angle");
+  if (nnz_a != nnz_t)
+    return fail(TOMO_ERR_NUMERIC, "ray-driven and pixel-driven entry counts differ: " + std::to_string(nnz_a) +
+                                      " vs " + std::to_string(nnz_t));
+  h->A.nnz = h->AT.nnz = nnz_a;
+  h->A.max_len = hs[1];
+  h->AT.max_len = hs[2];
+
+  size_t freeb = 0, totalb = 0;
+  TOMO_CUDA(cudaMemGetInfo(&freeb, &totalb));
+  size_t need = (size_t)nnz_a * 16 + (size_t)(lp != TOMO_F32 ? nnz_a * 9 + (rows + cols) * 48 : 0);
+  if (need + (size_t)(1ull << 30) > freeb)
+    return fail(TOMO_ERR_OOM, "matrix needs " + std::to_string(need) + " bytes, device has " +
+                                  std::to_string(freeb) + " free");
+  TOMO_TRY(dmalloc(&h->A.ci, nnz_a));
+  TOMO_TRY(dmalloc(&h->A.v, nnz_a));
+  TOMO_TRY(dmalloc(&h->AT.ci, nnz_a));
+  TOMO_TRY(dmalloc(&h->AT.v, nnz_a));
+  k_fill_rays<<<grid_for_warps(rows), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, h->A.rp,
+                                                          h->A.ci, h->A.v, h->R);
+  TOMO_CUDA(cudaGetLastError());
+  k_pixels<true><<<grid_for_warps(cols), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, nullptr,
+                                                             h->AT.rp, h->AT.ci, h->AT.v, h->C, scratch);
+  TOMO_CUDA(cudaGetLastError());
+  h->bytes_f32 = (rows + 1 + cols + 1) * 8 + nnz_a * 16;
+
+  if (lp != TOMO_F32) {
+    TOMO_TRY(build_lp(h, false, st, cnt, part, scratch));
+    TOMO_TRY(build_lp(h, true, st, cnt, part, scratch));
+  }
+  TOMO_CUDA(cudaMemcpyAsync(hs, scratch, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  if (hs[0] == 2)
+    return fail(TOMO_ERR_UNSUPPORTED, "a 16-entry chunk spans more than 65535 columns (geometry too large "
+                                      "for 16-bit offsets)");
+  if (hs[0] != 0) return fail(TOMO_ERR_NUMERIC, "pixel enumeration found more than two bins per angle");
+  guard.keep = true;
+  *out = h;
+  return TOMO_OK;
+}
+
+}  // namespace tomo

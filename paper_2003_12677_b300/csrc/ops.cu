@@ -1,0 +1,999 @@
+// ops.cu -- batched projector / backprojector SpMM and the SIRT / CGLS drivers.
+//
+// Slices are independent (Sec. 3.1: each tomogram and sinogram is processed on
+// its own), so a batch of B slices is one SpMM with B right-hand sides (Sec. 3:
+// SpMV for one sinogram, SpMM for a stack).  Vectors live on the device
+// interleaved as (rows, B): the B values of one row are contiguous, so every
+// matrix entry is read once per batch and its gathered operand row is one
+// coalesced B*4-byte segment.  The transpose is a stored matrix of its own
+// (Sec. 3.1), so both directions are row-parallel and need no atomics.
+//
+// SIRT and CGLS (Sec. 2.1) are fused into the SpMM epilogues (residual and
+// update of SIRT, norms of CGLS) plus small elementwise and scalar kernels;
+// one iteration is captured once as a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace tomo {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+template <int V>
+struct Vec {
+  float v[V];
+};
+
+template <int V>
+__device__ __forceinline__ Vec<V> ldg_vec(const float *p) {
+  Vec<V> r;
+  if constexpr (V == 4) {
+    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else if constexpr (V == 2) {
+    float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else {
+    r.v[0] = __ldg(p);
+  }
+  return r;
+}
+
+template <int V>
+__device__ __forceinline__ Vec<V> ld_vec(const float *p) {
+  Vec<V> r;
+  if constexpr (V == 4) {
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else if constexpr (V == 2) {
+    float2 t = *reinterpret_cast<const float2 *>(p);
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else {
+    r.v[0] = *p;
+  }
+  return r;
+}
+
+template <int V>
+__device__ __forceinline__ void st_vec(float *p, const Vec<V> &a) {
+  if constexpr (V == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+  } else if constexpr (V == 2) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a.v[0], a.v[1]);
+  } else {
+    *p = a.v[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Epilogues.  Called once per (row, lane) with the lane's V accumulated slices
+// starting at slice s0; `ss` collects per-slice squared norms when kNorm.
+// ---------------------------------------------------------------------------
+struct EpiStore {  // Y = acc
+  static constexpr bool kNorm = false;
+  float *Y;
+  int ld;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
+    st_vec<V>(Y + row * ld + s0, a);
+  }
+};
+
+struct EpiSirtResidual {  // r = R o (b - acc)
+  static constexpr bool kNorm = false;
+  float *r;
+  const float *b, *R;
+  int ld;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
+    float w = __ldg(R + row);
+    Vec<V> bv = ldg_vec<V>(b + row * ld + s0);
+#pragma unroll
+    for (int t = 0; t < V; ++t) a.v[t] = w * (bv.v[t] - a.v[t]);
+    st_vec<V>(r + row * ld + s0, a);
+  }
+};
+
+struct EpiSirtUpdate {  // x += lambda C o acc
+  static constexpr bool kNorm = false;
+  float *x;
+  const float *C;
+  float lam;
+  int ld;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
+    float w = lam * __ldg(C + row);
+    Vec<V> xv = ld_vec<V>(x + row * ld + s0);
+#pragma unroll
+    for (int t = 0; t < V; ++t) xv.v[t] = fmaf(w, a.v[t], xv.v[t]);
+    st_vec<V>(x + row * ld + s0, xv);
+  }
+};
+
+struct EpiStoreNorm {  // Y = acc, ss += acc^2
+  static constexpr bool kNorm = true;
+  float *Y;
+  int ld;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *ss) const {
+    st_vec<V>(Y + row * ld + s0, a);
+#pragma unroll
+    for (int t = 0; t < V; ++t) ss[t] += (double)a.v[t] * (double)a.v[t];
+  }
+};
+
+struct EpiResidualNorm {  // r = b - acc, ss += r^2
+  static constexpr bool kNorm = true;
+  float *r;
+  const float *b;
+  int ld;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *ss) const {
+    Vec<V> bv = ldg_vec<V>(b + row * ld + s0);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      a.v[t] = bv.v[t] - a.v[t];
+      ss[t] += (double)a.v[t] * (double)a.v[t];
+    }
+    st_vec<V>(r + row * ld + s0, a);
+  }
+};
+
+// Deterministic per-block reduction of ss[V] (slices s0..s0+V-1 of each thread)
+// into part[blockIdx.x * B + s].
+template <int V>
+__device__ void block_norms(const double *ss, int s0, int B, double *part) {
+  __shared__ double red[kThreads][4];
+  __shared__ int red_s0[kThreads];
+#pragma unroll
+  for (int t = 0; t < V; ++t) red[threadIdx.x][t] = ss[t];
+  red_s0[threadIdx.x] = s0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < B; s += blockDim.x) {
+    double acc = 0.0;
+    for (int t = 0; t < kThreads; ++t) {
+      int d = s - red_s0[t];
+      if (d >= 0 && d < V) acc += red[t][d];
+    }
+    part[(int64_t)blockIdx.x * B + s] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 CSR SpMM, B >= 4: L = B/4 lanes per row own 4 slices each (float4),
+// G = 32/L rows per warp.  Grid-stride over row groups.
+// ---------------------------------------------------------------------------
+template <int B, class Epi>
+__global__ void __launch_bounds__(kThreads) k_spmm_f32(const int64_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ ci,
+                                                       const float *__restrict__ val, int64_t rows,
+                                                       const float *__restrict__ X, Epi epi,
+                                                       double *__restrict__ part) {
+  constexpr int L = B / 4, G = 32 / L;
+  const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float *Xl = X + l * 4;
+  double ss[4] = {0, 0, 0, 0};
+  for (int64_t rg = warp; rg * G < rows; rg += nwarps) {
+    const int64_t row = rg * G + g;
+    if (row >= rows) continue;
+    Vec<4> acc = {{0.f, 0.f, 0.f, 0.f}};
+    int64_t e = __ldg(rp + row);
+    const int64_t end = __ldg(rp + row + 1);
+    for (; e + 8 <= end; e += 8) {
+      int c[8];
+      float w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[u] = __ldg(ci + e + u);
+        w[u] = __ldg(val + e + u);
+      }
+      Vec<4> xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = ldg_vec<4>(Xl + (size_t)c[u] * B);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc.v[t] = fmaf(w[u], xv[u].v[t], acc.v[t]);
+    }
+    for (; e < end; ++e) {
+      int c = __ldg(ci + e);
+      float w = __ldg(val + e);
+      Vec<4> xv = ldg_vec<4>(Xl + (size_t)c * B);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc.v[t] = fmaf(w, xv.v[t], acc.v[t]);
+    }
+    epi.template operator()<4>(row, l * 4, acc, ss);
+  }
+  if constexpr (Epi::kNorm) block_norms<4>(ss, l * 4, B, part);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 CSR SpMM for B in {1, 2}: P lanes split the entries of one row (CSR
+// vector form), each lane holds all B slices, shuffle reduction at the end.
+// ---------------------------------------------------------------------------
+template <int B, int P, class Epi>
+__global__ void __launch_bounds__(kThreads) k_spmv_f32(const int64_t *__restrict__ rp,
+                                                       const int32_t *__restrict__ ci,
+                                                       const float *__restrict__ val, int64_t rows,
+                                                       const float *__restrict__ X, Epi epi,
+                                                       double *__restrict__ part) {
+  constexpr int G = 32 / P;
+  const int lane = threadIdx.x & 31, p = lane % P, g = lane / P;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double ss[B];
+#pragma unroll
+  for (int t = 0; t < B; ++t) ss[t] = 0.0;
+  for (int64_t rg = warp; rg * G < rows; rg += nwarps) {
+    const int64_t row = rg * G + g;
+    const bool ok = row < rows;
+    Vec<B> acc;
+#pragma unroll
+    for (int t = 0; t < B; ++t) acc.v[t] = 0.f;
+    if (ok) {
+      int64_t e = __ldg(rp + row) + p;
+      const int64_t end = __ldg(rp + row + 1);
+      for (; e + 3 * P < end; e += 4 * P) {
+        int c[4];
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          c[u] = __ldg(ci + e + u * P);
+          w[u] = __ldg(val + e + u * P);
+        }
+        Vec<B> xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = ldg_vec<B>(X + (size_t)c[u] * B);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int t = 0; t < B; ++t) acc.v[t] = fmaf(w[u], xv[u].v[t], acc.v[t]);
+      }
+      for (; e < end; e += P) {
+        int c = __ldg(ci + e);
+        float w = __ldg(val + e);
+        Vec<B> xv = ldg_vec<B>(X + (size_t)c * B);
+#pragma unroll
+        for (int t = 0; t < B; ++t) acc.v[t] = fmaf(w, xv.v[t], acc.v[t]);
+      }
+    }
+#pragma unroll
+    for (int o = P / 2; o; o >>= 1)
+#pragma unroll
+      for (int t = 0; t < B; ++t) acc.v[t] += __shfl_xor_sync(0xffffffffu, acc.v[t], o);
+    if (ok && p == 0) epi.template operator()<B>(row, 0, acc, ss);
+  }
+  if constexpr (Epi::kNorm) block_norms<B>(ss, 0, B, part);
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit SpMM (values bf16 / f16 times a per-angle FP32 scale, uint16 column
+// offsets against a 32-bit base per 16-entry chunk).  Same lane mapping as
+// k_spmm_f32 (B >= 4).  kTrans selects A^T (scale per gathered column's angle)
+// versus A (scale per output row's angle).
+// ---------------------------------------------------------------------------
+template <bool kBf16>
+__device__ __forceinline__ float w16(uint32_t ow) {
+  if constexpr (kBf16) {
+    return __uint_as_float(ow & 0xffff0000u);
+  } else {
+    return __half2float(__ushort_as_half((unsigned short)(ow >> 16)));
+  }
+}
+
+// a / d for 0 <= a < 2^31 and small d: float estimate, then one exact correction
+__device__ __forceinline__ int div_exact(int a, int d, float inv_d) {
+  int q = (int)((float)a * inv_d);
+  if (q * d > a) --q;
+  else if ((q + 1) * d <= a) ++q;
+  return q;
+}
+
+template <int B, bool kBf16, bool kTrans, class Epi>
+__global__ void __launch_bounds__(kThreads) k_spmm_lp(const int64_t *__restrict__ cp,
+                                                      const int32_t *__restrict__ base,
+                                                      const uint32_t *__restrict__ ow, int64_t rows,
+                                                      const float *__restrict__ scale, int np, float inv_np,
+                                                      const float *__restrict__ X, Epi epi,
+                                                      double *__restrict__ part) {
+  constexpr int L = B / 4, G = 32 / L;
+  const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float *Xl = X + l * 4;
+  double ss[4] = {0, 0, 0, 0};
+  for (int64_t rg = warp; rg * G < rows; rg += nwarps) {
+    const int64_t row = rg * G + g;
+    if (row >= rows) continue;
+    Vec<4> acc = {{0.f, 0.f, 0.f, 0.f}};
+    const int64_t c0 = __ldg(cp + row), c1 = __ldg(cp + row + 1);
+    for (int64_t ch = c0; ch < c1; ++ch) {
+      const int cb = __ldg(base + ch);
+      const uint4 *q = reinterpret_cast<const uint4 *>(ow + ch * 16);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint4 p0 = __ldg(q + 2 * h), p1 = __ldg(q + 2 * h + 1);
+        uint32_t pk[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+        Vec<4> xv[8];
+        int cc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cc[u] = cb + (int)(pk[u] & 0xffffu);
+          xv[u] = ldg_vec<4>(Xl + (size_t)cc[u] * B);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float w = w16<kBf16>(pk[u]);
+          if constexpr (kTrans) w *= __ldg(scale + div_exact(cc[u], np, inv_np));
+#pragma unroll
+          for (int t = 0; t < 4; ++t) acc.v[t] = fmaf(w, xv[u].v[t], acc.v[t]);
+        }
+      }
+    }
+    if constexpr (!kTrans) {
+      float s = __ldg(scale + div_exact((int)row, np, inv_np));
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc.v[t] *= s;
+    }
+    epi.template operator()<4>(row, l * 4, acc, ss);
+  }
+  if constexpr (Epi::kNorm) block_norms<4>(ss, l * 4, B, part);
+}
+
+// ---------------------------------------------------------------------------
+// Layout: slice-major (n_z, n) <-> interleaved (n, B), through shared memory.
+// ---------------------------------------------------------------------------
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_interleave(const float *__restrict__ src, int64_t n, int cnt,
+                                                         float *__restrict__ dst) {
+  constexpr int TI = 32;
+  __shared__ float tile[B][TI + 1];
+  const int64_t i0 = (int64_t)blockIdx.x * TI;
+  for (int t = threadIdx.x; t < B * TI; t += blockDim.x) {
+    int s = t / TI, i = t % TI;
+    float v = 0.f;
+    if (s < cnt && i0 + i < n) v = src[(int64_t)s * n + i0 + i];
+    tile[s][i] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < B * TI; t += blockDim.x) {
+    int i = t / B, s = t % B;
+    if (i0 + i < n) dst[(i0 + i) * B + s] = tile[s][i];
+  }
+}
+
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_deinterleave(const float *__restrict__ src, int64_t n,
+                                                           int cnt, float *__restrict__ dst) {
+  constexpr int TI = 32;
+  __shared__ float tile[B][TI + 1];
+  const int64_t i0 = (int64_t)blockIdx.x * TI;
+  for (int t = threadIdx.x; t < B * TI; t += blockDim.x) {
+    int i = t / B, s = t % B;
+    if (i0 + i < n) tile[s][i] = src[(i0 + i) * B + s];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < B * TI; t += blockDim.x) {
+    int s = t / TI, i = t % TI;
+    if (s < cnt && i0 + i < n) dst[(int64_t)s * n + i0 + i] = tile[s][i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CGLS scalar and vector kernels.  Per-slice scalars (FP64), 8 per slice:
+//   [0] gamma = ||s||^2   [1] alpha   [2] beta   [3] frozen (0/1)
+// ---------------------------------------------------------------------------
+__device__ double block_sum_slice(const double *part, int nblk, int B, int s) {
+  __shared__ double red[kThreads];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += part[(int64_t)b * B + s];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = kThreads / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// one block per slice
+__global__ void __launch_bounds__(kThreads) k_cgls_init(const double *part, int nblk, int B, double *scal,
+                                                        int *it) {
+  int s = blockIdx.x;
+  double g = block_sum_slice(part, nblk, B, s);
+  if (threadIdx.x == 0) {
+    scal[s * 8 + 0] = g;
+    scal[s * 8 + 1] = 0.0;
+    scal[s * 8 + 2] = 0.0;
+    scal[s * 8 + 3] = 0.0;
+    if (s == 0) *it = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cgls_alpha(const double *part, int nblk, int B, double *scal) {
+  int s = blockIdx.x;
+  double qq = block_sum_slice(part, nblk, B, s);
+  if (threadIdx.x == 0) {
+    double gam = scal[s * 8 + 0];
+    bool frozen = scal[s * 8 + 3] != 0.0 || gam == 0.0 || qq == 0.0;
+    scal[s * 8 + 3] = frozen ? 1.0 : 0.0;
+    scal[s * 8 + 1] = frozen ? 0.0 : gam / qq;
+  }
+}
+
+// gamma' = ||s||^2, beta = gamma'/gamma, history of ||r|| (rr partials optional)
+__global__ void __launch_bounds__(kThreads) k_cgls_beta(const double *part_s, int nblk, const double *part_r,
+                                                        int nblk_r, int B, double *scal, double *hist,
+                                                        const int *it, int s0, int cnt, int nz) {
+  int s = blockIdx.x;
+  double gs = block_sum_slice(part_s, nblk, B, s);
+  double rr = part_r ? block_sum_slice(part_r, nblk_r, B, s) : 0.0;
+  if (threadIdx.x == 0) {
+    bool frozen = scal[s * 8 + 3] != 0.0;
+    if (frozen) {
+      scal[s * 8 + 2] = 0.0;
+    } else {
+      scal[s * 8 + 2] = gs / scal[s * 8 + 0];
+      scal[s * 8 + 0] = gs;
+    }
+    if (hist && s < cnt) hist[(int64_t)(*it) * nz + s0 + s] = sqrt(rr);
+  }
+}
+
+// x += alpha p (cols); r -= alpha q (rows), optional ||r||^2 partials
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_cgls_step(float *__restrict__ x, const float *__restrict__ p,
+                                                        int64_t ncols, float *__restrict__ r,
+                                                        const float *__restrict__ q, int64_t nrows,
+                                                        const double *__restrict__ scal,
+                                                        double *__restrict__ part_r) {
+  constexpr int V = B >= 4 ? 4 : B;
+  constexpr int PER = B / V;  // vectors per row
+  const int64_t nvx = ncols * PER, nvr = nrows * PER;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  // every thread keeps one fixed slice offset (nth is a multiple of PER)
+  const int s0 = (int)(tid % PER) * V;
+  float al[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) al[t] = (float)scal[(s0 + t) * 8 + 1];
+  for (int64_t i = tid; i < nvx; i += nth) {
+    Vec<V> xv = ld_vec<V>(x + i * V), pv = ld_vec<V>(p + i * V);
+#pragma unroll
+    for (int t = 0; t < V; ++t) xv.v[t] = fmaf(al[t], pv.v[t], xv.v[t]);
+    st_vec<V>(x + i * V, xv);
+  }
+  double ss[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) ss[t] = 0.0;
+  for (int64_t i = tid; i < nvr; i += nth) {
+    Vec<V> rv = ld_vec<V>(r + i * V), qv = ld_vec<V>(q + i * V);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      rv.v[t] = fmaf(-al[t], qv.v[t], rv.v[t]);
+      ss[t] += (double)rv.v[t] * (double)rv.v[t];
+    }
+    st_vec<V>(r + i * V, rv);
+  }
+  if (part_r) block_norms<V>(ss, s0, B, part_r);
+}
+
+// p = s + beta p (cols); advances the iteration counter
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_cgls_dir(float *__restrict__ p, const float *__restrict__ s,
+                                                       int64_t ncols, const double *__restrict__ scal,
+                                                       int *it) {
+  constexpr int V = B >= 4 ? 4 : B;
+  constexpr int PER = B / V;
+  const int64_t nv = ncols * PER;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int s0 = (int)(tid % PER) * V;
+  float be[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) be[t] = (float)scal[(s0 + t) * 8 + 2];
+  for (int64_t i = tid; i < nv; i += nth) {
+    Vec<V> pv = ld_vec<V>(p + i * V), sv = ld_vec<V>(s + i * V);
+#pragma unroll
+    for (int t = 0; t < V; ++t) pv.v[t] = fmaf(be[t], pv.v[t], sv.v[t]);
+    st_vec<V>(p + i * V, pv);
+  }
+  if (tid == 0 && it) ++*it;
+}
+
+// ---------------------------------------------------------------------------
+// launch plumbing
+// ---------------------------------------------------------------------------
+struct Op {  // one SpMM operand (A or A^T) in the selected encoding
+  const Csr *m;
+  const Lp *lp;
+  bool trans;
+  bool bf16;
+  const float *scale;
+  int np;
+};
+
+inline int spmm_grid(int64_t rows, int G) {
+  int64_t groups = (rows + G - 1) / G;
+  int64_t blocks = (groups + kWarps - 1) / kWarps;
+  int64_t cap = (int64_t)num_sms() * 8;
+  return (int)std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+inline int max_spmm_grid() { return num_sms() * 8; }
+
+template <int B, class Epi>
+void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream_t st) {
+  if constexpr (B >= 4) {
+    constexpr int G = 32 / (B / 4);
+    int grid = spmm_grid(op.m->rows, G);
+    if (op.lp) {
+      float inv_np = 1.0f / (float)op.np;
+      const Lp &L = *op.lp;
+      if (op.bf16) {
+        if (op.trans)
+          k_spmm_lp<B, true, true, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
+                                                                   op.np, inv_np, X, epi, part);
+        else
+          k_spmm_lp<B, true, false, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
+                                                                    op.np, inv_np, X, epi, part);
+      } else {
+        if (op.trans)
+          k_spmm_lp<B, false, true, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
+                                                                    op.np, inv_np, X, epi, part);
+        else
+          k_spmm_lp<B, false, false, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
+                                                                     op.np, inv_np, X, epi, part);
+      }
+    } else {
+      k_spmm_f32<B, Epi><<<grid, kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, op.m->rows, X, epi, part);
+    }
+  } else {
+    constexpr int P = 32;
+    int grid = spmm_grid(op.m->rows, 32 / P);
+    k_spmv_f32<B, P, Epi><<<grid, kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, op.m->rows, X, epi, part);
+  }
+}
+
+inline int elem_grid(int64_t n_vec) {
+  int64_t blocks = (n_vec + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)num_sms() * 8;
+  return (int)std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+template <int B>
+void interleave(const float *src, int64_t n, int cnt, float *dst, cudaStream_t st) {
+  k_interleave<B><<<(unsigned)((n + 31) / 32), kThreads, 0, st>>>(src, n, cnt, dst);
+}
+template <int B>
+void deinterleave(const float *src, int64_t n, int cnt, float *dst, cudaStream_t st) {
+  k_deinterleave<B><<<(unsigned)((n + 31) / 32), kThreads, 0, st>>>(src, n, cnt, dst);
+}
+
+// carve a workspace into 256-byte aligned pieces (p == nullptr: size only)
+struct Carver {
+  char *p;
+  size_t used = 0;
+  template <typename T>
+  T *take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T *r = p ? reinterpret_cast<T *>(p + used) : nullptr;
+    used += bytes;
+    return r;
+  }
+};
+
+// Private stream used only to record graphs (capture executes nothing); the
+// recorded graph is then launched on the caller's stream.  One per host thread.
+tomo_status capture_stream(cudaStream_t *out) {
+  thread_local cudaStream_t s = nullptr;
+  thread_local int dev = -1;
+  int cur = 0;
+  TOMO_CUDA(cudaGetDevice(&cur));
+  if (!s || dev != cur) {
+    TOMO_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    dev = cur;
+  }
+  *out = s;
+  return TOMO_OK;
+}
+
+// RAII for library-allocated workspaces (stream-ordered)
+struct WsHolder {
+  void *p = nullptr;
+  cudaStream_t st = nullptr;
+  ~WsHolder() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+// Optional per-launch timing: an event pair around every kernel, summed per
+// kind into the caller's tomo_timing when the call finishes.
+enum Kind { kA = 0, kAT = 1, kOther = 2 };
+struct Timer {
+  tomo_timing *t = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kinds;
+  void begin(cudaStream_t s) {
+    if (!t) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+  }
+  void end(cudaStream_t s, int kind) {
+    if (!t) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    kinds.push_back(kind);
+  }
+  tomo_status finish(cudaStream_t s) {
+    if (!t) return TOMO_OK;
+    TOMO_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < kinds.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      t->ms[kinds[i]] += ms;
+      t->launches[kinds[i]] += 1;
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    kinds.clear();
+    return TOMO_OK;
+  }
+};
+
+#define TIMED(tm, st, kind, ...) \
+  do {                           \
+    (tm).begin(st);              \
+    __VA_ARGS__;                 \
+    (tm).end(st, kind);          \
+  } while (0)
+
+Op make_op(const tomo_matrix *h, bool trans, const Exec &ex) {
+  Op op;
+  op.m = trans ? &h->AT : &h->A;
+  op.lp = ex.lp ? (trans ? &h->lpAT : &h->lpA) : nullptr;
+  op.trans = trans;
+  op.bf16 = h->lp_dtype == TOMO_BF16;
+  op.scale = h->ang_scale;
+  op.np = h->np;
+  return op;
+}
+
+// ---------------------------------------------------------------------------
+// project / backproject
+// ---------------------------------------------------------------------------
+template <int B>
+tomo_status project_t(const tomo_matrix *h, bool trans, const float *in, float *out, int32_t nz, int layout,
+                      const Exec &ex, void *ws, cudaStream_t st) {
+  Op op = make_op(h, trans, ex);
+  Timer tm{ex.timing};
+  const int kind = trans ? kAT : kA;
+  const int64_t nin = op.m->cols, nout = op.m->rows;
+  if (layout == TOMO_INTERLEAVED || B == 1) {
+    // interleaved with n_z == B (or a single slice per pass): operate in place
+    for (int32_t s0 = 0; s0 < nz; s0 += B)
+      TIMED(tm, st, kind,
+            launch_spmm<B>(op, in + (int64_t)s0 * nin, EpiStore{out + (int64_t)s0 * nout, B}, nullptr, st));
+    TOMO_CUDA(cudaGetLastError());
+    return tm.finish(st);
+  }
+  Carver cv{(char *)ws};
+  float *xi = cv.take<float>(nin * B);
+  float *yi = cv.take<float>(nout * B);
+  for (int32_t s0 = 0; s0 < nz; s0 += B) {
+    int cnt = std::min<int32_t>(B, nz - s0);
+    TIMED(tm, st, kOther, interleave<B>(in + (int64_t)s0 * nin, nin, cnt, xi, st));
+    TIMED(tm, st, kind, launch_spmm<B>(op, xi, EpiStore{yi, B}, nullptr, st));
+    TIMED(tm, st, kOther, deinterleave<B>(yi, nout, cnt, out + (int64_t)s0 * nout, st));
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return tm.finish(st);
+}
+
+// ---------------------------------------------------------------------------
+// SIRT
+// ---------------------------------------------------------------------------
+template <int B>
+tomo_status sirt_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters, float lam,
+                   const Exec &ex, void *ws, cudaStream_t st) {
+  Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
+  const int64_t rows = h->A.rows, cols = h->A.cols;
+  Carver cv{(char *)ws};
+  float *r = cv.take<float>(rows * B);
+  float *bi = B > 1 ? cv.take<float>(rows * B) : nullptr;
+  float *xi = B > 1 ? cv.take<float>(cols * B) : nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TOMO_CUDA(cudaStreamIsCapturing(st, &cs));
+  Timer tm{ex.timing};
+  const bool use_graph = ex.graph && !ex.timing && cs == cudaStreamCaptureStatusNone && iters > 1;
+  cudaStream_t cap = nullptr;
+  for (int32_t s0 = 0; s0 < nz; s0 += B) {
+    int cnt = std::min<int32_t>(B, nz - s0);
+    const float *bb = sino + (int64_t)s0 * rows;
+    float *xx = x + (int64_t)s0 * cols;
+    if (B > 1) {
+      TIMED(tm, st, kOther, interleave<B>(bb, rows, cnt, bi, st));
+      TIMED(tm, st, kOther, interleave<B>(xx, cols, cnt, xi, st));
+      bb = bi;
+      xx = xi;
+    }
+    auto one_iter = [&](cudaStream_t s) {
+      TIMED(tm, s, kA, launch_spmm<B>(A, xx, EpiSirtResidual{r, bb, h->R, B}, nullptr, s));
+      TIMED(tm, s, kAT, launch_spmm<B>(AT, r, EpiSirtUpdate{xx, h->C, lam, B}, nullptr, s));
+    };
+    if (use_graph) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      TOMO_TRY(capture_stream(&cap));
+      TOMO_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      one_iter(cap);
+      TOMO_CUDA(cudaStreamEndCapture(cap, &graph));
+      TOMO_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      for (int32_t it = 0; it < iters; ++it) TOMO_CUDA(cudaGraphLaunch(exec, st));
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+    } else {
+      for (int32_t it = 0; it < iters; ++it) one_iter(st);
+    }
+    if (B > 1) TIMED(tm, st, kOther, deinterleave<B>(xi, cols, cnt, x + (int64_t)s0 * cols, st));
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return tm.finish(st);
+}
+
+// ---------------------------------------------------------------------------
+// CGLS
+// ---------------------------------------------------------------------------
+template <int B>
+tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
+                   int32_t recompute, double *hist, const Exec &ex, void *ws, cudaStream_t st) {
+  Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
+  const int64_t rows = h->A.rows, cols = h->A.cols;
+  const int pg = max_spmm_grid();
+  Carver cv{(char *)ws};
+  float *r = cv.take<float>(rows * B);
+  float *q = cv.take<float>(rows * B);
+  float *p = cv.take<float>(cols * B);
+  float *s = cv.take<float>(cols * B);
+  double *part_a = cv.take<double>((size_t)pg * B);
+  double *part_b = cv.take<double>((size_t)pg * B);
+  double *part_r = cv.take<double>((size_t)pg * B);
+  double *scal = cv.take<double>(B * 8);
+  int *itc = cv.take<int>(4);
+  float *bi = B > 1 ? cv.take<float>(rows * B) : nullptr;
+  float *xi = B > 1 ? cv.take<float>(cols * B) : nullptr;
+
+  constexpr int G = B >= 4 ? 32 / (B / 4) : 1;
+  const int gA = spmm_grid(rows, G);
+  const int gT = spmm_grid(cols, G);
+  constexpr int PER = B >= 4 ? B / 4 : 1;
+  const int ge = elem_grid((rows > cols ? rows : cols) * PER);
+
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TOMO_CUDA(cudaStreamIsCapturing(st, &cs));
+  Timer tm{ex.timing};
+  const bool use_graph = ex.graph && !ex.timing && cs == cudaStreamCaptureStatusNone && iters > 1;
+  cudaStream_t cap = nullptr;
+
+  for (int32_t s0 = 0; s0 < nz; s0 += B) {
+    int cnt = std::min<int32_t>(B, nz - s0);
+    const float *bb = sino + (int64_t)s0 * rows;
+    float *xx = x + (int64_t)s0 * cols;
+    if (B > 1) {
+      TIMED(tm, st, kOther, interleave<B>(bb, rows, cnt, bi, st));
+      bb = bi;
+      xx = xi;
+    }
+    // x = 0, r = b, s = A^T r, p = s, gamma = ||s||^2
+    TOMO_CUDA(cudaMemsetAsync(xx, 0, sizeof(float) * cols * B, st));
+    TOMO_CUDA(cudaMemcpyAsync(r, bb, sizeof(float) * rows * B, cudaMemcpyDeviceToDevice, st));
+    TIMED(tm, st, kAT, launch_spmm<B>(AT, r, EpiStoreNorm{s, B}, part_b, st));
+    TOMO_CUDA(cudaMemcpyAsync(p, s, sizeof(float) * cols * B, cudaMemcpyDeviceToDevice, st));
+    TIMED(tm, st, kOther, (k_cgls_init<<<B, kThreads, 0, st>>>(part_b, gT, B, scal, itc)));
+    TOMO_CUDA(cudaGetLastError());
+
+    // the residual-norm partials come from the SpMM grid (gA blocks) on a
+    // recompute iteration and from the elementwise grid (ge blocks) otherwise
+    auto one_iter = [&](cudaStream_t sm, bool recomp) {
+      // q = A p, ||q||^2
+      TIMED(tm, sm, kA, launch_spmm<B>(A, p, EpiStoreNorm{q, B}, part_a, sm));
+      // alpha = gamma / ||q||^2
+      TIMED(tm, sm, kOther, (k_cgls_alpha<<<B, kThreads, 0, sm>>>(part_a, gA, B, scal)));
+      // x += alpha p, r -= alpha q
+      TIMED(tm, sm, kOther,
+            (k_cgls_step<B><<<ge, kThreads, 0, sm>>>(xx, p, cols, r, q, rows, scal, hist ? part_r : nullptr)));
+      // every `recompute` iterations: r = b - A x
+      if (recomp) TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidualNorm{r, bb, B}, part_r, sm));
+      // s = A^T r, ||s||^2
+      TIMED(tm, sm, kAT, launch_spmm<B>(AT, r, EpiStoreNorm{s, B}, part_b, sm));
+      // beta = ||s||^2 / gamma, residual history
+      TIMED(tm, sm, kOther,
+            (k_cgls_beta<<<B, kThreads, 0, sm>>>(part_b, gT, hist ? part_r : nullptr, recomp ? gA : ge, B, scal,
+                                                 hist, itc, s0, cnt, nz)));
+      // p = s + beta p
+      TIMED(tm, sm, kOther, (k_cgls_dir<B><<<ge, kThreads, 0, sm>>>(p, s, cols, scal, itc)));
+    };
+    if (use_graph) {
+      TOMO_TRY(capture_stream(&cap));
+      cudaGraph_t g0 = nullptr, g1 = nullptr;
+      cudaGraphExec_t e0 = nullptr, e1 = nullptr;
+      TOMO_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      one_iter(cap, false);
+      TOMO_CUDA(cudaStreamEndCapture(cap, &g0));
+      TOMO_CUDA(cudaGraphInstantiate(&e0, g0, 0));
+      if (recompute > 0) {
+        TOMO_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        one_iter(cap, true);
+        TOMO_CUDA(cudaStreamEndCapture(cap, &g1));
+        TOMO_CUDA(cudaGraphInstantiate(&e1, g1, 0));
+      }
+      for (int32_t it = 0; it < iters; ++it) {
+        bool rc = recompute > 0 && (it + 1) % recompute == 0;
+        TOMO_CUDA(cudaGraphLaunch(rc ? e1 : e0, st));
+      }
+      cudaGraphExecDestroy(e0);
+      cudaGraphDestroy(g0);
+      if (e1) cudaGraphExecDestroy(e1);
+      if (g1) cudaGraphDestroy(g1);
+    } else {
+      for (int32_t it = 0; it < iters; ++it) one_iter(st, recompute > 0 && (it + 1) % recompute == 0);
+    }
+    if (B > 1) TIMED(tm, st, kOther, deinterleave<B>(xi, cols, cnt, x + (int64_t)s0 * cols, st));
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return tm.finish(st);
+}
+
+template <template <int> class F, typename... Args>
+tomo_status dispatch(int B, Args &&...args) {
+  switch (B) {
+    case 1: return F<1>::run(args...);
+    case 2: return F<2>::run(args...);
+    case 4: return F<4>::run(args...);
+    case 8: return F<8>::run(args...);
+    case 16: return F<16>::run(args...);
+    case 32: return F<32>::run(args...);
+    case 64: return F<64>::run(args...);
+    default: return fail(TOMO_ERR_UNSUPPORTED, "batch width must be 1, 2, 4, 8, 16, 32 or 64");
+  }
+}
+
+template <int B>
+struct ProjectF {
+  template <typename... A>
+  static tomo_status run(A &&...a) { return project_t<B>(a...); }
+};
+template <int B>
+struct SirtF {
+  template <typename... A>
+  static tomo_status run(A &&...a) { return sirt_t<B>(a...); }
+};
+template <int B>
+struct CglsF {
+  template <typename... A>
+  static tomo_status run(A &&...a) { return cgls_t<B>(a...); }
+};
+
+bool valid_width(int b) { return b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32 || b == 64; }
+
+tomo_status with_ws(const tomo_matrix *h, int op, int32_t nz, const Exec &ex, void *&ws, WsHolder &hold,
+                    cudaStream_t st) {
+  size_t need = workspace_bytes(h, op, nz, ex);
+  if (ws || need == 0) return TOMO_OK;
+  cudaError_t e = cudaMallocAsync(&hold.p, need, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TOMO_ERR_OOM, "workspace allocation of " + std::to_string(need) + " bytes failed");
+  }
+  hold.st = st;
+  ws = hold.p;
+  return TOMO_OK;
+}
+
+}  // namespace
+
+tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t nz, Exec *ex) {
+  Exec e;
+  int req = o ? o->batch_width : 0;
+  if (req != 0 && !valid_width(req))
+    return fail(TOMO_ERR_UNSUPPORTED, "batch_width must be 0, 1, 2, 4, 8, 16, 32 or 64");
+  if (req == 0) {
+    int b = 1;
+    while (b < nz && b < 16) b <<= 1;
+    req = b;
+  }
+  e.B = req;
+  e.graph = o ? o->use_graph != 0 : true;
+  e.timing = o ? o->timing : nullptr;
+  if (o && o->precision == 1) {
+    if (h->lp_dtype == TOMO_F32) return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without 16-bit values");
+    if (e.B < 4) return fail(TOMO_ERR_UNSUPPORTED, "the 16-bit kernels need batch_width >= 4");
+    e.lp = true;
+  } else if (o && o->precision != 0) {
+    return fail(TOMO_ERR_INVALID_ARG, "precision must be 0 or 1");
+  }
+  *ex = e;
+  return TOMO_OK;
+}
+
+size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex) {
+  (void)nz;
+  const int64_t rows = h->A.rows, cols = h->A.cols;
+  const int B = ex.B;
+  Carver cv{nullptr};
+  switch (op) {
+    case TOMO_OP_PROJECT:
+    case TOMO_OP_BACKPROJECT:
+      if (B > 1) {
+        cv.take<float>(cols * B);
+        cv.take<float>(rows * B);
+      }
+      break;
+    case TOMO_OP_SIRT:
+      cv.take<float>(rows * B);
+      if (B > 1) {
+        cv.take<float>(rows * B);
+        cv.take<float>(cols * B);
+      }
+      break;
+    case TOMO_OP_CGLS: {
+      const int pg = max_spmm_grid();
+      cv.take<float>(rows * B);
+      cv.take<float>(rows * B);
+      cv.take<float>(cols * B);
+      cv.take<float>(cols * B);
+      cv.take<double>((size_t)pg * B);
+      cv.take<double>((size_t)pg * B);
+      cv.take<double>((size_t)pg * B);
+      cv.take<double>(B * 8);
+      cv.take<int>(4);
+      if (B > 1) {
+        cv.take<float>(rows * B);
+        cv.take<float>(cols * B);
+      }
+      break;
+    }
+    default:
+      return 0;
+  }
+  return cv.used;
+}
+
+tomo_status run_project(const tomo_matrix *h, bool transpose, const float *in, float *out, int32_t nz,
+                        int layout, const Exec &ex, void *ws, cudaStream_t st) {
+  WsHolder hold;
+  TOMO_TRY(with_ws(h, transpose ? TOMO_OP_BACKPROJECT : TOMO_OP_PROJECT, nz, ex, ws, hold, st));
+  return dispatch<ProjectF>(ex.B, h, transpose, in, out, nz, layout, ex, ws, st);
+}
+
+tomo_status run_sirt(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
+                     float lambda, const Exec &ex, void *ws, cudaStream_t st) {
+  WsHolder hold;
+  TOMO_TRY(with_ws(h, TOMO_OP_SIRT, nz, ex, ws, hold, st));
+  return dispatch<SirtF>(ex.B, h, sino, x, nz, iters, lambda, ex, ws, st);
+}
+
+tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
+                     int32_t recompute, double *hist, const Exec &ex, void *ws, cudaStream_t st) {
+  WsHolder hold;
+  TOMO_TRY(with_ws(h, TOMO_OP_CGLS, nz, ex, ws, hold, st));
+  return dispatch<CglsF>(ex.B, h, sino, x, nz, iters, recompute, hist, ex, ws, st);
+}
+
+}  // namespace tomo

@@ -1,0 +1,209 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (ctypes binding).
+
+Bars: row pointers and column indices bit-exact; FP32 values equal to the
+oracle's FP64 chord lengths rounded to nearest; FP32 SpMM within 1e-5
+relative L2 per slice; SIRT and CGLS iterates within 1e-4 relative L2;
+16-bit SpMM within 5e-3 (bf16) / 1e-3 (f16).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_12677_b300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # the gpu marker is only run on a GPU machine
+    pytest.skip("needs CUDA", allow_module_level=True)
+
+import paper_2003_12677_b300 as tomo  # noqa: E402
+from paper_2003_12677_b300 import _lib  # noqa: E402
+
+WIDTHS = [1, 2, 4, 8, 16, 32, 64]
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def per_slice_rel(a, b):
+    a = np.asarray(a, np.float64).reshape(len(a), -1)
+    b = np.asarray(b, np.float64).reshape(len(b), -1)
+    return np.array([rel_l2(a[i], b[i]) for i in range(len(a))])
+
+
+_cache = {}
+
+
+def pair(nx, nt, n_p=None, ny=None, angles=None, center=None, values="f32"):
+    """(oracle geometry, oracle A, oracle A^T, GPU matrix) for one geometry."""
+    key = (nx, nt, n_p, ny, None if angles is None else tuple(angles), center, values)
+    if key not in _cache:
+        g = oracle.Geometry(nx, nx if ny is None else ny, nx if n_p is None else n_p, nt,
+                            None if angles is None else np.asarray(angles), center)
+        A = oracle.build_matrix(g)
+        M = tomo.Matrix(nx, nt, n_p=n_p, n_y=ny, angles=angles, center=center, values=values)
+        _cache[key] = (g, A, A.transpose(), M)
+    return _cache[key]
+
+
+GEOMS = [
+    dict(nx=128, nt=180),                                   # the 128x128, 180-angle workload
+    dict(nx=37, nt=23, n_p=41, center=19.7),                # odd sizes, shifted axis
+    dict(nx=40, nt=7, ny=29, n_p=50),                       # rectangular image, wide detector
+    dict(nx=16, nt=6, angles=[0.0, math.pi / 4, math.pi / 2, 3 * math.pi / 4, 1e-9, math.pi - 1e-9]),
+    dict(nx=1, nt=1),                                       # one pixel, one ray
+]
+
+
+@pytest.mark.parametrize("geo", GEOMS)
+def test_structure_and_values_bitexact(geo):
+    g, A, AT, M = pair(**geo)
+    assert M.nnz == A.nnz
+    rp, col, val = M.export_csr()
+    np.testing.assert_array_equal(rp, A.row_ptr)
+    np.testing.assert_array_equal(col, A.col)
+    np.testing.assert_array_equal(val, A.val.astype(np.float32))
+    rp, col, val = M.export_csr(transpose=True)
+    np.testing.assert_array_equal(rp, AT.row_ptr)
+    np.testing.assert_array_equal(col, AT.col)
+    np.testing.assert_array_equal(val, AT.val.astype(np.float32))
+
+
+@pytest.mark.parametrize("geo", GEOMS[:3])
+def test_sirt_normalisers(geo):
+    g, A, AT, M = pair(**geo)
+    R, C = M.export_norms()
+    np.testing.assert_allclose(R, oracle.inv_row_sums(A).astype(np.float32), rtol=2e-7, atol=0)
+    np.testing.assert_allclose(C, oracle.inv_row_sums(AT).astype(np.float32), rtol=2e-7, atol=0)
+
+
+@pytest.mark.parametrize("B", WIDTHS)
+@pytest.mark.parametrize("nz", [1, 3, 9])
+def test_project_backproject_f32(B, nz):
+    g, A, AT, M = pair(nx=96, nt=60, n_p=101, center=50.3)
+    x = inputs.random_slices((nz, 96, 96), seed=100 + nz)
+    y = inputs.random_slices((nz, 60, 101), seed=200 + nz)
+    yd = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=B).cpu().numpy()
+    xd = tomo.backproject(M, torch.from_numpy(y).cuda(), batch_width=B).cpu().numpy()
+    assert per_slice_rel(yd, A.apply(x)).max() < 1e-5
+    assert per_slice_rel(xd, AT.apply(y)).max() < 1e-5
+
+
+@pytest.mark.parametrize("B", WIDTHS)
+def test_interleaved_layout(B):
+    g, A, AT, M = pair(nx=64, nt=45)
+    x = inputs.random_slices((B, 64 * 64), seed=7)
+    xi = torch.from_numpy(np.ascontiguousarray(x.T)).cuda()
+    yi = tomo.project(M, xi, interleaved=True).cpu().numpy()
+    assert per_slice_rel(yi.T, A.apply(x)).max() < 1e-5
+    xb = tomo.backproject(M, torch.from_numpy(np.ascontiguousarray(yi)).cuda(), interleaved=True).cpu().numpy()
+    assert per_slice_rel(xb.T, AT.apply(yi.T)).max() < 1e-5
+
+
+def test_adjoint_identity_f32():
+    g, A, AT, M = pair(nx=128, nt=180)
+    x = torch.from_numpy(inputs.random_slices((4, 128, 128), 1)).cuda()
+    y = torch.from_numpy(inputs.random_slices((4, 180, 128), 2)).cuda()
+    lhs = torch.sum(tomo.project(M, x).double() * y.double()).item()
+    rhs = torch.sum(x.double() * tomo.backproject(M, y).double()).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+@pytest.mark.parametrize("B", [1, 4, 16])
+def test_sirt_128(B):
+    """one 128x128 slice, 180 angles, Poisson 1e5, SIRT 50 (and a 3-slice batch)."""
+    c = inputs.workload_case("sirt_128x180_b1")
+    g, A, AT, M = pair(nx=128, nt=180)
+    sino = np.concatenate([c.sino, c.sino * 0.5, c.sino[:, ::-1]]) if B > 1 else c.sino
+    sino = np.ascontiguousarray(sino)
+    ref = oracle.sirt(A, AT, sino.reshape(len(sino), -1), 50, 1.0)
+    got = tomo.sirt(M, torch.from_numpy(sino).cuda(), 50, batch_width=B).cpu().numpy()
+    assert per_slice_rel(got, ref).max() < 1e-4
+
+
+def test_sirt_lambda_and_start():
+    g, A, AT, M = pair(nx=37, nt=23, n_p=41, center=19.7)
+    rng = np.random.default_rng(3)
+    b = rng.random((2, A.rows)).astype(np.float32)
+    x0 = rng.random((2, 37 * 37)).astype(np.float32)
+    ref = oracle.sirt(A, AT, b, 20, 0.7, x0=x0)
+    got = tomo.sirt(M, torch.from_numpy(b).cuda(), 20, lam=0.7,
+                    x0=torch.from_numpy(x0.reshape(2, 37, 37)).cuda(), batch_width=2).cpu().numpy()
+    assert per_slice_rel(got, ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("B,nz", [(1, 2), (4, 5), (16, 16), (64, 3)])
+@pytest.mark.parametrize("graph", [True, False])
+def test_cgls(B, nz, graph):
+    g, A, AT, M = pair(nx=64, nt=90)
+    c = inputs.make_case(64, 90, nz, seed=55, phantom="ellipsoids3d", noise="gaussian", level=0.05)
+    ref, href = oracle.cgls(A, AT, c.sino.reshape(nz, -1), 50)
+    got, h = tomo.cgls(M, torch.from_numpy(c.sino).cuda(), 50, history=True, batch_width=B, use_graph=graph)
+    assert per_slice_rel(got.cpu().numpy(), ref).max() < 1e-4
+    np.testing.assert_allclose(h.cpu().numpy(), href, rtol=1e-4)
+
+
+def test_cgls_residual_recompute():
+    g, A, AT, M = pair(nx=64, nt=90)
+    c = inputs.make_case(64, 90, 4, seed=56, phantom="ellipsoids3d", noise="gaussian", level=0.05)
+    ref, _ = oracle.cgls(A, AT, c.sino.reshape(4, -1), 50)
+    got = tomo.cgls(M, torch.from_numpy(c.sino).cuda(), 50, recompute_every=10, batch_width=4)
+    assert per_slice_rel(got.cpu().numpy(), ref).max() < 1e-4
+
+
+def test_cgls_zero_sinogram_is_frozen():
+    g, A, AT, M = pair(nx=64, nt=90)
+    z = torch.zeros((3, 90, 64), device="cuda")
+    x, h = tomo.cgls(M, z, 5, history=True, batch_width=4)
+    assert torch.all(x == 0) and torch.all(h == 0)
+
+
+@pytest.mark.parametrize("values,tol", [("bf16", 5e-3), ("f16", 1e-3)])
+@pytest.mark.parametrize("B", [4, 16, 64])
+def test_lowprec_spmm(values, tol, B):
+    g, A, AT, M = pair(nx=128, nt=180, values=values)
+    x = inputs.random_slices((5, 128, 128), seed=31)
+    y = inputs.random_slices((5, 180, 128), seed=32)
+    yd = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=B, precision=1).cpu().numpy()
+    xd = tomo.backproject(M, torch.from_numpy(y).cuda(), batch_width=B, precision=1).cpu().numpy()
+    assert per_slice_rel(yd, A.apply(x)).max() < tol
+    assert per_slice_rel(xd, AT.apply(y)).max() < tol
+
+
+def test_autograd_matches_oracle_gradient():
+    """loss = ||A x - b||^2 + mu TV_eps(x): GPU autograd gradient vs the FP64
+    oracle gradient on 64 random directions (relative 1e-4)."""
+    n, nt, nz = 64, 60, 2
+    g, A, AT, M = pair(nx=n, nt=nt)
+    rng = np.random.default_rng(12)
+    x = rng.random((nz, n, n)).astype(np.float32)
+    b = rng.random((nz, nt, n)).astype(np.float32)
+    mu, eps = 1e-3, 1e-3
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    r = tomo.radon(xt, M) - torch.from_numpy(b).cuda()
+    loss = (r * r).sum() + mu * tomo.tv_loss(xt, eps)
+    loss.backward()
+    gd = xt.grad.double().cpu().numpy().reshape(nz, -1)
+    f, gref = oracle.loss_grad(A, AT, n, n, x.reshape(nz, -1), b.reshape(nz, -1), mu, eps)
+    assert abs(loss.item() - f) <= 1e-5 * abs(f)
+    for _ in range(64):
+        v = rng.standard_normal(gd.shape)
+        v /= np.linalg.norm(v)
+        a, e = float(np.sum(gd * v)), float(np.sum(gref * v))
+        assert abs(a - e) <= 1e-4 * np.linalg.norm(gref)
+
+
+def test_errors_are_reported():
+    with pytest.raises(_lib.TomoError):
+        tomo.Matrix(0, 10)
+    g, A, AT, M = pair(nx=64, nt=45)
+    with pytest.raises(_lib.TomoError):
+        tomo.project(M, torch.zeros((3, 64, 64), device="cuda"), batch_width=3)
+    with pytest.raises(_lib.TomoError):
+        tomo.project(M, torch.zeros((1, 64, 64), device="cuda"), precision=1)
