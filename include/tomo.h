@@ -188,6 +188,29 @@ TOMO_API tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x
                                int32_t recompute_every, double *resnorm_hist, const tomo_exec_opts *opts,
                                void *workspace, size_t workspace_bytes, void *stream);
 
+/* SIRT exactly as tomo_sirt, for callers that cannot allocate GPU memory at
+ * all.  The paper has no counterpart; this entry point exists for programs
+ * that reconstruct inside a fixed memory budget, such as a reconstruction
+ * loop embedded in a detector's acquisition software: cudaMalloc / cudaFree
+ * may synchronise the device (stalling the streams that move frames) and may
+ * fail under memory pressure in the middle of a scan, so such a caller can
+ * neither pass a workspace it allocated nor let the library allocate one.
+ *
+ * The call allocates nothing.  Its scratch is a 16 MiB array compiled into
+ * the library; every GPU that loads the library reserves it until the process
+ * exits.  The first call on a device looks up that array's device address;
+ * make that first call before any stream capture on that device.  Batch width
+ * is chosen internally (the widest of 16, 8, 4, 2, 1, not above n_z, whose
+ * scratch fits); a geometry whose residual alone exceeds 16 MiB (more than
+ * 4,194,304 rays) is rejected with TOMO_ERR_INVALID_ARG and a message giving
+ * the bytes it would need.  All calls share the one array: calls that can
+ * overlap on the GPU (different streams, or different host threads) race on
+ * it and must be serialised by the caller.  Nothing in the array has to start
+ * at zero; every word a call reads it has written first.  Arguments as for
+ * tomo_sirt; kernels are launched on `stream` without CUDA graphs. */
+TOMO_API tomo_status tomo_sirt_noalloc(const tomo_matrix *A, const float *sino, float *x, int32_t n_z,
+                                       int32_t iters, float lambda, void *stream);
+
 /* Human-readable name of a status code (static string). */
 TOMO_API const char *tomo_status_string(tomo_status s);
 

@@ -6,7 +6,8 @@ The torch-facing API (``Matrix``, ``project``, ``backproject``, ``sirt``,
 on first use so that ``paper_2003_12677_b300.inputs`` stays importable without
 torch.
 """
-_API = {"Matrix", "project", "backproject", "sirt", "cgls", "TomoProject", "radon", "tv_loss", "new_timing"}
+_API = {"Matrix", "project", "backproject", "sirt", "cgls", "TomoProject", "radon", "tv_loss", "new_timing",
+        "sirt_noalloc"}
 
 
 def __getattr__(name):

@@ -17,7 +17,7 @@ SLICE_MAJOR, INTERLEAVED = 0, 1
 # every entry point include/tomo.h declares
 EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
            "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
-           "tomo_sirt", "tomo_cgls", "tomo_status_string", "tomo_last_error"]
+           "tomo_sirt", "tomo_cgls", "tomo_sirt_noalloc", "tomo_status_string", "tomo_last_error"]
 
 
 class TomoError(RuntimeError):
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
         "tomo_backproject": [P, P, P, I32, I32, ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_sirt": [P, P, P, I32, I32, ctypes.c_float, ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_cgls": [P, P, P, I32, I32, I32, P, ctypes.POINTER(ExecOpts), P, SZ, P],
+        "tomo_sirt_noalloc": [P, P, P, I32, I32, ctypes.c_float, P],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

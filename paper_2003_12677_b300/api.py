@@ -209,6 +209,24 @@ def sirt(M: Matrix, sino: torch.Tensor, iters: int, lam: float = 1.0, x0: Option
     return x
 
 
+def sirt_noalloc(M: Matrix, sino: torch.Tensor, iters: int, lam: float = 1.0,
+                 x0: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """SIRT through tomo_sirt_noalloc: no GPU memory is allocated by the library
+    (its scratch is a fixed 16 MiB array inside libtomo).  `out` (or a new
+    tensor when None, allocated here by torch) receives the result."""
+    _check_tensor(sino, "sino")
+    nz = _nz(sino, M.rows, "sino")
+    if out is None:
+        out = torch.zeros((nz, M.n_y, M.n_x), device=sino.device)
+    if x0 is None:
+        out.zero_()
+    else:
+        out.copy_(x0)
+    _check_tensor(out, "out", (nz, M.n_y, M.n_x))
+    _lib.call("tomo_sirt_noalloc", M.handle, _ptr(sino), _ptr(out), nz, iters, ctypes.c_float(lam), _stream())
+    return out
+
+
 def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, history: bool = False,
          batch_width: int = 0, precision: int = 0, use_graph: bool = True, out: Optional[torch.Tensor] = None,
          workspace: Optional[torch.Tensor] = None, timing=None):
