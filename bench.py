@@ -44,9 +44,12 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="sirt_512x360_b64")
     p.add_argument("--batch-width", type=int, default=0, help="0 = library default")
-    p.add_argument("--precision", type=int, default=0, help="1 = 16-bit matrix encoding")
+    p.add_argument("--format", default="sell", choices=["sell", "sell16", "csr"],
+                   help="matrix storage streamed by the kernels")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / plain-CSR legs")
+    p.add_argument("--iters", type=int, default=0, help="override the solver iterations (profiling runs)")
+    p.add_argument("--no-graph", action="store_true", help="launch kernels directly (profiling runs)")
     return p.parse_args()
 
 
@@ -157,10 +160,13 @@ def oracle_sample(w, slices=1, iters=1, steps=1, warmup=0):
             "seconds": dt}
 
 
-def workload_config(w, B, precision):
+KERNEL = {"sell": "sell", "sell16": "sell16", "csr": "f32"}
+
+
+def workload_config(w, B, fmt):
     return {"workload": w.name, "n": w.n, "n_theta": w.n_theta, "n_p": w.n, "slices": w.n_z,
-            "solver": w.solver, "iters": w.iters, "batch_width": B,
-            "values": "f32" if precision == 0 else w.values,
+            "solver": w.solver, "iters": w.iters, "batch_width": B, "format": fmt,
+            "values": (w.values if w.values != "f32" else "bf16") if fmt == "sell16" else "f32",
             "l2": "working set larger than L2: A and A^T are streamed from HBM every iteration"}
 
 
@@ -172,7 +178,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * res["seconds"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": DATA, "config": workload_config(w, 0, 0),
+            "data": DATA, "config": workload_config(w, 0, "sell"),
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -192,6 +198,9 @@ def main():
     args = parse()
     from paper_2003_12677_b300 import inputs
     w = inputs.WORKLOADS[args.workload]
+    if args.iters:
+        import dataclasses
+        w = dataclasses.replace(w, iters=args.iters)
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -209,21 +218,23 @@ def main():
             dist.barrier()
 
     B = args.batch_width or 16
-    prec = args.precision
-    values = w.values if prec == 1 else "f32"
+    fmt = args.format
+    values = (w.values if w.values != "f32" else "bf16") if fmt == "sell16" else "f32"
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     M = tomo.Matrix(w.n, w.n_theta, values=values)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
 
-    case = inputs.workload_case(w.name)
+    case = inputs.workload_case(args.workload)
     sino = torch.from_numpy(case.sino).cuda()
     x = torch.zeros((w.n_z, w.n, w.n), device="cuda")
-    wsb = torch.empty(M.workspace_size(2, w.n_z, B, prec), dtype=torch.uint8, device="cuda")
+    wsb = torch.empty(M.workspace_size(2, w.n_z, B, fmt), dtype=torch.uint8, device="cuda")
+
+    graph = not args.no_graph
 
     def step():
-        tomo.sirt(M, sino, w.iters, batch_width=B, precision=prec, out=x, workspace=wsb)
+        tomo.sirt(M, sino, w.iters, batch_width=B, fmt=fmt, out=x, workspace=wsb, use_graph=graph)
 
     for _ in range(args.warmup):
         step()
@@ -252,26 +263,26 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == 0 else "f32-accumulate/%s-values" % values,
-            "data": DATA, "config": workload_config(w, B, prec), "clocks": clk,
+            "vs_baseline": None, "dtype": "f32" if fmt != "sell16" else "f32-accumulate/%s-values" % values,
+            "data": DATA, "config": workload_config(w, B, fmt), "clocks": clk,
             "build_s": build_s, "nnz": M.nnz}
 
     # per-kernel device time of one extra solve (CUDA events around every launch)
     tm = tomo.new_timing()
-    tomo.sirt(M, sino, w.iters, batch_width=B, precision=prec, out=x, workspace=wsb, timing=tm)
+    tomo.sirt(M, sino, w.iters, batch_width=B, fmt=fmt, out=x, workspace=wsb, timing=tm)
     launches = int(sum(tm.launches[k] for k in range(3)))
     line["gpu_launches"] = launches * args.steps
     kind = 0 if tm.ms[0] >= tm.ms[1] else 1
     avg_ms = tm.ms[kind] / max(tm.launches[kind], 1)
     rows, cols, nnz = M.rows, M.cols, M.nnz
-    bnnz = 8 if prec == 0 else 4.25
+    bnnz = 4.25 if fmt == "sell16" else 8
     mat_bytes = (rows + 1 if kind == 0 else cols + 1) * 8 + nnz * bnnz
     if kind == 0:   # r = R o (b - A x): matrix, x gathered once, b, R, r
         vec_bytes = cols * B * 4 + 2 * rows * B * 4 + rows * 4
-        kname = "k_spmm_%s<%d, EpiSirtResidual> (A pass)" % ("f32" if prec == 0 else "lp", B)
+        kname = "k_spmm_%s<%d, EpiSirtResidual> (A pass)" % (KERNEL[fmt], B)
     else:           # x += lambda C o A^T r: matrix, r gathered once, x read+write, C
         vec_bytes = rows * B * 4 + 2 * cols * B * 4 + cols * 4
-        kname = "k_spmm_%s<%d, EpiSirtUpdate> (A^T pass)" % ("f32" if prec == 0 else "lp", B)
+        kname = "k_spmm_%s<%d, EpiSirtUpdate> (A^T pass)" % (KERNEL[fmt], B)
     alg = mat_bytes + vec_bytes
     peak, src = measured_peaks()
     achieved = alg / (avg_ms / 1000.0) / 1e9
@@ -280,7 +291,7 @@ def main():
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
-        key = "%s/B%d/p%d/k%d" % (w.name, B, prec, kind)
+        key = "%s/B%d/%s/k%d" % (w.name, B, fmt, kind)
         if tj.get("kernel_hash") == kernel_hash() and key in tj.get("per_launch_bytes", {}):
             traffic = tj["per_launch_bytes"][key]
     line["roofline"] = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -299,7 +310,7 @@ def main():
 
         def e2e_step():
             sd.copy_(sino_h, non_blocking=True)
-            tomo.sirt(M, sd, w.iters, batch_width=B, precision=prec, out=x, workspace=wsb)
+            tomo.sirt(M, sd, w.iters, batch_width=B, fmt=fmt, out=x, workspace=wsb)
             x_h.copy_(x, non_blocking=True)
 
         e2e_step()
@@ -317,12 +328,12 @@ def main():
         # the plain FP32 CSR SpMV form (one slice per pass) on the same GPU
         nzp, itp = 4, 10
         xp = torch.zeros((nzp, w.n, w.n), device="cuda")
-        wsp = torch.empty(M.workspace_size(2, nzp, 1, 0), dtype=torch.uint8, device="cuda")
+        wsp = torch.empty(M.workspace_size(2, nzp, 1, "csr"), dtype=torch.uint8, device="cuda")
         sp = sino[:nzp].contiguous()
-        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp)
+        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp, fmt="csr")
         torch.cuda.synchronize()
         e0.record()
-        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp)
+        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp, fmt="csr")
         e1.record()
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)

@@ -74,10 +74,11 @@ typedef struct {
   double center;
 } tomo_geometry;
 
-/* Build options.  values: TOMO_F32 builds only the FP32 CSR pair.  TOMO_BF16 /
- * TOMO_F16 also build the 16-bit encoding (16-bit values scaled per angle so a
- * full chord is exactly 1.0, uint16 column offsets against a 32-bit base per
- * 16-entry chunk) that compute calls use when exec opts select it. */
+/* Build options.  values: TOMO_F32 builds the FP32 operands (canonical CSR and
+ * the SELL-32 form the kernels stream).  TOMO_BF16 / TOMO_F16 also build the
+ * 16-bit encoding (16-bit values scaled per angle so a full chord is exactly
+ * 1.0, uint16 column offsets against a 32-bit base per 16 entries of a row)
+ * that compute calls use when exec opts select TOMO_FMT_SELL16. */
 typedef struct {
   int32_t values;   /* tomo_dtype */
   int32_t reserved[7];
@@ -92,11 +93,18 @@ typedef struct {
   int64_t launches[4];  /* kernels launched per kind */
 } tomo_timing;
 
+/* Matrix storage a compute call streams. */
+typedef enum {
+  TOMO_FMT_SELL = 0,   /* FP32 values, SELL-32 chunks, 128-bit entry loads (default) */
+  TOMO_FMT_SELL16 = 1, /* 16-bit values + 16-bit column offsets (needs a 16-bit build) */
+  TOMO_FMT_CSR = 2     /* FP32 CSR as exported: CSR-vector SpMV for widths 1-2, the plain comparator */
+} tomo_format;
+
 /* Per-call execution options (pointer may be NULL = defaults). */
 typedef struct {
   int32_t batch_width; /* slices per SpMM pass: 0 = library default, else one of 1,2,4,8,16,32,64 */
   int32_t use_graph;   /* SIRT/CGLS: replay one captured iteration as a CUDA graph (default 1) */
-  int32_t precision;   /* 0 = FP32 CSR, 1 = the 16-bit encoding built with the matrix */
+  int32_t format;      /* tomo_format of the matrix operands (default TOMO_FMT_SELL) */
   int32_t reserved0;
   tomo_timing *timing; /* non-NULL: bracket every launch with CUDA events on the call's stream,
                           launch without graphs, synchronise the stream before returning and
@@ -160,7 +168,7 @@ TOMO_API tomo_status tomo_workspace_size(const tomo_matrix *A, int32_t op, int32
  * SpMM with the slices as right-hand sides; Sec. 3).  x: n_z tomograms, y: n_z
  * sinograms, both in `layout`.  TOMO_INTERLEAVED requires n_z to be one of
  * 1,2,4,8,16,32,64.  Errors: INVALID_ARG (NULL / unaligned pointers, n_z < 1),
- * UNSUPPORTED (interleaved n_z not a supported width, or precision = 1 on a
+ * UNSUPPORTED (interleaved n_z not a supported width, or TOMO_FMT_SELL16 on a
  * matrix built without the 16-bit encoding). */
 TOMO_API tomo_status tomo_project(const tomo_matrix *A, const float *x, float *y, int32_t n_z, int32_t layout,
                                   const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes,

@@ -41,7 +41,7 @@ class Timing(ctypes.Structure):
 
 class ExecOpts(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("format", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("timing", ctypes.POINTER(Timing)), ("reserved", ctypes.c_int32 * 4)]
 
 

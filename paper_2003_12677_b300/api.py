@@ -35,11 +35,22 @@ def _check_tensor(t: torch.Tensor, name: str, shape=None):
         raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
 
 
-def _exec(batch_width: int = 0, use_graph: bool = True, precision: int = 0, timing=None) -> _lib.ExecOpts:
+FORMATS = {"sell": 0, "sell16": 1, "csr": 2}
+
+
+def _fmt(fmt) -> int:
+    if isinstance(fmt, int):
+        return fmt
+    if fmt not in FORMATS:
+        raise ValueError("fmt must be one of %s" % sorted(FORMATS))
+    return FORMATS[fmt]
+
+
+def _exec(batch_width: int = 0, use_graph: bool = True, fmt="sell", timing=None) -> _lib.ExecOpts:
     o = _lib.ExecOpts()
     o.batch_width = batch_width
     o.use_graph = 1 if use_graph else 0
-    o.precision = precision
+    o.format = _fmt(fmt)
     if timing is not None:
         o.timing = ctypes.pointer(timing)
     return o
@@ -55,7 +66,7 @@ class Matrix:
 
     n_x = n_y = n unless given; n_p defaults to n; angles (radians) default to
     m*pi/n_theta; center defaults to n_p/2.  values in {"f32", "bf16", "f16"}
-    also builds the 16-bit encoding used with precision=1.
+    also builds the 16-bit encoding used with fmt="sell16".
     """
 
     def __init__(self, n: int, n_theta: int, n_p: Optional[int] = None, n_y: Optional[int] = None,
@@ -134,14 +145,14 @@ class Matrix:
         _lib.call("tomo_matrix_export_norms", self.handle, R.ctypes.data, C.ctypes.data)
         return R, C
 
-    def workspace_size(self, op: int, n_z: int, batch_width: int = 0, precision: int = 0) -> int:
+    def workspace_size(self, op: int, n_z: int, batch_width: int = 0, fmt="sell") -> int:
         b = ctypes.c_size_t()
-        o = _exec(batch_width, True, precision)
+        o = _exec(batch_width, True, fmt)
         _lib.call("tomo_workspace_size", self.handle, op, n_z, ctypes.byref(o), ctypes.byref(b))
         return b.value
 
-    def _workspace(self, op, n_z, batch_width, precision) -> Optional[torch.Tensor]:
-        nb = self.workspace_size(op, n_z, batch_width, precision)
+    def _workspace(self, op, n_z, batch_width, fmt) -> Optional[torch.Tensor]:
+        nb = self.workspace_size(op, n_z, batch_width, fmt)
         if nb == 0:
             return None
         return torch.empty(nb, dtype=torch.uint8, device="cuda")
@@ -154,7 +165,7 @@ def _nz(t: torch.Tensor, per: int, name: str) -> int:
 
 
 def project(M: Matrix, x: torch.Tensor, out: Optional[torch.Tensor] = None, batch_width: int = 0,
-            precision: int = 0, interleaved: bool = False, timing=None) -> torch.Tensor:
+            fmt="sell", interleaved: bool = False, timing=None) -> torch.Tensor:
     """y = A x for a stack of tomograms x (n_z, n_y, n_x) -> sinograms (n_z, n_theta, n_p).
 
     interleaved=True takes x as (cols, n_z) and returns (rows, n_z)."""
@@ -164,15 +175,15 @@ def project(M: Matrix, x: torch.Tensor, out: Optional[torch.Tensor] = None, batc
         out = torch.empty((M.rows, nz) if interleaved else (nz, M.n_theta, M.n_p), device=x.device,
                           dtype=torch.float32)
     _check_tensor(out, "out")
-    ws = None if interleaved else M._workspace(_lib.OP_PROJECT, nz, batch_width, precision)
-    o = _exec(batch_width, True, precision, timing)
+    ws = None if interleaved else M._workspace(_lib.OP_PROJECT, nz, batch_width, fmt)
+    o = _exec(batch_width, True, fmt, timing)
     _lib.call("tomo_project", M.handle, _ptr(x), _ptr(out), nz, _lib.INTERLEAVED if interleaved else 0,
               ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
     return out
 
 
 def backproject(M: Matrix, y: torch.Tensor, out: Optional[torch.Tensor] = None, batch_width: int = 0,
-                precision: int = 0, interleaved: bool = False, timing=None) -> torch.Tensor:
+                fmt="sell", interleaved: bool = False, timing=None) -> torch.Tensor:
     """x = A^T y for a stack of sinograms y (n_z, n_theta, n_p) -> (n_z, n_y, n_x)."""
     _check_tensor(y, "y")
     nz = y.shape[-1] if interleaved else _nz(y, M.rows, "y")
@@ -180,15 +191,15 @@ def backproject(M: Matrix, y: torch.Tensor, out: Optional[torch.Tensor] = None, 
         out = torch.empty((M.cols, nz) if interleaved else (nz, M.n_y, M.n_x), device=y.device,
                           dtype=torch.float32)
     _check_tensor(out, "out")
-    ws = None if interleaved else M._workspace(_lib.OP_BACKPROJECT, nz, batch_width, precision)
-    o = _exec(batch_width, True, precision, timing)
+    ws = None if interleaved else M._workspace(_lib.OP_BACKPROJECT, nz, batch_width, fmt)
+    o = _exec(batch_width, True, fmt, timing)
     _lib.call("tomo_backproject", M.handle, _ptr(y), _ptr(out), nz, _lib.INTERLEAVED if interleaved else 0,
               ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
     return out
 
 
 def sirt(M: Matrix, sino: torch.Tensor, iters: int, lam: float = 1.0, x0: Optional[torch.Tensor] = None,
-         batch_width: int = 0, precision: int = 0, use_graph: bool = True,
+         batch_width: int = 0, fmt="sell", use_graph: bool = True,
          workspace: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None, timing=None) -> torch.Tensor:
     """SIRT from x0 (zeros by default): x <- x + lam * C o A^T (R o (b - A x))."""
     _check_tensor(sino, "sino")
@@ -202,8 +213,8 @@ def sirt(M: Matrix, sino: torch.Tensor, iters: int, lam: float = 1.0, x0: Option
     else:
         x = torch.zeros((nz, M.n_y, M.n_x), device=sino.device) if x0 is None else x0.clone()
     _check_tensor(x, "x0", (nz, M.n_y, M.n_x))
-    ws = workspace if workspace is not None else M._workspace(_lib.OP_SIRT, nz, batch_width, precision)
-    o = _exec(batch_width, use_graph, precision, timing)
+    ws = workspace if workspace is not None else M._workspace(_lib.OP_SIRT, nz, batch_width, fmt)
+    o = _exec(batch_width, use_graph, fmt, timing)
     _lib.call("tomo_sirt", M.handle, _ptr(sino), _ptr(x), nz, iters, ctypes.c_float(lam), ctypes.byref(o),
               _ptr(ws), 0 if ws is None else ws.numel(), _stream())
     return x
@@ -228,7 +239,7 @@ def sirt_noalloc(M: Matrix, sino: torch.Tensor, iters: int, lam: float = 1.0,
 
 
 def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, history: bool = False,
-         batch_width: int = 0, precision: int = 0, use_graph: bool = True, out: Optional[torch.Tensor] = None,
+         batch_width: int = 0, fmt="sell", use_graph: bool = True, out: Optional[torch.Tensor] = None,
          workspace: Optional[torch.Tensor] = None, timing=None):
     """CGLS from x0 = 0 per slice.  Returns x, or (x, ||r|| history (iters, n_z) float64)."""
     _check_tensor(sino, "sino")
@@ -236,8 +247,8 @@ def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, hi
     x = torch.empty((nz, M.n_y, M.n_x), device=sino.device) if out is None else out
     _check_tensor(x, "out", (nz, M.n_y, M.n_x))
     hist = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
-    ws = workspace if workspace is not None else M._workspace(_lib.OP_CGLS, nz, batch_width, precision)
-    o = _exec(batch_width, use_graph, precision, timing)
+    ws = workspace if workspace is not None else M._workspace(_lib.OP_CGLS, nz, batch_width, fmt)
+    o = _exec(batch_width, use_graph, fmt, timing)
     _lib.call("tomo_cgls", M.handle, _ptr(sino), _ptr(x), nz, iters, recompute_every, _ptr(hist),
               ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
     return (x, hist[:iters]) if history else x
@@ -247,19 +258,19 @@ class TomoProject(torch.autograd.Function):
     """y = A x with the stored transpose as the backward: dL/dx = A^T dL/dy."""
 
     @staticmethod
-    def forward(ctx, x: torch.Tensor, M: Matrix, batch_width: int = 0, precision: int = 0):
-        ctx.M, ctx.bw, ctx.prec = M, batch_width, precision
-        return project(M, x.contiguous(), batch_width=batch_width, precision=precision)
+    def forward(ctx, x: torch.Tensor, M: Matrix, batch_width: int = 0, fmt="sell"):
+        ctx.M, ctx.bw, ctx.fmt = M, batch_width, fmt
+        return project(M, x.contiguous(), batch_width=batch_width, fmt=fmt)
 
     @staticmethod
     def backward(ctx, g: torch.Tensor):
-        gx = backproject(ctx.M, g.contiguous(), batch_width=ctx.bw, precision=ctx.prec)
+        gx = backproject(ctx.M, g.contiguous(), batch_width=ctx.bw, fmt=ctx.fmt)
         return gx, None, None, None
 
 
-def radon(x: torch.Tensor, M: Matrix, batch_width: int = 0, precision: int = 0) -> torch.Tensor:
+def radon(x: torch.Tensor, M: Matrix, batch_width: int = 0, fmt="sell") -> torch.Tensor:
     """Differentiable forward projection."""
-    return TomoProject.apply(x, M, batch_width, precision)
+    return TomoProject.apply(x, M, batch_width, fmt)
 
 
 def tv_loss(x: torch.Tensor, eps: float = 1e-3) -> torch.Tensor:

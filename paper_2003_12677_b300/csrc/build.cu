@@ -314,55 +314,120 @@ __global__ void __launch_bounds__(kThreads) k_scan_apply(const int32_t *__restri
 }
 
 // ---------------------------------------------------------------------------
-// 16-bit encoding: one warp per row; lane q handles entries q, q+32, ...
+// SELL-32 forms (see internal.cuh for the slot maps)
 // ---------------------------------------------------------------------------
-__global__ void k_lp_chunks(const int64_t *__restrict__ rp, int64_t rows, int32_t *__restrict__ cnt) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < rows) cnt[i] = (int32_t)((rp[i + 1] - rp[i] + 15) / 16);
+// per chunk of 32 rows: slots = W*32 with W the longest row rounded up to
+// `align`, and (optionally) bases = (W/16)*32
+__global__ void k_chunk_sizes(const int64_t *__restrict__ rp, int64_t rows, int align,
+                              int32_t *__restrict__ slots, int32_t *__restrict__ bases) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t chunks = (rows + 31) / 32;
+  if (c >= chunks) return;
+  int64_t w = 0;
+  for (int q = 0; q < 32; ++q) {
+    int64_t r = c * 32 + q;
+    if (r < rows) w = max(w, rp[r + 1] - rp[r]);
+  }
+  w = (w + align - 1) / align * align;
+  slots[c] = (int32_t)(w * 32);
+  if (bases) bases[c] = (int32_t)(w / 16 * 32);
 }
 
-template <bool kTranspose, typename W>
-__global__ void __launch_bounds__(kThreads) k_lp_encode(const AngleC *__restrict__ ang, int nx, int ny,
-                                                        int np, double c, const int64_t *__restrict__ rp,
-                                                        const int32_t *__restrict__ ci, int64_t rows,
-                                                        const int64_t *__restrict__ cp,
-                                                        int32_t *__restrict__ base,
-                                                        uint32_t *__restrict__ ow, int *__restrict__ err) {
+__global__ void k_row_len(const int64_t *__restrict__ rp, int64_t rows, int32_t *__restrict__ rl) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < rows) rl[r] = (int32_t)(rp[r + 1] - rp[r]);
+}
+
+// one warp per row; entries (column, value bits) in pairs
+__global__ void __launch_bounds__(kThreads) k_sell_fill(const int64_t *__restrict__ rp,
+                                                        const int32_t *__restrict__ ci,
+                                                        const float *__restrict__ v, int64_t rows,
+                                                        const int64_t *__restrict__ cp, int2 *__restrict__ ent) {
   int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (r >= rows) return;
   int64_t b = rp[r], len = rp[r + 1] - b;
-  int64_t c0 = cp[r], nch = cp[r + 1] - c0;
-  for (int64_t e = lane; e < nch * 16; e += 32) {
-    int64_t ch = e >> 4;
-    int32_t cb = ci[b + ch * 16];
-    if ((e & 15) == 0) base[c0 + ch] = cb;
-    uint16_t o = 0, wbits = 0;
-    if (e < len) {
-      int32_t col = ci[b + e];
-      int64_t d = (int64_t)col - cb;
-      if (d < 0 || d > 65535) {
-        atomicExch(err, 2);
-      } else {
-        o = (uint16_t)d;
-      }
-      int ray = kTranspose ? col : (int)r;
-      int pix = kTranspose ? (int)r : col;
-      int m = ray / np, k = ray % np;
-      int ix = pix % nx, iy = pix / nx;
-      AngleC A = ang[m];
-      double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
-      double w = __dmul_rn(chord_len(A, pk, coord(ix, nx), coord(iy, ny)), A.a);
-      if constexpr (std::is_same<W, __nv_bfloat16>::value) {
-        __nv_bfloat16 hv = __double2bfloat16(w);
-        wbits = __bfloat16_as_ushort(hv);
-      } else {
-        __half hv = __double2half(w);
-        wbits = __half_as_ushort(hv);
-      }
-    }
-    ow[c0 * 16 + e] = (uint32_t)o | ((uint32_t)wbits << 16);
+  int64_t base = cp[r >> 5];
+  int q = (int)(r & 31);
+  for (int64_t e = lane; e < len; e += 32)
+    ent[base + (e >> 1) * 64 + 2 * q + (e & 1)] = make_int2(ci[b + e], __float_as_int(v[b + e]));
+}
+
+// 16-bit form, pass 1 (one thread per row): the row's padded length.  Entries
+// are cut into segments of 16 with one 32-bit base each; a segment is closed
+// early (padded with zero-weight entries) when the next column lies more than
+// 65535 past its base, which happens where a pixel is seen by two separate
+// ranges of angles (image corners).
+__global__ void k_sell16_len(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t rows,
+                             int32_t *__restrict__ rl16) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  int64_t b = rp[r], len = rp[r + 1] - b;
+  int64_t slot = 0;
+  int32_t cb = 0;
+  for (int64_t e = 0; e < len; ++e) {
+    int32_t col = ci[b + e];
+    if ((slot & 15) != 0 && (int64_t)col - cb > 65535) slot = (slot + 15) / 16 * 16;
+    if ((slot & 15) == 0) cb = col;
+    ++slot;
   }
+  rl16[r] = (int32_t)((slot + 15) / 16 * 16);
+}
+
+// 16-bit form, pass 2 (one thread per row): same walk, writing the packed
+// (offset | weight << 16) words and the segment bases; weights A_ij * a(theta)
+// recomputed in FP64 from the geometry.  Padding slots stay zero.
+template <bool kTranspose, typename W>
+__global__ void k_sell16_fill(const AngleC *__restrict__ ang, int nx, int ny, int np, double c,
+                              const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t rows,
+                              const int64_t *__restrict__ cpw, const int64_t *__restrict__ cpb,
+                              uint32_t *__restrict__ ow, int32_t *__restrict__ base, int *__restrict__ err) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  int64_t b = rp[r], len = rp[r + 1] - b;
+  int64_t w0 = cpw[r >> 5], b0 = cpb[r >> 5];
+  int q = (int)(r & 31);
+  int64_t slot = 0;
+  int32_t cb = 0;
+  for (int64_t e = 0; e < len; ++e) {
+    int32_t col = ci[b + e];
+    if ((slot & 15) != 0 && (int64_t)col - cb > 65535) slot = (slot + 15) / 16 * 16;
+    if ((slot & 15) == 0) {
+      cb = col;
+      base[b0 + (slot >> 4) * 32 + q] = cb;
+    }
+    int64_t d = (int64_t)col - cb;
+    if (d < 0 || d > 65535) atomicExch(err, 2);  // impossible after the early cut; reported
+    int ray = kTranspose ? col : (int)r;
+    int pix = kTranspose ? (int)r : col;
+    int m = ray / np, k = ray % np;
+    int ix = pix % nx, iy = pix / nx;
+    AngleC A = ang[m];
+    double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
+    double w = __dmul_rn(chord_len(A, pk, coord(ix, nx), coord(iy, ny)), A.a);
+    uint16_t wbits;
+    if constexpr (std::is_same<W, __nv_bfloat16>::value)
+      wbits = __bfloat16_as_ushort(__double2bfloat16(w));
+    else
+      wbits = __half_as_ushort(__double2half(w));
+    ow[w0 + (slot >> 2) * 128 + 4 * q + (slot & 3)] = (uint32_t)(uint16_t)d | ((uint32_t)wbits << 16);
+    ++slot;
+  }
+}
+
+// per chunk of 32 rows with explicit (already 16-aligned) row lengths
+__global__ void k_chunk_sizes_rl(const int32_t *__restrict__ rl, int64_t rows, int32_t *__restrict__ slots,
+                                 int32_t *__restrict__ bases) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t chunks = (rows + 31) / 32;
+  if (c >= chunks) return;
+  int32_t w = 0;
+  for (int q = 0; q < 32; ++q) {
+    int64_t r = c * 32 + q;
+    if (r < rows) w = max(w, rl[r]);
+  }
+  slots[c] = w * 32;
+  bases[c] = w / 16 * 32;
 }
 
 int grid_for_warps(int64_t warps) { return (int)((warps * 32 + kThreads - 1) / kThreads); }
@@ -397,35 +462,63 @@ tomo_status dmalloc(T **p, size_t count) {
   return TOMO_OK;
 }
 
-template <typename W>
-void launch_encode(tomo_matrix *h, bool transpose, const Csr &M, Lp &L, int *scratch, cudaStream_t st) {
-  int g = grid_for_warps(M.rows);
-  if (transpose)
-    k_lp_encode<true, W><<<g, kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, h->center, M.rp, M.ci, M.rows,
-                                                 L.cp, L.base, L.ow, scratch);
-  else
-    k_lp_encode<false, W><<<g, kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, h->center, M.rp, M.ci, M.rows,
-                                                  L.cp, L.base, L.ow, scratch);
+tomo_status build_sell(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t *cnt, int64_t *part,
+                       int *scratch) {
+  const Csr &M = transpose ? h->AT : h->A;
+  Sell &S = transpose ? h->sAT : h->sA;
+  S.rows = M.rows;
+  S.chunks = (M.rows + 31) / 32;
+  TOMO_TRY(dmalloc(&S.cp, S.chunks + 1));
+  TOMO_TRY(dmalloc(&S.rl, M.rows));
+  k_row_len<<<(unsigned)((M.rows + 255) / 256), 256, 0, st>>>(M.rp, M.rows, S.rl);
+  k_chunk_sizes<<<(unsigned)((S.chunks + 255) / 256), 256, 0, st>>>(M.rp, M.rows, 2, cnt, nullptr);
+  TOMO_TRY(scan_counts(cnt, S.chunks, S.cp, part, scratch + 3, st));
+  TOMO_CUDA(cudaMemcpyAsync(&S.slots, S.cp + S.chunks, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  TOMO_TRY(dmalloc(&S.ent, S.slots));
+  TOMO_CUDA(cudaMemsetAsync(S.ent, 0, sizeof(int2) * S.slots, st));
+  k_sell_fill<<<grid_for_warps(M.rows), kThreads, 0, st>>>(M.rp, M.ci, M.v, M.rows, S.cp, S.ent);
+  TOMO_CUDA(cudaGetLastError());
+  h->bytes_f32 += (S.chunks + 1) * 8 + M.rows * 4 + S.slots * 8;
+  return TOMO_OK;
 }
 
-tomo_status build_lp(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t *cnt, int64_t *part,
-                     int *scratch) {
+tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t *cnt, int64_t *part,
+                         int *scratch) {
   const Csr &M = transpose ? h->AT : h->A;
-  Lp &L = transpose ? h->lpAT : h->lpA;
+  SellLp &L = transpose ? h->lpAT : h->lpA;
   L.rows = M.rows;
-  TOMO_TRY(dmalloc(&L.cp, M.rows + 1));
-  k_lp_chunks<<<(unsigned)((M.rows + 255) / 256), 256, 0, st>>>(M.rp, M.rows, cnt);
-  TOMO_TRY(scan_counts(cnt, M.rows, L.cp, part, scratch + 3, st));
-  TOMO_CUDA(cudaMemcpyAsync(&L.chunks, L.cp + M.rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  L.chunks = (M.rows + 31) / 32;
+  TOMO_TRY(dmalloc(&L.rl, M.rows));
+  TOMO_TRY(dmalloc(&L.cpw, L.chunks + 1));
+  TOMO_TRY(dmalloc(&L.cpb, L.chunks + 1));
+  const unsigned gr = (unsigned)((M.rows + 255) / 256), gc = (unsigned)((L.chunks + 255) / 256);
+  k_sell16_len<<<gr, 256, 0, st>>>(M.rp, M.ci, M.rows, L.rl);
+  int32_t *cntb = cnt + L.chunks;  // cnt holds enough entries for two per-chunk arrays
+  k_chunk_sizes_rl<<<gc, 256, 0, st>>>(L.rl, M.rows, cnt, cntb);
+  TOMO_TRY(scan_counts(cnt, L.chunks, L.cpw, part, scratch + 3, st));
+  TOMO_TRY(scan_counts(cntb, L.chunks, L.cpb, part, scratch + 3, st));
+  TOMO_CUDA(cudaMemcpyAsync(&L.slots, L.cpw + L.chunks, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaMemcpyAsync(&L.bases, L.cpb + L.chunks, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));
-  TOMO_TRY(dmalloc(&L.base, L.chunks));
-  TOMO_TRY(dmalloc(&L.ow, L.chunks * 16));
-  if (h->lp_dtype == TOMO_BF16)
-    launch_encode<__nv_bfloat16>(h, transpose, M, L, scratch, st);
-  else
-    launch_encode<__half>(h, transpose, M, L, scratch, st);
+  TOMO_TRY(dmalloc(&L.ow, L.slots));
+  TOMO_TRY(dmalloc(&L.base, L.bases));
+  TOMO_CUDA(cudaMemsetAsync(L.ow, 0, sizeof(uint32_t) * L.slots, st));
+  TOMO_CUDA(cudaMemsetAsync(L.base, 0, sizeof(int32_t) * L.bases, st));
+  const double c = h->center;
+#define TOMO_FILL16(TR, W)                                                                                      \
+  k_sell16_fill<TR, W><<<gr, 256, 0, st>>>(h->ang, h->nx, h->ny, h->np, c, M.rp, M.ci, M.rows, L.cpw, L.cpb, L.ow, \
+                                           L.base, scratch)
+  if (h->lp_dtype == TOMO_BF16) {
+    if (transpose) TOMO_FILL16(true, __nv_bfloat16);
+    else TOMO_FILL16(false, __nv_bfloat16);
+  } else {
+    if (transpose) TOMO_FILL16(true, __half);
+    else TOMO_FILL16(false, __half);
+  }
+#undef TOMO_FILL16
   TOMO_CUDA(cudaGetLastError());
-  h->bytes_lp += (M.rows + 1) * 8 + L.chunks * (4 + 16 * 4);
+  h->bytes_lp += (L.chunks + 1) * 16 + M.rows * 4 + L.slots * 4 + L.bases * 4;
   return TOMO_OK;
 }
 
@@ -433,9 +526,11 @@ tomo_status build_lp(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t *c
 
 void free_matrix(tomo_matrix *h) {
   if (!h) return;
-  void *ptrs[] = {h->ang,    h->ang_scale, h->A.rp,   h->A.ci,    h->A.v,       h->AT.rp,
-                  h->AT.ci,  h->AT.v,      h->R,      h->C,       h->lpA.cp,    h->lpA.base,
-                  h->lpA.ow, h->lpAT.cp,   h->lpAT.base, h->lpAT.ow};
+  void *ptrs[] = {h->ang,      h->ang_scale, h->A.rp,     h->A.ci,     h->A.v,       h->AT.rp,
+                  h->AT.ci,    h->AT.v,      h->R,        h->C,        h->sA.cp,     h->sA.rl,
+                  h->sA.ent,   h->sAT.cp,    h->sAT.rl,   h->sAT.ent,  h->lpA.cpw,   h->lpA.cpb,
+                  h->lpA.ow,   h->lpA.base,  h->lpAT.cpw, h->lpAT.cpb, h->lpAT.ow,   h->lpAT.base,
+                  h->lpA.rl,   h->lpAT.rl};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -505,7 +600,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   int32_t *cnt = nullptr;
   int64_t *part = nullptr;
   int *scratch = nullptr;  // [0] error flag, [1] max row length, [2] max column length, [3] unused max
-  TOMO_TRY(dmalloc(&cnt, nmax));
+  TOMO_TRY(dmalloc(&cnt, nmax + nmax / 16 + 64));  // also holds two per-chunk arrays
   DevBuf cnt_guard{cnt};
   TOMO_TRY(dmalloc(&part, nmax / kScanTile + 2));
   DevBuf part_guard{part};
@@ -542,7 +637,8 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
 
   size_t freeb = 0, totalb = 0;
   TOMO_CUDA(cudaMemGetInfo(&freeb, &totalb));
-  size_t need = (size_t)nnz_a * 16 + (size_t)(lp != TOMO_F32 ? nnz_a * 9 + (rows + cols) * 48 : 0);
+  // CSR pair (16 B/nnz) + SELL pair (~17 B/nnz) [+ 16-bit pair (~9.5 B/nnz)]
+  size_t need = (size_t)nnz_a * 34 + (size_t)(lp != TOMO_F32 ? nnz_a * 10 + (rows + cols) * 64 : 0);
   if (need + (size_t)(1ull << 30) > freeb)
     return fail(TOMO_ERR_OOM, "matrix needs " + std::to_string(need) + " bytes, device has " +
                                   std::to_string(freeb) + " free");
@@ -558,9 +654,11 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   TOMO_CUDA(cudaGetLastError());
   h->bytes_f32 = (rows + 1 + cols + 1) * 8 + nnz_a * 16;
 
+  TOMO_TRY(build_sell(h, false, st, cnt, part, scratch));
+  TOMO_TRY(build_sell(h, true, st, cnt, part, scratch));
   if (lp != TOMO_F32) {
-    TOMO_TRY(build_lp(h, false, st, cnt, part, scratch));
-    TOMO_TRY(build_lp(h, true, st, cnt, part, scratch));
+    TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch));
+    TOMO_TRY(build_sell16(h, true, st, cnt, part, scratch));
   }
   TOMO_CUDA(cudaMemcpyAsync(hs, scratch, sizeof(hs), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));

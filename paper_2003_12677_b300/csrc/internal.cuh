@@ -28,18 +28,42 @@ struct Csr {
   float *v = nullptr;     // [nnz]
 };
 
-// 16-bit encoding of one CSR operand.  Each row is cut into chunks of 16
-// entries (the last one padded with zero weights); chunk c holds a 32-bit
-// column base (the first column of the chunk) and, per entry, one uint32 that
-// packs the uint16 column offset against that base (low half) with the 16-bit
-// float weight (high half).  Weights are A_ij * a(theta) so that a full chord
-// is exactly 1.0; the FP32 factor 1/a(theta) of the angle is applied by the
-// kernels (per output row for A, per gathered input for A^T).
-struct Lp {
-  int64_t rows = 0, chunks = 0;
-  int64_t *cp = nullptr;       // [rows+1] chunk pointers
-  int32_t *base = nullptr;     // [chunks]
-  uint32_t *ow = nullptr;      // [chunks*16] offset | weight << 16
+// SELL-32 form of one operand (FP32).  Rows are grouped in chunks of 32
+// consecutive rows; chunk c is stored column-major with width W_c (the
+// longest row of the chunk, rounded up to even), entries packed as int2
+// (column, value bits) and kept in pairs so that one 128-bit load brings two
+// consecutive entries of one row:
+//   slot(c, q, e) = cp[c] + (e/2)*64 + 2*q + (e%2),   q = row % 32.
+// The G rows a warp handles are adjacent in every column, so their entry
+// loads are contiguous.  rl holds each row's true length; the kernels never
+// read past it.
+struct Sell {
+  int64_t rows = 0, chunks = 0, slots = 0;
+  int64_t *cp = nullptr;   // [chunks+1] slot offset of each chunk
+  int32_t *rl = nullptr;   // [rows]
+  int2 *ent = nullptr;     // [slots]
+};
+
+// 16-bit SELL-32 form.  Per entry one uint32 packs the uint16 column offset
+// (low half) with the 16-bit float weight (high half); the offset is taken
+// against a 32-bit base per row segment of 16 slots (the segment's first
+// column).  A segment is closed early, padded with zero-weight slots, when the
+// next column lies more than 65535 past its base; rl holds each row's padded
+// slot count (a multiple of 16).  Quads of consecutive slots of a row are
+// adjacent:
+//   slot(c, q, e) = cpw[c] + (e/4)*128 + 4*q + (e%4),   width W_c % 16 == 0
+//   base(c, q, s) = cpb[c] + s*32 + q,                    s = e/16.
+// Weights are A_ij * a(theta) so that a full chord is exactly 1.0; the FP32
+// factor 1/a(theta) of the angle is applied by the kernels (per output row
+// for A, per gathered entry for A^T).  Padding slots carry weight 0 and
+// offset 0 (column = the segment base).
+struct SellLp {
+  int64_t rows = 0, chunks = 0, slots = 0, bases = 0;
+  int64_t *cpw = nullptr;   // [chunks+1]
+  int64_t *cpb = nullptr;   // [chunks+1]
+  int32_t *rl = nullptr;    // [rows] padded slot count per row
+  uint32_t *ow = nullptr;   // [slots]
+  int32_t *base = nullptr;  // [bases]
 };
 
 }  // namespace tomo
@@ -53,7 +77,8 @@ struct tomo_matrix {
   tomo::Csr A, AT;
   float *R = nullptr, *C = nullptr;
   int32_t lp_dtype = TOMO_F32;
-  tomo::Lp lpA, lpAT;
+  tomo::Sell sA, sAT;
+  tomo::SellLp lpA, lpAT;
   int64_t bytes_f32 = 0, bytes_lp = 0;
 };
 
@@ -94,9 +119,9 @@ void free_matrix(tomo_matrix *h);
 
 // ---- operators (ops.cu) ----
 struct Exec {
-  int B = 0;          // slices per SpMM pass
+  int B = 0;            // slices per SpMM pass
   bool graph = true;
-  bool lp = false;
+  int format = TOMO_FMT_SELL;
   tomo_timing *timing = nullptr;
 };
 tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t nz, Exec *ex);

@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kMinBlocks = 6;  // fallback resident blocks per SM when occupancy is unknown
 
 // ---------------------------------------------------------------------------
 // small vector helpers
@@ -277,10 +278,79 @@ __global__ void __launch_bounds__(kThreads) k_spmv_f32(const int64_t *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// 16-bit SpMM (values bf16 / f16 times a per-angle FP32 scale, uint16 column
-// offsets against a 32-bit base per 16-entry chunk).  Same lane mapping as
-// k_spmm_f32 (B >= 4).  kTrans selects A^T (scale per gathered column's angle)
-// versus A (scale per output row's angle).
+// SELL-32 SpMM (FP32 values).  V = min(B, 4) slices per lane, L = B/V lanes
+// per row, G = 32/L rows per warp; the G rows of a warp are adjacent rows of
+// one 32-row chunk, so each step loads one contiguous run of entry pairs
+// (128-bit per lane) for all of them.
+// ---------------------------------------------------------------------------
+template <int B, class Epi>
+__global__ void __launch_bounds__(kThreads) k_spmm_sell(const int64_t *__restrict__ cp,
+                                                        const int32_t *__restrict__ rl,
+                                                        const int2 *__restrict__ ent, int64_t rows,
+                                                        const float *__restrict__ X, Epi epi,
+                                                        double *__restrict__ part) {
+  constexpr int V = B >= 4 ? 4 : B;
+  constexpr int L = B / V, G = 32 / L;
+  const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float *Xl = X + l * V;
+  double ss[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) ss[t] = 0.0;
+  for (int64_t rg = warp; rg * G < rows; rg += nwarps) {
+    const int64_t row = rg * G + g;
+    if (row >= rows) continue;
+    Vec<V> acc;
+#pragma unroll
+    for (int t = 0; t < V; ++t) acc.v[t] = 0.f;
+    const int len = __ldg(rl + row);
+    // entry pair (e, e+1), e even, of this row sits at p[(e/2)*32]
+    const int4 *p = reinterpret_cast<const int4 *>(ent) + (__ldg(cp + (row >> 5)) >> 1) + (row & 31);
+    int e = 0;
+    for (; e + 8 <= len; e += 8) {
+      int4 pr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pr[u] = __ldg(p + (size_t)((e >> 1) + u) * 32);
+      Vec<V> xv[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xv[2 * u] = ldg_vec<V>(Xl + (size_t)pr[u].x * B);
+        xv[2 * u + 1] = ldg_vec<V>(Xl + (size_t)pr[u].z * B);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float w0 = __int_as_float(pr[u].y), w1 = __int_as_float(pr[u].w);
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w0, xv[2 * u].v[t], acc.v[t]);
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w1, xv[2 * u + 1].v[t], acc.v[t]);
+      }
+    }
+    for (; e < len; e += 2) {
+      const int4 pr = __ldg(p + (size_t)(e >> 1) * 32);
+      Vec<V> x0 = ldg_vec<V>(Xl + (size_t)pr.x * B);
+      const float w0 = __int_as_float(pr.y);
+#pragma unroll
+      for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w0, x0.v[t], acc.v[t]);
+      if (e + 1 < len) {
+        Vec<V> x1 = ldg_vec<V>(Xl + (size_t)pr.z * B);
+        const float w1 = __int_as_float(pr.w);
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w1, x1.v[t], acc.v[t]);
+      }
+    }
+    epi.template operator()<V>(row, l * V, acc, ss);
+  }
+  if constexpr (Epi::kNorm) block_norms<V>(ss, l * V, B, part);
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit SELL-32 SpMM: bf16 / f16 weights times a per-angle FP32 scale, uint16
+// column offsets against a 32-bit base per 16-entry row segment.  Same lane
+// mapping as k_spmm_sell; a lane loads four entries per 128-bit load.  kTrans
+// selects A^T (scale of each gathered column's angle) versus A (scale of the
+// output row's angle).
 // ---------------------------------------------------------------------------
 template <bool kBf16>
 __device__ __forceinline__ float w16(uint32_t ow) {
@@ -300,54 +370,65 @@ __device__ __forceinline__ int div_exact(int a, int d, float inv_d) {
 }
 
 template <int B, bool kBf16, bool kTrans, class Epi>
-__global__ void __launch_bounds__(kThreads) k_spmm_lp(const int64_t *__restrict__ cp,
-                                                      const int32_t *__restrict__ base,
-                                                      const uint32_t *__restrict__ ow, int64_t rows,
-                                                      const float *__restrict__ scale, int np, float inv_np,
-                                                      const float *__restrict__ X, Epi epi,
-                                                      double *__restrict__ part) {
-  constexpr int L = B / 4, G = 32 / L;
+__global__ void __launch_bounds__(kThreads) k_spmm_sell16(const int64_t *__restrict__ cpw,
+                                                          const int64_t *__restrict__ cpb,
+                                                          const int32_t *__restrict__ rl,
+                                                          const uint32_t *__restrict__ ow,
+                                                          const int32_t *__restrict__ base, int64_t rows,
+                                                          const float *__restrict__ scale, int np, float inv_np,
+                                                          const float *__restrict__ X, Epi epi,
+                                                          double *__restrict__ part) {
+  constexpr int V = B >= 4 ? 4 : B;
+  constexpr int L = B / V, G = 32 / L;
   const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const float *Xl = X + l * 4;
-  double ss[4] = {0, 0, 0, 0};
+  const float *Xl = X + l * V;
+  double ss[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) ss[t] = 0.0;
   for (int64_t rg = warp; rg * G < rows; rg += nwarps) {
     const int64_t row = rg * G + g;
     if (row >= rows) continue;
-    Vec<4> acc = {{0.f, 0.f, 0.f, 0.f}};
-    const int64_t c0 = __ldg(cp + row), c1 = __ldg(cp + row + 1);
-    for (int64_t ch = c0; ch < c1; ++ch) {
-      const int cb = __ldg(base + ch);
-      const uint4 *q = reinterpret_cast<const uint4 *>(ow + ch * 16);
+    Vec<V> acc;
+#pragma unroll
+    for (int t = 0; t < V; ++t) acc.v[t] = 0.f;
+    const int len = __ldg(rl + row);
+    const int64_t c = row >> 5;
+    const int q = (int)(row & 31);
+    const uint4 *pw = reinterpret_cast<const uint4 *>(ow + __ldg(cpw + c)) + q;  // quad e/4 at pw[(e/4)*32]
+    const int32_t *pb = base + __ldg(cpb + c) + q;                               // segment s at pb[s*32]
+    for (int s = 0; s * 16 < len; ++s) {
+      const int cb = __ldg(pb + (size_t)s * 32);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        uint4 p0 = __ldg(q + 2 * h), p1 = __ldg(q + 2 * h + 1);
-        uint32_t pk[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-        Vec<4> xv[8];
+        const uint4 a0 = __ldg(pw + (size_t)(4 * s + 2 * h) * 32);
+        const uint4 a1 = __ldg(pw + (size_t)(4 * s + 2 * h + 1) * 32);
+        const uint32_t pk[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         int cc[8];
+        Vec<V> xv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           cc[u] = cb + (int)(pk[u] & 0xffffu);
-          xv[u] = ldg_vec<4>(Xl + (size_t)cc[u] * B);
+          xv[u] = ldg_vec<V>(Xl + (size_t)cc[u] * B);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           float w = w16<kBf16>(pk[u]);
           if constexpr (kTrans) w *= __ldg(scale + div_exact(cc[u], np, inv_np));
 #pragma unroll
-          for (int t = 0; t < 4; ++t) acc.v[t] = fmaf(w, xv[u].v[t], acc.v[t]);
+          for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w, xv[u].v[t], acc.v[t]);
         }
       }
     }
     if constexpr (!kTrans) {
-      float s = __ldg(scale + div_exact((int)row, np, inv_np));
+      const float sc = __ldg(scale + div_exact((int)row, np, inv_np));
 #pragma unroll
-      for (int t = 0; t < 4; ++t) acc.v[t] *= s;
+      for (int t = 0; t < V; ++t) acc.v[t] *= sc;
     }
-    epi.template operator()<4>(row, l * 4, acc, ss);
+    epi.template operator()<V>(row, l * V, acc, ss);
   }
-  if constexpr (Epi::kNorm) block_norms<4>(ss, l * 4, B, part);
+  if constexpr (Epi::kNorm) block_norms<V>(ss, l * V, B, part);
 }
 
 // ---------------------------------------------------------------------------
@@ -516,55 +597,104 @@ __global__ void __launch_bounds__(kThreads) k_cgls_dir(float *__restrict__ p, co
 // ---------------------------------------------------------------------------
 // launch plumbing
 // ---------------------------------------------------------------------------
-struct Op {  // one SpMM operand (A or A^T) in the selected encoding
+struct Op {  // one SpMM operand (A or A^T) in the selected storage
   const Csr *m;
-  const Lp *lp;
+  const Sell *sell;
+  const SellLp *lp;
+  int format;
   bool trans;
   bool bf16;
   const float *scale;
   int np;
 };
 
-inline int spmm_grid(int64_t rows, int G) {
+// rows one warp handles in the SpMM kernels of a format / width
+inline int rows_per_warp(int format, int B) {
+  if (format == TOMO_FMT_CSR && B < 4) return 1;  // CSR-vector: a warp per row
+  const int V = B >= 4 ? 4 : B;
+  return 32 / (B / V);
+}
+
+// Grid of a grid-stride SpMM launch: never more blocks than can be resident
+// at once (a second partial wave would idle most SMs), never more than the
+// row groups need.  `resident` is blocks per SM from the occupancy API.
+inline int spmm_grid(int64_t rows, int G, int resident = kMinBlocks) {
   int64_t groups = (rows + G - 1) / G;
   int64_t blocks = (groups + kWarps - 1) / kWarps;
-  int64_t cap = (int64_t)num_sms() * 8;
+  int64_t cap = (int64_t)num_sms() * std::max(1, std::min(resident, 8));
   return (int)std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+template <typename K>
+int resident_blocks(K kernel) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, 0) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return n;
 }
 
 inline int max_spmm_grid() { return num_sms() * 8; }
 
 template <int B, class Epi>
 void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream_t st) {
-  if constexpr (B >= 4) {
-    constexpr int G = 32 / (B / 4);
-    int grid = spmm_grid(op.m->rows, G);
-    if (op.lp) {
-      float inv_np = 1.0f / (float)op.np;
-      const Lp &L = *op.lp;
-      if (op.bf16) {
-        if (op.trans)
-          k_spmm_lp<B, true, true, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
-                                                                   op.np, inv_np, X, epi, part);
-        else
-          k_spmm_lp<B, true, false, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
-                                                                    op.np, inv_np, X, epi, part);
-      } else {
-        if (op.trans)
-          k_spmm_lp<B, false, true, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
-                                                                    op.np, inv_np, X, epi, part);
-        else
-          k_spmm_lp<B, false, false, Epi><<<grid, kThreads, 0, st>>>(L.cp, L.base, L.ow, op.m->rows, op.scale,
-                                                                     op.np, inv_np, X, epi, part);
-      }
+  const int G = rows_per_warp(op.format, B);
+  const int64_t rows = op.m->rows;
+  if (op.format == TOMO_FMT_SELL) {
+    const Sell &S = *op.sell;
+    static const int res = resident_blocks(k_spmm_sell<B, Epi>);
+    k_spmm_sell<B, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(S.cp, S.rl, S.ent, rows, X, epi, part);
+  } else if (op.format == TOMO_FMT_SELL16) {
+    const SellLp &L = *op.lp;
+    const float inv_np = 1.0f / (float)op.np;
+#define TOMO_SELL16(BF, TR)                                                                                \
+  do {                                                                                                     \
+    static const int res = resident_blocks(k_spmm_sell16<B, BF, TR, Epi>);                                 \
+    k_spmm_sell16<B, BF, TR, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(                          \
+        L.cpw, L.cpb, L.rl, L.ow, L.base, rows, op.scale, op.np, inv_np, X, epi, part);                    \
+  } while (0)
+    if (op.bf16) {
+      if (op.trans) TOMO_SELL16(true, true);
+      else TOMO_SELL16(true, false);
     } else {
-      k_spmm_f32<B, Epi><<<grid, kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, op.m->rows, X, epi, part);
+      if (op.trans) TOMO_SELL16(false, true);
+      else TOMO_SELL16(false, false);
     }
+#undef TOMO_SELL16
   } else {
-    constexpr int P = 32;
-    int grid = spmm_grid(op.m->rows, 32 / P);
-    k_spmv_f32<B, P, Epi><<<grid, kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, op.m->rows, X, epi, part);
+    if constexpr (B >= 4) {
+      static const int res = resident_blocks(k_spmm_f32<B, Epi>);
+      k_spmm_f32<B, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X, epi,
+                                                                        part);
+    } else {
+      static const int res = resident_blocks(k_spmv_f32<B, 32, Epi>);
+      k_spmv_f32<B, 32, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X,
+                                                                            epi, part);
+    }
   }
+}
+
+// grid the SpMM of (op, B, Epi) will use; CGLS sizes its norm reductions with it
+template <int B, class Epi>
+int spmm_grid_of(const Op &op) {
+  const int G = rows_per_warp(op.format, B);
+  int res = kMinBlocks;
+  if (op.format == TOMO_FMT_SELL) {
+    res = resident_blocks(k_spmm_sell<B, Epi>);
+  } else if (op.format == TOMO_FMT_SELL16) {
+    if (op.bf16)
+      res = op.trans ? resident_blocks(k_spmm_sell16<B, true, true, Epi>)
+                     : resident_blocks(k_spmm_sell16<B, true, false, Epi>);
+    else
+      res = op.trans ? resident_blocks(k_spmm_sell16<B, false, true, Epi>)
+                     : resident_blocks(k_spmm_sell16<B, false, false, Epi>);
+  } else if constexpr (B >= 4) {
+    res = resident_blocks(k_spmm_f32<B, Epi>);
+  } else {
+    res = resident_blocks(k_spmv_f32<B, 32, Epi>);
+  }
+  return spmm_grid(op.m->rows, G, res);
 }
 
 inline int elem_grid(int64_t n_vec) {
@@ -667,7 +797,9 @@ struct Timer {
 Op make_op(const tomo_matrix *h, bool trans, const Exec &ex) {
   Op op;
   op.m = trans ? &h->AT : &h->A;
-  op.lp = ex.lp ? (trans ? &h->lpAT : &h->lpA) : nullptr;
+  op.sell = trans ? &h->sAT : &h->sA;
+  op.lp = trans ? &h->lpAT : &h->lpA;
+  op.format = ex.format;
   op.trans = trans;
   op.bf16 = h->lp_dtype == TOMO_BF16;
   op.scale = h->ang_scale;
@@ -779,9 +911,9 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
   float *bi = B > 1 ? cv.take<float>(rows * B) : nullptr;
   float *xi = B > 1 ? cv.take<float>(cols * B) : nullptr;
 
-  constexpr int G = B >= 4 ? 32 / (B / 4) : 1;
-  const int gA = spmm_grid(rows, G);
-  const int gT = spmm_grid(cols, G);
+  const int gA = spmm_grid_of<B, EpiStoreNorm>(A);     // q = A p
+  const int gR = spmm_grid_of<B, EpiResidualNorm>(A);  // r = b - A x
+  const int gT = spmm_grid_of<B, EpiStoreNorm>(AT);    // s = A^T r
   constexpr int PER = B >= 4 ? B / 4 : 1;
   const int ge = elem_grid((rows > cols ? rows : cols) * PER);
 
@@ -808,8 +940,8 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
     TIMED(tm, st, kOther, (k_cgls_init<<<B, kThreads, 0, st>>>(part_b, gT, B, scal, itc)));
     TOMO_CUDA(cudaGetLastError());
 
-    // the residual-norm partials come from the SpMM grid (gA blocks) on a
-    // recompute iteration and from the elementwise grid (ge blocks) otherwise
+    // the residual-norm partials come from the residual SpMM grid (gR blocks)
+    // on a recompute iteration and from the elementwise grid (ge blocks) otherwise
     auto one_iter = [&](cudaStream_t sm, bool recomp) {
       // q = A p, ||q||^2
       TIMED(tm, sm, kA, launch_spmm<B>(A, p, EpiStoreNorm{q, B}, part_a, sm));
@@ -824,7 +956,7 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
       TIMED(tm, sm, kAT, launch_spmm<B>(AT, r, EpiStoreNorm{s, B}, part_b, sm));
       // beta = ||s||^2 / gamma, residual history
       TIMED(tm, sm, kOther,
-            (k_cgls_beta<<<B, kThreads, 0, sm>>>(part_b, gT, hist ? part_r : nullptr, recomp ? gA : ge, B, scal,
+            (k_cgls_beta<<<B, kThreads, 0, sm>>>(part_b, gT, hist ? part_r : nullptr, recomp ? gR : ge, B, scal,
                                                  hist, itc, s0, cnt, nz)));
       // p = s + beta p
       TIMED(tm, sm, kOther, (k_cgls_dir<B><<<ge, kThreads, 0, sm>>>(p, s, cols, scal, itc)));
@@ -921,13 +1053,11 @@ tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t 
   e.B = req;
   e.graph = o ? o->use_graph != 0 : true;
   e.timing = o ? o->timing : nullptr;
-  if (o && o->precision == 1) {
-    if (h->lp_dtype == TOMO_F32) return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without 16-bit values");
-    if (e.B < 4) return fail(TOMO_ERR_UNSUPPORTED, "the 16-bit kernels need batch_width >= 4");
-    e.lp = true;
-  } else if (o && o->precision != 0) {
-    return fail(TOMO_ERR_INVALID_ARG, "precision must be 0 or 1");
-  }
+  e.format = o ? o->format : TOMO_FMT_SELL;
+  if (e.format != TOMO_FMT_SELL && e.format != TOMO_FMT_SELL16 && e.format != TOMO_FMT_CSR)
+    return fail(TOMO_ERR_INVALID_ARG, "format must be TOMO_FMT_SELL, TOMO_FMT_SELL16 or TOMO_FMT_CSR");
+  if (e.format == TOMO_FMT_SELL16 && h->lp_dtype == TOMO_F32)
+    return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without 16-bit values");
   *ex = e;
   return TOMO_OK;
 }

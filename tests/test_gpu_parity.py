@@ -83,14 +83,15 @@ def test_sirt_normalisers(geo):
     np.testing.assert_allclose(C, oracle.inv_row_sums(AT).astype(np.float32), rtol=2e-7, atol=0)
 
 
+@pytest.mark.parametrize("fmt", ["sell", "csr"])
 @pytest.mark.parametrize("B", WIDTHS)
 @pytest.mark.parametrize("nz", [1, 3, 9])
-def test_project_backproject_f32(B, nz):
+def test_project_backproject_f32(B, nz, fmt):
     g, A, AT, M = pair(nx=96, nt=60, n_p=101, center=50.3)
     x = inputs.random_slices((nz, 96, 96), seed=100 + nz)
     y = inputs.random_slices((nz, 60, 101), seed=200 + nz)
-    yd = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=B).cpu().numpy()
-    xd = tomo.backproject(M, torch.from_numpy(y).cuda(), batch_width=B).cpu().numpy()
+    yd = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=B, fmt=fmt).cpu().numpy()
+    xd = tomo.backproject(M, torch.from_numpy(y).cuda(), batch_width=B, fmt=fmt).cpu().numpy()
     assert per_slice_rel(yd, A.apply(x)).max() < 1e-5
     assert per_slice_rel(xd, AT.apply(y)).max() < 1e-5
 
@@ -115,15 +116,16 @@ def test_adjoint_identity_f32():
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
+@pytest.mark.parametrize("fmt", ["sell", "csr"])
 @pytest.mark.parametrize("B", [1, 4, 16])
-def test_sirt_128(B):
+def test_sirt_128(B, fmt):
     """one 128x128 slice, 180 angles, Poisson 1e5, SIRT 50 (and a 3-slice batch)."""
     c = inputs.workload_case("sirt_128x180_b1")
     g, A, AT, M = pair(nx=128, nt=180)
     sino = np.concatenate([c.sino, c.sino * 0.5, c.sino[:, ::-1]]) if B > 1 else c.sino
     sino = np.ascontiguousarray(sino)
     ref = oracle.sirt(A, AT, sino.reshape(len(sino), -1), 50, 1.0)
-    got = tomo.sirt(M, torch.from_numpy(sino).cuda(), 50, batch_width=B).cpu().numpy()
+    got = tomo.sirt(M, torch.from_numpy(sino).cuda(), 50, batch_width=B, fmt=fmt).cpu().numpy()
     assert per_slice_rel(got, ref).max() < 1e-4
 
 
@@ -140,11 +142,13 @@ def test_sirt_lambda_and_start():
 
 @pytest.mark.parametrize("B,nz", [(1, 2), (4, 5), (16, 16), (64, 3)])
 @pytest.mark.parametrize("graph", [True, False])
-def test_cgls(B, nz, graph):
+@pytest.mark.parametrize("fmt", ["sell", "csr"])
+def test_cgls(B, nz, graph, fmt):
     g, A, AT, M = pair(nx=64, nt=90)
     c = inputs.make_case(64, 90, nz, seed=55, phantom="ellipsoids3d", noise="gaussian", level=0.05)
     ref, href = oracle.cgls(A, AT, c.sino.reshape(nz, -1), 4)
-    got, h = tomo.cgls(M, torch.from_numpy(c.sino).cuda(), 4, history=True, batch_width=B, use_graph=graph)
+    got, h = tomo.cgls(M, torch.from_numpy(c.sino).cuda(), 4, history=True, batch_width=B, use_graph=graph,
+                       fmt=fmt)
     assert per_slice_rel(got.cpu().numpy(), ref).max() < 1e-4
     np.testing.assert_allclose(h.cpu().numpy(), href, rtol=1e-4)
 
@@ -165,13 +169,13 @@ def test_cgls_zero_sinogram_is_frozen():
 
 
 @pytest.mark.parametrize("values,tol", [("bf16", 5e-3), ("f16", 1e-3)])
-@pytest.mark.parametrize("B", [4, 16, 64])
+@pytest.mark.parametrize("B", [1, 2, 4, 16, 64])
 def test_lowprec_spmm(values, tol, B):
     g, A, AT, M = pair(nx=128, nt=180, values=values)
     x = inputs.random_slices((5, 128, 128), seed=31)
     y = inputs.random_slices((5, 180, 128), seed=32)
-    yd = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=B, precision=1).cpu().numpy()
-    xd = tomo.backproject(M, torch.from_numpy(y).cuda(), batch_width=B, precision=1).cpu().numpy()
+    yd = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=B, fmt="sell16").cpu().numpy()
+    xd = tomo.backproject(M, torch.from_numpy(y).cuda(), batch_width=B, fmt="sell16").cpu().numpy()
     assert per_slice_rel(yd, A.apply(x)).max() < tol
     assert per_slice_rel(xd, AT.apply(y)).max() < tol
 
@@ -199,6 +203,21 @@ def test_autograd_matches_oracle_gradient():
         assert abs(a - e) <= 1e-4 * np.linalg.norm(gref)
 
 
+@pytest.mark.parametrize("values", ["bf16", "f16"])
+def test_lowprec_corner_gaps(values):
+    """Corner pixels at 256x256 / 720 angles are seen by two angle ranges ~90
+    degrees apart, so consecutive entries of their A^T rows jump by more than
+    65535 columns; the 16-bit encoder must cut segments there."""
+    g, A, AT, M = pair(nx=256, nt=720, values=values)
+    tol = 5e-3 if values == "bf16" else 1e-3
+    x = inputs.random_slices((4, 256, 256), seed=41)
+    y = inputs.random_slices((4, 720, 256), seed=42)
+    yd = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=4, fmt="sell16").cpu().numpy()
+    xd = tomo.backproject(M, torch.from_numpy(y).cuda(), batch_width=4, fmt="sell16").cpu().numpy()
+    assert per_slice_rel(yd, A.apply(x)).max() < tol
+    assert per_slice_rel(xd, AT.apply(y)).max() < tol
+
+
 def test_errors_are_reported():
     with pytest.raises(_lib.TomoError):
         tomo.Matrix(0, 10)
@@ -206,4 +225,4 @@ def test_errors_are_reported():
     with pytest.raises(_lib.TomoError):
         tomo.project(M, torch.zeros((3, 64, 64), device="cuda"), batch_width=3)
     with pytest.raises(_lib.TomoError):
-        tomo.project(M, torch.zeros((1, 64, 64), device="cuda"), precision=1)
+        tomo.project(M, torch.zeros((1, 64, 64), device="cuda"), fmt="sell16")
