@@ -43,9 +43,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="sirt_512x360_b64")
-    p.add_argument("--batch-width", type=int, default=0, help="0 = library default")
-    p.add_argument("--format", default="sell", choices=["sell", "sell16", "csr"],
-                   help="matrix storage streamed by the kernels")
+    p.add_argument("--batch-width", type=int, default=0, help="0 = autotuned")
+    p.add_argument("--format", default="auto", choices=["auto", "sell", "sell16", "csr"],
+                   help="matrix storage streamed by the kernels (auto = autotuned over FP32 formats)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / plain-CSR legs")
     p.add_argument("--iters", type=int, default=0, help="override the solver iterations (profiling runs)")
@@ -217,7 +217,6 @@ def main():
         if world > 1:
             dist.barrier()
 
-    B = args.batch_width or 16
     fmt = args.format
     values = (w.values if w.values != "f32" else "bf16") if fmt == "sell16" else "f32"
     torch.cuda.synchronize()
@@ -225,6 +224,14 @@ def main():
     M = tomo.Matrix(w.n, w.n_theta, values=values)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
+    tune = None
+    if args.batch_width == 0 or fmt == "auto":
+        tune = M.autotune(w.n_z)
+        B = args.batch_width or tune["batch_width"]
+        if fmt == "auto":
+            fmt = tune["format"]
+    else:
+        B = args.batch_width
 
     case = inputs.workload_case(args.workload)
     sino = torch.from_numpy(case.sino).cuda()
@@ -266,6 +273,10 @@ def main():
             "vs_baseline": None, "dtype": "f32" if fmt != "sell16" else "f32-accumulate/%s-values" % values,
             "data": DATA, "config": workload_config(w, B, fmt), "clocks": clk,
             "build_s": build_s, "nnz": M.nnz}
+    if tune is not None:
+        line["autotune"] = {"chosen": [tune["batch_width"], tune["format"]],
+                            "table": [[t["batch_width"], t["format"], round(t["slice_iters_per_s"])]
+                                      for t in tune["table"]]}
 
     # per-kernel device time of one extra solve (CUDA events around every launch)
     tm = tomo.new_timing()

@@ -97,12 +97,14 @@ typedef struct {
 typedef enum {
   TOMO_FMT_SELL = 0,   /* FP32 values, SELL-32 chunks, 128-bit entry loads (default) */
   TOMO_FMT_SELL16 = 1, /* 16-bit values + 16-bit column offsets (needs a 16-bit build) */
-  TOMO_FMT_CSR = 2     /* FP32 CSR as exported: CSR-vector SpMV for widths 1-2, the plain comparator */
+  TOMO_FMT_CSR = 2,    /* FP32 CSR as exported: CSR-vector SpMV for widths 1-2, the plain comparator */
+  TOMO_FMT_AUTO = 3    /* the format tomo_autotune chose for this slice count (else TOMO_FMT_SELL) */
 } tomo_format;
 
 /* Per-call execution options (pointer may be NULL = defaults). */
 typedef struct {
-  int32_t batch_width; /* slices per SpMM pass: 0 = library default, else one of 1,2,4,8,16,32,64 */
+  int32_t batch_width; /* slices per SpMM pass: 0 = the width tomo_autotune chose for this slice count,
+                          else the library default; or one of 1,2,4,8,16,32,64 */
   int32_t use_graph;   /* SIRT/CGLS: replay one captured iteration as a CUDA graph (default 1) */
   int32_t format;      /* tomo_format of the matrix operands (default TOMO_FMT_SELL) */
   int32_t reserved0;
@@ -218,6 +220,30 @@ TOMO_API tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x
  * tomo_sirt; kernels are launched on `stream` without CUDA graphs. */
 TOMO_API tomo_status tomo_sirt_noalloc(const tomo_matrix *A, const float *sino, float *x, int32_t n_z,
                                        int32_t iters, float lambda, void *stream);
+
+/* One timed candidate of tomo_autotune. */
+typedef struct {
+  int32_t batch_width, format;
+  double ms_per_iter;        /* one SIRT iteration (A pass + A^T pass) over one batch of batch_width slices */
+  double slice_iters_per_s;  /* for n_z slices: n_z / (ceil(n_z / batch_width) * ms_per_iter) */
+} tomo_tune_entry;
+
+/* Autotuner (batch width and matrix storage; the row block of a warp follows
+ * from the width).  The paper picks no such parameters; it relies on library
+ * SpMV.  Times one SIRT iteration (the A pass with the residual epilogue and
+ * the A^T pass with the update epilogue, the same kernels tomo_sirt replays)
+ * on device scratch for every width 1..64 not above n_z rounded up to a
+ * power of two, and for TOMO_FMT_SELL, TOMO_FMT_CSR and, when allow_16bit is
+ * non-zero and the matrix has a 16-bit encoding, TOMO_FMT_SELL16.  Writes up
+ * to `cap` candidates to `table` (nullable) and their count to *n_table,
+ * returns the fastest in *best (batch_width, format) with its rate in *rate,
+ * and remembers it in the handle for later calls with that n_z that pass
+ * batch_width = 0 or format = TOMO_FMT_AUTO.  Allocates its scratch with
+ * cudaMalloc and synchronises `stream`.  Not to be called while other calls
+ * on the same handle are being queued from another thread. */
+TOMO_API tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo_exec_opts *best,
+                                   double *rate, tomo_tune_entry *table, int32_t cap, int32_t *n_table,
+                                   void *stream);
 
 /* Human-readable name of a status code (static string). */
 TOMO_API const char *tomo_status_string(tomo_status s);

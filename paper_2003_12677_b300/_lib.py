@@ -17,7 +17,8 @@ SLICE_MAJOR, INTERLEAVED = 0, 1
 # every entry point include/tomo.h declares
 EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
            "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
-           "tomo_sirt", "tomo_cgls", "tomo_sirt_noalloc", "tomo_status_string", "tomo_last_error"]
+           "tomo_sirt", "tomo_cgls", "tomo_sirt_noalloc", "tomo_autotune", "tomo_status_string",
+           "tomo_last_error"]
 
 
 class TomoError(RuntimeError):
@@ -43,6 +44,11 @@ class ExecOpts(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("format", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("timing", ctypes.POINTER(Timing)), ("reserved", ctypes.c_int32 * 4)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("batch_width", ctypes.c_int32), ("format", ctypes.c_int32),
+                ("ms_per_iter", ctypes.c_double), ("slice_iters_per_s", ctypes.c_double)]
 
 
 class MatrixInfo(ctypes.Structure):
@@ -76,6 +82,8 @@ def load(path: str = LIB_PATH):
         "tomo_sirt": [P, P, P, I32, I32, ctypes.c_float, ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_cgls": [P, P, P, I32, I32, I32, P, ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_sirt_noalloc": [P, P, P, I32, I32, ctypes.c_float, P],
+        "tomo_autotune": [P, I32, I32, ctypes.POINTER(ExecOpts), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(TuneEntry), I32, ctypes.POINTER(I32), P],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

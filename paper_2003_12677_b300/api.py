@@ -35,7 +35,8 @@ def _check_tensor(t: torch.Tensor, name: str, shape=None):
         raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
 
 
-FORMATS = {"sell": 0, "sell16": 1, "csr": 2}
+FORMATS = {"sell": 0, "sell16": 1, "csr": 2, "auto": 3}
+FORMAT_NAMES = {v: k for k, v in FORMATS.items()}
 
 
 def _fmt(fmt) -> int:
@@ -144,6 +145,20 @@ class Matrix:
         C = np.empty(self.cols, np.float32)
         _lib.call("tomo_matrix_export_norms", self.handle, R.ctypes.data, C.ctypes.data)
         return R, C
+
+    def autotune(self, n_z: int, allow_16bit: bool = False) -> dict:
+        """Time every (batch width, format) for n_z slices on the device; the
+        fastest is remembered for calls with batch_width=0 / fmt="auto"."""
+        best = _lib.ExecOpts()
+        rate = ctypes.c_double()
+        table = (_lib.TuneEntry * 32)()
+        n = ctypes.c_int32()
+        _lib.call("tomo_autotune", self.handle, n_z, int(allow_16bit), ctypes.byref(best), ctypes.byref(rate),
+                  table, 32, ctypes.byref(n), _stream())
+        rows = [{"batch_width": t.batch_width, "format": FORMAT_NAMES[t.format], "ms_per_iter": t.ms_per_iter,
+                 "slice_iters_per_s": t.slice_iters_per_s} for t in table[:min(n.value, 32)]]
+        return {"batch_width": best.batch_width, "format": FORMAT_NAMES[best.format],
+                "slice_iters_per_s": rate.value, "table": rows}
 
     def workspace_size(self, op: int, n_z: int, batch_width: int = 0, fmt="sell") -> int:
         b = ctypes.c_size_t()

@@ -187,6 +187,15 @@ tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t
   return run_cgls(A, sino, x, n_z, iters, recompute_every, resnorm_hist, ex, workspace, (cudaStream_t)stream);
 }
 
+tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo_exec_opts *best, double *rate,
+                          tomo_tune_entry *table, int32_t cap, int32_t *n_table, void *stream) {
+  if (!A || !best) return fail(TOMO_ERR_INVALID_ARG, "matrix and best must be non-NULL");
+  if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
+  if (cap < 0 || (cap > 0 && !table)) return fail(TOMO_ERR_INVALID_ARG, "table must hold cap entries");
+  DeviceGuard dg(A->device);
+  return run_autotune(A, n_z, allow_16bit != 0, best, rate, table, cap, n_table, (cudaStream_t)stream);
+}
+
 const char *tomo_status_string(tomo_status s) {
   switch (s) {
     case TOMO_OK: return "TOMO_OK";

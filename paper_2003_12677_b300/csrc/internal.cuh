@@ -80,6 +80,8 @@ struct tomo_matrix {
   tomo::Sell sA, sAT;
   tomo::SellLp lpA, lpAT;
   int64_t bytes_f32 = 0, bytes_lp = 0;
+  // last tomo_autotune result (0 / -1: none)
+  int32_t tuned_nz = 0, tuned_B = 0, tuned_fmt = -1;
 };
 
 namespace tomo {
@@ -132,5 +134,7 @@ tomo_status run_sirt(const tomo_matrix *h, const float *sino, float *x, int32_t 
                      float lambda, const Exec &ex, void *ws, cudaStream_t st);
 tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
                      int32_t recompute, double *hist, const Exec &ex, void *ws, cudaStream_t st);
+tomo_status run_autotune(tomo_matrix *h, int32_t nz, bool allow16, tomo_exec_opts *best, double *rate,
+                         tomo_tune_entry *table, int32_t cap, int32_t *n_table, cudaStream_t st);
 
 }  // namespace tomo

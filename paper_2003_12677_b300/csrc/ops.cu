@@ -13,6 +13,7 @@
 // one iteration is captured once as a CUDA graph and replayed.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -1042,20 +1043,26 @@ tomo_status with_ws(const tomo_matrix *h, int op, int32_t nz, const Exec &ex, vo
 
 tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t nz, Exec *ex) {
   Exec e;
+  const bool tuned = h->tuned_B > 0 && h->tuned_nz == nz;
   int req = o ? o->batch_width : 0;
   if (req != 0 && !valid_width(req))
     return fail(TOMO_ERR_UNSUPPORTED, "batch_width must be 0, 1, 2, 4, 8, 16, 32 or 64");
   if (req == 0) {
-    int b = 1;
-    while (b < nz && b < 16) b <<= 1;
-    req = b;
+    if (tuned) {
+      req = h->tuned_B;
+    } else {
+      int b = 1;
+      while (b < nz && b < 16) b <<= 1;
+      req = b;
+    }
   }
   e.B = req;
   e.graph = o ? o->use_graph != 0 : true;
   e.timing = o ? o->timing : nullptr;
   e.format = o ? o->format : TOMO_FMT_SELL;
+  if (e.format == TOMO_FMT_AUTO) e.format = tuned ? h->tuned_fmt : TOMO_FMT_SELL;
   if (e.format != TOMO_FMT_SELL && e.format != TOMO_FMT_SELL16 && e.format != TOMO_FMT_CSR)
-    return fail(TOMO_ERR_INVALID_ARG, "format must be TOMO_FMT_SELL, TOMO_FMT_SELL16 or TOMO_FMT_CSR");
+    return fail(TOMO_ERR_INVALID_ARG, "format must be a tomo_format value");
   if (e.format == TOMO_FMT_SELL16 && h->lp_dtype == TOMO_F32)
     return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without 16-bit values");
   *ex = e;
@@ -1124,6 +1131,96 @@ tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t 
   WsHolder hold;
   TOMO_TRY(with_ws(h, TOMO_OP_CGLS, nz, ex, ws, hold, st));
   return dispatch<CglsF>(ex.B, h, sino, x, nz, iters, recompute, hist, ex, ws, st);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time one SIRT iteration pair per (format, width) candidate
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int B>
+tomo_status time_sirt_pair(const tomo_matrix *h, int format, float *x, float *r, float *b, cudaStream_t st,
+                           double *ms_out) {
+  Exec ex;
+  ex.B = B;
+  ex.format = format;
+  Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
+  auto pair = [&]() {
+    launch_spmm<B>(A, x, EpiSirtResidual{r, b, h->R, B}, nullptr, st);
+    launch_spmm<B>(AT, r, EpiSirtUpdate{x, h->C, 0.0f, B}, nullptr, st);
+  };
+  for (int i = 0; i < 2; ++i) pair();
+  cudaEvent_t e0, e1;
+  TOMO_CUDA(cudaEventCreate(&e0));
+  TOMO_CUDA(cudaEventCreate(&e1));
+  const int reps = 5;
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < reps; ++i) pair();
+  cudaEventRecord(e1, st);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TOMO_CUDA(err);
+  TOMO_CUDA(cudaGetLastError());
+  *ms_out = ms / reps;
+  return TOMO_OK;
+}
+
+template <int B>
+struct TimeF {
+  template <typename... A>
+  static tomo_status run(A &&...a) { return time_sirt_pair<B>(a...); }
+};
+
+}  // namespace
+
+tomo_status run_autotune(tomo_matrix *h, int32_t nz, bool allow16, tomo_exec_opts *best, double *rate,
+                         tomo_tune_entry *table, int32_t cap, int32_t *n_table, cudaStream_t st) {
+  int bmax = 1;
+  while (bmax < nz && bmax < 64) bmax <<= 1;
+  std::vector<int> fmts = {TOMO_FMT_SELL, TOMO_FMT_CSR};
+  if (allow16 && h->lp_dtype != TOMO_F32) fmts.push_back(TOMO_FMT_SELL16);
+  const int64_t rows = h->A.rows, cols = h->A.cols;
+  float *x = nullptr, *r = nullptr, *b = nullptr;
+  struct Free {
+    float **p[3];
+    ~Free() {
+      for (auto q : p)
+        if (*q) cudaFree(*q);
+    }
+  } guard{{&x, &r, &b}};
+  TOMO_CUDA(cudaMalloc(&x, sizeof(float) * cols * bmax));
+  TOMO_CUDA(cudaMalloc(&r, sizeof(float) * rows * bmax));
+  TOMO_CUDA(cudaMalloc(&b, sizeof(float) * rows * bmax));
+  TOMO_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * cols * bmax, st));
+  TOMO_CUDA(cudaMemsetAsync(b, 0, sizeof(float) * rows * bmax, st));
+  int n = 0;
+  double best_rate = -1.0;
+  for (int f : fmts) {
+    for (int B = 1; B <= bmax; B <<= 1) {
+      double ms = 0.0;
+      TOMO_TRY(dispatch<TimeF>(B, h, f, x, r, b, st, &ms));
+      const double chunks = (double)((nz + B - 1) / B);
+      const double rt = ms > 0 ? nz / (chunks * ms) * 1000.0 : 0.0;
+      if (table && n < cap) table[n] = tomo_tune_entry{B, f, ms, rt};
+      ++n;
+      if (rt > best_rate) {
+        best_rate = rt;
+        std::memset(best, 0, sizeof(*best));
+        best->batch_width = B;
+        best->format = f;
+        best->use_graph = 1;
+      }
+    }
+  }
+  if (n_table) *n_table = n;
+  if (rate) *rate = best_rate;
+  h->tuned_nz = nz;
+  h->tuned_B = best->batch_width;
+  h->tuned_fmt = best->format;
+  return TOMO_OK;
 }
 
 }  // namespace tomo

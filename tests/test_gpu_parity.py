@@ -218,6 +218,21 @@ def test_lowprec_corner_gaps(values):
     assert per_slice_rel(xd, AT.apply(y)).max() < tol
 
 
+def test_autotune_choice_is_used_by_default():
+    g, A, AT, M = pair(nx=128, nt=180)
+    res = M.autotune(6)
+    assert res["batch_width"] in (1, 2, 4, 8) and res["format"] in ("sell", "csr")
+    assert len(res["table"]) == 2 * 4 and res["slice_iters_per_s"] > 0
+    assert max(t["slice_iters_per_s"] for t in res["table"]) == res["slice_iters_per_s"]
+    c = inputs.make_case(128, 180, 6, seed=9, phantom="ellipsoids3d", noise="poisson", level=1e4)
+    sino = torch.from_numpy(c.sino).cuda()
+    auto = tomo.sirt(M, sino, 10, batch_width=0, fmt="auto")
+    expl = tomo.sirt(M, sino, 10, batch_width=res["batch_width"], fmt=res["format"])
+    assert torch.equal(auto, expl)   # same kernels, same order: bit-identical
+    ref = oracle.sirt(A, AT, c.sino.reshape(6, -1), 10)
+    assert per_slice_rel(auto.cpu().numpy(), ref).max() < 1e-4
+
+
 def test_errors_are_reported():
     with pytest.raises(_lib.TomoError):
         tomo.Matrix(0, 10)
