@@ -245,6 +245,31 @@ TOMO_API tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16
                                    double *rate, tomo_tune_entry *table, int32_t cap, int32_t *n_table,
                                    void *stream);
 
+/* CGLS state of n_z slices (checkpoint / resume), caller-owned DEVICE
+ * buffers, slice-major: r (n_z, rows) = b - A x, p (n_z, cols) the search
+ * direction, gamma (n_z) = ||A^T r||^2 in FP64, frozen (n_z) 1 for a slice
+ * that has converged (gamma or ||A p||^2 reached 0), else 0.  r and p
+ * 16-byte aligned. */
+typedef struct {
+  float *r;
+  float *p;
+  double *gamma;
+  int32_t *frozen;
+} tomo_cgls_state;
+
+/* CGLS (Sec. 2.1) continued from a saved state: `in` (nullable) holds the
+ * state after some iterations and x (n_z, n_y, n_x) the matching iterate;
+ * with in = NULL the call starts from x0 = 0 exactly as tomo_cgls.  `out`
+ * (nullable) receives the state after the last iteration.  Iteration
+ * numbering (the recompute cadence and the rows of resnorm_hist) restarts at
+ * 0 in every call, so k iterations then a resume for m give the same bits as
+ * k + m iterations when recompute_every divides k (or is 0). */
+TOMO_API tomo_status tomo_cgls_resume(const tomo_matrix *A, const float *sino, float *x, int32_t n_z,
+                                      int32_t iters, int32_t recompute_every, double *resnorm_hist,
+                                      const tomo_cgls_state *in, tomo_cgls_state *out,
+                                      const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes,
+                                      void *stream);
+
 /* Human-readable name of a status code (static string). */
 TOMO_API const char *tomo_status_string(tomo_status s);
 

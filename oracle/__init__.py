@@ -237,6 +237,21 @@ def cgls(A: CSR, AT: CSR, b, iters: int):
     return x, hist[:iters]
 
 
+def cgls_resume(A: CSR, AT: CSR, x, r, p, gamma, frozen, iters: int):
+    """Continue CGLS from a state; returns (x, r, p, gamma, frozen, hist) in FP64."""
+    x = np.ascontiguousarray(np.array(x, np.float64).reshape(-1, A.cols))
+    nz = x.shape[0]
+    r = np.ascontiguousarray(np.array(r, np.float64).reshape(nz, A.rows))
+    p = np.ascontiguousarray(np.array(p, np.float64).reshape(nz, A.cols))
+    gamma = np.ascontiguousarray(np.array(gamma, np.float64).reshape(nz))
+    frozen = np.ascontiguousarray(np.array(frozen, np.int32).reshape(nz))
+    hist = np.zeros((max(iters, 1), nz))
+    _load().oracle_cgls_resume(_i64(A.rows), _i64(A.cols), _p(A.row_ptr), _p(A.col), _p(A.val),
+                               _p(AT.row_ptr), _p(AT.col), _p(AT.val), _i32(nz), _p(x), _p(r), _p(p),
+                               _p(gamma), _p(frozen), _i32(iters), _p(hist))
+    return x, r, p, gamma, frozen, hist[:iters]
+
+
 def loss_grad(A: CSR, AT: CSR, nx: int, ny: int, x, b, mu: float = 1e-3, eps: float = 1e-3):
     """(f, grad) of sum ||A x - b||^2 + mu * TV_eps(x); x (nz, ny*nx), b (nz, rows)."""
     x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, A.cols))

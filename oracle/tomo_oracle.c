@@ -299,14 +299,40 @@ static double dot(int64_t n, const double *a, const double *b) {
 }
 
 /* CGLS (Sec. 2.1; Hestenes-Stiefel form for min ||A x - b||), independently per
- * slice, from x0 = 0:
- *   r = b, s = A^T r, p = s, gamma = ||s||^2
- *   repeat: q = A p, alpha = gamma/||q||^2, x += alpha p, r -= alpha q,
- *           s = A^T r, gamma' = ||s||^2, beta = gamma'/gamma, p = s + beta p.
- * A slice whose gamma or ||q||^2 reaches 0 is converged and stops changing.
+ * slice.  One iteration from the state (x, r = b - A x, p, gamma = ||A^T r||^2):
+ *   q = A p, alpha = gamma/||q||^2, x += alpha p, r -= alpha q,
+ *   s = A^T r, gamma' = ||s||^2, beta = gamma'/gamma, p = s + beta p.
+ * A slice whose gamma or ||q||^2 is 0 is converged and stops changing (frozen).
  * hist (nullable, iters x nz) receives ||r|| after each iteration.
  * Pinned: iterate k equals the minimiser of ||A x - b|| over the Krylov space
  * K_k(A^T A, A^T b); after rank-many steps it equals the lstsq solution. */
+static void cgls_iterate(int64_t rows, int64_t cols, const int64_t *arp, const int32_t *aci, const double *av,
+                         const int64_t *trp, const int32_t *tci, const double *tv, double *xz, double *r,
+                         double *p, double *gamma, int32_t *frozen, int32_t iters, double *hist, int32_t nz,
+                         int32_t z, double *q, double *s) {
+  for (int32_t it = 0; it < iters; ++it) {
+    if (!*frozen) {
+      oracle_spmv(rows, cols, arp, aci, av, 1, p, q);
+      double qq = dot(rows, q, q);
+      if (*gamma == 0.0 || qq == 0.0) {
+        *frozen = 1;
+      } else {
+        double alpha = *gamma / qq;
+        for (int64_t j = 0; j < cols; ++j) xz[j] += alpha * p[j];
+        for (int64_t i = 0; i < rows; ++i) r[i] -= alpha * q[i];
+        oracle_spmv(cols, rows, trp, tci, tv, 1, r, s);
+        double gnew = dot(cols, s, s);
+        double beta = gnew / *gamma;
+        for (int64_t j = 0; j < cols; ++j) p[j] = s[j] + beta * p[j];
+        *gamma = gnew;
+      }
+    }
+    if (hist) hist[(int64_t)it * nz + z] = sqrt(dot(rows, r, r));
+  }
+}
+
+/* CGLS from x0 = 0: r = b, s = A^T r, p = s, gamma = ||s||^2, then `iters`
+ * iterations (see cgls_iterate). */
 void oracle_cgls(int64_t rows, int64_t cols,
                  const int64_t *arp, const int32_t *aci, const double *av,
                  const int64_t *trp, const int32_t *tci, const double *tv,
@@ -322,31 +348,29 @@ void oracle_cgls(int64_t rows, int64_t cols,
     oracle_spmv(cols, rows, trp, tci, tv, 1, r, s);
     memcpy(p, s, sizeof(double) * cols);
     double gamma = dot(cols, s, s);
-    int frozen = 0;
-    for (int32_t it = 0; it < iters; ++it) {
-      if (!frozen) {
-        oracle_spmv(rows, cols, arp, aci, av, 1, p, q);
-        double qq = dot(rows, q, q);
-        if (gamma == 0.0 || qq == 0.0) {
-          frozen = 1;
-        } else {
-          double alpha = gamma / qq;
-          for (int64_t j = 0; j < cols; ++j) xz[j] += alpha * p[j];
-          for (int64_t i = 0; i < rows; ++i) r[i] -= alpha * q[i];
-          oracle_spmv(cols, rows, trp, tci, tv, 1, r, s);
-          double gnew = dot(cols, s, s);
-          double beta = gnew / gamma;
-          for (int64_t j = 0; j < cols; ++j) p[j] = s[j] + beta * p[j];
-          gamma = gnew;
-        }
-      }
-      if (hist) hist[(int64_t)it * nz + z] = sqrt(dot(rows, r, r));
-    }
+    int32_t frozen = 0;
+    cgls_iterate(rows, cols, arp, aci, av, trp, tci, tv, xz, r, p, &gamma, &frozen, iters, hist, nz, z, q, s);
   }
   free(r);
   free(q);
   free(s);
   free(p);
+}
+
+/* CGLS continued from a given state: x (nz, cols), r (nz, rows), p (nz, cols),
+ * gamma (nz), frozen (nz), all updated in place by `iters` iterations. */
+void oracle_cgls_resume(int64_t rows, int64_t cols,
+                        const int64_t *arp, const int32_t *aci, const double *av,
+                        const int64_t *trp, const int32_t *tci, const double *tv,
+                        int32_t nz, double *x, double *r, double *p, double *gamma, int32_t *frozen,
+                        int32_t iters, double *hist) {
+  double *q = (double *)malloc(sizeof(double) * rows);
+  double *s = (double *)malloc(sizeof(double) * cols);
+  for (int32_t z = 0; z < nz; ++z)
+    cgls_iterate(rows, cols, arp, aci, av, trp, tci, tv, x + (int64_t)z * cols, r + (int64_t)z * rows,
+                 p + (int64_t)z * cols, gamma + z, frozen + z, iters, hist, nz, z, q, s);
+  free(q);
+  free(s);
 }
 
 /* Model-based objective of Sec. 2.1 with an unweighted norm and TV prior:

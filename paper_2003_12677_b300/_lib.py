@@ -17,8 +17,8 @@ SLICE_MAJOR, INTERLEAVED = 0, 1
 # every entry point include/tomo.h declares
 EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
            "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
-           "tomo_sirt", "tomo_cgls", "tomo_sirt_noalloc", "tomo_autotune", "tomo_status_string",
-           "tomo_last_error"]
+           "tomo_sirt", "tomo_cgls", "tomo_cgls_resume", "tomo_sirt_noalloc", "tomo_autotune",
+           "tomo_status_string", "tomo_last_error"]
 
 
 class TomoError(RuntimeError):
@@ -51,6 +51,11 @@ class TuneEntry(ctypes.Structure):
                 ("ms_per_iter", ctypes.c_double), ("slice_iters_per_s", ctypes.c_double)]
 
 
+class CglsState(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_void_p), ("p", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("frozen", ctypes.c_void_p)]
+
+
 class MatrixInfo(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("bytes_f32", ctypes.c_int64), ("bytes_lp", ctypes.c_int64),
@@ -81,6 +86,8 @@ def load(path: str = LIB_PATH):
         "tomo_backproject": [P, P, P, I32, I32, ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_sirt": [P, P, P, I32, I32, ctypes.c_float, ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_cgls": [P, P, P, I32, I32, I32, P, ctypes.POINTER(ExecOpts), P, SZ, P],
+        "tomo_cgls_resume": [P, P, P, I32, I32, I32, P, ctypes.POINTER(CglsState), ctypes.POINTER(CglsState),
+                             ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_sirt_noalloc": [P, P, P, I32, I32, ctypes.c_float, P],
         "tomo_autotune": [P, I32, I32, ctypes.POINTER(ExecOpts), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(TuneEntry), I32, ctypes.POINTER(I32), P],

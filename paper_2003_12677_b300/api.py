@@ -253,20 +253,54 @@ def sirt_noalloc(M: Matrix, sino: torch.Tensor, iters: int, lam: float = 1.0,
     return out
 
 
+def _state_struct(st: dict) -> _lib.CglsState:
+    s = _lib.CglsState()
+    s.r, s.p = st["r"].data_ptr(), st["p"].data_ptr()
+    s.gamma, s.frozen = st["gamma"].data_ptr(), st["frozen"].data_ptr()
+    return s
+
+
 def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, history: bool = False,
          batch_width: int = 0, fmt="sell", use_graph: bool = True, out: Optional[torch.Tensor] = None,
-         workspace: Optional[torch.Tensor] = None, timing=None):
-    """CGLS from x0 = 0 per slice.  Returns x, or (x, ||r|| history (iters, n_z) float64)."""
+         workspace: Optional[torch.Tensor] = None, timing=None, resume: Optional[dict] = None,
+         return_state: bool = False):
+    """CGLS per slice.  Starts from x0 = 0, or from `resume` (a dict with the
+    iterate "x" and the state "r", "p", "gamma", "frozen" as returned with
+    return_state=True).  Returns x, then the ||r|| history (iters, n_z) if
+    history, then the final state dict if return_state."""
     _check_tensor(sino, "sino")
     nz = _nz(sino, M.rows, "sino")
-    x = torch.empty((nz, M.n_y, M.n_x), device=sino.device) if out is None else out
+    if resume is not None:
+        x = resume["x"].clone() if out is None else out.copy_(resume["x"])
+    else:
+        x = torch.empty((nz, M.n_y, M.n_x), device=sino.device) if out is None else out
     _check_tensor(x, "out", (nz, M.n_y, M.n_x))
     hist = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
     ws = workspace if workspace is not None else M._workspace(_lib.OP_CGLS, nz, batch_width, fmt)
     o = _exec(batch_width, use_graph, fmt, timing)
-    _lib.call("tomo_cgls", M.handle, _ptr(sino), _ptr(x), nz, iters, recompute_every, _ptr(hist),
+    sin = None
+    if resume is not None:
+        for k in ("r", "p"):
+            _check_tensor(resume[k], "resume[%s]" % k)
+        sin = _state_struct(resume)
+    state = None
+    sout = None
+    if return_state:
+        state = {"r": torch.empty((nz, M.n_theta, M.n_p), device=sino.device),
+                 "p": torch.empty((nz, M.n_y, M.n_x), device=sino.device),
+                 "gamma": torch.empty(nz, device=sino.device, dtype=torch.float64),
+                 "frozen": torch.empty(nz, device=sino.device, dtype=torch.int32)}
+        sout = _state_struct(state)
+    _lib.call("tomo_cgls_resume", M.handle, _ptr(sino), _ptr(x), nz, iters, recompute_every, _ptr(hist),
+              None if sin is None else ctypes.byref(sin), None if sout is None else ctypes.byref(sout),
               ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
-    return (x, hist[:iters]) if history else x
+    res = [x]
+    if history:
+        res.append(hist[:iters])
+    if return_state:
+        state["x"] = x.clone()
+        res.append(state)
+    return res[0] if len(res) == 1 else tuple(res)
 
 
 class TomoProject(torch.autograd.Function):

@@ -172,19 +172,40 @@ tomo_status tomo_sirt(const tomo_matrix *A, const float *sino, float *x, int32_t
   return run_sirt(A, sino, x, n_z, iters, lambda, ex, workspace, (cudaStream_t)stream);
 }
 
-tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
-                      int32_t recompute_every, double *resnorm_hist, const tomo_exec_opts *opts, void *workspace,
-                      size_t workspace_bytes, void *stream) {
+static tomo_status check_state(const tomo_cgls_state *s, const char *name) {
+  if (!s) return TOMO_OK;
+  if (!s->gamma || !s->frozen) return fail(TOMO_ERR_INVALID_ARG, std::string(name) + ": gamma and frozen must be set");
+  TOMO_TRY(check_vec(s->r, "state r"));
+  TOMO_TRY(check_vec(s->p, "state p"));
+  if (((uintptr_t)s->gamma & 7u) || ((uintptr_t)s->frozen & 3u))
+    return fail(TOMO_ERR_INVALID_ARG, std::string(name) + ": gamma / frozen misaligned");
+  return TOMO_OK;
+}
+
+tomo_status tomo_cgls_resume(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
+                             int32_t recompute_every, double *resnorm_hist, const tomo_cgls_state *in,
+                             tomo_cgls_state *out, const tomo_exec_opts *opts, void *workspace,
+                             size_t workspace_bytes, void *stream) {
   if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
   TOMO_TRY(check_vec(sino, "sino"));
   TOMO_TRY(check_vec(x, "x"));
+  TOMO_TRY(check_state(in, "in"));
+  TOMO_TRY(check_state(out, "out"));
   if (n_z < 1 || iters < 0 || recompute_every < 0)
     return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1, iters >= 0 and recompute_every >= 0");
   DeviceGuard dg(A->device);
   Exec ex;
   TOMO_TRY(resolve_exec(A, opts, n_z, &ex));
   TOMO_TRY(check_ws(A, TOMO_OP_CGLS, n_z, ex, workspace, workspace_bytes));
-  return run_cgls(A, sino, x, n_z, iters, recompute_every, resnorm_hist, ex, workspace, (cudaStream_t)stream);
+  return run_cgls(A, sino, x, n_z, iters, recompute_every, resnorm_hist, in, out, ex, workspace,
+                  (cudaStream_t)stream);
+}
+
+tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
+                      int32_t recompute_every, double *resnorm_hist, const tomo_exec_opts *opts, void *workspace,
+                      size_t workspace_bytes, void *stream) {
+  return tomo_cgls_resume(A, sino, x, n_z, iters, recompute_every, resnorm_hist, nullptr, nullptr, opts, workspace,
+                          workspace_bytes, stream);
 }
 
 tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo_exec_opts *best, double *rate,

@@ -133,7 +133,8 @@ tomo_status run_project(const tomo_matrix *h, bool transpose, const float *in, f
 tomo_status run_sirt(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
                      float lambda, const Exec &ex, void *ws, cudaStream_t st);
 tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
-                     int32_t recompute, double *hist, const Exec &ex, void *ws, cudaStream_t st);
+                     int32_t recompute, double *hist, const tomo_cgls_state *in, tomo_cgls_state *out,
+                     const Exec &ex, void *ws, cudaStream_t st);
 tomo_status run_autotune(tomo_matrix *h, int32_t nz, bool allow16, tomo_exec_opts *best, double *rate,
                          tomo_tune_entry *table, int32_t cap, int32_t *n_table, cudaStream_t st);
 

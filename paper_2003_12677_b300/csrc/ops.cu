@@ -534,6 +534,25 @@ __global__ void __launch_bounds__(kThreads) k_cgls_beta(const double *part_s, in
   }
 }
 
+// state in / out: per-slice gamma and frozen flag (padding slices frozen)
+__global__ void k_cgls_load(double *scal, const double *gamma, const int32_t *frozen, int cnt, int B, int *it) {
+  for (int s = threadIdx.x; s < B; s += blockDim.x) {
+    const bool real = s < cnt;
+    scal[s * 8 + 0] = real ? gamma[s] : 0.0;
+    scal[s * 8 + 1] = 0.0;
+    scal[s * 8 + 2] = 0.0;
+    scal[s * 8 + 3] = (!real || frozen[s] != 0) ? 1.0 : 0.0;
+  }
+  if (threadIdx.x == 0) *it = 0;
+}
+
+__global__ void k_cgls_save(const double *scal, double *gamma, int32_t *frozen, int cnt) {
+  for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
+    gamma[s] = scal[s * 8 + 0];
+    frozen[s] = scal[s * 8 + 3] != 0.0 ? 1 : 0;
+  }
+}
+
 // x += alpha p (cols); r -= alpha q (rows), optional ||r||^2 partials
 template <int B>
 __global__ void __launch_bounds__(kThreads) k_cgls_step(float *__restrict__ x, const float *__restrict__ p,
@@ -895,7 +914,8 @@ tomo_status sirt_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
 // ---------------------------------------------------------------------------
 template <int B>
 tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
-                   int32_t recompute, double *hist, const Exec &ex, void *ws, cudaStream_t st) {
+                   int32_t recompute, double *hist, const tomo_cgls_state *sin, tomo_cgls_state *sout,
+                   const Exec &ex, void *ws, cudaStream_t st) {
   Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
   const int64_t rows = h->A.rows, cols = h->A.cols;
   const int pg = max_spmm_grid();
@@ -933,12 +953,25 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
       bb = bi;
       xx = xi;
     }
-    // x = 0, r = b, s = A^T r, p = s, gamma = ||s||^2
-    TOMO_CUDA(cudaMemsetAsync(xx, 0, sizeof(float) * cols * B, st));
-    TOMO_CUDA(cudaMemcpyAsync(r, bb, sizeof(float) * rows * B, cudaMemcpyDeviceToDevice, st));
-    TIMED(tm, st, kAT, launch_spmm<B>(AT, r, EpiStoreNorm{s, B}, part_b, st));
-    TOMO_CUDA(cudaMemcpyAsync(p, s, sizeof(float) * cols * B, cudaMemcpyDeviceToDevice, st));
-    TIMED(tm, st, kOther, (k_cgls_init<<<B, kThreads, 0, st>>>(part_b, gT, B, scal, itc)));
+    if (sin) {
+      // resume: x, r, p, gamma and the frozen flags from the caller's state
+      if (B > 1) {
+        TIMED(tm, st, kOther, interleave<B>(x + (int64_t)s0 * cols, cols, cnt, xi, st));
+        TIMED(tm, st, kOther, interleave<B>(sin->r + (int64_t)s0 * rows, rows, cnt, r, st));
+        TIMED(tm, st, kOther, interleave<B>(sin->p + (int64_t)s0 * cols, cols, cnt, p, st));
+      } else {
+        TOMO_CUDA(cudaMemcpyAsync(r, sin->r + (int64_t)s0 * rows, sizeof(float) * rows, cudaMemcpyDeviceToDevice, st));
+        TOMO_CUDA(cudaMemcpyAsync(p, sin->p + (int64_t)s0 * cols, sizeof(float) * cols, cudaMemcpyDeviceToDevice, st));
+      }
+      TIMED(tm, st, kOther, (k_cgls_load<<<1, 64, 0, st>>>(scal, sin->gamma + s0, sin->frozen + s0, cnt, B, itc)));
+    } else {
+      // x = 0, r = b, s = A^T r, p = s, gamma = ||s||^2
+      TOMO_CUDA(cudaMemsetAsync(xx, 0, sizeof(float) * cols * B, st));
+      TOMO_CUDA(cudaMemcpyAsync(r, bb, sizeof(float) * rows * B, cudaMemcpyDeviceToDevice, st));
+      TIMED(tm, st, kAT, launch_spmm<B>(AT, r, EpiStoreNorm{s, B}, part_b, st));
+      TOMO_CUDA(cudaMemcpyAsync(p, s, sizeof(float) * cols * B, cudaMemcpyDeviceToDevice, st));
+      TIMED(tm, st, kOther, (k_cgls_init<<<B, kThreads, 0, st>>>(part_b, gT, B, scal, itc)));
+    }
     TOMO_CUDA(cudaGetLastError());
 
     // the residual-norm partials come from the residual SpMM grid (gR blocks)
@@ -986,6 +1019,16 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
       if (g1) cudaGraphDestroy(g1);
     } else {
       for (int32_t it = 0; it < iters; ++it) one_iter(st, recompute > 0 && (it + 1) % recompute == 0);
+    }
+    if (sout) {
+      if (B > 1) {
+        TIMED(tm, st, kOther, deinterleave<B>(r, rows, cnt, sout->r + (int64_t)s0 * rows, st));
+        TIMED(tm, st, kOther, deinterleave<B>(p, cols, cnt, sout->p + (int64_t)s0 * cols, st));
+      } else {
+        TOMO_CUDA(cudaMemcpyAsync(sout->r + (int64_t)s0 * rows, r, sizeof(float) * rows, cudaMemcpyDeviceToDevice, st));
+        TOMO_CUDA(cudaMemcpyAsync(sout->p + (int64_t)s0 * cols, p, sizeof(float) * cols, cudaMemcpyDeviceToDevice, st));
+      }
+      TIMED(tm, st, kOther, (k_cgls_save<<<1, 64, 0, st>>>(scal, sout->gamma + s0, sout->frozen + s0, cnt)));
     }
     if (B > 1) TIMED(tm, st, kOther, deinterleave<B>(xi, cols, cnt, x + (int64_t)s0 * cols, st));
   }
@@ -1127,10 +1170,11 @@ tomo_status run_sirt(const tomo_matrix *h, const float *sino, float *x, int32_t 
 }
 
 tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
-                     int32_t recompute, double *hist, const Exec &ex, void *ws, cudaStream_t st) {
+                     int32_t recompute, double *hist, const tomo_cgls_state *in, tomo_cgls_state *out,
+                     const Exec &ex, void *ws, cudaStream_t st) {
   WsHolder hold;
   TOMO_TRY(with_ws(h, TOMO_OP_CGLS, nz, ex, ws, hold, st));
-  return dispatch<CglsF>(ex.B, h, sino, x, nz, iters, recompute, hist, ex, ws, st);
+  return dispatch<CglsF>(ex.B, h, sino, x, nz, iters, recompute, hist, in, out, ex, ws, st);
 }
 
 // ---------------------------------------------------------------------------

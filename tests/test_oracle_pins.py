@@ -307,6 +307,32 @@ def test_cgls_reaches_lstsq():
     assert np.linalg.norm(x[0] - ref) <= 1e-6 * np.linalg.norm(ref)
 
 
+def test_cgls_resume_continues_the_same_recurrence():
+    """The cold state (x = 0, r = b, p = A^T b, gamma = |A^T b|^2) resumed for
+    k iterations is the k-iteration run bit for bit, and resuming that state
+    for m more is the (k+m)-iteration run bit for bit; the state's residual
+    equals b - A x to rounding."""
+    g, A, AT = _small_system()
+    D = A.dense()
+    b = np.random.default_rng(10).random((2, A.rows))
+    x12, h12 = oracle.cgls(A, AT, b, 12)
+    x5, _ = oracle.cgls(A, AT, b, 5)
+    s0 = AT.apply(b)
+    gamma0 = np.zeros(2)
+    for z in range(2):          # sequential sum, as the oracle accumulates it
+        acc = 0.0
+        for v in s0[z]:
+            acc += v * v
+        gamma0[z] = acc
+    xs, rs, ps, gs, fs, _ = oracle.cgls_resume(A, AT, np.zeros((2, A.cols)), b, s0, gamma0,
+                                               np.zeros(2, np.int32), 5)
+    np.testing.assert_array_equal(xs, x5)
+    np.testing.assert_allclose(rs, b - x5 @ D.T, rtol=0, atol=1e-12 * np.abs(b).max())
+    xr, _, _, _, _, hr = oracle.cgls_resume(A, AT, xs, rs, ps, gs, fs, 7)
+    np.testing.assert_array_equal(xr, x12)
+    np.testing.assert_array_equal(hr, h12[5:])
+
+
 def test_cgls_zero_rhs_freezes():
     g, A, AT = _small_system()
     x, hist = oracle.cgls(A, AT, np.zeros((1, A.rows)), 5)
