@@ -107,11 +107,14 @@ typedef struct {
                           else the library default; or one of 1,2,4,8,16,32,64 */
   int32_t use_graph;   /* SIRT/CGLS: replay one captured iteration as a CUDA graph (default 1) */
   int32_t format;      /* tomo_format of the matrix operands (default TOMO_FMT_SELL) */
-  int32_t reserved0;
+  float timeout_s;     /* tomo_cgls_batched: limit of each grid-barrier wait in seconds (0 = 10) */
   tomo_timing *timing; /* non-NULL: bracket every launch with CUDA events on the call's stream,
                           launch without graphs, synchronise the stream before returning and
                           ADD the measured times and counts into *timing */
-  int32_t reserved[4];
+  int32_t test_flags;  /* test hook, 0 in normal use.  bit 0: in tomo_cgls_batched one block of
+                          the persistent launch never arrives at a grid barrier, so the others
+                          wait out timeout_s and the call returns TOMO_ERR_TIMEOUT */
+  int32_t reserved[3];
 } tomo_exec_opts;
 
 typedef struct tomo_matrix tomo_matrix; /* opaque, immutable after build */
@@ -221,6 +224,54 @@ TOMO_API tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x
 TOMO_API tomo_status tomo_sirt_noalloc(const tomo_matrix *A, const float *sino, float *x, int32_t n_z,
                                        int32_t iters, float lambda, void *stream);
 
+/* CGLS state of n_z slices (checkpoint / resume), caller-owned DEVICE
+ * buffers, slice-major: r (n_z, rows) = b - A x, p (n_z, cols) the search
+ * direction, gamma (n_z) = ||A^T r||^2 in FP64, frozen (n_z) 1 for a slice
+ * that has converged (gamma or ||A p||^2 reached 0), else 0.  r and p
+ * 16-byte aligned. */
+typedef struct {
+  float *r;
+  float *p;
+  double *gamma;
+  int32_t *frozen;
+} tomo_cgls_state;
+
+/* One reconstruction request of tomo_cgls_batched: DEVICE buffers sino
+ * (n_z, n_theta, n_p) and x (n_z, n_y, n_x), both 16-byte aligned, on the
+ * geometry of A; resnorm_hist (DEVICE, nullable) receives ||r|| as
+ * (iters, n_z).  state_in (nullable): continue from that CGLS state, with x
+ * holding the matching iterate on entry; state_out (nullable): receives the
+ * state after the last iteration (see tomo_cgls_resume). */
+typedef struct {
+  const tomo_matrix *A;
+  const float *sino;
+  float *x;
+  int32_t n_z;
+  int32_t reserved;
+  double *resnorm_hist;
+  const tomo_cgls_state *state_in;
+  tomo_cgls_state *state_out;
+} tomo_request;
+
+/* CGLS (Sec. 2.1) for many requests of uneven size in ONE persistent launch
+ * (Sec. 3.1 splits uneven slice counts into chunks; here requests sharing a
+ * geometry handle are packed batch_width slices at a time).  Every slice runs
+ * `iters` iterations from x0 = 0 as in tomo_cgls (no residual recompute).
+ * opts: batch_width 4, 8, 16 (default) or 32; format TOMO_FMT_SELL (default)
+ * or TOMO_FMT_SELL16 (every matrix built with the same 16-bit type);
+ * timeout_s bounds each grid-barrier wait.  All matrices on one device.  The
+ * launch is cooperative (every block resident), the barriers are bounded: a
+ * wait that runs out stops every block and the call returns TOMO_ERR_TIMEOUT.
+ * Workspace as tomo_cgls_batched_workspace reports (NULL: allocated by the
+ * call).  Synchronises `stream`. */
+TOMO_API tomo_status tomo_cgls_batched(const tomo_request *reqs, int32_t n_reqs, int32_t iters,
+                                       const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes,
+                                       void *stream);
+
+/* Workspace bytes tomo_cgls_batched needs for these requests and options. */
+TOMO_API tomo_status tomo_cgls_batched_workspace(const tomo_request *reqs, int32_t n_reqs,
+                                                 const tomo_exec_opts *opts, size_t *bytes);
+
 /* One timed candidate of tomo_autotune. */
 typedef struct {
   int32_t batch_width, format;
@@ -244,18 +295,6 @@ typedef struct {
 TOMO_API tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo_exec_opts *best,
                                    double *rate, tomo_tune_entry *table, int32_t cap, int32_t *n_table,
                                    void *stream);
-
-/* CGLS state of n_z slices (checkpoint / resume), caller-owned DEVICE
- * buffers, slice-major: r (n_z, rows) = b - A x, p (n_z, cols) the search
- * direction, gamma (n_z) = ||A^T r||^2 in FP64, frozen (n_z) 1 for a slice
- * that has converged (gamma or ||A p||^2 reached 0), else 0.  r and p
- * 16-byte aligned. */
-typedef struct {
-  float *r;
-  float *p;
-  double *gamma;
-  int32_t *frozen;
-} tomo_cgls_state;
 
 /* CGLS (Sec. 2.1) continued from a saved state: `in` (nullable) holds the
  * state after some iterations and x (n_z, n_y, n_x) the matching iterate;

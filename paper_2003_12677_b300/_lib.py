@@ -17,7 +17,8 @@ SLICE_MAJOR, INTERLEAVED = 0, 1
 # every entry point include/tomo.h declares
 EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
            "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
-           "tomo_sirt", "tomo_cgls", "tomo_cgls_resume", "tomo_sirt_noalloc", "tomo_autotune",
+           "tomo_sirt", "tomo_cgls", "tomo_cgls_resume", "tomo_cgls_batched", "tomo_cgls_batched_workspace",
+           "tomo_sirt_noalloc", "tomo_autotune",
            "tomo_status_string", "tomo_last_error"]
 
 
@@ -42,8 +43,9 @@ class Timing(ctypes.Structure):
 
 class ExecOpts(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("format", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("timing", ctypes.POINTER(Timing)), ("reserved", ctypes.c_int32 * 4)]
+                ("format", ctypes.c_int32), ("timeout_s", ctypes.c_float),
+                ("timing", ctypes.POINTER(Timing)), ("test_flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -54,6 +56,12 @@ class TuneEntry(ctypes.Structure):
 class CglsState(ctypes.Structure):
     _fields_ = [("r", ctypes.c_void_p), ("p", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
                 ("frozen", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("sino", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("n_z", ctypes.c_int32), ("reserved", ctypes.c_int32), ("resnorm_hist", ctypes.c_void_p),
+                ("state_in", ctypes.POINTER(CglsState)), ("state_out", ctypes.POINTER(CglsState))]
 
 
 class MatrixInfo(ctypes.Structure):
@@ -89,6 +97,9 @@ def load(path: str = LIB_PATH):
         "tomo_cgls_resume": [P, P, P, I32, I32, I32, P, ctypes.POINTER(CglsState), ctypes.POINTER(CglsState),
                              ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_sirt_noalloc": [P, P, P, I32, I32, ctypes.c_float, P],
+        "tomo_cgls_batched": [ctypes.POINTER(Request), I32, I32, ctypes.POINTER(ExecOpts), P, SZ, P],
+        "tomo_cgls_batched_workspace": [ctypes.POINTER(Request), I32, ctypes.POINTER(ExecOpts),
+                                        ctypes.POINTER(SZ)],
         "tomo_autotune": [P, I32, I32, ctypes.POINTER(ExecOpts), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(TuneEntry), I32, ctypes.POINTER(I32), P],
     }

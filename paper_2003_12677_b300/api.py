@@ -303,6 +303,65 @@ def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, hi
     return res[0] if len(res) == 1 else tuple(res)
 
 
+def _new_state(M: Matrix, nz: int, device) -> dict:
+    return {"r": torch.empty((nz, M.n_theta, M.n_p), device=device),
+            "p": torch.empty((nz, M.n_y, M.n_x), device=device),
+            "gamma": torch.empty(nz, device=device, dtype=torch.float64),
+            "frozen": torch.empty(nz, device=device, dtype=torch.int32)}
+
+
+def cgls_batched(requests, iters: int, batch_width: int = 16, fmt="sell", history: bool = False,
+                 timeout_s: float = 0.0, test_flags: int = 0, workspace: Optional[torch.Tensor] = None,
+                 resume=None, return_state: bool = False):
+    """CGLS for a list of (Matrix, sinogram stack) requests of uneven geometry
+    and slice count, all in one persistent launch.  Returns the list of
+    reconstructions, then (if history) the list of ||r|| histories
+    (iters, n_z), then (if return_state) the list of state dicts (with "x"),
+    which `resume` accepts back (one per request, or None)."""
+    reqs = (_lib.Request * len(requests))()
+    outs, hists, states, keep = [], [], [], []
+    for i, (M, sino) in enumerate(requests):
+        _check_tensor(sino, "sino")
+        nz = _nz(sino, M.rows, "sino")
+        rs = resume[i] if resume is not None else None
+        x = rs["x"].clone() if rs is not None else torch.empty((nz, M.n_y, M.n_x), device=sino.device)
+        h = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
+        reqs[i].A = M.handle.value
+        reqs[i].sino = sino.data_ptr()
+        reqs[i].x = x.data_ptr()
+        reqs[i].n_z = nz
+        reqs[i].resnorm_hist = 0 if h is None else h.data_ptr()
+        if rs is not None:
+            sin = _state_struct(rs)
+            keep.append(sin)
+            reqs[i].state_in = ctypes.pointer(sin)
+        if return_state:
+            st = _new_state(M, nz, sino.device)
+            sout = _state_struct(st)
+            keep.append(sout)
+            reqs[i].state_out = ctypes.pointer(sout)
+            states.append(st)
+        outs.append(x)
+        hists.append(h)
+    o = _exec(batch_width, True, fmt)
+    o.timeout_s = timeout_s
+    o.test_flags = test_flags
+    if workspace is None:
+        nb = ctypes.c_size_t()
+        _lib.call("tomo_cgls_batched_workspace", reqs, len(requests), ctypes.byref(o), ctypes.byref(nb))
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    _lib.call("tomo_cgls_batched", reqs, len(requests), iters, ctypes.byref(o), _ptr(workspace), workspace.numel(),
+              _stream())
+    res = [outs]
+    if history:
+        res.append([h[:iters] for h in hists])
+    if return_state:
+        for st, x in zip(states, outs):
+            st["x"] = x.clone()
+        res.append(states)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
 class TomoProject(torch.autograd.Function):
     """y = A x with the stored transpose as the backward: dL/dx = A^T dL/dy."""
 

@@ -208,6 +208,20 @@ tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t
                           workspace_bytes, stream);
 }
 
+tomo_status tomo_cgls_batched(const tomo_request *reqs, int32_t n_reqs, int32_t iters, const tomo_exec_opts *opts,
+                              void *workspace, size_t workspace_bytes, void *stream) {
+  if (!reqs || n_reqs < 1 || !reqs[0].A) return fail(TOMO_ERR_INVALID_ARG, "need at least one request");
+  if (workspace && !aligned16(workspace)) return fail(TOMO_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+  DeviceGuard dg(reqs[0].A->device);
+  return run_cgls_batched(reqs, n_reqs, iters, opts, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+tomo_status tomo_cgls_batched_workspace(const tomo_request *reqs, int32_t n_reqs, const tomo_exec_opts *opts,
+                                        size_t *bytes) {
+  if (!bytes) return fail(TOMO_ERR_INVALID_ARG, "bytes must be non-NULL");
+  return batched_workspace(reqs, n_reqs, opts, bytes);
+}
+
 tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo_exec_opts *best, double *rate,
                           tomo_tune_entry *table, int32_t cap, int32_t *n_table, void *stream) {
   if (!A || !best) return fail(TOMO_ERR_INVALID_ARG, "matrix and best must be non-NULL");

@@ -16,157 +16,44 @@
 #include <cstring>
 #include <vector>
 
-#include "internal.cuh"
+#include "spmm.cuh"
 
 namespace tomo {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 constexpr int kMinBlocks = 6;  // fallback resident blocks per SM when occupancy is unknown
 
 // ---------------------------------------------------------------------------
-// small vector helpers
+// SELL-32 kernels: grid-stride over row groups (see spmm.cuh)
 // ---------------------------------------------------------------------------
-template <int V>
-struct Vec {
-  float v[V];
-};
-
-template <int V>
-__device__ __forceinline__ Vec<V> ldg_vec(const float *p) {
-  Vec<V> r;
-  if constexpr (V == 4) {
-    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-  } else if constexpr (V == 2) {
-    float2 t = __ldg(reinterpret_cast<const float2 *>(p));
-    r.v[0] = t.x; r.v[1] = t.y;
-  } else {
-    r.v[0] = __ldg(p);
-  }
-  return r;
+template <int B, class Epi>
+__global__ void __launch_bounds__(kThreads) k_spmm_sell(const int64_t *__restrict__ cp,
+                                                        const int32_t *__restrict__ rl,
+                                                        const int2 *__restrict__ ent, int64_t rows,
+                                                        const float *__restrict__ X, Epi epi,
+                                                        double *__restrict__ part) {
+  constexpr int V = Lanes<B>::V, G = Lanes<B>::G, L = Lanes<B>::L;
+  double ss[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) ss[t] = 0.0;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  sell_rowgroups<B>(cp, rl, ent, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
+  if constexpr (Epi::kNorm) block_norms<V>(ss, ((threadIdx.x & 31) % L) * V, B, part);
 }
 
-template <int V>
-__device__ __forceinline__ Vec<V> ld_vec(const float *p) {
-  Vec<V> r;
-  if constexpr (V == 4) {
-    float4 t = *reinterpret_cast<const float4 *>(p);
-    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-  } else if constexpr (V == 2) {
-    float2 t = *reinterpret_cast<const float2 *>(p);
-    r.v[0] = t.x; r.v[1] = t.y;
-  } else {
-    r.v[0] = *p;
-  }
-  return r;
-}
-
-template <int V>
-__device__ __forceinline__ void st_vec(float *p, const Vec<V> &a) {
-  if constexpr (V == 4) {
-    *reinterpret_cast<float4 *>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
-  } else if constexpr (V == 2) {
-    *reinterpret_cast<float2 *>(p) = make_float2(a.v[0], a.v[1]);
-  } else {
-    *p = a.v[0];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Epilogues.  Called once per (row, lane) with the lane's V accumulated slices
-// starting at slice s0; `ss` collects per-slice squared norms when kNorm.
-// ---------------------------------------------------------------------------
-struct EpiStore {  // Y = acc
-  static constexpr bool kNorm = false;
-  float *Y;
-  int ld;
-  template <int V>
-  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
-    st_vec<V>(Y + row * ld + s0, a);
-  }
-};
-
-struct EpiSirtResidual {  // r = R o (b - acc)
-  static constexpr bool kNorm = false;
-  float *r;
-  const float *b, *R;
-  int ld;
-  template <int V>
-  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
-    float w = __ldg(R + row);
-    Vec<V> bv = ldg_vec<V>(b + row * ld + s0);
+template <int B, bool kBf16, bool kTrans, class Epi>
+__global__ void __launch_bounds__(kThreads) k_spmm_sell16(Sell16View M, int64_t rows, const float *__restrict__ X,
+                                                          Epi epi, double *__restrict__ part) {
+  constexpr int V = Lanes<B>::V, G = Lanes<B>::G, L = Lanes<B>::L;
+  double ss[V];
 #pragma unroll
-    for (int t = 0; t < V; ++t) a.v[t] = w * (bv.v[t] - a.v[t]);
-    st_vec<V>(r + row * ld + s0, a);
-  }
-};
-
-struct EpiSirtUpdate {  // x += lambda C o acc
-  static constexpr bool kNorm = false;
-  float *x;
-  const float *C;
-  float lam;
-  int ld;
-  template <int V>
-  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
-    float w = lam * __ldg(C + row);
-    Vec<V> xv = ld_vec<V>(x + row * ld + s0);
-#pragma unroll
-    for (int t = 0; t < V; ++t) xv.v[t] = fmaf(w, a.v[t], xv.v[t]);
-    st_vec<V>(x + row * ld + s0, xv);
-  }
-};
-
-struct EpiStoreNorm {  // Y = acc, ss += acc^2
-  static constexpr bool kNorm = true;
-  float *Y;
-  int ld;
-  template <int V>
-  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *ss) const {
-    st_vec<V>(Y + row * ld + s0, a);
-#pragma unroll
-    for (int t = 0; t < V; ++t) ss[t] += (double)a.v[t] * (double)a.v[t];
-  }
-};
-
-struct EpiResidualNorm {  // r = b - acc, ss += r^2
-  static constexpr bool kNorm = true;
-  float *r;
-  const float *b;
-  int ld;
-  template <int V>
-  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *ss) const {
-    Vec<V> bv = ldg_vec<V>(b + row * ld + s0);
-#pragma unroll
-    for (int t = 0; t < V; ++t) {
-      a.v[t] = bv.v[t] - a.v[t];
-      ss[t] += (double)a.v[t] * (double)a.v[t];
-    }
-    st_vec<V>(r + row * ld + s0, a);
-  }
-};
-
-// Deterministic per-block reduction of ss[V] (slices s0..s0+V-1 of each thread)
-// into part[blockIdx.x * B + s].
-template <int V>
-__device__ void block_norms(const double *ss, int s0, int B, double *part) {
-  __shared__ double red[kThreads][4];
-  __shared__ int red_s0[kThreads];
-#pragma unroll
-  for (int t = 0; t < V; ++t) red[threadIdx.x][t] = ss[t];
-  red_s0[threadIdx.x] = s0;
-  __syncthreads();
-  for (int s = threadIdx.x; s < B; s += blockDim.x) {
-    double acc = 0.0;
-    for (int t = 0; t < kThreads; ++t) {
-      int d = s - red_s0[t];
-      if (d >= 0 && d < V) acc += red[t][d];
-    }
-    part[(int64_t)blockIdx.x * B + s] = acc;
-  }
+  for (int t = 0; t < V; ++t) ss[t] = 0.0;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  sell16_rowgroups<B, kBf16, kTrans>(M, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
+  if constexpr (Epi::kNorm) block_norms<V>(ss, ((threadIdx.x & 31) % L) * V, B, part);
 }
 
 // ---------------------------------------------------------------------------
@@ -276,160 +163,6 @@ __global__ void __launch_bounds__(kThreads) k_spmv_f32(const int64_t *__restrict
     if (ok && p == 0) epi.template operator()<B>(row, 0, acc, ss);
   }
   if constexpr (Epi::kNorm) block_norms<B>(ss, 0, B, part);
-}
-
-// ---------------------------------------------------------------------------
-// SELL-32 SpMM (FP32 values).  V = min(B, 4) slices per lane, L = B/V lanes
-// per row, G = 32/L rows per warp; the G rows of a warp are adjacent rows of
-// one 32-row chunk, so each step loads one contiguous run of entry pairs
-// (128-bit per lane) for all of them.
-// ---------------------------------------------------------------------------
-template <int B, class Epi>
-__global__ void __launch_bounds__(kThreads) k_spmm_sell(const int64_t *__restrict__ cp,
-                                                        const int32_t *__restrict__ rl,
-                                                        const int2 *__restrict__ ent, int64_t rows,
-                                                        const float *__restrict__ X, Epi epi,
-                                                        double *__restrict__ part) {
-  constexpr int V = B >= 4 ? 4 : B;
-  constexpr int L = B / V, G = 32 / L;
-  const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const float *Xl = X + l * V;
-  double ss[V];
-#pragma unroll
-  for (int t = 0; t < V; ++t) ss[t] = 0.0;
-  for (int64_t rg = warp; rg * G < rows; rg += nwarps) {
-    const int64_t row = rg * G + g;
-    if (row >= rows) continue;
-    Vec<V> acc;
-#pragma unroll
-    for (int t = 0; t < V; ++t) acc.v[t] = 0.f;
-    const int len = __ldg(rl + row);
-    // entry pair (e, e+1), e even, of this row sits at p[(e/2)*32]
-    const int4 *p = reinterpret_cast<const int4 *>(ent) + (__ldg(cp + (row >> 5)) >> 1) + (row & 31);
-    int e = 0;
-    for (; e + 8 <= len; e += 8) {
-      int4 pr[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) pr[u] = __ldg(p + (size_t)((e >> 1) + u) * 32);
-      Vec<V> xv[8];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        xv[2 * u] = ldg_vec<V>(Xl + (size_t)pr[u].x * B);
-        xv[2 * u + 1] = ldg_vec<V>(Xl + (size_t)pr[u].z * B);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float w0 = __int_as_float(pr[u].y), w1 = __int_as_float(pr[u].w);
-#pragma unroll
-        for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w0, xv[2 * u].v[t], acc.v[t]);
-#pragma unroll
-        for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w1, xv[2 * u + 1].v[t], acc.v[t]);
-      }
-    }
-    for (; e < len; e += 2) {
-      const int4 pr = __ldg(p + (size_t)(e >> 1) * 32);
-      Vec<V> x0 = ldg_vec<V>(Xl + (size_t)pr.x * B);
-      const float w0 = __int_as_float(pr.y);
-#pragma unroll
-      for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w0, x0.v[t], acc.v[t]);
-      if (e + 1 < len) {
-        Vec<V> x1 = ldg_vec<V>(Xl + (size_t)pr.z * B);
-        const float w1 = __int_as_float(pr.w);
-#pragma unroll
-        for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w1, x1.v[t], acc.v[t]);
-      }
-    }
-    epi.template operator()<V>(row, l * V, acc, ss);
-  }
-  if constexpr (Epi::kNorm) block_norms<V>(ss, l * V, B, part);
-}
-
-// ---------------------------------------------------------------------------
-// 16-bit SELL-32 SpMM: bf16 / f16 weights times a per-angle FP32 scale, uint16
-// column offsets against a 32-bit base per 16-entry row segment.  Same lane
-// mapping as k_spmm_sell; a lane loads four entries per 128-bit load.  kTrans
-// selects A^T (scale of each gathered column's angle) versus A (scale of the
-// output row's angle).
-// ---------------------------------------------------------------------------
-template <bool kBf16>
-__device__ __forceinline__ float w16(uint32_t ow) {
-  if constexpr (kBf16) {
-    return __uint_as_float(ow & 0xffff0000u);
-  } else {
-    return __half2float(__ushort_as_half((unsigned short)(ow >> 16)));
-  }
-}
-
-// a / d for 0 <= a < 2^31 and small d: float estimate, then one exact correction
-__device__ __forceinline__ int div_exact(int a, int d, float inv_d) {
-  int q = (int)((float)a * inv_d);
-  if (q * d > a) --q;
-  else if ((q + 1) * d <= a) ++q;
-  return q;
-}
-
-template <int B, bool kBf16, bool kTrans, class Epi>
-__global__ void __launch_bounds__(kThreads) k_spmm_sell16(const int64_t *__restrict__ cpw,
-                                                          const int64_t *__restrict__ cpb,
-                                                          const int32_t *__restrict__ rl,
-                                                          const uint32_t *__restrict__ ow,
-                                                          const int32_t *__restrict__ base, int64_t rows,
-                                                          const float *__restrict__ scale, int np, float inv_np,
-                                                          const float *__restrict__ X, Epi epi,
-                                                          double *__restrict__ part) {
-  constexpr int V = B >= 4 ? 4 : B;
-  constexpr int L = B / V, G = 32 / L;
-  const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const float *Xl = X + l * V;
-  double ss[V];
-#pragma unroll
-  for (int t = 0; t < V; ++t) ss[t] = 0.0;
-  for (int64_t rg = warp; rg * G < rows; rg += nwarps) {
-    const int64_t row = rg * G + g;
-    if (row >= rows) continue;
-    Vec<V> acc;
-#pragma unroll
-    for (int t = 0; t < V; ++t) acc.v[t] = 0.f;
-    const int len = __ldg(rl + row);
-    const int64_t c = row >> 5;
-    const int q = (int)(row & 31);
-    const uint4 *pw = reinterpret_cast<const uint4 *>(ow + __ldg(cpw + c)) + q;  // quad e/4 at pw[(e/4)*32]
-    const int32_t *pb = base + __ldg(cpb + c) + q;                               // segment s at pb[s*32]
-    for (int s = 0; s * 16 < len; ++s) {
-      const int cb = __ldg(pb + (size_t)s * 32);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint4 a0 = __ldg(pw + (size_t)(4 * s + 2 * h) * 32);
-        const uint4 a1 = __ldg(pw + (size_t)(4 * s + 2 * h + 1) * 32);
-        const uint32_t pk[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        int cc[8];
-        Vec<V> xv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          cc[u] = cb + (int)(pk[u] & 0xffffu);
-          xv[u] = ldg_vec<V>(Xl + (size_t)cc[u] * B);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          float w = w16<kBf16>(pk[u]);
-          if constexpr (kTrans) w *= __ldg(scale + div_exact(cc[u], np, inv_np));
-#pragma unroll
-          for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w, xv[u].v[t], acc.v[t]);
-        }
-      }
-    }
-    if constexpr (!kTrans) {
-      const float sc = __ldg(scale + div_exact((int)row, np, inv_np));
-#pragma unroll
-      for (int t = 0; t < V; ++t) acc.v[t] *= sc;
-    }
-    epi.template operator()<V>(row, l * V, acc, ss);
-  }
-  if constexpr (Epi::kNorm) block_norms<V>(ss, l * V, B, part);
 }
 
 // ---------------------------------------------------------------------------
@@ -668,11 +401,11 @@ void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream
   } else if (op.format == TOMO_FMT_SELL16) {
     const SellLp &L = *op.lp;
     const float inv_np = 1.0f / (float)op.np;
-#define TOMO_SELL16(BF, TR)                                                                                \
-  do {                                                                                                     \
-    static const int res = resident_blocks(k_spmm_sell16<B, BF, TR, Epi>);                                 \
-    k_spmm_sell16<B, BF, TR, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(                          \
-        L.cpw, L.cpb, L.rl, L.ow, L.base, rows, op.scale, op.np, inv_np, X, epi, part);                    \
+    const Sell16View view{L.cpw, L.cpb, L.rl, L.ow, L.base, op.scale, op.np, inv_np};
+#define TOMO_SELL16(BF, TR)                                                                                    \
+  do {                                                                                                         \
+    static const int res = resident_blocks(k_spmm_sell16<B, BF, TR, Epi>);                                     \
+    k_spmm_sell16<B, BF, TR, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(view, rows, X, epi, part);    \
   } while (0)
     if (op.bf16) {
       if (op.trans) TOMO_SELL16(true, true);
