@@ -80,8 +80,10 @@ typedef struct {
  * 1.0, uint16 column offsets against a 32-bit base per 16 entries of a row)
  * that compute calls use when exec opts select TOMO_FMT_SELL16. */
 typedef struct {
-  int32_t values;   /* tomo_dtype */
-  int32_t reserved[7];
+  int32_t values;        /* tomo_dtype */
+  int32_t no_fp32_sell;  /* non-zero: skip the FP32 SELL-32 pair (saves ~8.4 B/nnz per operand when
+                            only the 16-bit or the CSR form will be streamed) */
+  int32_t reserved[6];
 } tomo_matrix_opts;
 
 /* Device time of the kernels one call launched, filled when a call is given

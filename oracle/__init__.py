@@ -58,6 +58,8 @@ def _load():
         lib.oracle_row.restype = _i64
         lib.oracle_weight.restype = _i32
         lib.oracle_loss_grad.restype = _dbl
+        lib.oracle_loss_grad_mf.restype = _dbl
+        lib.oracle_pixel_row.restype = _i64
         _lib = lib
     return _lib
 
@@ -180,6 +182,18 @@ def row(g: Geometry, i: int):
     return col[:n].copy(), val[:n].copy()
 
 
+def pixel_row(g: Geometry, j: int):
+    """Row j of A^T (one pixel): (ray indices int32, chord lengths float64)."""
+    cs, sn = g.trig()
+    cap = 2 * g.n_theta + 8
+    col = np.empty(cap, np.int32)
+    val = np.empty(cap, np.float64)
+    n = _load().oracle_pixel_row(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()), _p(cs), _p(sn),
+                                 _i64(int(j)), _p(col), _p(val), _i64(cap))
+    assert n <= cap
+    return col[:n].copy(), val[:n].copy()
+
+
 def project(A: CSR, x) -> np.ndarray:
     return A.apply(x)
 
@@ -250,6 +264,18 @@ def cgls_resume(A: CSR, AT: CSR, x, r, p, gamma, frozen, iters: int):
                                _p(AT.row_ptr), _p(AT.col), _p(AT.val), _i32(nz), _p(x), _p(r), _p(p),
                                _p(gamma), _p(frozen), _i32(iters), _p(hist))
     return x, r, p, gamma, frozen, hist[:iters]
+
+
+def loss_grad_mf(g: Geometry, x, b, mu: float = 1e-3, eps: float = 1e-3):
+    """loss_grad with the matrix-free projector pair (no stored matrix)."""
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, g.cols))
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1, g.rows))
+    nz = x.shape[0]
+    cs, sn = g.trig()
+    grad = np.empty_like(x)
+    f = _load().oracle_loss_grad_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()), _p(cs),
+                                    _p(sn), _i32(nz), _p(x), _p(b), _dbl(mu), _dbl(eps), _p(grad))
+    return float(f), grad
 
 
 def loss_grad(A: CSR, AT: CSR, nx: int, ny: int, x, b, mu: float = 1e-3, eps: float = 1e-3):

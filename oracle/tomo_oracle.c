@@ -173,6 +173,31 @@ int64_t oracle_row(int32_t nx, int32_t ny, int32_t np_, double c, double cs, dou
   return n;
 }
 
+/* One row of A^T (pixel j = iy*nx + ix): its rays (m, k) in increasing
+ * m*n_p + k with their chord lengths, from the same candidate bins as
+ * oracle_count.  Returns the entry count; writes at most cap entries. */
+int64_t oracle_pixel_row(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c, const double *cs,
+                         const double *sn, int64_t j, int32_t *col, double *val, int64_t cap) {
+  int32_t ix = (int32_t)(j % nx), iy = (int32_t)(j / nx);
+  int64_t n = 0;
+  for (int32_t m = 0; m < nt; ++m) {
+    int64_t k0;
+    candidate_bins(c, cs[m], sn[m], nx, ny, ix, iy, &k0);
+    for (int64_t k = k0; k < k0 + 5; ++k) {
+      double L;
+      if (k < 0 || k >= np_) continue;
+      if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L)) {
+        if (n < cap) {
+          col[n] = (int32_t)((int64_t)m * np_ + k);
+          val[n] = L;
+        }
+        ++n;
+      }
+    }
+  }
+  return n;
+}
+
 /* Plain CSR transpose (counting sort by column; rows of the result come out
  * with ascending column indices because source rows are scanned in order). */
 void oracle_transpose(int64_t rows, int64_t cols, const int64_t *rp, const int32_t *ci,
@@ -373,25 +398,11 @@ void oracle_cgls_resume(int64_t rows, int64_t cols,
   free(s);
 }
 
-/* Model-based objective of Sec. 2.1 with an unweighted norm and TV prior:
- *   f(x) = sum_s ||A x_s - b_s||^2 + mu * sum_s sum_pixels sqrt(Dx^2 + Dy^2 + eps^2),
- * Dx, Dy forward differences within the slice, 0 on the last column / row.
- * Returns f; grad (nz, cols) receives 2 A^T (A x - b) + mu * dTV/dx.
- * Pinned: central finite differences; TV value of hand-computed images. */
-double oracle_loss_grad(int64_t rows, int64_t cols,
-                        const int64_t *arp, const int32_t *aci, const double *av,
-                        const int64_t *trp, const int32_t *tci, const double *tv,
-                        int32_t nx, int32_t ny, int32_t nz, const double *x, const double *b,
-                        double mu, double eps, double *grad) {
-  double *r = (double *)malloc(sizeof(double) * rows * nz);
-  oracle_spmv(rows, cols, arp, aci, av, nz, x, r);
+/* TV term of the model-based objective: adds mu * sum sqrt(Dx^2 + Dy^2 + eps^2)
+ * over every slice to the returned value and its gradient to grad. */
+static double tv_add(int32_t nx, int32_t ny, int32_t nz, const double *x, double mu, double eps, double *grad) {
+  int64_t cols = (int64_t)nx * ny;
   double f = 0.0;
-  for (int64_t i = 0; i < rows * nz; ++i) {
-    r[i] -= b[i];
-    f += r[i] * r[i];
-  }
-  oracle_spmv(cols, rows, trp, tci, tv, nz, r, grad);
-  for (int64_t j = 0; j < cols * nz; ++j) grad[j] *= 2.0;
   for (int32_t s = 0; s < nz; ++s) {
     const double *u = x + (int64_t)s * cols;
     double *g = grad + (int64_t)s * cols;
@@ -413,6 +424,48 @@ double oracle_loss_grad(int64_t rows, int64_t cols,
         }
       }
   }
+  return f;
+}
+
+/* Model-based objective of Sec. 2.1 with an unweighted norm and TV prior:
+ *   f(x) = sum_s ||A x_s - b_s||^2 + mu * sum_s sum_pixels sqrt(Dx^2 + Dy^2 + eps^2),
+ * Dx, Dy forward differences within the slice, 0 on the last column / row.
+ * Returns f; grad (nz, cols) receives 2 A^T (A x - b) + mu * dTV/dx.
+ * Pinned: central finite differences; TV value of hand-computed images. */
+double oracle_loss_grad(int64_t rows, int64_t cols,
+                        const int64_t *arp, const int32_t *aci, const double *av,
+                        const int64_t *trp, const int32_t *tci, const double *tv,
+                        int32_t nx, int32_t ny, int32_t nz, const double *x, const double *b,
+                        double mu, double eps, double *grad) {
+  double *r = (double *)malloc(sizeof(double) * rows * nz);
+  oracle_spmv(rows, cols, arp, aci, av, nz, x, r);
+  double f = 0.0;
+  for (int64_t i = 0; i < rows * nz; ++i) {
+    r[i] -= b[i];
+    f += r[i] * r[i];
+  }
+  oracle_spmv(cols, rows, trp, tci, tv, nz, r, grad);
+  for (int64_t j = 0; j < cols * nz; ++j) grad[j] *= 2.0;
+  f += tv_add(nx, ny, nz, x, mu, eps, grad);
+  free(r);
+  return f;
+}
+
+/* The same objective and gradient with the matrix-free projector pair. */
+double oracle_loss_grad_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c, const double *cs,
+                           const double *sn, int32_t nz, const double *x, const double *b, double mu, double eps,
+                           double *grad) {
+  int64_t rows = (int64_t)nt * np_, cols = (int64_t)nx * ny;
+  double *r = (double *)malloc(sizeof(double) * rows * nz);
+  oracle_project_mf(nx, ny, np_, nt, c, cs, sn, nz, x, r);
+  double f = 0.0;
+  for (int64_t i = 0; i < rows * nz; ++i) {
+    r[i] -= b[i];
+    f += r[i] * r[i];
+  }
+  oracle_backproject_mf(nx, ny, np_, nt, c, cs, sn, nz, r, grad);
+  for (int64_t j = 0; j < cols * nz; ++j) grad[j] *= 2.0;
+  f += tv_add(nx, ny, nz, x, mu, eps, grad);
   free(r);
   return f;
 }

@@ -637,8 +637,10 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
 
   size_t freeb = 0, totalb = 0;
   TOMO_CUDA(cudaMemGetInfo(&freeb, &totalb));
-  // CSR pair (16 B/nnz) + SELL pair (~17 B/nnz) [+ 16-bit pair (~9.5 B/nnz)]
-  size_t need = (size_t)nnz_a * 34 + (size_t)(lp != TOMO_F32 ? nnz_a * 10 + (rows + cols) * 64 : 0);
+  // CSR pair (16 B/nnz) [+ SELL pair (~17 B/nnz)] [+ 16-bit pair (~9.5 B/nnz)]
+  const bool sell32 = !(o && o->no_fp32_sell);
+  size_t need = (size_t)nnz_a * (16 + (sell32 ? 18 : 0)) +
+                (size_t)(lp != TOMO_F32 ? nnz_a * 10 + (rows + cols) * 64 : 0);
   if (need + (size_t)(1ull << 30) > freeb)
     return fail(TOMO_ERR_OOM, "matrix needs " + std::to_string(need) + " bytes, device has " +
                                   std::to_string(freeb) + " free");
@@ -654,8 +656,10 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   TOMO_CUDA(cudaGetLastError());
   h->bytes_f32 = (rows + 1 + cols + 1) * 8 + nnz_a * 16;
 
-  TOMO_TRY(build_sell(h, false, st, cnt, part, scratch));
-  TOMO_TRY(build_sell(h, true, st, cnt, part, scratch));
+  if (!(o && o->no_fp32_sell)) {
+    TOMO_TRY(build_sell(h, false, st, cnt, part, scratch));
+    TOMO_TRY(build_sell(h, true, st, cnt, part, scratch));
+  }
   if (lp != TOMO_F32) {
     TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch));
     TOMO_TRY(build_sell16(h, true, st, cnt, part, scratch));

@@ -74,6 +74,7 @@ extern "C" tomo_status tomo_sirt_noalloc(const tomo_matrix *A, const float *sino
   if (n_z < 1 || iters < 0) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1 and iters >= 0");
   if (!std::isfinite(lambda))
     return fail(TOMO_ERR_INVALID_ARG, "lambda must be finite");
+  if (!A->sA.ent) return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without the FP32 SELL form");
   CurrentDevice cd(A->device);
   // widest batch (at most 16, at most the slice count) whose scratch fits
   Exec ex;

@@ -461,6 +461,8 @@ tomo_status check_requests(const tomo_request *reqs, int32_t n, int B, int fmt) 
         return fail(TOMO_ERR_INVALID_ARG, "a request's CGLS state has a NULL buffer");
     if (dev < 0) dev = q.A->device;
     if (q.A->device != dev) return fail(TOMO_ERR_INVALID_ARG, "all requests must live on one device");
+    if (fmt == TOMO_FMT_SELL && !q.A->sA.ent)
+      return fail(TOMO_ERR_UNSUPPORTED, "a matrix was built without the FP32 SELL form");
     if (fmt == TOMO_FMT_SELL16) {
       if (q.A->lp_dtype == TOMO_F32) return fail(TOMO_ERR_UNSUPPORTED, "a matrix was built without 16-bit values");
       if (lp == -2) lp = q.A->lp_dtype;

@@ -202,6 +202,29 @@ def test_adjoint_identity_fp64():
     assert abs(lhs - rhs) <= 1e-13 * abs(lhs) * 10
 
 
+def test_pixel_rows_are_the_transpose_rows():
+    g = oracle.Geometry(30, 26, 34, 19, center=16.4)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    for j in list(range(0, A.cols, 53)) + [0, A.cols - 1]:
+        c, v = oracle.pixel_row(g, j)
+        np.testing.assert_array_equal(c, AT.col[AT.row_ptr[j]:AT.row_ptr[j + 1]])
+        np.testing.assert_array_equal(v, AT.val[AT.row_ptr[j]:AT.row_ptr[j + 1]])
+
+
+def test_matrix_free_loss_grad_equals_stored():
+    g = oracle.Geometry(20, 20, 22, 15)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    rng = np.random.default_rng(21)
+    x = rng.random((2, A.cols))
+    b = rng.random((2, A.rows))
+    f1, g1 = oracle.loss_grad(A, AT, 20, 20, x, b)
+    f2, g2 = oracle.loss_grad_mf(g, x, b)
+    assert f1 == f2
+    np.testing.assert_array_equal(g1, g2)
+
+
 def test_matrix_free_equals_stored():
     g = oracle.Geometry(33, 33, 35, 21, center=17.2)
     A = oracle.build_matrix(g)
