@@ -166,6 +166,11 @@ __device__ void block_norms(const double *ss, int s0, int B, double *part) {
   block_norms_to<V>(ss, s0, B, part + (int64_t)blockIdx.x * B);
 }
 
+// Every SELL entry word is loaded exactly once per pass (one 128-bit load per
+// pair or quad), so those loads carry the streaming (evict-first) hint and
+// leave L2 to the gathered operand vector, which the whole pass reuses.  (The
+// CSR kernels read each sector of indices with several loads and keep the
+// default policy.)
 // ---------------------------------------------------------------------------
 // SELL-32 row groups (FP32 values).  V = min(B, 4) slices per lane, L = B/V
 // lanes per row, G = 32/L rows per warp; the G rows of a warp are adjacent
@@ -211,7 +216,7 @@ __device__ __forceinline__ void sell_rowgroups(const int64_t *__restrict__ cp, c
     for (; e + 8 <= len; e += 8) {
       int4 pr[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pr[u] = __ldg(p + (size_t)((e >> 1) + u) * 32);
+      for (int u = 0; u < 4; ++u) pr[u] = __ldcs(p + (size_t)((e >> 1) + u) * 32);
       Vec<V> xv[8];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -228,7 +233,7 @@ __device__ __forceinline__ void sell_rowgroups(const int64_t *__restrict__ cp, c
       }
     }
     for (; e < len; e += 2) {
-      const int4 pr = __ldg(p + (size_t)(e >> 1) * 32);
+      const int4 pr = __ldcs(p + (size_t)(e >> 1) * 32);
       Vec<V> x0 = gather<V, kNC>(Xl + (size_t)pr.x * B);
       const float w0 = __int_as_float(pr.y);
 #pragma unroll
@@ -296,11 +301,11 @@ __device__ __forceinline__ void sell16_rowgroups(const Sell16View &M, int64_t ro
     const uint4 *pw = reinterpret_cast<const uint4 *>(M.ow + __ldg(M.cpw + c)) + q;  // quad e/4 at pw[(e/4)*32]
     const int32_t *pb = M.base + __ldg(M.cpb + c) + q;                               // segment s at pb[s*32]
     for (int s = 0; s * 16 < len; ++s) {
-      const int cb = __ldg(pb + (size_t)s * 32);
+      const int cb = __ldcs(pb + (size_t)s * 32);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const uint4 a0 = __ldg(pw + (size_t)(4 * s + 2 * h) * 32);
-        const uint4 a1 = __ldg(pw + (size_t)(4 * s + 2 * h + 1) * 32);
+        const uint4 a0 = __ldcs(pw + (size_t)(4 * s + 2 * h) * 32);
+        const uint4 a1 = __ldcs(pw + (size_t)(4 * s + 2 * h + 1) * 32);
         const uint32_t pk[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         int cc[8];
         Vec<V> xv[8];
