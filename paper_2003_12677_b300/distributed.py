@@ -1,0 +1,71 @@
+"""Slice distribution over processes (one GPU each), following Sec. 3.1.
+
+Slices are independent, so ranks need no exchange while they iterate.  The
+paper's rule: a process handles at most `chunk` slices per loop; when the
+stack holds more slices than all processes can take at once, every process
+loops over similar-size chunks, and only the last loop chunk is split
+unequally, with the last ranks receiving one slice less than the first ones.
+
+`slice_plan` gives each rank's slice ranges; `gather_slices` collects the
+per-rank results on rank 0 through torch.distributed (NCCL for CUDA tensors,
+gloo for CPU tensors).  Each rank builds its own copy of the projector: the
+build is deterministic, so every replica is bit-identical.
+"""
+from __future__ import annotations
+
+from typing import List, Optional, Tuple
+
+import torch
+import torch.distributed as dist
+
+
+def slice_plan(n_z: int, world: int, chunk: Optional[int] = None) -> List[List[Tuple[int, int]]]:
+    """Per-rank lists of [begin, end) slice ranges, one range per loop.
+
+    chunk: at most this many slices per rank per loop (None: one loop)."""
+    if n_z < 0 or world < 1:
+        raise ValueError("n_z >= 0 and world >= 1 required")
+    per = max(1, -(-n_z // world)) if chunk is None else int(chunk)
+    if per < 1:
+        raise ValueError("chunk must be >= 1")
+    plan: List[List[Tuple[int, int]]] = [[] for _ in range(world)]
+    start = 0
+    while start < n_z:
+        rem = n_z - start
+        if rem >= per * world:
+            sizes = [per] * world
+        else:
+            # last loop: split the remainder as evenly as possible, the first
+            # ranks taking one slice more than the last ones
+            q, r = divmod(rem, world)
+            sizes = [q + (1 if k < r else 0) for k in range(world)]
+        for k, sz in enumerate(sizes):
+            if sz > 0:
+                plan[k].append((start, start + sz))
+            start += sz
+    return plan
+
+
+def rank_slices(n_z: int, world: int, rank: int, chunk: Optional[int] = None) -> List[int]:
+    """Flat list of the slice indices one rank owns."""
+    return [s for b, e in slice_plan(n_z, world, chunk)[rank] for s in range(b, e)]
+
+
+def gather_slices(local: torch.Tensor, n_z: int, chunk: Optional[int] = None, dst: int = 0) -> Optional[torch.Tensor]:
+    """Assemble (n_z, ...) on rank `dst` from each rank's (n_local, ...) results
+    (ordered like rank_slices).  Other ranks return None."""
+    world, rank = dist.get_world_size(), dist.get_rank()
+    owned = [rank_slices(n_z, world, k, chunk) for k in range(world)]
+    tail = tuple(local.shape[1:])
+    maxn = max(len(o) for o in owned)
+    pad = torch.zeros((maxn,) + tail, dtype=local.dtype, device=local.device)
+    pad[: local.shape[0]] = local
+    bufs = [torch.empty_like(pad) for _ in range(world)] if rank == dst else None
+    dist.gather(pad, bufs, dst=dst)
+    if rank != dst:
+        return None
+    out = torch.empty((n_z,) + tail, dtype=local.dtype, device=local.device)
+    for k in range(world):
+        for i, s in enumerate(owned[k]):
+            out[s] = bufs[k][i]
+    return out
