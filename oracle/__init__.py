@@ -48,11 +48,25 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_variant(source: str, out_path: str) -> str:
+    """Compile a modified copy of the oracle source (used by the mutation
+    tests, which plant mistakes and check that the pins catch them)."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+                           "-ffp-contract=off", "-fno-fast-math", src, "-o", out_path, "-lm"])
+    return out_path
+
+
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        path = os.environ.get("TOMO_ORACLE_LIB")  # mutation tests load a planted variant
+        if not path:
+            build()
+            path = _LIB
+        lib = ctypes.CDLL(path)
         lib.oracle_threads.restype = _i32
         lib.oracle_count.restype = _i64
         lib.oracle_row.restype = _i64

@@ -1,0 +1,57 @@
+"""Strength of the oracle's pins: plant one plausible mistake at a time in a
+copy of the oracle source (a transposed operand, a wrong sign, a dropped
+term, a wrong index) and check that the pin suite fails on every mutant."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "tomo_oracle.c")
+
+MUTANTS = {
+    "chord: transposed cos/sin": ("double t = x * cs + y * sn;", "double t = x * sn + y * cs;"),
+    "bin centre: wrong sign of c": ("double pk = ((double)k + 0.5) - c;", "double pk = ((double)k + 0.5) + c;"),
+    "plateau: 1/e for 1/a": ("*len = 1.0 / a;", "*len = 1.0 / e;"),
+    "ramp: a+e for a*e": ("*len = (h - del) / (a * e);", "*len = (h - del) / (a + e);"),
+    "half width: a-e for a+e": ("double h = 0.5 * (a + e);", "double h = 0.5 * (a - e);"),
+    "column index transposed": ("col[e] = iy * nx + ix;", "col[e] = ix * ny + iy;"),
+    "SIRT: row weights R dropped": ("r[s * rows + i] = R[i] * (b[s * rows + i] - r[s * rows + i]);",
+                                   "r[s * rows + i] = (b[s * rows + i] - r[s * rows + i]);"),
+    "SIRT: relaxation lambda dropped": ("x[s * cols + j] += lambda * C[j] * g[s * cols + j];",
+                                       "x[s * cols + j] += C[j] * g[s * cols + j];"),
+    "SIRT: column weights C dropped": ("x[s * cols + j] += lambda * C[j] * g[s * cols + j];",
+                                      "x[s * cols + j] += lambda * g[s * cols + j];"),
+    "CGLS: beta inverted": ("double beta = gnew / *gamma;", "double beta = *gamma / gnew;"),
+    "CGLS: residual update sign": ("for (int64_t i = 0; i < rows; ++i) r[i] -= alpha * q[i];",
+                                  "for (int64_t i = 0; i < rows; ++i) r[i] += alpha * q[i];"),
+    "TV gradient: neighbour sign": ("g[j + nx] += mu * dy / t;", "g[j + nx] -= mu * dy / t;"),
+    "transpose: wrong row index": ("tci[d] = (int32_t)i;", "tci[d] = (int32_t)(rows - 1 - i);"),
+    "normaliser: sum for 1/sum": ("out[i] = s != 0.0 ? 1.0 / s : 0.0;", "out[i] = s != 0.0 ? s : 0.0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    before, after = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(before) == 1, name
+    lib = oracle.build_variant(src.replace(before, after), str(tmp_path / "liboracle_mutant.so"))
+    env = dict(os.environ, TOMO_ORACLE_LIB=lib, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        "-x", "-q", "-p", "no:cacheprovider"], env=env, capture_output=True, text=True,
+                       cwd=ROOT, timeout=600)
+    assert r.returncode != 0, "pins did not catch: " + name
+
+
+def test_unmutated_variant_passes(tmp_path):
+    """Control: the same build-and-run path with the source unchanged passes."""
+    lib = oracle.build_variant(open(SRC).read(), str(tmp_path / "liboracle_same.so"))
+    env = dict(os.environ, TOMO_ORACLE_LIB=lib, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        "-q", "-p", "no:cacheprovider"], env=env, capture_output=True, text=True, cwd=ROOT,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:]
