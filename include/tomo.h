@@ -83,7 +83,10 @@ typedef struct {
   int32_t values;        /* tomo_dtype */
   int32_t no_fp32_sell;  /* non-zero: skip the FP32 SELL-32 pair (saves ~8.4 B/nnz per operand when
                             only the 16-bit or the CSR form will be streamed) */
-  int32_t reserved[6];
+  int32_t drop_csr;      /* non-zero: free the CSR pair once the SELL forms are built (saves 8 B/nnz
+                            per operand); export calls and TOMO_FMT_CSR then report UNSUPPORTED.
+                            Needs at least one SELL form. */
+  int32_t reserved[5];
 } tomo_matrix_opts;
 
 /* Device time of the kernels one call launched, filled when a call is given

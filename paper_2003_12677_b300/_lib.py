@@ -34,7 +34,8 @@ class Geometry(ctypes.Structure):
 
 
 class MatrixOpts(ctypes.Structure):
-    _fields_ = [("values", ctypes.c_int32), ("no_fp32_sell", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("values", ctypes.c_int32), ("no_fp32_sell", ctypes.c_int32), ("drop_csr", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class Timing(ctypes.Structure):

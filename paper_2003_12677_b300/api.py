@@ -68,11 +68,13 @@ class Matrix:
     n_x = n_y = n unless given; n_p defaults to n; angles (radians) default to
     m*pi/n_theta; center defaults to n_p/2.  values in {"f32", "bf16", "f16"}
     also builds the 16-bit encoding used with fmt="sell16"; fp32_sell=False
-    skips the FP32 SELL-32 copy (memory for very large geometries).
+    skips the FP32 SELL-32 copy and keep_csr=False frees the CSR pair after
+    the SELL forms are built (memory for very large geometries).
     """
 
     def __init__(self, n: int, n_theta: int, n_p: Optional[int] = None, n_y: Optional[int] = None,
-                 angles=None, center: Optional[float] = None, values: str = "f32", fp32_sell: bool = True):
+                 angles=None, center: Optional[float] = None, values: str = "f32", fp32_sell: bool = True,
+                 keep_csr: bool = True):
         self._h = None
         lib = _lib.load()
         if not torch.cuda.is_available():
@@ -95,6 +97,7 @@ class Matrix:
         o = _lib.MatrixOpts()
         o.values = _lib.DTYPES[values]
         o.no_fp32_sell = 0 if fp32_sell else 1
+        o.drop_csr = 0 if keep_csr else 1
         h = ctypes.c_void_p()
         _lib.check(lib.tomo_build_matrix(ctypes.byref(g), ctypes.byref(o), _stream(), ctypes.byref(h)),
                    "tomo_build_matrix")

@@ -88,6 +88,7 @@ tomo_status tomo_matrix_export_rows(const tomo_matrix *A, int32_t transpose, int
   const Csr &M = transpose ? A->AT : A->A;
   if (row_begin < 0 || row_end < row_begin || row_end > M.rows)
     return fail(TOMO_ERR_INVALID_ARG, "row range out of bounds");
+  if (!M.ci) return fail(TOMO_ERR_UNSUPPORTED, "matrix was built with drop_csr: nothing to export");
   DeviceGuard dg(A->device);
   const int64_t n = row_end - row_begin;
   if (cudaMemcpy(row_ptr, M.rp + row_begin, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -547,6 +547,8 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   int32_t lp = o ? o->values : TOMO_F32;
   if (lp != TOMO_F32 && lp != TOMO_BF16 && lp != TOMO_F16)
     return fail(TOMO_ERR_INVALID_ARG, "opts.values must be TOMO_F32, TOMO_BF16 or TOMO_F16");
+  if (o && o->drop_csr && o->no_fp32_sell && lp == TOMO_F32)
+    return fail(TOMO_ERR_INVALID_ARG, "drop_csr needs a SELL form (FP32 SELL or 16-bit values)");
   double c = std::isnan(g->center) ? 0.5 * (double)g->n_p : g->center;
   if (!std::isfinite(c)) return fail(TOMO_ERR_INVALID_ARG, "center must be finite or NaN");
   const int nt = g->n_theta;
@@ -666,6 +668,13 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   }
   TOMO_CUDA(cudaMemcpyAsync(hs, scratch, sizeof(hs), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));
+  if (o && o->drop_csr) {
+    for (void **p : {(void **)&h->A.ci, (void **)&h->A.v, (void **)&h->AT.ci, (void **)&h->AT.v}) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    h->bytes_f32 -= nnz_a * 16;
+  }
   if (hs[0] == 2)
     return fail(TOMO_ERR_UNSUPPORTED, "a 16-entry chunk spans more than 65535 columns (geometry too large "
                                       "for 16-bit offsets)");

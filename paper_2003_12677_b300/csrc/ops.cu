@@ -843,6 +843,8 @@ tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t 
     return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without 16-bit values");
   if (e.format == TOMO_FMT_SELL && !h->sA.ent)
     return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without the FP32 SELL form (no_fp32_sell)");
+  if (e.format == TOMO_FMT_CSR && !h->A.ci)
+    return fail(TOMO_ERR_UNSUPPORTED, "matrix was built with drop_csr");
   *ex = e;
   return TOMO_OK;
 }
@@ -959,9 +961,11 @@ tomo_status run_autotune(tomo_matrix *h, int32_t nz, bool allow16, tomo_exec_opt
                          tomo_tune_entry *table, int32_t cap, int32_t *n_table, cudaStream_t st) {
   int bmax = 1;
   while (bmax < nz && bmax < 64) bmax <<= 1;
+  if (!h->sA.ent && !h->A.ci && !(allow16 && h->lp_dtype != TOMO_F32))
+    return fail(TOMO_ERR_UNSUPPORTED, "no FP32 form to tune (built with no_fp32_sell and drop_csr)");
   std::vector<int> fmts;
   if (h->sA.ent) fmts.push_back(TOMO_FMT_SELL);
-  fmts.push_back(TOMO_FMT_CSR);
+  if (h->A.ci) fmts.push_back(TOMO_FMT_CSR);
   if (allow16 && h->lp_dtype != TOMO_F32) fmts.push_back(TOMO_FMT_SELL16);
   const int64_t rows = h->A.rows, cols = h->A.cols;
   float *x = nullptr, *r = nullptr, *b = nullptr;

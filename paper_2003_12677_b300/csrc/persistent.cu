@@ -49,7 +49,7 @@ struct PBatch {
   const int2 *entA, *entT;
   Sell16View lA, lT;
   int64_t rows, cols;
-  float *b, *x, *r, *q, *p, *s;
+  float *x, *r, *q, *p, *s;
   double *scal;                      // B x 8
   double *part_q, *part_r, *part_s;  // items x B
   int32_t itemA0, nitemA, itemT0, nitemT;
@@ -122,8 +122,8 @@ __device__ bool grid_barrier(const PPlan &P) {
   return s_ok != 0;
 }
 
-// The SpMM gathers use coherent loads (kNC = false); the epilogues read only
-// b (written in the first phase, then constant) and never gathered data.
+// The SpMM gathers use coherent loads (kNC = false); the epilogues of this
+// kernel read nothing but their own output row.
 template <int B, int kFmt, bool kTrans, class Epi>
 __device__ void spmm_item(const PBatch &bt, const PItem &it, const float *X, const Epi &epi, double *ss) {
   const int64_t w = threadIdx.x >> 5;
@@ -157,27 +157,23 @@ __device__ double batch_sum(const double *part, int nitem, int B, int s) {
   return r;
 }
 
-template <int B, int kFmt>
-__global__ void __launch_bounds__(kThreads) k_cgls_persistent(PPlan P) {
-  constexpr int V = Lanes<B>::V, L = Lanes<B>::L, PER = B / V;
-  const int lane_s0 = ((threadIdx.x & 31) % L) * V;  // slice offset of this lane in SpMM phases
+// Each phase is its own non-inlined function: the kernel's register budget is
+// then set by the busiest phase (an SpMM) rather than by everything the
+// phases would keep live across each other if inlined into one body.
+
+// layout in: fresh slices r = b (the sinogram), x = 0; resumed slices x, r, p
+// from the caller
+template <int B>
+__device__ __noinline__ void ph_layout_in(const PPlan &P) {
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  const int nbp = P.nbatch * B;  // (batch, slice) pairs
-
-  if ((int)blockIdx.x == P.skip_block) return;  // test hook: a block that never arrives
-
-  // ---- layout in: b from the requests; fresh slices r = b, x = 0; resumed
-  // slices x, r and p from the caller -----------------------------------------
   for (int bi = 0; bi < P.nbatch; ++bi) {
     const PBatch &bt = P.batches[bi];
     const PSlot *sl = P.slots + (int64_t)bi * B;
     for (int64_t e = gtid; e < bt.rows * B; e += gthreads) {
       const int64_t i = e / B;
       const int s = (int)(e % B);
-      const float v = sl[s].sino ? sl[s].sino[i] : 0.f;
-      bt.b[e] = v;
-      bt.r[e] = sl[s].resume ? sl[s].r_in[i] : v;
+      bt.r[e] = sl[s].resume ? sl[s].r_in[i] : (sl[s].sino ? sl[s].sino[i] : 0.f);
     }
     for (int64_t e = gtid; e < bt.cols * B; e += gthreads) {
       const int64_t j = e / B;
@@ -186,22 +182,37 @@ __global__ void __launch_bounds__(kThreads) k_cgls_persistent(PPlan P) {
       if (sl[s].resume) bt.p[e] = sl[s].p_in[j];
     }
   }
-  if (!grid_barrier(P)) return;
+}
 
-  // ---- s = A^T r, ||s||^2 ---------------------------------------------------
-  for (int it = blockIdx.x; it < P.nitemT; it += gridDim.x) {
-    const PItem &item = P.itemsT[it];
+// SpMM over every batch's items: out = M X with per-item norm partials;
+// kTrans: A^T (T items, X = r, out = s) else A (A items, X = p, out = q)
+template <int B, int kFmt, bool kTrans>
+__device__ __noinline__ void ph_spmm(const PPlan &P) {
+  constexpr int V = Lanes<B>::V, L = Lanes<B>::L;
+  const int lane_s0 = ((threadIdx.x & 31) % L) * V;
+  const int nitem = kTrans ? P.nitemT : P.nitemA;
+  for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+    const PItem &item = kTrans ? P.itemsT[it] : P.itemsA[it];
     const PBatch &bt = P.batches[item.batch];
     double ss[V];
 #pragma unroll
     for (int t = 0; t < V; ++t) ss[t] = 0.0;
-    spmm_item<B, kFmt, true>(bt, item, bt.r, EpiStoreNorm{bt.s, B}, ss);
-    block_norms_to<V>(ss, lane_s0, B, bt.part_s + (int64_t)(it - bt.itemT0) * B);
+    if constexpr (kTrans) {
+      spmm_item<B, kFmt, true>(bt, item, bt.r, EpiStoreNorm{bt.s, B}, ss);
+      block_norms_to<V>(ss, lane_s0, B, bt.part_s + (int64_t)(it - bt.itemT0) * B);
+    } else {
+      spmm_item<B, kFmt, false>(bt, item, bt.p, EpiStoreNorm{bt.q, B}, ss);
+      block_norms_to<V>(ss, lane_s0, B, bt.part_q + (int64_t)(it - bt.itemA0) * B);
+    }
   }
-  if (!grid_barrier(P)) return;
+}
 
-  // ---- gamma = ||s||^2, p = s (resumed slices: gamma, frozen from the state) --
-  for (int pr = blockIdx.x; pr < nbp; pr += gridDim.x) {
+// gamma = ||s||^2 (resumed slices: gamma, frozen from the state), p = s
+template <int B>
+__device__ __noinline__ void ph_init_scalars(const PPlan &P) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int pr = blockIdx.x; pr < P.nbatch * B; pr += gridDim.x) {
     const PBatch &bt = P.batches[pr / B];
     const int s = pr % B;
     const PSlot &sl = P.slots[pr];
@@ -219,123 +230,109 @@ __global__ void __launch_bounds__(kThreads) k_cgls_persistent(PPlan P) {
     for (int64_t e = gtid; e < bt.cols * B; e += gthreads)
       if (!sl[e % B].resume) bt.p[e] = bt.s[e];
   }
-  if (!grid_barrier(P)) return;
+}
 
-  for (int iter = 0; iter < P.iters; ++iter) {
-    // ---- q = A p, ||q||^2 ----------------------------------------------------
-    for (int it = blockIdx.x; it < P.nitemA; it += gridDim.x) {
-      const PItem &item = P.itemsA[it];
-      const PBatch &bt = P.batches[item.batch];
-      double ss[V];
-#pragma unroll
-      for (int t = 0; t < V; ++t) ss[t] = 0.0;
-      spmm_item<B, kFmt, false>(bt, item, bt.p, EpiStoreNorm{bt.q, B}, ss);
-      block_norms_to<V>(ss, lane_s0, B, bt.part_q + (int64_t)(it - bt.itemA0) * B);
+// alpha = gamma / ||q||^2
+template <int B>
+__device__ __noinline__ void ph_alpha(const PPlan &P) {
+  for (int pr = blockIdx.x; pr < P.nbatch * B; pr += gridDim.x) {
+    const PBatch &bt = P.batches[pr / B];
+    const int s = pr % B;
+    const double qq = batch_sum(bt.part_q, bt.nitemA, B, s);
+    if (threadIdx.x == 0) {
+      const double gam = bt.scal[s * 8 + 0];
+      const bool frozen = bt.scal[s * 8 + 3] != 0.0 || gam == 0.0 || qq == 0.0;
+      bt.scal[s * 8 + 3] = frozen ? 1.0 : 0.0;
+      bt.scal[s * 8 + 1] = frozen ? 0.0 : gam / qq;
     }
-    if (!grid_barrier(P)) return;
-
-    // ---- alpha = gamma / ||q||^2 -----------------------------------------------
-    for (int pr = blockIdx.x; pr < nbp; pr += gridDim.x) {
-      const PBatch &bt = P.batches[pr / B];
-      const int s = pr % B;
-      const double qq = batch_sum(bt.part_q, bt.nitemA, B, s);
-      if (threadIdx.x == 0) {
-        const double gam = bt.scal[s * 8 + 0];
-        const bool frozen = bt.scal[s * 8 + 3] != 0.0 || gam == 0.0 || qq == 0.0;
-        bt.scal[s * 8 + 3] = frozen ? 1.0 : 0.0;
-        bt.scal[s * 8 + 1] = frozen ? 0.0 : gam / qq;
-      }
-    }
-    if (!grid_barrier(P)) return;
-
-    // ---- r -= alpha q (A items, ||r||^2 partials); x += alpha p (T items) ------
-    for (int it = blockIdx.x; it < P.nitemA + P.nitemT; it += gridDim.x) {
-      const bool onA = it < P.nitemA;
-      const PItem &item = onA ? P.itemsA[it] : P.itemsT[it - P.nitemA];
-      const PBatch &bt = P.batches[item.batch];
-      const int64_t n = onA ? bt.rows : bt.cols;
-      constexpr int G = Lanes<B>::G;
-      const int64_t e0 = item.rg0 * G * PER, e1 = std::min<int64_t>(item.rg1 * G, n) * PER;  // vector index range
-      // this thread's slice offset must be fixed: kThreads is a multiple of PER
-      const int s0 = (int)((threadIdx.x % PER) * V);
-      float al[V];
-#pragma unroll
-      for (int t = 0; t < V; ++t) al[t] = (float)bt.scal[(s0 + t) * 8 + 1];
-      double ss[V];
-#pragma unroll
-      for (int t = 0; t < V; ++t) ss[t] = 0.0;
-      for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-        if (onA) {
-          Vec<V> rv = ld_vec<V>(bt.r + i * V), qv = ld_vec<V>(bt.q + i * V);
-#pragma unroll
-          for (int t = 0; t < V; ++t) {
-            rv.v[t] = fmaf(-al[t], qv.v[t], rv.v[t]);
-            ss[t] += (double)rv.v[t] * (double)rv.v[t];
-          }
-          st_vec<V>(bt.r + i * V, rv);
-        } else {
-          Vec<V> xv = ld_vec<V>(bt.x + i * V), pv = ld_vec<V>(bt.p + i * V);
-#pragma unroll
-          for (int t = 0; t < V; ++t) xv.v[t] = fmaf(al[t], pv.v[t], xv.v[t]);
-          st_vec<V>(bt.x + i * V, xv);
-        }
-      }
-      if (onA) block_norms_to<V>(ss, s0, B, bt.part_r + (int64_t)(it - bt.itemA0) * B);
-    }
-    if (!grid_barrier(P)) return;
-
-    // ---- s = A^T r, ||s||^2 ----------------------------------------------------
-    for (int it = blockIdx.x; it < P.nitemT; it += gridDim.x) {
-      const PItem &item = P.itemsT[it];
-      const PBatch &bt = P.batches[item.batch];
-      double ss[V];
-#pragma unroll
-      for (int t = 0; t < V; ++t) ss[t] = 0.0;
-      spmm_item<B, kFmt, true>(bt, item, bt.r, EpiStoreNorm{bt.s, B}, ss);
-      block_norms_to<V>(ss, lane_s0, B, bt.part_s + (int64_t)(it - bt.itemT0) * B);
-    }
-    if (!grid_barrier(P)) return;
-
-    // ---- beta = gamma'/gamma, residual history ----------------------------------
-    for (int pr = blockIdx.x; pr < nbp; pr += gridDim.x) {
-      const PBatch &bt = P.batches[pr / B];
-      const int s = pr % B;
-      const double gs = batch_sum(bt.part_s, bt.nitemT, B, s);
-      const double rr = batch_sum(bt.part_r, bt.nitemA, B, s);
-      if (threadIdx.x == 0) {
-        if (bt.scal[s * 8 + 3] != 0.0) {
-          bt.scal[s * 8 + 2] = 0.0;
-        } else {
-          bt.scal[s * 8 + 2] = gs / bt.scal[s * 8 + 0];
-          bt.scal[s * 8 + 0] = gs;
-        }
-        const PSlot &sl = P.slots[(int64_t)(pr / B) * B + s];
-        if (sl.sino && sl.hist) sl.hist[(int64_t)iter * sl.hist_ld] = sqrt(rr);
-      }
-    }
-    if (!grid_barrier(P)) return;
-
-    // ---- p = s + beta p -----------------------------------------------------------
-    for (int it = blockIdx.x; it < P.nitemT; it += gridDim.x) {
-      const PItem &item = P.itemsT[it];
-      const PBatch &bt = P.batches[item.batch];
-      constexpr int G = Lanes<B>::G;
-      const int64_t e0 = item.rg0 * G * PER, e1 = std::min<int64_t>(item.rg1 * G, bt.cols) * PER;
-      const int s0 = (int)((threadIdx.x % PER) * V);
-      float be[V];
-#pragma unroll
-      for (int t = 0; t < V; ++t) be[t] = (float)bt.scal[(s0 + t) * 8 + 2];
-      for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
-        Vec<V> pv = ld_vec<V>(bt.p + i * V), sv = ld_vec<V>(bt.s + i * V);
-#pragma unroll
-        for (int t = 0; t < V; ++t) pv.v[t] = fmaf(be[t], pv.v[t], sv.v[t]);
-        st_vec<V>(bt.p + i * V, pv);
-      }
-    }
-    if (!grid_barrier(P)) return;
   }
+}
 
-  // ---- layout out: x (and the state, where asked) to the requests ------------
+// r -= alpha q (A items, ||r||^2 partials); x += alpha p (T items)
+template <int B>
+__device__ __noinline__ void ph_step(const PPlan &P) {
+  constexpr int V = Lanes<B>::V, G = Lanes<B>::G, PER = B / V;
+  for (int it = blockIdx.x; it < P.nitemA + P.nitemT; it += gridDim.x) {
+    const bool onA = it < P.nitemA;
+    const PItem &item = onA ? P.itemsA[it] : P.itemsT[it - P.nitemA];
+    const PBatch &bt = P.batches[item.batch];
+    const int64_t n = onA ? bt.rows : bt.cols;
+    const int64_t e0 = item.rg0 * G * PER, e1 = std::min<int64_t>(item.rg1 * G, n) * PER;  // vector indices
+    // this thread's slice offset is fixed: kThreads is a multiple of PER
+    const int s0 = (int)((threadIdx.x % PER) * V);
+    float al[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) al[t] = (float)bt.scal[(s0 + t) * 8 + 1];
+    double ss[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) ss[t] = 0.0;
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+      if (onA) {
+        Vec<V> rv = ld_vec<V>(bt.r + i * V), qv = ld_vec<V>(bt.q + i * V);
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+          rv.v[t] = fmaf(-al[t], qv.v[t], rv.v[t]);
+          ss[t] += (double)rv.v[t] * (double)rv.v[t];
+        }
+        st_vec<V>(bt.r + i * V, rv);
+      } else {
+        Vec<V> xv = ld_vec<V>(bt.x + i * V), pv = ld_vec<V>(bt.p + i * V);
+#pragma unroll
+        for (int t = 0; t < V; ++t) xv.v[t] = fmaf(al[t], pv.v[t], xv.v[t]);
+        st_vec<V>(bt.x + i * V, xv);
+      }
+    }
+    if (onA) block_norms_to<V>(ss, s0, B, bt.part_r + (int64_t)(it - bt.itemA0) * B);
+  }
+}
+
+// beta = gamma'/gamma, residual history
+template <int B>
+__device__ __noinline__ void ph_beta(const PPlan &P, int iter) {
+  for (int pr = blockIdx.x; pr < P.nbatch * B; pr += gridDim.x) {
+    const PBatch &bt = P.batches[pr / B];
+    const int s = pr % B;
+    const double gs = batch_sum(bt.part_s, bt.nitemT, B, s);
+    const double rr = batch_sum(bt.part_r, bt.nitemA, B, s);
+    if (threadIdx.x == 0) {
+      if (bt.scal[s * 8 + 3] != 0.0) {
+        bt.scal[s * 8 + 2] = 0.0;
+      } else {
+        bt.scal[s * 8 + 2] = gs / bt.scal[s * 8 + 0];
+        bt.scal[s * 8 + 0] = gs;
+      }
+      const PSlot &sl = P.slots[pr];
+      if (sl.sino && sl.hist) sl.hist[(int64_t)iter * sl.hist_ld] = sqrt(rr);
+    }
+  }
+}
+
+// p = s + beta p
+template <int B>
+__device__ __noinline__ void ph_direction(const PPlan &P) {
+  constexpr int V = Lanes<B>::V, G = Lanes<B>::G, PER = B / V;
+  for (int it = blockIdx.x; it < P.nitemT; it += gridDim.x) {
+    const PItem &item = P.itemsT[it];
+    const PBatch &bt = P.batches[item.batch];
+    const int64_t e0 = item.rg0 * G * PER, e1 = std::min<int64_t>(item.rg1 * G, bt.cols) * PER;
+    const int s0 = (int)((threadIdx.x % PER) * V);
+    float be[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) be[t] = (float)bt.scal[(s0 + t) * 8 + 2];
+    for (int64_t i = e0 + threadIdx.x; i < e1; i += blockDim.x) {
+      Vec<V> pv = ld_vec<V>(bt.p + i * V), sv = ld_vec<V>(bt.s + i * V);
+#pragma unroll
+      for (int t = 0; t < V; ++t) pv.v[t] = fmaf(be[t], pv.v[t], sv.v[t]);
+      st_vec<V>(bt.p + i * V, pv);
+    }
+  }
+}
+
+// layout out: x (and the state, where asked) to the requests
+template <int B>
+__device__ __noinline__ void ph_layout_out(const PPlan &P) {
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   for (int bi = 0; bi < P.nbatch; ++bi) {
     const PBatch &bt = P.batches[bi];
     const PSlot *sl = P.slots + (int64_t)bi * B;
@@ -354,6 +351,32 @@ __global__ void __launch_bounds__(kThreads) k_cgls_persistent(PPlan P) {
       if (sl[s].f_out) *sl[s].f_out = bt.scal[s * 8 + 3] != 0.0 ? 1 : 0;
     }
   }
+}
+
+template <int B, int kFmt>
+__global__ void __launch_bounds__(kThreads) k_cgls_persistent(PPlan P) {
+  if ((int)blockIdx.x == P.skip_block) return;  // test hook: a block that never arrives
+  ph_layout_in<B>(P);
+  if (!grid_barrier(P)) return;
+  ph_spmm<B, kFmt, true>(P);  // s = A^T r, ||s||^2
+  if (!grid_barrier(P)) return;
+  ph_init_scalars<B>(P);  // gamma, p = s
+  if (!grid_barrier(P)) return;
+  for (int iter = 0; iter < P.iters; ++iter) {
+    ph_spmm<B, kFmt, false>(P);  // q = A p, ||q||^2
+    if (!grid_barrier(P)) return;
+    ph_alpha<B>(P);
+    if (!grid_barrier(P)) return;
+    ph_step<B>(P);  // r -= alpha q, x += alpha p
+    if (!grid_barrier(P)) return;
+    ph_spmm<B, kFmt, true>(P);  // s = A^T r, ||s||^2
+    if (!grid_barrier(P)) return;
+    ph_beta<B>(P, iter);
+    if (!grid_barrier(P)) return;
+    ph_direction<B>(P);  // p = s + beta p
+    if (!grid_barrier(P)) return;
+  }
+  ph_layout_out<B>(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -434,7 +457,7 @@ tomo_status plan_layout(const tomo_request *reqs, int32_t n, int B, Layout *L) {
     for (int64_t rg = 0; rg < rgT; rg += kItemRowGroups)
       L->itemsT.push_back(PItem{(int32_t)bi, 0, rg, std::min<int64_t>(rg + kItemRowGroups, rgT)});
     const int64_t nA = L->itemsA.size() - L->itemA0.back(), nT = L->itemsT.size() - L->itemT0.back();
-    bytes += 3 * align256(sizeof(float) * rows * B) + 3 * align256(sizeof(float) * cols * B) +
+    bytes += 2 * align256(sizeof(float) * rows * B) + 3 * align256(sizeof(float) * cols * B) +
              align256(sizeof(double) * B * 8) + 2 * align256(sizeof(double) * nA * B) +
              align256(sizeof(double) * nT * B);
   }
@@ -562,7 +585,6 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
     b.itemT0 = L.itemT0[bi];
     b.nitemA = (int32_t)((bi + 1 < L.batches.size() ? L.itemA0[bi + 1] : (int32_t)L.itemsA.size()) - b.itemA0);
     b.nitemT = (int32_t)((bi + 1 < L.batches.size() ? L.itemT0[bi + 1] : (int32_t)L.itemsT.size()) - b.itemT0);
-    b.b = (float *)take(sizeof(float) * b.rows * B);
     b.r = (float *)take(sizeof(float) * b.rows * B);
     b.q = (float *)take(sizeof(float) * b.rows * B);
     b.x = (float *)take(sizeof(float) * b.cols * B);

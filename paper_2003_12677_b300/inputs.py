@@ -222,6 +222,10 @@ def workload_case(name: str, slices: Optional[Sequence[int]] = None) -> Case:
     return make_case(w.n, w.n_theta, w.n_z, w.seed, w.phantom, w.noise, w.noise_level, slices)
 
 
+WORKLOADS["uneven_256"] = Workload("uneven_256", 2048, 1024, 0, "cgls", 30, "poisson", 1e5, "ellipses2d",
+                                  values="bf16", seed=12677 + 5)
+
+
 @dataclasses.dataclass
 class Request:
     n: int

@@ -349,6 +349,19 @@ def test_autotune_choice_is_used_by_default():
     assert per_slice_rel(auto.cpu().numpy(), ref).max() < 1e-4
 
 
+def test_drop_csr_keeps_sell_paths():
+    g, A, AT, M0 = pair(nx=64, nt=90)
+    M = tomo.Matrix(64, 90, keep_csr=False)
+    x = inputs.random_slices((3, 64, 64), seed=61)
+    y = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=4).cpu().numpy()
+    assert per_slice_rel(y, A.apply(x)).max() < 1e-5
+    with pytest.raises(_lib.TomoError):
+        M.export_csr()
+    with pytest.raises(_lib.TomoError):
+        tomo.project(M, torch.from_numpy(x).cuda(), fmt="csr")
+    assert M.autotune(3)["format"] == "sell"
+
+
 def test_errors_are_reported():
     with pytest.raises(_lib.TomoError):
         tomo.Matrix(0, 10)
