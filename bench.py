@@ -174,7 +174,7 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    res = oracle_sample(w, slices=1, iters=1, steps=args.steps, warmup=args.warmup)
+    res = oracle_sample(w, slices=4, iters=2, steps=args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * res["seconds"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -358,6 +358,40 @@ def run_alternate(args, w):
     return 0
 
 
+def cusparse_leg(M, B, torch):
+    """The paper's GPU path as context: the same A and A^T (exported CSR) as
+    torch sparse CSR tensors, y = A x and x' = A^T y through cuSPARSE SpMM
+    (torch.sparse.mm) at batch width B and as SpMV (width 1).  No solver
+    update is included, which favours this leg slightly."""
+    def csr(transpose):
+        rp, col, val = M.export_csr(transpose=transpose)
+        n = len(rp) - 1
+        return torch.sparse_csr_tensor(torch.from_numpy(rp.astype("int32")), torch.from_numpy(col),
+                                       torch.from_numpy(val), size=(n, M.rows if transpose else M.cols)).cuda()
+
+    A, AT = csr(False), csr(True)
+    out = {"unit": UNIT, "form": "torch.sparse.mm on CSR (cuSPARSE SpMM / SpMV), A and A^T stored"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for width, reps in ((B, 10), (1, 10)):
+        x = torch.rand((M.cols, width), device="cuda")
+        for _ in range(3):
+            y = torch.sparse.mm(A, x)
+            x = torch.sparse.mm(AT, y)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            y = torch.sparse.mm(A, x)
+            x = torch.sparse.mm(AT, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["value" if width == B else "value_width1"] = width / (ms / 1000.0)
+        out["batch_width" if width == B else "spmv_width"] = width
+    del A, AT
+    torch.cuda.empty_cache()
+    return out
+
+
 def kernel_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2003_12677_b300", "csrc")
@@ -485,6 +519,20 @@ def main():
                         "frac": achieved / peak, "traffic": traffic, "peak_source": src + " (burst copy)",
                         "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
                         "kernel_share": tm.ms[kind] / max(sum(tm.ms[k] for k in range(3)), 1e-12)}
+    # the two on-chip ceilings beside HBM: gathered-operand delivery (each
+    # nonzero brings B*4 bytes of the gathered vector row through L1, at most
+    # 128 B per clock per SM) and FP32 FMA (2 flops per nonzero per slice)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 2032.0
+    gathered = nnz * B * 4
+    line["ceilings"] = {
+        "operand_delivery": {"achieved": gathered / (avg_ms / 1000.0) / 1e9, "unit": "GB/s",
+                             "peak": sms * 128 * mhz * 1e6 / 1e9, "bytes_per_launch": gathered,
+                             "peak_source": "128 B/clk/SM x %d SMs x median SM clock" % sms},
+        "fma": {"achieved": 2.0 * nnz * B / (avg_ms / 1000.0) / 1e12, "unit": "TFLOP/s",
+                "peak": sms * 128 * 2 * mhz * 1e6 / 1e12, "peak_source": "128 FP32 FMA/clk/SM"}}
+    for c in line["ceilings"].values():
+        c["frac"] = c["achieved"] / c["peak"]
     step_bytes = w.iters * ((rows + cols + 2) * 8 + 2 * nnz * bnnz
                             + (3 * rows + 3 * cols) * B * 4) * math.ceil(w.n_z / B)
     line["hbm_gbs_step"] = step_bytes / (ms / 1000.0) / 1e9
@@ -528,10 +576,14 @@ def main():
                                  "form": "FP32 CSR SpMV (batch width 1, warp per row)",
                                  "sample": "%d slices x %d SIRT iterations" % (nzp, itp)}
         line["speedup_vs_plain_f32_csr"] = value / line["plain_f32_csr"]["value"]
+        try:
+            line["cusparse_f32_csr"] = cusparse_leg(M, B, torch)
+        except Exception as e:  # context only, never fatal for the GPU number
+            line["cusparse_f32_csr"] = {"error": str(e)}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = oracle_sample(w, slices=1, iters=2, steps=1)
+            line["cpu_baseline"] = oracle_sample(w, slices=4, iters=16, steps=1)
         except Exception as e:  # reported, never fatal for the GPU number
             line["cpu_baseline"] = {"error": str(e)}
 

@@ -119,7 +119,11 @@ typedef struct {
   int32_t test_flags;  /* test hook, 0 in normal use.  bit 0: in tomo_cgls_batched one block of
                           the persistent launch never arrives at a grid barrier, so the others
                           wait out timeout_s and the call returns TOMO_ERR_TIMEOUT */
-  int32_t reserved[3];
+  int32_t async;       /* tomo_cgls_batched: non-zero returns once the launch is queued, without
+                          synchronising; the launch's device status then goes to the stream's
+                          status word (tomo_stream_status).  Sinograms, tomograms, states and
+                          the workspace must stay valid until the stream passes the launch. */
+  int32_t reserved[2];
 } tomo_exec_opts;
 
 typedef struct tomo_matrix tomo_matrix; /* opaque, immutable after build */
@@ -268,7 +272,9 @@ typedef struct {
  * launch is cooperative (every block resident), the barriers are bounded: a
  * wait that runs out stops every block and the call returns TOMO_ERR_TIMEOUT.
  * Workspace as tomo_cgls_batched_workspace reports (NULL: allocated by the
- * call).  Synchronises `stream`. */
+ * call, stream-ordered).  Synchronises `stream` and returns the launch's
+ * status, unless opts->async is set: then it returns after queueing and the
+ * status is read later with tomo_stream_status. */
 TOMO_API tomo_status tomo_cgls_batched(const tomo_request *reqs, int32_t n_reqs, int32_t iters,
                                        const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes,
                                        void *stream);
@@ -313,6 +319,17 @@ TOMO_API tomo_status tomo_cgls_resume(const tomo_matrix *A, const float *sino, f
                                       const tomo_cgls_state *in, tomo_cgls_state *out,
                                       const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes,
                                       void *stream);
+
+/* Device-side status of `stream` (a stream of the CURRENT device; NULL = the
+ * legacy default stream).  Calls queued without synchronising (tomo_cgls_batched
+ * with opts->async) record the status of their bounded waits in one status
+ * word per (device, stream) that the library keeps.  This call synchronises
+ * the stream, returns the first non-OK status recorded since the previous
+ * tomo_stream_status on it (TOMO_ERR_TIMEOUT: a grid-barrier wait ran out and
+ * the launch stopped early, its outputs incomplete) and resets the word; it
+ * returns TOMO_ERR_CUDA when the synchronisation itself reports an error.
+ * The word is allocated (4 bytes) on first use and kept until process exit. */
+TOMO_API tomo_status tomo_stream_status(void *stream);
 
 /* Human-readable name of a status code (static string). */
 TOMO_API const char *tomo_status_string(tomo_status s);

@@ -18,7 +18,7 @@ SLICE_MAJOR, INTERLEAVED = 0, 1
 EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
            "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
            "tomo_sirt", "tomo_cgls", "tomo_cgls_resume", "tomo_cgls_batched", "tomo_cgls_batched_workspace",
-           "tomo_sirt_noalloc", "tomo_autotune",
+           "tomo_sirt_noalloc", "tomo_autotune", "tomo_stream_status",
            "tomo_status_string", "tomo_last_error"]
 
 
@@ -46,7 +46,7 @@ class ExecOpts(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("format", ctypes.c_int32), ("timeout_s", ctypes.c_float),
                 ("timing", ctypes.POINTER(Timing)), ("test_flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("async_", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
                                         ctypes.POINTER(SZ)],
         "tomo_autotune": [P, I32, I32, ctypes.POINTER(ExecOpts), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(TuneEntry), I32, ctypes.POINTER(I32), P],
+        "tomo_stream_status": [P],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -120,6 +121,10 @@ def check(code: int, func: str):
     if code != TOMO_OK:
         msg = _lib.tomo_last_error().decode() if _lib is not None else ""
         raise TomoError(code, func, msg)
+
+
+def status_name(code: int) -> str:
+    return load().tomo_status_string(code).decode()
 
 
 def call(name: str, *args):

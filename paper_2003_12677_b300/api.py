@@ -317,12 +317,19 @@ def _new_state(M: Matrix, nz: int, device) -> dict:
 
 def cgls_batched(requests, iters: int, batch_width: int = 16, fmt="sell", history: bool = False,
                  timeout_s: float = 0.0, test_flags: int = 0, workspace: Optional[torch.Tensor] = None,
-                 resume=None, return_state: bool = False):
+                 resume=None, return_state: bool = False, asynchronous: bool = False):
     """CGLS for a list of (Matrix, sinogram stack) requests of uneven geometry
     and slice count, all in one persistent launch.  Returns the list of
     reconstructions, then (if history) the list of ||r|| histories
     (iters, n_z), then (if return_state) the list of state dicts (with "x"),
-    which `resume` accepts back (one per request, or None)."""
+    which `resume` accepts back (one per request, or None).
+
+    asynchronous: return once the launch is queued on the current stream; its
+    device status is read later with `stream_status()`.  The returned tensors
+    are valid once the stream passes the launch (torch's stream semantics);
+    the inputs and the workspace must be kept alive until then (the caching
+    allocator keeps them when they stay referenced, or when they were allocated
+    on this stream)."""
     reqs = (_lib.Request * len(requests))()
     outs, hists, states, keep = [], [], [], []
     for i, (M, sino) in enumerate(requests):
@@ -351,6 +358,7 @@ def cgls_batched(requests, iters: int, batch_width: int = 16, fmt="sell", histor
     o = _exec(batch_width, True, fmt)
     o.timeout_s = timeout_s
     o.test_flags = test_flags
+    o.async_ = 1 if asynchronous else 0
     if workspace is None:
         nb = ctypes.c_size_t()
         _lib.call("tomo_cgls_batched_workspace", reqs, len(requests), ctypes.byref(o), ctypes.byref(nb))
@@ -365,6 +373,15 @@ def cgls_batched(requests, iters: int, batch_width: int = 16, fmt="sell", histor
             st["x"] = x.clone()
         res.append(states)
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def stream_status(stream: Optional[torch.cuda.Stream] = None) -> str:
+    """Synchronise `stream` (default: torch's current stream) and return the
+    name of the first device status recorded on it since the last call
+    ("TOMO_OK", or e.g. "TOMO_ERR_TIMEOUT" from an asynchronous batched
+    launch whose bounded barrier wait ran out); the word is reset."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _lib.status_name(_lib.load().tomo_stream_status(ctypes.c_void_p(s.cuda_stream)))
 
 
 class TomoProject(torch.autograd.Function):

@@ -136,6 +136,10 @@ tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t 
                      int32_t recompute, double *hist, const tomo_cgls_state *in, tomo_cgls_state *out,
                      const Exec &ex, void *ws, cudaStream_t st);
 tomo_status batched_workspace(const tomo_request *reqs, int32_t n, const tomo_exec_opts *o, size_t *bytes);
+// per-stream status word (status.cu)
+int *stream_status_word(cudaStream_t st);
+tomo_status fold_status(const int *src, cudaStream_t st);
+tomo_status read_stream_status(cudaStream_t st);
 tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters, const tomo_exec_opts *o,
                              void *ws, size_t ws_bytes, cudaStream_t st);
 tomo_status run_autotune(tomo_matrix *h, int32_t nz, bool allow16, tomo_exec_opts *best, double *rate,

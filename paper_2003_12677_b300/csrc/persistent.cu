@@ -632,6 +632,7 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
     default: s = launch_fmt<32>(plan, fmt, lp_dtype, st); break;
   }
   TOMO_TRY(s);
+  if (o && o->async) return fold_status(&bar->status, st);  // read later by tomo_stream_status
   int status = 0;
   TOMO_CUDA(cudaMemcpyAsync(&status, &bar->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));

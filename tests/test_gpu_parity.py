@@ -277,6 +277,30 @@ def test_cgls_batched_barrier_timeout_is_reported():
     assert per_slice_rel(xs[0].cpu().numpy(), ref).max() < 1e-4
 
 
+def test_cgls_batched_async_status_word():
+    """Asynchronous batched launches: the call returns once queued; the
+    stream's status word then reads TOMO_OK for a normal launch (whose result
+    equals the synchronous one bit for bit) and TOMO_ERR_TIMEOUT for a launch
+    in which one block never arrives; reading the word resets it."""
+    reqs, refs = _uneven_case()
+    assert tomo.stream_status() == "TOMO_OK"
+    ref_xs = tomo.cgls_batched(reqs[:3], 5, batch_width=8)
+    xs = tomo.cgls_batched(reqs[:3], 5, batch_width=8, asynchronous=True)
+    assert tomo.stream_status() == "TOMO_OK"
+    for x, r in zip(xs, ref_xs):
+        assert torch.equal(x, r)
+    tomo.cgls_batched(reqs[:2], 3, batch_width=4, timeout_s=0.05, test_flags=1, asynchronous=True)
+    assert tomo.stream_status() == "TOMO_ERR_TIMEOUT"
+    assert tomo.stream_status() == "TOMO_OK"
+    # a side stream keeps a word of its own
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        tomo.cgls_batched(reqs[:2], 3, batch_width=4, timeout_s=0.05, test_flags=1, asynchronous=True)
+    assert tomo.stream_status() == "TOMO_OK"
+    assert tomo.stream_status(side) == "TOMO_ERR_TIMEOUT"
+
+
 def test_cgls_zero_sinogram_is_frozen():
     g, A, AT, M = pair(nx=64, nt=90)
     z = torch.zeros((3, 90, 64), device="cuda")
