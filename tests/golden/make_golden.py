@@ -27,7 +27,7 @@ CASES = {
     # non-square grid, odd detector, shifted axis, user angles (one negative, one past pi)
     "rect_7x5_9_shifted": dict(nx=7, ny=5, n_p=9, n_theta=5, angles=[-0.3, 0.0, 0.7, 1.9, 3.3], center=3.7),
 }
-SIRT_ITERS, CGLS_ITERS, SLICES = 10, 6, 2
+SIRT_ITERS, CGLS_ITERS, SLICES = 10, 4, 2
 
 
 def make(name, spec):
