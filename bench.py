@@ -583,7 +583,7 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = oracle_sample(w, slices=4, iters=16, steps=1)
+            line["cpu_baseline"] = oracle_sample(w, slices=8, iters=48, steps=1)
         except Exception as e:  # reported, never fatal for the GPU number
             line["cpu_baseline"] = {"error": str(e)}
 
