@@ -12,6 +12,10 @@ Function map (paper: "Sparse Matrix-Based HPC Tomography"):
   project_mf / backproject_mf   the same without storing A
   sirt / cgls       Sec. 2.1 iterative solvers (classical SIRT, textbook CGLS)
   loss_grad         Sec. 2.1 model-based objective with a TV prior
+  ramp_response / ramp_filter   Sec. 2.1 preconditioner P = F^dagger D^(1/2) F
+                    along the detector, D a Hamming-windowed ramp
+  sirt_bb / sirt_bb_resume      Sec. 3.1 SIRT with that preconditioning and the
+                    Barzilai-Borwein step; its first step is FBP (Sec. 2.1)
 """
 from __future__ import annotations
 
@@ -302,3 +306,101 @@ def loss_grad(A: CSR, AT: CSR, nx: int, ny: int, x, b, mu: float = 1e-3, eps: fl
                                  _p(AT.row_ptr), _p(AT.col), _p(AT.val), _i32(nx), _i32(ny),
                                  _i32(nz), _p(x), _p(b), _dbl(mu), _dbl(eps), _p(g))
     return float(f), g
+
+
+# ---------------------------------------------------------------------------
+# Preconditioned SIRT with the Barzilai-Borwein step (Sec. 3.1; objective of
+# Sec. 2.1).  The filter is written in the Fourier domain exactly as the
+# preconditioner is defined (zero-pad, FFT, multiply by D, inverse FFT, crop);
+# numpy's FFT serves as the library step.
+# ---------------------------------------------------------------------------
+def ramp_pad(n_p: int) -> int:
+    """Padded length N: the smallest power of two >= 2 n_p (no wrap-around)."""
+    n = 1
+    while n < 2 * n_p:
+        n *= 2
+    return n
+
+
+def ramp_response(n_p: int, window: bool = True) -> np.ndarray:
+    """D on the N-point DFT grid (real, even).  D = R * w: R is the DFT of the
+    band-limited ramp's sampled kernel (1/4 at 0, -1/(pi n)^2 at odd n, 0 at
+    even n, truncated to |n| < N/2), w the Hamming window 0.54 + 0.46 cos(2 pi f)
+    at frequency f = min(k, N - k)/N cycles per bin (1 at DC, 0.08 at Nyquist)."""
+    N = ramp_pad(n_p)
+    n = np.arange(N)
+    n = np.where(n < N // 2, n, n - N)          # signed tap index
+    h = np.zeros(N)
+    h[n == 0] = 0.25
+    odd = (n % 2) != 0
+    h[odd] = -1.0 / (math.pi * n[odd]) ** 2
+    R = np.fft.fft(h).real
+    if not window:
+        return R
+    f = np.abs(n) / N
+    return R * (0.54 + 0.46 * np.cos(2.0 * math.pi * f))
+
+
+def ramp_filter(y, n_p: int, D: Optional[np.ndarray] = None) -> np.ndarray:
+    """P^T P y = F^dagger D F y for every projection row (length n_p) of y
+    (nz, n_theta * n_p): zero-pad to N, DFT, multiply by D, inverse DFT, crop."""
+    D = ramp_response(n_p) if D is None else D
+    N = D.shape[0]
+    y = np.asarray(y, np.float64)
+    nz = y.reshape(-1, y.shape[-1]).shape[0]
+    rows = y.reshape(nz, -1, n_p)
+    pad = np.zeros(rows.shape[:2] + (N,))
+    pad[..., :n_p] = rows
+    out = np.fft.ifft(np.fft.fft(pad, axis=-1) * D, axis=-1).real[..., :n_p]
+    return out.reshape(nz, -1)
+
+
+def sirt_bb_resume(A: CSR, AT: CSR, n_p: int, b, x, g_prev, alpha_prev, frozen, iters: int,
+                   first_step: Optional[float] = None, D: Optional[np.ndarray] = None):
+    """Continue preconditioned BB-SIRT from a state.  Per slice, iteration k:
+        r  = b - A x                        (its norm is hist[k])
+        gn = A^T P^T P r                    (= -grad of 1/2 ||P (A x - b)||^2)
+        alpha = first_step                  when there is no previous step (g_prev None)
+              = <s,s>/<s,y> (BB1) with s = alpha_prev g_prev, y = -(gn - g_prev)
+        x  = x + alpha gn
+    A slice is frozen (alpha = 0 from then on) when <s,s> or <s,y> is not
+    positive.  Returns (x, gn, alpha, frozen, hist (iters, nz)), all FP64."""
+    b = np.asarray(b, np.float64).reshape(-1, A.rows)
+    nz = b.shape[0]
+    x = np.array(x, np.float64).reshape(nz, A.cols)
+    D = ramp_response(n_p) if D is None else D
+    alpha = np.array(alpha_prev, np.float64).reshape(nz) if alpha_prev is not None else np.zeros(nz)
+    frozen = np.array(frozen, bool).reshape(nz) if frozen is not None else np.zeros(nz, bool)
+    gp = None if g_prev is None else np.array(g_prev, np.float64).reshape(nz, A.cols)
+    n_theta = A.rows // n_p
+    a0 = math.pi / n_theta if first_step is None else float(first_step)
+    hist = np.zeros((iters, nz))
+    for k in range(iters):
+        r = b - project(A, x)
+        hist[k] = np.sqrt(np.einsum("ij,ij->i", r, r))
+        gn = backproject(AT, ramp_filter(r, n_p, D))
+        for s in range(nz):
+            if frozen[s]:
+                a = 0.0
+            elif gp is None:
+                a = a0
+            else:
+                ss = alpha[s] * alpha[s] * float(np.dot(gp[s], gp[s]))
+                sy = -alpha[s] * float(np.dot(gp[s], gn[s] - gp[s]))
+                if ss > 0.0 and sy > 0.0:
+                    a = ss / sy
+                else:
+                    a, frozen[s] = 0.0, True
+            x[s] += a * gn[s]
+            alpha[s] = a
+        gp = gn
+    return x, gp, alpha, frozen, hist
+
+
+def sirt_bb(A: CSR, AT: CSR, n_p: int, b, iters: int, first_step: Optional[float] = None,
+            D: Optional[np.ndarray] = None):
+    """BB-SIRT from x0 = 0: returns (x (nz, cols), hist (iters, nz) of ||b - A x_k||)."""
+    b = np.asarray(b, np.float64).reshape(-1, A.rows)
+    x0 = np.zeros((b.shape[0], A.cols))
+    x, _, _, _, hist = sirt_bb_resume(A, AT, n_p, b, x0, None, None, None, iters, first_step, D)
+    return x, hist

@@ -55,3 +55,46 @@ def test_unmutated_variant_passes(tmp_path):
                         "-q", "-p", "no:cacheprovider"], env=env, capture_output=True, text=True, cwd=ROOT,
                        timeout=600)
     assert r.returncode == 0, r.stdout[-2000:]
+
+
+# Mistakes planted in the Python half of the oracle (the preconditioned BB-SIRT
+# of Sec. 3.1 and its filter): a mutated copy of the package is put first on
+# the path, with the unmodified C library.
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
+PY_MUTANTS = {
+    "BB: first step not the FBP weight": ("a0 = math.pi / n_theta if first_step is None",
+                                          "a0 = 1.0 / n_theta if first_step is None"),
+    "BB: step along the gradient": ("x[s] += a * gn[s]", "x[s] -= a * gn[s]"),
+    "BB: BB1 ratio inverted": ("a = ss / sy", "a = sy / ss"),
+    "BB: sign of y": ("sy = -alpha[s] * float(np.dot(gp[s], gn[s] - gp[s]))",
+                      "sy = alpha[s] * float(np.dot(gp[s], gn[s] - gp[s]))"),
+    "filter: Hamming window dropped": ("return R * (0.54 + 0.46 * np.cos(2.0 * math.pi * f))", "return R"),
+    "filter: odd ramp taps positive": ("h[odd] = -1.0 / (math.pi * n[odd]) ** 2",
+                                       "h[odd] = 1.0 / (math.pi * n[odd]) ** 2"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_catch_planted_python_mistake(name, tmp_path):
+    before, after = PY_MUTANTS[name]
+    src = open(PY_SRC).read()
+    assert src.count(before) == 1, name
+    r = _run_python_variant(tmp_path, src.replace(before, after))
+    assert r.returncode != 0, "pins did not catch: " + name
+
+
+def _run_python_variant(tmp_path, source):
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    (pkg / "__init__.py").write_text(source)
+    (pkg / "tomo_oracle.c").write_text(open(SRC).read())
+    env = dict(os.environ, TOMO_ORACLE_LIB=oracle.build(), PYTHONPATH=str(tmp_path) + os.pathsep + ROOT)
+    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                           "-x", "-q", "-p", "no:cacheprovider", "-k", "bb or ramp or ramlak"], env=env,
+                          capture_output=True, text=True, cwd=str(tmp_path), timeout=600)
+
+
+def test_unmutated_python_variant_passes(tmp_path):
+    """Control: the copied package, unchanged, passes the same pins."""
+    r = _run_python_variant(tmp_path, open(PY_SRC).read())
+    assert r.returncode == 0, r.stdout[-2000:]

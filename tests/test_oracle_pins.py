@@ -398,3 +398,121 @@ def test_gradient_finite_differences():
         fd = (fp - fm) / (2 * h)
         an = float(np.sum(grad * v))
         assert abs(fd - an) <= 1e-7 * max(1.0, abs(an))
+
+
+# ---------------------------------------------------------------------------
+# preconditioned SIRT with the Barzilai-Borwein step (Sec. 3.1 / Sec. 2.1)
+# ---------------------------------------------------------------------------
+
+def ramlak(n):
+    """Band-limited ramp sampled at unit spacing (Kak & Slaney, Ch. 3):
+    1/4 at 0, 0 at even n, -1/(pi n)^2 at odd n."""
+    if n == 0:
+        return 0.25
+    return 0.0 if n % 2 == 0 else -1.0 / (math.pi * n) ** 2
+
+
+@pytest.mark.parametrize("n_p", [8, 13, 64])
+def test_unwindowed_filter_is_the_ramlak_convolution(n_p):
+    """Without the window, filtering a unit impulse at bin j gives the sampled
+    band-limited ramp h[k - j] at every bin k (closed form, no wrap-around)."""
+    D = oracle.ramp_response(n_p, window=False)
+    for j in (0, n_p // 2, n_p - 1):
+        y = np.zeros((1, n_p))
+        y[0, j] = 1.0
+        out = oracle.ramp_filter(y, n_p, D)[0]
+        ref = np.array([ramlak(k - j) for k in range(n_p)])
+        np.testing.assert_allclose(out, ref, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n_p", [8, 100, 512])
+def test_ramp_response_is_a_ramp_with_hamming_ends(n_p):
+    """The unwindowed response approximates |f| (cycles per bin) to O(1/N),
+    and the Hamming window is 1 at DC and 0.08 at the Nyquist frequency."""
+    R = oracle.ramp_response(n_p, window=False)
+    D = oracle.ramp_response(n_p)
+    N = R.shape[0]
+    assert N >= 2 * n_p and N & (N - 1) == 0
+    f = np.minimum(np.arange(N), N - np.arange(N)) / N
+    assert np.abs(R - f).max() <= 0.5 / N
+    assert np.all(R > 0)
+    assert D[0] == pytest.approx(R[0], rel=1e-15)
+    assert D[N // 2] == pytest.approx(0.08 * R[N // 2], rel=1e-12)
+
+
+def test_bb_first_step_is_fbp_of_a_disk():
+    """Sec. 2.1: FBP is the first step of the preconditioned steepest descent
+    from 0.  With the analytic projections of a centred uniform disk (density 1,
+    radius 0.3 n), the first BB-SIRT iterate is 1 inside the disk to 1% and
+    near 0 outside it within the field of view (the square's corners project
+    past the detector at some angles and are left out)."""
+    n, nt = 128, 180
+    g = oracle.Geometry(n, n, n, nt)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    R = 0.3 * n
+    p = np.arange(n) + 0.5 - n / 2
+    b = np.tile(np.where(np.abs(p) < R, 2 * np.sqrt(np.maximum(R * R - p * p, 0.0)), 0.0), nt)
+    x1, hist = oracle.sirt_bb(A, AT, n, b[None], 1)
+    c = np.arange(n) + 0.5 - n / 2
+    X, Y = np.meshgrid(c, c)
+    rr = np.sqrt(X ** 2 + Y ** 2).ravel()
+    assert abs(x1[0][rr < 0.8 * R].mean() - 1.0) < 0.01
+    assert x1[0][rr < 0.8 * R].std() < 0.02
+    ring = (rr > 1.3 * R) & (rr < 0.5 * n)  # outside the disk, inside the detector's field of view
+    assert np.abs(x1[0][ring]).mean() < 0.01
+    assert hist[0, 0] == pytest.approx(np.linalg.norm(b))
+
+
+def test_bb_converges_to_preconditioned_least_squares():
+    """The fixed point is argmin ||P (A x - b)||, solved independently as a
+    dense least-squares problem with P^T P = L L^T (Cholesky of the cropped
+    circulant); the BB iterates reach it to 1e-9."""
+    g = oracle.Geometry(8, 8, 8, 16)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    b = np.random.default_rng(1).random((2, A.rows))
+    x, _ = oracle.sirt_bb(A, AT, 8, b, 1000)
+    Ad = scipy.sparse.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.rows, A.cols)).toarray()
+    hN = np.fft.ifft(oracle.ramp_response(8)).real
+    N = hN.shape[0]
+    T = np.array([[hN[(k - j) % N] for j in range(8)] for k in range(8)])
+    L = np.linalg.cholesky(np.kron(np.eye(16), T))
+    for s in range(2):
+        ref = np.linalg.lstsq(L.T @ Ad, L.T @ b[s], rcond=None)[0]
+        assert np.linalg.norm(x[s] - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_bb_step_is_exact_for_a_scaled_identity_hessian():
+    """On f(x) = c/2 ||x - x*||^2 the BB1 step is 1/c, so the second step lands
+    on x* exactly (Barzilai & Borwein, 1988).  Here A is the identity-like
+    theta = 0 projector of a 1-pixel-high image (each ray meets one pixel with
+    a unit chord) and the filter acts on single-bin rows, so the Hessian is
+    D_eff * I with one scalar D_eff."""
+    g = oracle.Geometry(1, 1, 1, 1)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    assert A.nnz == 1 and A.val[0] == 1.0
+    b = np.array([[3.0]])
+    x, hist = oracle.sirt_bb(A, AT, 1, b, 3, first_step=0.7)
+    assert x[0, 0] == pytest.approx(3.0, rel=1e-14)
+    assert hist[2, 0] == pytest.approx(0.0, abs=1e-13)
+
+
+def test_bb_resume_continues_the_same_iteration():
+    g = oracle.Geometry(16, 16, 16, 20)
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    b = np.random.default_rng(4).random((3, A.rows))
+    x_all, h_all = oracle.sirt_bb(A, AT, 16, b, 9)
+    x, gp, a, fr, h1 = oracle.sirt_bb_resume(A, AT, 16, b, np.zeros((3, A.cols)), None, None, None, 4)
+    x, gp, a, fr, h2 = oracle.sirt_bb_resume(A, AT, 16, b, x, gp, a, fr, 5)
+    np.testing.assert_array_equal(x, x_all)
+    np.testing.assert_array_equal(np.vstack([h1, h2]), h_all)
+
+
+def test_bb_zero_data_freezes():
+    g = oracle.Geometry(8, 8, 8, 6)
+    A = oracle.build_matrix(g)
+    x, hist = oracle.sirt_bb(A, A.transpose(), 8, np.zeros((1, A.rows)), 4)
+    assert np.all(x == 0) and np.all(hist == 0)
