@@ -138,7 +138,13 @@ typedef struct {
 } tomo_matrix_info_t;
 
 /* Operations that need scratch memory; see tomo_workspace_size. */
-typedef enum { TOMO_OP_PROJECT = 0, TOMO_OP_BACKPROJECT = 1, TOMO_OP_SIRT = 2, TOMO_OP_CGLS = 3 } tomo_op;
+typedef enum {
+  TOMO_OP_PROJECT = 0,
+  TOMO_OP_BACKPROJECT = 1,
+  TOMO_OP_SIRT = 2,
+  TOMO_OP_CGLS = 3,
+  TOMO_OP_SIRT_BB = 4
+} tomo_op;
 
 /* Build A and A^T on the current device (Sec. 3.1: entries generated from the
  * geometry, zero / out-of-range entries dropped, CSR sorted by row and by
@@ -244,6 +250,39 @@ typedef struct {
   double *gamma;
   int32_t *frozen;
 } tomo_cgls_state;
+
+/* State of the BB-step SIRT of n_z slices, caller-owned DEVICE buffers,
+ * slice-major: g (n_z, cols) = A^T P^T P (b - A x) of the last step (16-byte
+ * aligned), alpha (n_z) the last step length (FP64), frozen (n_z) 1 for a
+ * slice whose BB step broke down (<s,s> or <s,y> not positive: converged).
+ * alpha = 0 with frozen = 0 means "no step taken yet". */
+typedef struct {
+  float *g;
+  double *alpha;
+  int32_t *frozen;
+} tomo_bb_state;
+
+/* SIRT with Hamming preconditioning and the Barzilai-Borwein step (Sec. 3.1:
+ * the paper's SIRT), minimising ||P (A x - b)||^2 per slice with the
+ * preconditioner P = F^dagger D^(1/2) F of Sec. 2.1 applied along the
+ * detector of every projection.  D is the N-point DFT of the sampled
+ * band-limited ramp (1/4 at 0, -1/(pi n)^2 at odd n) times the Hamming window
+ * 0.54 + 0.46 cos(2 pi f), N the smallest power of two >= 2 n_p; P^T P runs as
+ * the exact Toeplitz product of those taps over the n_p bins (no FFT).
+ * Iteration k, per slice: r = b - A x (||r|| -> resnorm_hist[k * n_z + z],
+ * DEVICE, nullable); g = A^T P^T P r; alpha = first_step for a slice's first
+ * step (first_step <= 0 selects pi / n_theta, which makes the first iterate
+ * from x = 0 the filtered backprojection, Sec. 2.1), else the BB step
+ * <s,s>/<s,y> with s the last step and y the change of -g, in FP64; a slice
+ * whose <s,s> or <s,y> is not positive is frozen; x += alpha g.
+ * x (n_z, n_y, n_x) is the starting iterate on entry (zero it for x0 = 0) and
+ * the result on return.  in (nullable): continue from a saved state (x the
+ * matching iterate); out (nullable): the state after the last iteration.
+ * Workspace: tomo_workspace_size with TOMO_OP_SIRT_BB. */
+TOMO_API tomo_status tomo_sirt_bb(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
+                                  double first_step, double *resnorm_hist, const tomo_bb_state *in,
+                                  tomo_bb_state *out, const tomo_exec_opts *opts, void *workspace,
+                                  size_t workspace_bytes, void *stream);
 
 /* One reconstruction request of tomo_cgls_batched: DEVICE buffers sino
  * (n_z, n_theta, n_p) and x (n_z, n_y, n_x), both 16-byte aligned, on the

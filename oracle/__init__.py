@@ -360,7 +360,8 @@ def sirt_bb_resume(A: CSR, AT: CSR, n_p: int, b, x, g_prev, alpha_prev, frozen, 
     """Continue preconditioned BB-SIRT from a state.  Per slice, iteration k:
         r  = b - A x                        (its norm is hist[k])
         gn = A^T P^T P r                    (= -grad of 1/2 ||P (A x - b)||^2)
-        alpha = first_step                  when there is no previous step (g_prev None)
+        alpha = first_step                  when the slice has no previous step
+                                            (g_prev None, or its alpha_prev 0 and not frozen)
               = <s,s>/<s,y> (BB1) with s = alpha_prev g_prev, y = -(gn - g_prev)
         x  = x + alpha gn
     A slice is frozen (alpha = 0 from then on) when <s,s> or <s,y> is not
@@ -382,7 +383,7 @@ def sirt_bb_resume(A: CSR, AT: CSR, n_p: int, b, x, g_prev, alpha_prev, frozen, 
         for s in range(nz):
             if frozen[s]:
                 a = 0.0
-            elif gp is None:
+            elif gp is None or alpha[s] == 0.0:  # no previous step for this slice
                 a = a0
             else:
                 ss = alpha[s] * alpha[s] * float(np.dot(gp[s], gp[s]))

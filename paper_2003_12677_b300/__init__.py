@@ -7,7 +7,8 @@ on first use so that ``paper_2003_12677_b300.inputs`` stays importable without
 torch.
 """
 _API = {"Matrix", "project", "backproject", "sirt", "cgls", "TomoProject", "radon", "tv_loss", "new_timing",
-        "sirt_noalloc", "cgls_batched", "stream_status"}
+        "sirt_noalloc", "cgls_batched", "stream_status",
+        "sirt_bb"}
 
 
 def __getattr__(name):

@@ -11,14 +11,14 @@ TOMO_OK = 0
 STATUS = {0: "TOMO_OK", 1: "TOMO_ERR_INVALID_ARG", 2: "TOMO_ERR_OOM", 3: "TOMO_ERR_CUDA",
           4: "TOMO_ERR_TIMEOUT", 5: "TOMO_ERR_UNSUPPORTED", 6: "TOMO_ERR_NUMERIC", 7: "TOMO_ERR_IO"}
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
-OP_PROJECT, OP_BACKPROJECT, OP_SIRT, OP_CGLS = 0, 1, 2, 3
+OP_PROJECT, OP_BACKPROJECT, OP_SIRT, OP_CGLS, OP_SIRT_BB = 0, 1, 2, 3, 4
 SLICE_MAJOR, INTERLEAVED = 0, 1
 
 # every entry point include/tomo.h declares
 EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
            "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
            "tomo_sirt", "tomo_cgls", "tomo_cgls_resume", "tomo_cgls_batched", "tomo_cgls_batched_workspace",
-           "tomo_sirt_noalloc", "tomo_autotune", "tomo_stream_status",
+           "tomo_sirt_noalloc", "tomo_autotune", "tomo_stream_status", "tomo_sirt_bb",
            "tomo_status_string", "tomo_last_error"]
 
 
@@ -57,6 +57,10 @@ class TuneEntry(ctypes.Structure):
 class CglsState(ctypes.Structure):
     _fields_ = [("r", ctypes.c_void_p), ("p", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
                 ("frozen", ctypes.c_void_p)]
+
+
+class BbState(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("frozen", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -104,6 +108,8 @@ def load(path: str = LIB_PATH):
         "tomo_autotune": [P, I32, I32, ctypes.POINTER(ExecOpts), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(TuneEntry), I32, ctypes.POINTER(I32), P],
         "tomo_stream_status": [P],
+        "tomo_sirt_bb": [P, P, P, I32, I32, ctypes.c_double, P, ctypes.POINTER(BbState), ctypes.POINTER(BbState),
+                         ctypes.POINTER(ExecOpts), P, SZ, P],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)

@@ -308,6 +308,58 @@ def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, hi
     return res[0] if len(res) == 1 else tuple(res)
 
 
+def sirt_bb(M: Matrix, sino: torch.Tensor, iters: int, first_step: float = 0.0, history: bool = False,
+            batch_width: int = 0, fmt="sell", use_graph: bool = True, x0: Optional[torch.Tensor] = None,
+            out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None, timing=None,
+            resume: Optional[dict] = None, return_state: bool = False):
+    """SIRT with Hamming preconditioning and the Barzilai-Borwein step (the
+    paper's SIRT).  Starts from x0 (default 0) with first step `first_step`
+    (0: pi / n_theta, so the first iterate from 0 is the FBP), or continues
+    from `resume` (a dict with "x", "g", "alpha", "frozen" as returned with
+    return_state=True).  Returns x, then the ||b - A x_k|| history (iters, n_z)
+    if history, then the final state dict if return_state."""
+    _check_tensor(sino, "sino")
+    nz = _nz(sino, M.rows, "sino")
+    shape = (nz, M.n_y, M.n_x)
+    x = torch.empty(shape, device=sino.device) if out is None else out
+    _check_tensor(x, "out", shape)
+    if resume is not None:
+        x.copy_(resume["x"])
+    elif x0 is not None:
+        x.copy_(x0)
+    else:
+        x.zero_()
+    hist = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
+    ws = workspace if workspace is not None else M._workspace(_lib.OP_SIRT_BB, nz, batch_width, fmt)
+    o = _exec(batch_width, use_graph, fmt, timing)
+
+    def struct(st):
+        b = _lib.BbState()
+        b.g, b.alpha, b.frozen = st["g"].data_ptr(), st["alpha"].data_ptr(), st["frozen"].data_ptr()
+        return b
+
+    sin = None
+    if resume is not None:
+        _check_tensor(resume["g"], "resume[g]")
+        sin = struct(resume)
+    state, sout = None, None
+    if return_state:
+        state = {"g": torch.empty(shape, device=sino.device),
+                 "alpha": torch.empty(nz, device=sino.device, dtype=torch.float64),
+                 "frozen": torch.empty(nz, device=sino.device, dtype=torch.int32)}
+        sout = struct(state)
+    _lib.call("tomo_sirt_bb", M.handle, _ptr(sino), _ptr(x), nz, iters, float(first_step), _ptr(hist),
+              None if sin is None else ctypes.byref(sin), None if sout is None else ctypes.byref(sout),
+              ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(), _stream())
+    res = [x]
+    if history:
+        res.append(hist[:iters])
+    if return_state:
+        state["x"] = x.clone()
+        res.append(state)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
 def _new_state(M: Matrix, nz: int, device) -> dict:
     return {"r": torch.empty((nz, M.n_theta, M.n_p), device=device),
             "p": torch.empty((nz, M.n_y, M.n_x), device=device),

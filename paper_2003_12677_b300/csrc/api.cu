@@ -119,7 +119,7 @@ tomo_status tomo_workspace_size(const tomo_matrix *A, int32_t op, int32_t n_z, c
                                 size_t *bytes) {
   if (!A || !bytes) return fail(TOMO_ERR_INVALID_ARG, "matrix and bytes must be non-NULL");
   if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
-  if (op < TOMO_OP_PROJECT || op > TOMO_OP_CGLS) return fail(TOMO_ERR_INVALID_ARG, "unknown op");
+  if (op < TOMO_OP_PROJECT || op > TOMO_OP_SIRT_BB) return fail(TOMO_ERR_INVALID_ARG, "unknown op");
   Exec ex;
   TOMO_TRY(resolve_exec(A, opts, n_z, &ex));
   *bytes = workspace_bytes(A, op, n_z, ex);
@@ -207,6 +207,34 @@ tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t
                       size_t workspace_bytes, void *stream) {
   return tomo_cgls_resume(A, sino, x, n_z, iters, recompute_every, resnorm_hist, nullptr, nullptr, opts, workspace,
                           workspace_bytes, stream);
+}
+
+static tomo_status check_bb_state(const tomo_bb_state *s, const char *name) {
+  if (!s) return TOMO_OK;
+  if (!s->alpha || !s->frozen) return fail(TOMO_ERR_INVALID_ARG, std::string(name) + ": alpha and frozen must be set");
+  TOMO_TRY(check_vec(s->g, "state g"));
+  if (((uintptr_t)s->alpha & 7u) || ((uintptr_t)s->frozen & 3u))
+    return fail(TOMO_ERR_INVALID_ARG, std::string(name) + ": alpha / frozen misaligned");
+  return TOMO_OK;
+}
+
+tomo_status tomo_sirt_bb(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
+                         double first_step, double *resnorm_hist, const tomo_bb_state *in, tomo_bb_state *out,
+                         const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes, void *stream) {
+  if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
+  TOMO_TRY(check_vec(sino, "sino"));
+  TOMO_TRY(check_vec(x, "x"));
+  TOMO_TRY(check_bb_state(in, "in"));
+  TOMO_TRY(check_bb_state(out, "out"));
+  if (n_z < 1 || iters < 0) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1 and iters >= 0");
+  if (!std::isfinite(first_step)) return fail(TOMO_ERR_INVALID_ARG, "first_step must be finite");
+  if (resnorm_hist && ((uintptr_t)resnorm_hist & 7u)) return fail(TOMO_ERR_INVALID_ARG, "resnorm_hist misaligned");
+  DeviceGuard dg(A->device);
+  Exec ex;
+  TOMO_TRY(resolve_exec(A, opts, n_z, &ex));
+  TOMO_TRY(check_ws(A, TOMO_OP_SIRT_BB, n_z, ex, workspace, workspace_bytes));
+  return run_sirt_bb(A, sino, x, n_z, iters, first_step, resnorm_hist, in, out, ex, workspace,
+                     (cudaStream_t)stream);
 }
 
 tomo_status tomo_cgls_batched(const tomo_request *reqs, int32_t n_reqs, int32_t iters, const tomo_exec_opts *opts,

@@ -524,13 +524,67 @@ tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Taps of the preconditioning filter P^T P = F^dagger D F along the detector
+// (Sec. 2.1), used by the BB-step SIRT of Sec. 3.1.  On the N-point DFT grid
+// (N = the smallest power of two >= 2 n_p, so a projection row zero-padded to
+// N never wraps), D_k = R_k w_k: R is the DFT of the sampled band-limited ramp
+// (1/4 at n = 0, -1/(pi n)^2 at odd n, 0 at even n, |n| <= N/2) and w the
+// Hamming window 0.54 + 0.46 cos(2 pi k / N).  The filter is then the
+// symmetric Toeplitz operator tap[|k - j|] on the n_p bins of a row, with
+// tap[d] = (1/N) sum_k D_k cos(2 pi k d / N).  FP64 sums, angles reduced
+// exactly as (k d mod N) / N before the cosine; the taps are rounded to FP32.
+// ---------------------------------------------------------------------------
+__global__ void k_ramp_response(int N, double *D) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > N / 2) return;
+  const double pi = 3.141592653589793;
+  double R = 0.25;
+  for (int n = 1; n < N / 2; n += 2) {
+    const int64_t kn = ((int64_t)k * n) % N;
+    R -= 2.0 / (pi * pi * (double)n * (double)n) * cos(2.0 * pi * (double)kn / (double)N);
+  }
+  if ((N / 2) & 1) {  // n = -N/2 is odd only for N = 2
+    const double hN = -1.0 / (pi * pi * (double)(N / 2) * (double)(N / 2));
+    R += (k & 1) ? -hN : hN;
+  }
+  D[k] = R * (0.54 + 0.46 * cos(2.0 * pi * (double)k / (double)N));
+}
+
+__global__ void k_ramp_taps(int N, const double *D, int np, float *tap) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= np) return;
+  const double pi = 3.141592653589793;
+  double h = D[0] + ((d & 1) ? -D[N / 2] : D[N / 2]);
+  for (int k = 1; k < N / 2; ++k) {
+    const int64_t kd = ((int64_t)k * d) % N;
+    h += 2.0 * D[k] * cos(2.0 * pi * (double)kd / (double)N);
+  }
+  tap[d] = (float)(h / (double)N);
+}
+
+tomo_status build_ramp(tomo_matrix *h, cudaStream_t st) {
+  int N = 2;
+  while (N < 2 * h->np) N *= 2;
+  double *D = nullptr;
+  TOMO_TRY(dmalloc(&D, N / 2 + 1));
+  DevBuf D_guard{D};
+  TOMO_TRY(dmalloc(&h->ramp, h->np));
+  k_ramp_response<<<(N / 2 + 1 + 127) / 128, 128, 0, st>>>(N, D);
+  TOMO_CUDA(cudaGetLastError());
+  k_ramp_taps<<<(h->np + 127) / 128, 128, 0, st>>>(N, D, h->np, h->ramp);
+  TOMO_CUDA(cudaGetLastError());
+  TOMO_CUDA(cudaStreamSynchronize(st));  // D is freed on return
+  return TOMO_OK;
+}
+
 void free_matrix(tomo_matrix *h) {
   if (!h) return;
   void *ptrs[] = {h->ang,      h->ang_scale, h->A.rp,     h->A.ci,     h->A.v,       h->AT.rp,
                   h->AT.ci,    h->AT.v,      h->R,        h->C,        h->sA.cp,     h->sA.rl,
                   h->sA.ent,   h->sAT.cp,    h->sAT.rl,   h->sAT.ent,  h->lpA.cpw,   h->lpA.cpb,
                   h->lpA.ow,   h->lpA.base,  h->lpAT.cpw, h->lpAT.cpb, h->lpAT.ow,   h->lpAT.base,
-                  h->lpA.rl,   h->lpAT.rl};
+                  h->lpA.rl,   h->lpAT.rl,   h->ramp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -679,6 +733,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
     return fail(TOMO_ERR_UNSUPPORTED, "a 16-entry chunk spans more than 65535 columns (geometry too large "
                                       "for 16-bit offsets)");
   if (hs[0] != 0) return fail(TOMO_ERR_NUMERIC, "pixel enumeration found more than two bins per angle");
+  TOMO_TRY(build_ramp(h, st));
   guard.keep = true;
   *out = h;
   return TOMO_OK;

@@ -76,6 +76,7 @@ struct tomo_matrix {
   float *ang_scale = nullptr;    // device [nt]: 1/a(theta_m) in FP32
   tomo::Csr A, AT;
   float *R = nullptr, *C = nullptr;
+  float *ramp = nullptr;         // device [np]: taps |d| = 0..np-1 of the preconditioning filter
   int32_t lp_dtype = TOMO_F32;
   tomo::Sell sA, sAT;
   tomo::SellLp lpA, lpAT;
@@ -135,6 +136,9 @@ tomo_status run_sirt(const tomo_matrix *h, const float *sino, float *x, int32_t 
 tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
                      int32_t recompute, double *hist, const tomo_cgls_state *in, tomo_cgls_state *out,
                      const Exec &ex, void *ws, cudaStream_t st);
+tomo_status run_sirt_bb(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
+                        double first_step, double *hist, const tomo_bb_state *in, tomo_bb_state *out,
+                        const Exec &ex, void *ws, cudaStream_t st);
 tomo_status batched_workspace(const tomo_request *reqs, int32_t n, const tomo_exec_opts *o, size_t *bytes);
 // per-stream status word (status.cu)
 int *stream_status_word(cudaStream_t st);

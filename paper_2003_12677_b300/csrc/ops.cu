@@ -348,6 +348,165 @@ __global__ void __launch_bounds__(kThreads) k_cgls_dir(float *__restrict__ p, co
 }
 
 // ---------------------------------------------------------------------------
+// Preconditioned SIRT with the Barzilai-Borwein step (Sec. 3.1; the
+// preconditioner P = F^dagger D^(1/2) F of Sec. 2.1).  Per-slice scalars
+// (FP64), 4 per slice: [0] alpha of the last step  [1] frozen (0/1)
+// [2] a previous step exists (0/1).
+// ---------------------------------------------------------------------------
+
+// rf = P^T P r on every projection row: rf[m, k, :] = sum_j tap[|k - j|] r[m, j, :]
+// over the n_p bins of row m, j ascending (interleaved (rows, B) vectors).
+// Block (256 threads) = NG bin groups x Q slice groups of V slices; a thread
+// owns KB adjacent output bins and keeps the KB taps it needs in registers,
+// shifting them by one bin per step of j.  Grid: (ceil(n_p / TK), n_theta).
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_ramp_filter(const float *__restrict__ r, float *__restrict__ rf,
+                                                          const float *__restrict__ tap, int np) {
+  constexpr int V = B >= 4 ? 4 : B, Q = B / V, KB = 4, NG = kThreads / Q, TK = NG * KB, TJ = 32;
+  __shared__ __align__(16) float rs[TJ * B];
+  const int q = threadIdx.x % Q, kg = threadIdx.x / Q;
+  const int64_t m = blockIdx.y;
+  const int k0 = blockIdx.x * TK + kg * KB;
+  const float *rm = r + m * np * B;
+  auto tapv = [&](int d) { d = d < 0 ? -d : d; return d < np ? __ldg(tap + d) : 0.f; };
+  float acc[KB][V];
+#pragma unroll
+  for (int i = 0; i < KB; ++i)
+#pragma unroll
+    for (int t = 0; t < V; ++t) acc[i][t] = 0.f;
+  for (int j0 = 0; j0 < np; j0 += TJ) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < TJ * B; t += kThreads) {
+      const int jj = t / B;
+      rs[t] = j0 + jj < np ? rm[(int64_t)(j0 + jj) * B + (t % B)] : 0.f;
+    }
+    __syncthreads();
+    float w[KB];  // w[i] = tap at offset k0 + i - j
+#pragma unroll
+    for (int i = 0; i < KB; ++i) w[i] = tapv(k0 + i - j0);
+#pragma unroll 8
+    for (int jj = 0; jj < TJ; ++jj) {
+      const Vec<V> xv = ld_vec<V>(rs + jj * B + q * V);
+#pragma unroll
+      for (int i = 0; i < KB; ++i)
+#pragma unroll
+        for (int t = 0; t < V; ++t) acc[i][t] = fmaf(w[i], xv.v[t], acc[i][t]);
+#pragma unroll
+      for (int i = KB - 1; i > 0; --i) w[i] = w[i - 1];
+      w[0] = tapv(k0 - (j0 + jj) - 1);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KB; ++i) {
+    if (k0 + i >= np) break;
+    Vec<V> o;
+#pragma unroll
+    for (int t = 0; t < V; ++t) o.v[t] = acc[i][t];
+    st_vec<V>(rf + (m * np + k0 + i) * B + q * V, o);
+  }
+}
+
+// per-slice partials of <g_prev, g_prev> and <g_prev, g - g_prev> (FP64)
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_bb_dots(const float *__restrict__ gp, const float *__restrict__ gn,
+                                                      int64_t ncols, double *__restrict__ part_p,
+                                                      double *__restrict__ part_q) {
+  constexpr int V = B >= 4 ? 4 : B;
+  constexpr int PER = B / V;
+  const int64_t nv = ncols * PER;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int s0 = (int)(tid % PER) * V;
+  double pp[V], pq[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) pp[t] = pq[t] = 0.0;
+  for (int64_t i = tid; i < nv; i += nth) {
+    const Vec<V> a = ld_vec<V>(gp + i * V), b = ld_vec<V>(gn + i * V);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const double ga = a.v[t];
+      pp[t] += ga * ga;
+      pq[t] += ga * ((double)b.v[t] - ga);
+    }
+  }
+  block_norms<V>(pp, s0, B, part_p);
+  block_norms<V>(pq, s0, B, part_q);
+}
+
+// one block per slice: the step alpha (first step, BB1 or frozen) and ||r||
+__global__ void __launch_bounds__(kThreads) k_bb_alpha(const double *part_p, const double *part_q, int nblk,
+                                                       const double *part_r, int nblk_r, int B, double *scal,
+                                                       double first_step, double *hist, const int *it, int s0,
+                                                       int cnt, int nz) {
+  const int s = blockIdx.x;
+  const double P = block_sum_slice(part_p, nblk, B, s);
+  const double Qd = block_sum_slice(part_q, nblk, B, s);
+  const double rr = block_sum_slice(part_r, nblk_r, B, s);
+  if (threadIdx.x == 0) {
+    const double a_prev = scal[s * 4 + 0];
+    double a = 0.0;
+    if (scal[s * 4 + 1] != 0.0) {
+      a = 0.0;
+    } else if (scal[s * 4 + 2] == 0.0) {
+      a = first_step;
+      scal[s * 4 + 2] = 1.0;
+    } else {
+      // s = a_prev g_prev, y = -(g - g_prev): <s,s> = a_prev^2 P, <s,y> = -a_prev Q
+      const double ss = a_prev * a_prev * P, sy = -a_prev * Qd;
+      if (ss > 0.0 && sy > 0.0) {
+        a = ss / sy;
+      } else {
+        scal[s * 4 + 1] = 1.0;
+      }
+    }
+    scal[s * 4 + 0] = a;
+    if (hist && s < cnt) hist[(int64_t)(*it) * nz + s0 + s] = sqrt(rr);
+  }
+}
+
+// x += alpha g; advances the iteration counter
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_bb_update(float *__restrict__ x, const float *__restrict__ g,
+                                                        int64_t ncols, const double *__restrict__ scal, int *it) {
+  constexpr int V = B >= 4 ? 4 : B;
+  constexpr int PER = B / V;
+  const int64_t nv = ncols * PER;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int s0 = (int)(tid % PER) * V;
+  float al[V];
+#pragma unroll
+  for (int t = 0; t < V; ++t) al[t] = (float)scal[(s0 + t) * 4 + 0];
+  for (int64_t i = tid; i < nv; i += nth) {
+    Vec<V> xv = ld_vec<V>(x + i * V);
+    const Vec<V> gv = ld_vec<V>(g + i * V);
+#pragma unroll
+    for (int t = 0; t < V; ++t) xv.v[t] = fmaf(al[t], gv.v[t], xv.v[t]);
+    st_vec<V>(x + i * V, xv);
+  }
+  if (tid == 0) ++*it;
+}
+
+// state in / out: alpha, frozen; padding slices (s >= cnt) frozen
+__global__ void k_bb_load(double *scal, const double *alpha, const int32_t *frozen, int cnt, int B, int *it) {
+  for (int s = threadIdx.x; s < B; s += blockDim.x) {
+    const bool real = s < cnt;
+    scal[s * 4 + 0] = (alpha && real) ? alpha[s] : 0.0;
+    scal[s * 4 + 1] = (!real || (frozen && frozen[s] != 0)) ? 1.0 : 0.0;
+    scal[s * 4 + 2] = (alpha && real && alpha[s] > 0.0) ? 1.0 : 0.0;  // alpha 0: no previous step
+    scal[s * 4 + 3] = 0.0;
+  }
+  if (threadIdx.x == 0) *it = 0;
+}
+
+__global__ void k_bb_save(const double *scal, double *alpha, int32_t *frozen, int cnt) {
+  for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
+    alpha[s] = scal[s * 4 + 0];
+    frozen[s] = scal[s * 4 + 1] != 0.0 ? 1 : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launch plumbing
 // ---------------------------------------------------------------------------
 struct Op {  // one SpMM operand (A or A^T) in the selected storage
@@ -769,6 +928,114 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
   return tm.finish(st);
 }
 
+// ---------------------------------------------------------------------------
+// BB-step SIRT driver.  One iteration: r = b - A x (+||r||^2), rf = P^T P r,
+// g = A^T rf, the two dots, alpha, x += alpha g.  g and g_prev alternate
+// between two buffers, so the iteration is captured as two graphs (even and
+// odd) and replayed alternately.
+// ---------------------------------------------------------------------------
+template <int B>
+tomo_status bb_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters, double first_step,
+                 double *hist, const tomo_bb_state *sin, tomo_bb_state *sout, const Exec &ex, void *ws,
+                 cudaStream_t st) {
+  Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
+  const int64_t rows = h->A.rows, cols = h->A.cols;
+  const int pg = max_spmm_grid();
+  Carver cv{(char *)ws};
+  float *r = cv.take<float>(rows * B);
+  float *rf = cv.take<float>(rows * B);
+  float *gb[2] = {cv.take<float>(cols * B), cv.take<float>(cols * B)};
+  double *part_r = cv.take<double>((size_t)pg * B);
+  double *part_p = cv.take<double>((size_t)pg * B);
+  double *part_q = cv.take<double>((size_t)pg * B);
+  double *scal = cv.take<double>(B * 4);
+  int *itc = cv.take<int>(4);
+  float *bi = B > 1 ? cv.take<float>(rows * B) : nullptr;
+  float *xi = B > 1 ? cv.take<float>(cols * B) : nullptr;
+
+  const int gR = spmm_grid_of<B, EpiResidualNorm>(A);
+  constexpr int PER = B >= 4 ? B / 4 : 1;
+  constexpr int TK = 4 * kThreads / PER;
+  const int ge = elem_grid(cols * PER);
+  const dim3 gf((unsigned)((h->np + TK - 1) / TK), (unsigned)h->nt);
+  const double a0 = first_step > 0.0 ? first_step : 3.141592653589793 / (double)h->nt;
+
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TOMO_CUDA(cudaStreamIsCapturing(st, &cs));
+  Timer tm{ex.timing};
+  const bool use_graph = ex.graph && !ex.timing && cs == cudaStreamCaptureStatusNone && iters > 2;
+  cudaStream_t cap = nullptr;
+
+  for (int32_t s0 = 0; s0 < nz; s0 += B) {
+    const int cnt = std::min<int32_t>(B, nz - s0);
+    const float *bb = sino + (int64_t)s0 * rows;
+    float *xx = x + (int64_t)s0 * cols;
+    if (B > 1) {
+      TIMED(tm, st, kOther, interleave<B>(bb, rows, cnt, bi, st));
+      TIMED(tm, st, kOther, interleave<B>(xx, cols, cnt, xi, st));
+      bb = bi;
+      xx = xi;
+    }
+    // the previous step's g (resume) sits in gb[1], the buffer iteration 0 reads
+    if (sin) {
+      if (B > 1) {
+        TIMED(tm, st, kOther, interleave<B>(sin->g + (int64_t)s0 * cols, cols, cnt, gb[1], st));
+      } else {
+        TOMO_CUDA(cudaMemcpyAsync(gb[1], sin->g + (int64_t)s0 * cols, sizeof(float) * cols,
+                                  cudaMemcpyDeviceToDevice, st));
+      }
+    } else {
+      TOMO_CUDA(cudaMemsetAsync(gb[1], 0, sizeof(float) * cols * B, st));
+    }
+    TIMED(tm, st, kOther,
+          (k_bb_load<<<1, 64, 0, st>>>(scal, sin ? sin->alpha + s0 : nullptr, sin ? sin->frozen + s0 : nullptr,
+                                       cnt, B, itc)));
+    TOMO_CUDA(cudaGetLastError());
+
+    auto one_iter = [&](cudaStream_t sm, float *g, float *gp) {
+      TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidualNorm{r, bb, B}, part_r, sm));
+      TIMED(tm, sm, kOther, (k_ramp_filter<B><<<gf, kThreads, 0, sm>>>(r, rf, h->ramp, h->np)));
+      TIMED(tm, sm, kAT, launch_spmm<B>(AT, rf, EpiStore{g, B}, nullptr, sm));
+      TIMED(tm, sm, kOther, (k_bb_dots<B><<<ge, kThreads, 0, sm>>>(gp, g, cols, part_p, part_q)));
+      TIMED(tm, sm, kOther,
+            (k_bb_alpha<<<B, kThreads, 0, sm>>>(part_p, part_q, ge, part_r, gR, B, scal, a0, hist, itc, s0, cnt,
+                                                nz)));
+      TIMED(tm, sm, kOther, (k_bb_update<B><<<ge, kThreads, 0, sm>>>(xx, g, cols, scal, itc)));
+    };
+    if (use_graph) {
+      TOMO_TRY(capture_stream(&cap));
+      cudaGraph_t gr[2] = {nullptr, nullptr};
+      cudaGraphExec_t ge2[2] = {nullptr, nullptr};
+      for (int k = 0; k < 2; ++k) {
+        TOMO_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        one_iter(cap, gb[k], gb[1 - k]);
+        TOMO_CUDA(cudaStreamEndCapture(cap, &gr[k]));
+        TOMO_CUDA(cudaGraphInstantiate(&ge2[k], gr[k], 0));
+      }
+      for (int32_t it = 0; it < iters; ++it) TOMO_CUDA(cudaGraphLaunch(ge2[it & 1], st));
+      for (int k = 0; k < 2; ++k) {
+        cudaGraphExecDestroy(ge2[k]);
+        cudaGraphDestroy(gr[k]);
+      }
+    } else {
+      for (int32_t it = 0; it < iters; ++it) one_iter(st, gb[it & 1], gb[1 - (it & 1)]);
+    }
+    if (sout) {
+      const float *last = gb[iters > 0 ? (iters - 1) & 1 : 1];
+      if (B > 1) {
+        TIMED(tm, st, kOther, deinterleave<B>(last, cols, cnt, sout->g + (int64_t)s0 * cols, st));
+      } else {
+        TOMO_CUDA(cudaMemcpyAsync(sout->g + (int64_t)s0 * cols, last, sizeof(float) * cols,
+                                  cudaMemcpyDeviceToDevice, st));
+      }
+      TIMED(tm, st, kOther, (k_bb_save<<<1, 64, 0, st>>>(scal, sout->alpha + s0, sout->frozen + s0, cnt)));
+    }
+    if (B > 1) TIMED(tm, st, kOther, deinterleave<B>(xi, cols, cnt, x + (int64_t)s0 * cols, st));
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return tm.finish(st);
+}
+
 template <template <int> class F, typename... Args>
 tomo_status dispatch(int B, Args &&...args) {
   switch (B) {
@@ -797,6 +1064,11 @@ template <int B>
 struct CglsF {
   template <typename... A>
   static tomo_status run(A &&...a) { return cgls_t<B>(a...); }
+};
+template <int B>
+struct BbF {
+  template <typename... A>
+  static tomo_status run(A &&...a) { return bb_t<B>(a...); }
 };
 
 bool valid_width(int b) { return b == 1 || b == 2 || b == 4 || b == 8 || b == 16 || b == 32 || b == 64; }
@@ -886,6 +1158,23 @@ size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex)
       }
       break;
     }
+    case TOMO_OP_SIRT_BB: {
+      const int pg = max_spmm_grid();
+      cv.take<float>(rows * B);
+      cv.take<float>(rows * B);
+      cv.take<float>(cols * B);
+      cv.take<float>(cols * B);
+      cv.take<double>((size_t)pg * B);
+      cv.take<double>((size_t)pg * B);
+      cv.take<double>((size_t)pg * B);
+      cv.take<double>(B * 4);
+      cv.take<int>(4);
+      if (B > 1) {
+        cv.take<float>(rows * B);
+        cv.take<float>(cols * B);
+      }
+      break;
+    }
     default:
       return 0;
   }
@@ -912,6 +1201,14 @@ tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t 
   WsHolder hold;
   TOMO_TRY(with_ws(h, TOMO_OP_CGLS, nz, ex, ws, hold, st));
   return dispatch<CglsF>(ex.B, h, sino, x, nz, iters, recompute, hist, in, out, ex, ws, st);
+}
+
+tomo_status run_sirt_bb(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
+                        double first_step, double *hist, const tomo_bb_state *in, tomo_bb_state *out,
+                        const Exec &ex, void *ws, cudaStream_t st) {
+  WsHolder hold;
+  TOMO_TRY(with_ws(h, TOMO_OP_SIRT_BB, nz, ex, ws, hold, st));
+  return dispatch<BbF>(ex.B, h, sino, x, nz, iters, first_step, hist, in, out, ex, ws, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,7 +36,7 @@ class Workload:
     n: int            # nx = ny = n_p
     n_theta: int
     n_z: int          # slices per batch
-    solver: str       # "sirt" | "cgls" | "gd"
+    solver: str       # "sirt" | "sirt_bb" | "cgls" | "gd"
     iters: int
     noise: str        # "poisson" | "gaussian"
     noise_level: float
@@ -221,6 +221,11 @@ def workload_case(name: str, slices: Optional[Sequence[int]] = None) -> Case:
     w = WORKLOADS[name]
     return make_case(w.n, w.n_theta, w.n_z, w.seed, w.phantom, w.noise, w.noise_level, slices)
 
+
+# the benchmark's 64-slice 512x512x360 data solved by the paper's SIRT (Hamming
+# preconditioning, BB step), 30 iterations
+WORKLOADS["sirt_bb_512x360_b64"] = Workload("sirt_bb_512x360_b64", 512, 360, 64, "sirt_bb", 30,
+                                           "poisson", 1e4, "ellipsoids3d", seed=12677 + 2)
 
 WORKLOADS["uneven_256"] = Workload("uneven_256", 2048, 1024, 0, "cgls", 30, "poisson", 1e5, "ellipses2d",
                                   values="bf16", seed=12677 + 5)
