@@ -34,9 +34,7 @@ __global__ void __launch_bounds__(kThreads) k_spmm_sell(const int64_t *__restric
                                                         const float *__restrict__ X, Epi epi,
                                                         double *__restrict__ part) {
   constexpr int V = Lanes<B>::V, G = Lanes<B>::G, L = Lanes<B>::L;
-  double ss[V];
-#pragma unroll
-  for (int t = 0; t < V; ++t) ss[t] = 0.0;
+  double *ss = norm_slots<V, Epi>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   sell_rowgroups<B>(cp, rl, ent, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
@@ -47,9 +45,7 @@ template <int B, bool kBf16, bool kTrans, class Epi>
 __global__ void __launch_bounds__(kThreads) k_spmm_sell16(Sell16View M, int64_t rows, const float *__restrict__ X,
                                                           Epi epi, double *__restrict__ part) {
   constexpr int V = Lanes<B>::V, G = Lanes<B>::G, L = Lanes<B>::L;
-  double ss[V];
-#pragma unroll
-  for (int t = 0; t < V; ++t) ss[t] = 0.0;
+  double *ss = norm_slots<V, Epi>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   sell16_rowgroups<B, kBf16, kTrans>(M, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
@@ -61,11 +57,9 @@ __global__ void __launch_bounds__(kThreads) k_spmm_sell16(Sell16View M, int64_t 
 // G = 32/L rows per warp.  Grid-stride over row groups.
 // ---------------------------------------------------------------------------
 template <int B, class Epi>
-__global__ void __launch_bounds__(kThreads) k_spmm_f32(const int64_t *__restrict__ rp,
-                                                       const int32_t *__restrict__ ci,
-                                                       const float *__restrict__ val, int64_t rows,
-                                                       const float *__restrict__ X, Epi epi,
-                                                       double *__restrict__ part) {
+__device__ __forceinline__ void csr_spmm(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                         const float *__restrict__ val, int64_t rows, const float *__restrict__ X,
+                                         Epi epi, double *__restrict__ part) {
   constexpr int L = B / 4, G = 32 / L;
   const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -104,6 +98,36 @@ __global__ void __launch_bounds__(kThreads) k_spmm_f32(const int64_t *__restrict
     epi.template operator()<4>(row, l * 4, acc, ss);
   }
   if constexpr (Epi::kNorm) block_norms<4>(ss, l * 4, B, part);
+}
+
+template <int B, class Epi>
+__global__ void __launch_bounds__(kThreads) k_spmm_f32(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                       const float *__restrict__ val, int64_t rows,
+                                                       const float *__restrict__ X, Epi epi,
+                                                       double *__restrict__ part) {
+  csr_spmm<B>(rp, ci, val, rows, X, epi, part);
+}
+
+// The norm epilogues carry 2 x 4 FP64 accumulators through the row loop;
+// unbounded they take 48 registers (5 blocks per SM).  Held at 6 blocks per
+// SM they fit 40 registers unspilled.  Measured at 512x512x360 (CGLS passes):
+// B = 64, 6 blocks 1.94 ms vs 5 blocks 2.63 ms; B = 16, 6 blocks 0.99 ms vs
+// 5 blocks 0.90 ms.  So the bounded form serves B >= 32 only.
+template <int B, class Epi>
+__global__ void __launch_bounds__(kThreads, 6) k_spmm_f32_norm(const int64_t *__restrict__ rp,
+                                                               const int32_t *__restrict__ ci,
+                                                               const float *__restrict__ val, int64_t rows,
+                                                               const float *__restrict__ X, Epi epi,
+                                                               double *__restrict__ part) {
+  csr_spmm<B>(rp, ci, val, rows, X, epi, part);
+}
+
+template <int B, class Epi>
+constexpr auto csr_kernel() {
+  if constexpr (Epi::kNorm && B >= 32)
+    return k_spmm_f32_norm<B, Epi>;
+  else
+    return k_spmm_f32<B, Epi>;
 }
 
 // ---------------------------------------------------------------------------
@@ -441,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_bb_alpha(const double *part_p, con
   const int s = blockIdx.x;
   const double P = block_sum_slice(part_p, nblk, B, s);
   const double Qd = block_sum_slice(part_q, nblk, B, s);
-  const double rr = block_sum_slice(part_r, nblk_r, B, s);
+  const double rr = part_r ? block_sum_slice(part_r, nblk_r, B, s) : 0.0;
   if (threadIdx.x == 0) {
     const double a_prev = scal[s * 4 + 0];
     double a = 0.0;
@@ -549,6 +573,11 @@ int resident_blocks(K kernel) {
 
 inline int max_spmm_grid() { return num_sms() * 8; }
 
+// The CSR gather kernels keep at most 6 blocks (48 warps) per SM: the
+// 32-register norm variants would fit 8, and measured 20-30% slower there
+// (more rows in flight share the same L1 for their gathered operand rows).
+constexpr int kCsrMaxBlocks = 6;
+
 template <int B, class Epi>
 void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream_t st) {
   const int G = rows_per_warp(op.format, B);
@@ -576,8 +605,8 @@ void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream
 #undef TOMO_SELL16
   } else {
     if constexpr (B >= 4) {
-      static const int res = resident_blocks(k_spmm_f32<B, Epi>);
-      k_spmm_f32<B, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X, epi,
+      static const int res = std::min(resident_blocks(csr_kernel<B, Epi>()), kCsrMaxBlocks);
+      csr_kernel<B, Epi>()<<<spmm_grid(rows, G, res), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X, epi,
                                                                         part);
     } else {
       static const int res = resident_blocks(k_spmv_f32<B, 32, Epi>);
@@ -602,7 +631,7 @@ int spmm_grid_of(const Op &op) {
       res = op.trans ? resident_blocks(k_spmm_sell16<B, false, true, Epi>)
                      : resident_blocks(k_spmm_sell16<B, false, false, Epi>);
   } else if constexpr (B >= 4) {
-    res = resident_blocks(k_spmm_f32<B, Epi>);
+    res = std::min(resident_blocks(csr_kernel<B, Epi>()), kCsrMaxBlocks);
   } else {
     res = resident_blocks(k_spmv_f32<B, 32, Epi>);
   }
@@ -993,13 +1022,17 @@ tomo_status bb_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, 
     TOMO_CUDA(cudaGetLastError());
 
     auto one_iter = [&](cudaStream_t sm, float *g, float *gp) {
-      TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidualNorm{r, bb, B}, part_r, sm));
+      // the residual norm is only reduced when its history is asked for
+      if (hist)
+        TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidualNorm{r, bb, B}, part_r, sm));
+      else
+        TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidual{r, bb, B}, nullptr, sm));
       TIMED(tm, sm, kOther, (k_ramp_filter<B><<<gf, kThreads, 0, sm>>>(r, rf, h->ramp, h->np)));
       TIMED(tm, sm, kAT, launch_spmm<B>(AT, rf, EpiStore{g, B}, nullptr, sm));
       TIMED(tm, sm, kOther, (k_bb_dots<B><<<ge, kThreads, 0, sm>>>(gp, g, cols, part_p, part_q)));
       TIMED(tm, sm, kOther,
-            (k_bb_alpha<<<B, kThreads, 0, sm>>>(part_p, part_q, ge, part_r, gR, B, scal, a0, hist, itc, s0, cnt,
-                                                nz)));
+            (k_bb_alpha<<<B, kThreads, 0, sm>>>(part_p, part_q, ge, hist ? part_r : nullptr, gR, B, scal, a0, hist,
+                                                itc, s0, cnt, nz)));
       TIMED(tm, sm, kOther, (k_bb_update<B><<<ge, kThreads, 0, sm>>>(xx, g, cols, scal, itc)));
     };
     if (use_graph) {

@@ -122,6 +122,20 @@ struct EpiStoreNorm {  // Y = acc, ss += acc^2
   }
 };
 
+struct EpiResidual {  // r = b - acc
+  static constexpr bool kNorm = false;
+  float *r;
+  const float *b;
+  int ld;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
+    Vec<V> bv = ldg_vec<V>(b + row * ld + s0);
+#pragma unroll
+    for (int t = 0; t < V; ++t) a.v[t] = bv.v[t] - a.v[t];
+    st_vec<V>(r + row * ld + s0, a);
+  }
+};
+
 struct EpiResidualNorm {  // r = b - acc, ss += r^2
   static constexpr bool kNorm = true;
   float *r;
@@ -141,12 +155,19 @@ struct EpiResidualNorm {  // r = b - acc, ss += r^2
 
 // Deterministic per-block reduction of ss[V] (slices s0..s0+V-1 of each thread)
 // into out[s], s < B.
+// The reduction array doubles as the per-thread accumulators of the norm
+// epilogues (norm_slots below): one 8 KB array per block, not two.
+__device__ __forceinline__ double (*norm_red())[4] {
+  __shared__ double red[kThreads][4];
+  return red;
+}
+
 template <int V>
 __device__ void block_norms_to(const double *ss, int s0, int B, double *out) {
-  __shared__ double red[kThreads][4];
+  double(*red)[4] = norm_red();
   __shared__ int red_s0[kThreads];
 #pragma unroll
-  for (int t = 0; t < V; ++t) red[threadIdx.x][t] = ss[t];
+  for (int t = 0; t < V; ++t) red[threadIdx.x][t] = ss[t];  // a no-op when ss is this thread's slot row
   red_s0[threadIdx.x] = s0;
   __syncthreads();
   for (int s = threadIdx.x; s < B; s += blockDim.x) {
@@ -158,6 +179,25 @@ __device__ void block_norms_to(const double *ss, int s0, int B, double *out) {
     out[s] = acc;
   }
   __syncthreads();  // red[] may be reused by the caller's next reduction
+}
+
+// Per-thread FP64 accumulators of the norm epilogues.  They live in shared
+// memory (each thread its own row of the reduction array, updated once per
+// output row), so the SpMM row loop does not carry 2 V extra registers: with
+// them in registers the norm variants needed 48-58 registers and lost one or
+// two resident blocks per SM.  Epilogues without a norm get nullptr and never
+// touch it.
+template <int V, class Epi>
+__device__ __forceinline__ double *norm_slots() {
+  static_assert(V <= 4, "four slots per thread");
+  if constexpr (Epi::kNorm) {
+    double *p = norm_red()[threadIdx.x];
+#pragma unroll
+    for (int t = 0; t < V; ++t) p[t] = 0.0;
+    return p;
+  } else {
+    return nullptr;
+  }
 }
 
 // ... into part[blockIdx.x * B + s]
