@@ -6,7 +6,8 @@ in ``tomo_oracle.c`` (built with gcc, ``-ffp-contract=off``, OpenMP) through
 ctypes and promotes every float32 input to float64.
 
 Function map (paper: "Sparse Matrix-Based HPC Tomography"):
-  build_matrix      Sec. 2 projection integral, discretised as chord lengths;
+  build_matrix      Sec. 2 projection integral, discretised as chord lengths
+                    (line model) or as areas in unit-width strips (strip model);
                     Sec. 3.1 CSR sorted by row and column, transpose stored apart
   project / backproject   y = A x, x' = A^T y per slice (Sec. 3, SpMV / SpMM)
   project_mf / backproject_mf   the same without storing A
@@ -90,6 +91,9 @@ def threads() -> int:
     return int(_load().oracle_threads())
 
 
+MODELS = {"line": 0, "strip": 1}
+
+
 @dataclasses.dataclass
 class Geometry:
     nx: int
@@ -98,6 +102,10 @@ class Geometry:
     n_theta: int
     angles: Optional[np.ndarray] = None   # radians; None -> m*pi/n_theta
     center: Optional[float] = None         # None -> n_p/2
+    model: str = "line"                    # "line" (chord length) | "strip" (area in a unit-width strip)
+
+    def model_id(self) -> int:
+        return MODELS[self.model]
 
     def theta(self) -> np.ndarray:
         if self.angles is not None:
@@ -167,7 +175,7 @@ def weight(g: Geometry, m: int, k: int, ix: int, iy: int) -> Optional[float]:
     cs, sn = g.trig()
     L = _dbl(0.0)
     hit = _load().oracle_weight(_i32(g.nx), _i32(g.ny), _dbl(g.c()), _dbl(cs[m]), _dbl(sn[m]),
-                                _i32(k), _i32(ix), _i32(iy), ctypes.byref(L))
+                                _i32(k), _i32(ix), _i32(iy), ctypes.byref(L), _i32(g.model_id()))
     return L.value if hit else None
 
 
@@ -177,13 +185,13 @@ def build_matrix(g: Geometry) -> CSR:
     cs, sn = g.trig()
     counts = np.empty(g.rows, np.int64)
     nnz = lib.oracle_count(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()),
-                           _p(cs), _p(sn), _p(counts))
+                           _p(cs), _p(sn), _p(counts), _i32(g.model_id()))
     rp = np.zeros(g.rows + 1, np.int64)
     np.cumsum(counts, out=rp[1:])
     col = np.empty(nnz, np.int32)
     val = np.empty(nnz, np.float64)
     lib.oracle_fill(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()),
-                    _p(cs), _p(sn), _p(rp), _p(col), _p(val))
+                    _p(cs), _p(sn), _p(rp), _p(col), _p(val), _i32(g.model_id()))
     return CSR(g.rows, g.cols, rp, col, val)
 
 
@@ -195,7 +203,7 @@ def row(g: Geometry, i: int):
     col = np.empty(cap, np.int32)
     val = np.empty(cap, np.float64)
     n = _load().oracle_row(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _dbl(g.c()), _dbl(cs[m]),
-                           _dbl(sn[m]), _i32(k), _p(col), _p(val), _i64(cap))
+                           _dbl(sn[m]), _i32(k), _p(col), _p(val), _i64(cap), _i32(g.model_id()))
     assert n <= cap
     return col[:n].copy(), val[:n].copy()
 
@@ -203,11 +211,11 @@ def row(g: Geometry, i: int):
 def pixel_row(g: Geometry, j: int):
     """Row j of A^T (one pixel): (ray indices int32, chord lengths float64)."""
     cs, sn = g.trig()
-    cap = 2 * g.n_theta + 8
+    cap = 3 * g.n_theta + 8
     col = np.empty(cap, np.int32)
     val = np.empty(cap, np.float64)
     n = _load().oracle_pixel_row(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()), _p(cs), _p(sn),
-                                 _i64(int(j)), _p(col), _p(val), _i64(cap))
+                                 _i64(int(j)), _p(col), _p(val), _i64(cap), _i32(g.model_id()))
     assert n <= cap
     return col[:n].copy(), val[:n].copy()
 
@@ -226,7 +234,7 @@ def project_mf(g: Geometry, x) -> np.ndarray:
     cs, sn = g.trig()
     y = np.empty((nz, g.rows))
     _load().oracle_project_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()),
-                              _p(cs), _p(sn), _i32(nz), _p(x), _p(y))
+                              _p(cs), _p(sn), _i32(nz), _p(x), _p(y), _i32(g.model_id()))
     return y
 
 
@@ -236,7 +244,7 @@ def backproject_mf(g: Geometry, y) -> np.ndarray:
     cs, sn = g.trig()
     x = np.empty((nz, g.cols))
     _load().oracle_backproject_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta),
-                                  _dbl(g.c()), _p(cs), _p(sn), _i32(nz), _p(y), _p(x))
+                                  _dbl(g.c()), _p(cs), _p(sn), _i32(nz), _p(y), _p(x), _i32(g.model_id()))
     return x
 
 
@@ -292,7 +300,8 @@ def loss_grad_mf(g: Geometry, x, b, mu: float = 1e-3, eps: float = 1e-3):
     cs, sn = g.trig()
     grad = np.empty_like(x)
     f = _load().oracle_loss_grad_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()), _p(cs),
-                                    _p(sn), _i32(nz), _p(x), _p(b), _dbl(mu), _dbl(eps), _p(grad))
+                                    _p(sn), _i32(nz), _p(x), _p(b), _dbl(mu), _dbl(eps), _p(grad),
+                                    _i32(g.model_id()))
     return float(f), grad
 
 

@@ -62,11 +62,26 @@ void oracle_trig(int32_t nt, const double *theta, double *cs, double *sn) {
   }
 }
 
-/* Chord length of ray (cs, sn, bin k) through pixel (ix, iy).
- * Returns 1 and stores the length when the pixel is hit (delta < h), else 0.
- * Pinned: Liang-Barsky clipping on 8x8 grids, theta = 0 and pi/2 special cases. */
+/* Strip model: F(s) = integral of the chord length over offsets [0, s], s >= 0.
+ * The chord length at offset s from the pixel centre's projection is a
+ * trapezoid: 1/a for |s| <= hm, (h - |s|)/(a e) for hm < |s| < h, 0 beyond;
+ * F reaches 1/2 (half the pixel's area) at s = h.  Operation order fixed. */
+static double strip_F(double s, double inv_a, double ae, double h, double hm) {
+  if (s <= hm) return s * inv_a;
+  if (s >= h) return 0.5;
+  return hm * inv_a + (s - hm) * (h - 0.5 * (s + hm)) / ae;
+}
+
+/* Weight of ray (cs, sn, bin k) and pixel (ix, iy).  model 0 (line): the
+ * chord length of the line x cos + y sin = p_k through the pixel square, hit
+ * iff delta < h.  model 1 (strip): the area of the pixel square inside the
+ * strip |x cos + y sin - p_k| < 1/2, i.e. the line integral of Sec. 2 averaged
+ * over a detector bin of unit width: F(delta + 1/2) - F(delta - 1/2) with F
+ * odd, hit iff delta < h + 1/2.  Returns 1 and stores the weight on a hit.
+ * Pinned: Liang-Barsky clipping (line) and polygon clipping (strip) on 8x8
+ * grids, theta = 0 and pi/2 special cases, exact mass of the strip model. */
 int oracle_weight(int32_t nx, int32_t ny, double c, double cs, double sn,
-                  int32_t k, int32_t ix, int32_t iy, double *len) {
+                  int32_t k, int32_t ix, int32_t iy, double *len, int32_t model) {
   double acs = fabs(cs), asn = fabs(sn);
   double a = acs > asn ? acs : asn;
   double e = acs > asn ? asn : acs;
@@ -78,6 +93,15 @@ int oracle_weight(int32_t nx, int32_t ny, double c, double cs, double sn,
   double t = x * cs + y * sn;
   double d = pk - t;
   double del = fabs(d);
+  if (model == 1) {
+    if (!(del < h + 0.5)) return 0;
+    double inv_a = 1.0 / a, ae = a * e;
+    double dp = del + 0.5, dm = del - 0.5;
+    double Fp = strip_F(dp, inv_a, ae, h, hm);
+    double Fm = dm >= 0.0 ? strip_F(dm, inv_a, ae, h, hm) : -strip_F(-dm, inv_a, ae, h, hm);
+    *len = Fp - Fm;
+    return 1;
+  }
   if (!(del < h)) return 0;
   if (del <= hm)
     *len = 1.0 / a;
@@ -87,9 +111,9 @@ int oracle_weight(int32_t nx, int32_t ny, double c, double cs, double sn,
 }
 
 /* Bins k whose ray can hit the pixel centred at t = x cs + y sn.
- * |p_k - t| < h <= 1/sqrt(2) means k lies within 0.71 of u = t + c - 1/2, so the
- * five integers floor(u)-2 .. floor(u)+2 contain every hit; each candidate is
- * then decided by oracle_weight itself. */
+ * |p_k - t| < h <= 1/sqrt(2) (line) or < h + 1/2 <= 1.21 (strip) means k lies
+ * within 1.21 of u = t + c - 1/2, so the five integers floor(u)-2 .. floor(u)+2
+ * contain every hit; each candidate is then decided by oracle_weight itself. */
 static void candidate_bins(double c, double cs, double sn, int32_t nx, int32_t ny,
                            int32_t ix, int32_t iy, int64_t *k0) {
   double x = ((double)ix + 0.5) - 0.5 * (double)nx;
@@ -100,7 +124,7 @@ static void candidate_bins(double c, double cs, double sn, int32_t nx, int32_t n
 
 /* Number of entries in each row of A (rows = n_theta * n_p).  Returns nnz. */
 int64_t oracle_count(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
-                     const double *cs, const double *sn, int64_t *row_count) {
+                     const double *cs, const double *sn, int64_t *row_count, int32_t model) {
   int64_t rows = (int64_t)nt * np_;
   memset(row_count, 0, sizeof(int64_t) * rows);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -112,7 +136,7 @@ int64_t oracle_count(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
         for (int64_t k = k0; k < k0 + 5; ++k) {
           double L;
           if (k < 0 || k >= np_) continue;
-          if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L))
+          if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L, model))
             row_count[(int64_t)m * np_ + k]++;
         }
       }
@@ -127,7 +151,7 @@ int64_t oracle_count(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
  * increasing j = iy*nx + ix. */
 void oracle_fill(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
                  const double *cs, const double *sn, const int64_t *row_ptr,
-                 int32_t *col, double *val) {
+                 int32_t *col, double *val, int32_t model) {
 #pragma omp parallel
   {
     int64_t *cursor = (int64_t *)malloc(sizeof(int64_t) * (size_t)np_);
@@ -141,7 +165,7 @@ void oracle_fill(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
           for (int64_t k = k0; k < k0 + 5; ++k) {
             double L;
             if (k < 0 || k >= np_) continue;
-            if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L)) {
+            if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L, model)) {
               int64_t e = cursor[k]++;
               col[e] = iy * nx + ix;
               val[e] = L;
@@ -156,12 +180,12 @@ void oracle_fill(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
 /* One row of A by brute force over every pixel (for sampling huge matrices).
  * Returns the entry count; writes at most cap entries. */
 int64_t oracle_row(int32_t nx, int32_t ny, int32_t np_, double c, double cs, double sn,
-                   int32_t k, int32_t *col, double *val, int64_t cap) {
+                   int32_t k, int32_t *col, double *val, int64_t cap, int32_t model) {
   int64_t n = 0;
   for (int32_t iy = 0; iy < ny; ++iy)
     for (int32_t ix = 0; ix < nx; ++ix) {
       double L;
-      if (oracle_weight(nx, ny, c, cs, sn, k, ix, iy, &L)) {
+      if (oracle_weight(nx, ny, c, cs, sn, k, ix, iy, &L, model)) {
         if (n < cap) {
           col[n] = iy * nx + ix;
           val[n] = L;
@@ -177,7 +201,7 @@ int64_t oracle_row(int32_t nx, int32_t ny, int32_t np_, double c, double cs, dou
  * m*n_p + k with their chord lengths, from the same candidate bins as
  * oracle_count.  Returns the entry count; writes at most cap entries. */
 int64_t oracle_pixel_row(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c, const double *cs,
-                         const double *sn, int64_t j, int32_t *col, double *val, int64_t cap) {
+                         const double *sn, int64_t j, int32_t *col, double *val, int64_t cap, int32_t model) {
   int32_t ix = (int32_t)(j % nx), iy = (int32_t)(j / nx);
   int64_t n = 0;
   for (int32_t m = 0; m < nt; ++m) {
@@ -186,7 +210,7 @@ int64_t oracle_pixel_row(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double
     for (int64_t k = k0; k < k0 + 5; ++k) {
       double L;
       if (k < 0 || k >= np_) continue;
-      if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L)) {
+      if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L, model)) {
         if (n < cap) {
           col[n] = (int32_t)((int64_t)m * np_ + k);
           val[n] = L;
@@ -236,7 +260,7 @@ void oracle_spmv(int64_t rows, int64_t cols, const int64_t *rp, const int32_t *c
  * Each row's terms are summed in increasing pixel order, as in the CSR form. */
 void oracle_project_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
                        const double *cs, const double *sn, int32_t nz,
-                       const double *x, double *y) {
+                       const double *x, double *y, int32_t model) {
   int64_t cols = (int64_t)nx * ny, rows = (int64_t)nt * np_;
   memset(y, 0, sizeof(double) * rows * nz);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -248,7 +272,7 @@ void oracle_project_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c
         for (int64_t k = k0; k < k0 + 5; ++k) {
           double L;
           if (k < 0 || k >= np_) continue;
-          if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L)) {
+          if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L, model)) {
             int64_t j = (int64_t)iy * nx + ix, i = (int64_t)m * np_ + k;
             for (int32_t s = 0; s < nz; ++s) y[s * rows + i] += L * x[s * cols + j];
           }
@@ -259,7 +283,7 @@ void oracle_project_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c
 /* Matrix-free x' = A^T y; each pixel sums its terms in increasing row order. */
 void oracle_backproject_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c,
                            const double *cs, const double *sn, int32_t nz,
-                           const double *y, double *x) {
+                           const double *y, double *x, int32_t model) {
   int64_t cols = (int64_t)nx * ny, rows = (int64_t)nt * np_;
 #pragma omp parallel for schedule(static)
   for (int64_t j = 0; j < cols; ++j) {
@@ -271,7 +295,7 @@ void oracle_backproject_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, doub
       for (int64_t k = k0; k < k0 + 5; ++k) {
         double L;
         if (k < 0 || k >= np_) continue;
-        if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L)) {
+        if (oracle_weight(nx, ny, c, cs[m], sn[m], (int32_t)k, ix, iy, &L, model)) {
           int64_t i = (int64_t)m * np_ + k;
           for (int32_t s = 0; s < nz; ++s) x[s * cols + j] += L * y[s * rows + i];
         }
@@ -454,16 +478,16 @@ double oracle_loss_grad(int64_t rows, int64_t cols,
 /* The same objective and gradient with the matrix-free projector pair. */
 double oracle_loss_grad_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c, const double *cs,
                            const double *sn, int32_t nz, const double *x, const double *b, double mu, double eps,
-                           double *grad) {
+                           double *grad, int32_t model) {
   int64_t rows = (int64_t)nt * np_, cols = (int64_t)nx * ny;
   double *r = (double *)malloc(sizeof(double) * rows * nz);
-  oracle_project_mf(nx, ny, np_, nt, c, cs, sn, nz, x, r);
+  oracle_project_mf(nx, ny, np_, nt, c, cs, sn, nz, x, r, model);
   double f = 0.0;
   for (int64_t i = 0; i < rows * nz; ++i) {
     r[i] -= b[i];
     f += r[i] * r[i];
   }
-  oracle_backproject_mf(nx, ny, np_, nt, c, cs, sn, nz, r, grad);
+  oracle_backproject_mf(nx, ny, np_, nt, c, cs, sn, nz, r, grad, model);
   for (int64_t j = 0; j < cols * nz; ++j) grad[j] *= 2.0;
   f += tv_add(nx, ny, nz, x, mu, eps, grad);
   free(r);

@@ -26,13 +26,16 @@ CASES = {
     "square_8x8_12": dict(nx=8, ny=8, n_p=8, n_theta=12, angles=None, center=None),
     # non-square grid, odd detector, shifted axis, user angles (one negative, one past pi)
     "rect_7x5_9_shifted": dict(nx=7, ny=5, n_p=9, n_theta=5, angles=[-0.3, 0.0, 0.7, 1.9, 3.3], center=3.7),
+    # the strip model (area of each pixel inside a unit-width strip) on the 8x8 square
+    "strip_8x8_12": dict(nx=8, ny=8, n_p=8, n_theta=12, angles=None, center=None, model="strip"),
 }
 SIRT_ITERS, CGLS_ITERS, SLICES = 10, 4, 2
 
 
 def make(name, spec):
     g = oracle.Geometry(spec["nx"], spec["ny"], spec["n_p"], spec["n_theta"],
-                        None if spec["angles"] is None else np.array(spec["angles"], np.float64), spec["center"])
+                        None if spec["angles"] is None else np.array(spec["angles"], np.float64), spec["center"],
+                        spec.get("model", "line"))
     A = oracle.build_matrix(g)
     AT = A.transpose()
     rng = np.random.default_rng(20031267)
@@ -41,7 +44,8 @@ def make(name, spec):
     sirt = oracle.sirt(A, AT, b, SIRT_ITERS)
     cgls, hist = oracle.cgls(A, AT, b, CGLS_ITERS)
     return {
-        "source": "tests/golden/make_golden.py (FP64 oracle: chord-length line model, SIRT, CGLS of Sec. 2.1)",
+        "source": "tests/golden/make_golden.py (FP64 oracle: %s model, SIRT, CGLS of Sec. 2.1)"
+                  % spec.get("model", "line"),
         "geometry": spec, "rows": A.rows, "cols": A.cols,
         "row_ptr": A.row_ptr.tolist(), "col": A.col.tolist(), "val": [repr(float(v)) for v in A.val],
         "x_true": [[repr(float(v)) for v in s] for s in x_true],

@@ -33,11 +33,12 @@ def load(path):
 def geometry(d):
     s = d["geometry"]
     return oracle.Geometry(s["nx"], s["ny"], s["n_p"], s["n_theta"],
-                           None if s["angles"] is None else np.array(s["angles"], np.float64), s["center"])
+                           None if s["angles"] is None else np.array(s["angles"], np.float64), s["center"],
+                           s.get("model", "line"))
 
 
 def test_fixtures_exist():
-    assert len(FILES) >= 2
+    assert len(FILES) >= 3
 
 
 @pytest.mark.parametrize("path", FILES, ids=[os.path.basename(p) for p in FILES])
@@ -76,7 +77,8 @@ def test_gpu_matches_golden(path):
     import paper_2003_12677_b300 as tomo
     d = load(path)
     s = d["geometry"]
-    M = tomo.Matrix(s["nx"], s["n_theta"], n_p=s["n_p"], n_y=s["ny"], angles=s["angles"], center=s["center"])
+    M = tomo.Matrix(s["nx"], s["n_theta"], n_p=s["n_p"], n_y=s["ny"], angles=s["angles"], center=s["center"],
+                    model=s.get("model", "line"))
     rp, col, val = M.export_csr()
     np.testing.assert_array_equal(rp, d["row_ptr"])
     np.testing.assert_array_equal(col, d["col"])

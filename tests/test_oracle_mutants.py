@@ -31,6 +31,10 @@ MUTANTS = {
     "TV gradient: neighbour sign": ("g[j + nx] += mu * dy / t;", "g[j + nx] -= mu * dy / t;"),
     "transpose: wrong row index": ("tci[d] = (int32_t)i;", "tci[d] = (int32_t)(rows - 1 - i);"),
     "normaliser: sum for 1/sum": ("out[i] = s != 0.0 ? 1.0 / s : 0.0;", "out[i] = s != 0.0 ? s : 0.0;"),
+    "strip: support without the half bin": ("if (!(del < h + 0.5)) return 0;", "if (!(del < h)) return 0;"),
+    "strip: window edge sign": ("double dp = del + 0.5, dm = del - 0.5;", "double dp = del + 0.5, dm = 0.5 - del;"),
+    "strip: ramp integral": ("return hm * inv_a + (s - hm) * (h - 0.5 * (s + hm)) / ae;",
+                             "return hm * inv_a + (s - hm) * (h - 0.5 * (s - hm)) / ae;"),
 }
 
 

@@ -178,8 +178,9 @@ def test_mass_conservation():
     assert rel.max() < 1e-3
 
 
-def test_transpose_is_exact_transpose():
-    g = oracle.Geometry(24, 20, 30, 13, center=14.6)
+@pytest.mark.parametrize("model", ["line", "strip"])
+def test_transpose_is_exact_transpose(model):
+    g = oracle.Geometry(24, 20, 30, 13, center=14.6, model=model)
     A = oracle.build_matrix(g)
     AT = A.transpose()
     S = scipy.sparse.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.rows, A.cols))
@@ -190,8 +191,9 @@ def test_transpose_is_exact_transpose():
     np.testing.assert_array_equal(AT.val, T.data)
 
 
-def test_adjoint_identity_fp64():
-    g = oracle.Geometry(40, 40, 44, 31)
+@pytest.mark.parametrize("model", ["line", "strip"])
+def test_adjoint_identity_fp64(model):
+    g = oracle.Geometry(40, 40, 44, 31, model=model)
     A = oracle.build_matrix(g)
     AT = A.transpose()
     rng = np.random.default_rng(5)
@@ -202,8 +204,9 @@ def test_adjoint_identity_fp64():
     assert abs(lhs - rhs) <= 1e-13 * abs(lhs) * 10
 
 
-def test_pixel_rows_are_the_transpose_rows():
-    g = oracle.Geometry(30, 26, 34, 19, center=16.4)
+@pytest.mark.parametrize("model", ["line", "strip"])
+def test_pixel_rows_are_the_transpose_rows(model):
+    g = oracle.Geometry(30, 26, 34, 19, center=16.4, model=model)
     A = oracle.build_matrix(g)
     AT = A.transpose()
     for j in list(range(0, A.cols, 53)) + [0, A.cols - 1]:
@@ -225,8 +228,9 @@ def test_matrix_free_loss_grad_equals_stored():
     np.testing.assert_array_equal(g1, g2)
 
 
-def test_matrix_free_equals_stored():
-    g = oracle.Geometry(33, 33, 35, 21, center=17.2)
+@pytest.mark.parametrize("model", ["line", "strip"])
+def test_matrix_free_equals_stored(model):
+    g = oracle.Geometry(33, 33, 35, 21, center=17.2, model=model)
     A = oracle.build_matrix(g)
     AT = A.transpose()
     rng = np.random.default_rng(9)
@@ -516,3 +520,93 @@ def test_bb_zero_data_freezes():
     A = oracle.build_matrix(g)
     x, hist = oracle.sirt_bb(A, A.transpose(), 8, np.zeros((1, A.rows)), 4)
     assert np.all(x == 0) and np.all(hist == 0)
+
+
+# ---------------------------------------------------------------------------
+# strip model: the area of the pixel square inside a unit-width strip
+# ---------------------------------------------------------------------------
+
+def clip_area(theta, p, xc, yc):
+    """Area of the unit square centred (xc, yc) inside |x cos t + y sin t - p| <= 1/2:
+    Sutherland-Hodgman clipping of the square against the two half-planes, then
+    the shoelace formula."""
+    c, s_ = math.cos(theta), math.sin(theta)
+    poly = [(xc - 0.5, yc - 0.5), (xc + 0.5, yc - 0.5), (xc + 0.5, yc + 0.5), (xc - 0.5, yc + 0.5)]
+    for sign, off in ((1.0, p + 0.5), (-1.0, -(p - 0.5))):   # sign*(x c + y s) <= off
+        f = lambda q: sign * (q[0] * c + q[1] * s_) - off  # noqa: E731
+        out = []
+        for i in range(len(poly)):
+            a, b = poly[i], poly[(i + 1) % len(poly)]
+            fa, fb = f(a), f(b)
+            if fa <= 0:
+                out.append(a)
+            if (fa < 0 < fb) or (fb < 0 < fa):
+                t = fa / (fa - fb)
+                out.append((a[0] + t * (b[0] - a[0]), a[1] + t * (b[1] - a[1])))
+        poly = out
+        if not poly:
+            return 0.0
+    area = 0.0
+    for i in range(len(poly)):
+        (x0, y0), (x1, y1) = poly[i], poly[(i + 1) % len(poly)]
+        area += x0 * y1 - x1 * y0
+    return abs(area) / 2
+
+
+@pytest.mark.parametrize("nx,ny,n_p,center,angles", [
+    (8, 8, 8, None, [0.0, math.pi / 4, math.pi / 2, 0.3, 1.1, 2.0, 2.9, 3.0]),
+    (8, 8, 11, 5.3, [0.05, 0.7, 1.5707, 1.6, 2.356194490192345, 3.1]),
+    (7, 9, 12, None, list(np.random.default_rng(3).uniform(0, math.pi, 10))),
+])
+def test_strip_weights_match_polygon_clipping(nx, ny, n_p, center, angles):
+    g = oracle.Geometry(nx, ny, n_p, len(angles), np.array(angles), center, model="strip")
+    c = g.c()
+    for m, th in enumerate(angles):
+        for k in range(n_p):
+            p = k + 0.5 - c
+            for iy in range(ny):
+                for ix in range(nx):
+                    ref = clip_area(th, p, ix + 0.5 - nx / 2, iy + 0.5 - ny / 2)
+                    w = oracle.weight(g, m, k, ix, iy)
+                    if w is None:
+                        assert ref < 1e-12, (m, k, ix, iy, ref)
+                    else:
+                        assert abs(w - ref) < 1e-12, (m, k, ix, iy, w, ref)
+
+
+def test_strip_mass_is_exact_per_angle():
+    """Each pixel's weights over the bins of one angle add up to its area, 1,
+    whenever its projection lies inside the detector (the strips tile the
+    detector line)."""
+    g = oracle.Geometry(24, 20, 30, 17, center=14.6, model="strip")
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    cs, sn = g.trig()
+    c = g.c()
+    checked = 0
+    for j in range(A.cols):
+        ix, iy = j % g.nx, j // g.nx
+        x, y = ix + 0.5 - g.nx / 2, iy + 0.5 - g.ny / 2
+        lo, hi = AT.row_ptr[j], AT.row_ptr[j + 1]
+        rays, vals = AT.col[lo:hi], AT.val[lo:hi]
+        for m in range(g.n_theta):
+            a = max(abs(cs[m]), abs(sn[m]))
+            e = min(abs(cs[m]), abs(sn[m]))
+            t = x * cs[m] + y * sn[m]
+            if t - 0.5 * (a + e) < -c or t + 0.5 * (a + e) > g.n_p - c:
+                continue
+            sel = (rays // g.n_p) == m
+            assert abs(vals[sel].sum() - 1.0) < 1e-12
+            checked += 1
+    assert checked > 0.8 * A.cols * g.n_theta
+
+
+def test_strip_theta_zero_is_column_sum():
+    """theta = 0 with bins aligned to pixel columns: each pixel lies entirely
+    in one strip (weight 1), so (A x)_k is the sum of image column k."""
+    n = 9
+    g = oracle.Geometry(n, n, n, 1, np.array([0.0]), model="strip")
+    A = oracle.build_matrix(g)
+    assert np.all(A.val == 1.0) and A.nnz == n * n
+    x = np.random.default_rng(2).random((1, n * n))
+    np.testing.assert_allclose(A.apply(x)[0], x.reshape(n, n).sum(axis=0), rtol=1e-15)
