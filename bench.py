@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip e2e / plain-CSR legs")
     p.add_argument("--iters", type=int, default=0, help="override the solver iterations (profiling runs)")
     p.add_argument("--no-graph", action="store_true", help="launch kernels directly (profiling runs)")
+    p.add_argument("--model", default="line", choices=["line", "strip"],
+                   help="matrix model: chord lengths (line) or areas in unit-width strips (strip)")
     return p.parse_args()
 
 
@@ -137,11 +139,11 @@ def bus_id_of(dev):
 # ---------------------------------------------------------------------------
 # oracle (CPU) leg: the FP64 reference timed on the host cores
 # ---------------------------------------------------------------------------
-def oracle_sample(w, slices=1, iters=1, steps=1, warmup=0):
+def oracle_sample(w, slices=1, iters=1, steps=1, warmup=0, model="line"):
     """Time oracle SIRT on a bounded sample of the workload; returns a dict."""
     import oracle
     from paper_2003_12677_b300 import inputs
-    g = oracle.Geometry(w.n, w.n, w.n, w.n_theta)
+    g = oracle.Geometry(w.n, w.n, w.n, w.n_theta, model=model)
     t0 = time.perf_counter()
     A = oracle.build_matrix(g)
     AT = A.transpose()
@@ -163,8 +165,8 @@ def oracle_sample(w, slices=1, iters=1, steps=1, warmup=0):
 KERNEL = {"sell": "sell", "sell16": "sell16", "csr": "f32"}
 
 
-def workload_config(w, B, fmt):
-    return {"workload": w.name, "n": w.n, "n_theta": w.n_theta, "n_p": w.n, "slices": w.n_z,
+def workload_config(w, B, fmt, model="line"):
+    return {"workload": w.name, "n": w.n, "n_theta": w.n_theta, "n_p": w.n, "slices": w.n_z, "model": model,
             "solver": w.solver, "iters": w.iters, "batch_width": B, "format": fmt,
             "values": (w.values if w.values != "f32" else "bf16") if fmt == "sell16" else "f32",
             "l2": "working set larger than L2: A and A^T are streamed from HBM every iteration"}
@@ -174,11 +176,11 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    res = oracle_sample(w, slices=4, iters=2, steps=args.steps, warmup=args.warmup)
+    res = oracle_sample(w, slices=4, iters=2, steps=args.steps, warmup=args.warmup, model=args.model)
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * res["seconds"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": DATA, "config": workload_config(w, 0, "sell"),
+            "data": DATA, "config": workload_config(w, 0, "sell", args.model),
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -471,7 +473,7 @@ def main():
     values = (w.values if w.values != "f32" else "bf16") if fmt == "sell16" else "f32"
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    M = tomo.Matrix(w.n, w.n_theta, values=values)
+    M = tomo.Matrix(w.n, w.n_theta, values=values, model=args.model)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     tune = None
@@ -521,7 +523,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if fmt != "sell16" else "f32-accumulate/%s-values" % values,
-            "data": DATA, "config": workload_config(w, B, fmt), "clocks": clk,
+            "data": DATA, "config": workload_config(w, B, fmt, args.model), "clocks": clk,
             "build_s": build_s, "nnz": M.nnz}
     if tune is not None:
         line["autotune"] = {"chosen": [tune["batch_width"], tune["format"]],
@@ -623,7 +625,7 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = oracle_sample(w, slices=8, iters=48, steps=1)
+            line["cpu_baseline"] = oracle_sample(w, slices=8, iters=48, steps=1, model=args.model)
         except Exception as e:  # reported, never fatal for the GPU number
             line["cpu_baseline"] = {"error": str(e)}
 

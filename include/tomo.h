@@ -74,6 +74,14 @@ typedef struct {
   double center;
 } tomo_geometry;
 
+/* Discretisation of the line integral of Sec. 2 over a pixel image. */
+typedef enum {
+  TOMO_MODEL_LINE = 0, /* chord length of the line x cos + y sin = p_k through the pixel square */
+  TOMO_MODEL_STRIP = 1 /* area of the pixel square inside the strip |x cos + y sin - p_k| < 1/2
+                          (the line integral averaged over a detector bin of unit width);
+                          about 1.7x the entries of the line model, exact per-angle mass */
+} tomo_model;
+
 /* Build options.  values: TOMO_F32 builds the FP32 operands (canonical CSR and
  * the SELL-32 form the kernels stream).  TOMO_BF16 / TOMO_F16 also build the
  * 16-bit encoding (16-bit values scaled per angle so a full chord is exactly
@@ -86,7 +94,8 @@ typedef struct {
   int32_t drop_csr;      /* non-zero: free the CSR pair once the SELL forms are built (saves 8 B/nnz
                             per operand); export calls and TOMO_FMT_CSR then report UNSUPPORTED.
                             Needs at least one SELL form. */
-  int32_t reserved[5];
+  int32_t model;         /* tomo_model (default TOMO_MODEL_LINE) */
+  int32_t reserved[4];
 } tomo_matrix_opts;
 
 /* Device time of the kernels one call launched, filled when a call is given

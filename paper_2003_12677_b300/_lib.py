@@ -35,7 +35,7 @@ class Geometry(ctypes.Structure):
 
 class MatrixOpts(ctypes.Structure):
     _fields_ = [("values", ctypes.c_int32), ("no_fp32_sell", ctypes.c_int32), ("drop_csr", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Timing(ctypes.Structure):

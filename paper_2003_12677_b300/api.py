@@ -62,6 +62,9 @@ def new_timing() -> _lib.Timing:
     return _lib.Timing()
 
 
+MODELS = {"line": 0, "strip": 1}
+
+
 class Matrix:
     """A and A^T for one parallel-beam geometry, resident on the current device.
 
@@ -74,7 +77,7 @@ class Matrix:
 
     def __init__(self, n: int, n_theta: int, n_p: Optional[int] = None, n_y: Optional[int] = None,
                  angles=None, center: Optional[float] = None, values: str = "f32", fp32_sell: bool = True,
-                 keep_csr: bool = True):
+                 keep_csr: bool = True, model: str = "line"):
         self._h = None
         lib = _lib.load()
         if not torch.cuda.is_available():
@@ -98,11 +101,13 @@ class Matrix:
         o.values = _lib.DTYPES[values]
         o.no_fp32_sell = 0 if fp32_sell else 1
         o.drop_csr = 0 if keep_csr else 1
+        o.model = MODELS[model]
         h = ctypes.c_void_p()
         _lib.check(lib.tomo_build_matrix(ctypes.byref(g), ctypes.byref(o), _stream(), ctypes.byref(h)),
                    "tomo_build_matrix")
         self._h = h
         self.values = values
+        self.model = model
         info = _lib.MatrixInfo()
         _lib.check(lib.tomo_matrix_info(self._h, ctypes.byref(info)), "tomo_matrix_info")
         self.rows, self.cols, self.nnz = info.rows, info.cols, info.nnz

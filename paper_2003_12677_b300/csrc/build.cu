@@ -12,8 +12,11 @@
 //     run of consecutive ix (the rounded predicate is monotone in x), so a warp
 //     per ray finds each run's ends and writes the columns in ascending order;
 //   * A^T, pixel-driven: for pixel (ix,iy) and angle m at most two bins k are
-//     hit, so a warp per pixel tests the candidates of 32 angles at a time and
-//     compacts the hits in (m, k) order.
+//     hit (three in the strip model), so a warp per pixel tests the candidates
+//     of 32 angles at a time and compacts the hits in (m, k) order.
+// Two discretisations share the enumeration: the line model (chord lengths)
+// and the strip model (the area of the pixel inside the unit-width strip of
+// bin k), which differ only in the support half width hs and the weight.
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -29,9 +32,12 @@ namespace {
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------
-// The chord rule in IEEE FP64 without contraction:
-//   t = fl(fl(x cs) + fl(y sn)), delta = |fl(p - t)|, hit iff delta < h,
-//   length = 1/a if delta <= hm else fl(fl(h - delta) / (a e)).
+// The weight rules in IEEE FP64 without contraction:
+//   t = fl(fl(x cs) + fl(y sn)), delta = |fl(p - t)|, hit iff delta < hs;
+//   line:  length = 1/a if delta <= hm else fl(fl(h - delta) / (a e)), hs = h;
+//   strip: F(delta + 1/2) - F(delta - 1/2), F odd, F(s) = s (1/a) for s <= hm,
+//          hm (1/a) + (s - hm)(h - (s + hm)/2) / (a e) for hm < s < h,
+//          1/2 for s >= h (F integrates the chord length), hs = h + 1/2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double coord(int i, int n) {
   return __dsub_rn(__dadd_rn((double)i, 0.5), 0.5 * (double)n);  // exact
@@ -43,11 +49,24 @@ __device__ __forceinline__ double chord_delta(const AngleC &A, double pk, double
 }
 
 __device__ __forceinline__ bool chord_hit(const AngleC &A, double pk, double x, double y) {
-  return chord_delta(A, pk, x, y) < A.h;
+  return chord_delta(A, pk, x, y) < A.hs;
 }
 
-__device__ __forceinline__ double chord_len(const AngleC &A, double pk, double x, double y) {
+__device__ __forceinline__ double strip_F(const AngleC &A, double s) {
+  if (s <= A.hm) return __dmul_rn(s, A.inv_a);
+  if (s >= A.h) return 0.5;
+  const double ramp = __dmul_rn(__dsub_rn(s, A.hm), __dsub_rn(A.h, __dmul_rn(0.5, __dadd_rn(s, A.hm))));
+  return __dadd_rn(__dmul_rn(A.hm, A.inv_a), __ddiv_rn(ramp, A.ae));
+}
+
+__device__ __forceinline__ double chord_len(const AngleC &A, int model, double pk, double x, double y) {
   double del = chord_delta(A, pk, x, y);
+  if (model == TOMO_MODEL_STRIP) {
+    const double dp = __dadd_rn(del, 0.5), dm = __dsub_rn(del, 0.5);
+    const double Fp = strip_F(A, dp);
+    const double Fm = dm >= 0.0 ? strip_F(A, dm) : -strip_F(A, -dm);
+    return __dsub_rn(Fp, Fm);
+  }
   return del <= A.hm ? A.inv_a : __ddiv_rn(__dsub_rn(A.h, del), A.ae);
 }
 
@@ -67,7 +86,7 @@ __device__ void row_run(const AngleC &A, double pk, int nx, double y, int &lo, i
     return;
   }
   double r = pk - y * A.sn;
-  double xa = (r - A.h) * A.inv_cs, xb = (r + A.h) * A.inv_cs;
+  double xa = (r - A.hs) * A.inv_cs, xb = (r + A.hs) * A.inv_cs;
   double off = 0.5 * nx - 0.5;
   double xl = fmin(xa, xb) + off, xh = fmax(xa, xb) + off;
   xl = fmin(fmax(xl, -16.0), nx + 16.0);
@@ -129,8 +148,8 @@ __global__ void __launch_bounds__(kThreads) k_count_rays(const AngleC *__restric
   if (lane == 0) cnt[w] = total;
 }
 
-__global__ void __launch_bounds__(kThreads) k_fill_rays(const AngleC *__restrict__ ang, int nx, int ny,
-                                                        int np, int nt, double c,
+__global__ void __launch_bounds__(kThreads) k_fill_rays(const AngleC *__restrict__ ang, int model, int nx,
+                                                        int ny, int np, int nt, double c,
                                                         const int64_t *__restrict__ rp,
                                                         int32_t *__restrict__ ci, float *__restrict__ v,
                                                         float *__restrict__ R) {
@@ -162,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_fill_rays(const AngleC *__restrict
         if (q + step < 32 && s_off[wl][q + step] <= e) q += step;
       int ix = s_lo[wl][q] + (e - s_off[wl][q]);
       int yy = iy0 + q;
-      double L = chord_len(A, pk, coord(ix, nx), coord(yy, ny));
+      double L = chord_len(A, model, pk, coord(ix, nx), coord(yy, ny));
       sum += L;
       ci[pos + e] = yy * nx + ix;
       v[pos + e] = __double2float_rn(L);
@@ -178,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_fill_rays(const AngleC *__restrict
 // A^T: count and fill, one warp per pixel, lanes over angles
 // ---------------------------------------------------------------------------
 template <bool kFill>
-__global__ void __launch_bounds__(kThreads) k_pixels(const AngleC *__restrict__ ang, int nx, int ny,
+__global__ void __launch_bounds__(kThreads) k_pixels(const AngleC *__restrict__ ang, int model, int nx, int ny,
                                                      int np, int nt, double c,
                                                      int32_t *__restrict__ cnt,
                                                      const int64_t *__restrict__ rp,
@@ -194,28 +213,29 @@ __global__ void __launch_bounds__(kThreads) k_pixels(const AngleC *__restrict__ 
   double sum = 0.0;
   for (int m0 = 0; m0 < nt; m0 += 32) {
     int m = m0 + lane;
+    constexpr int kMaxBins = 3;  // hits per angle: 2 (line), 3 (strip)
     int nh = 0;
-    int kh[2] = {0, 0};
-    double Lh[2] = {0.0, 0.0};
+    int kh[kMaxBins] = {0, 0, 0};
+    double Lh[kMaxBins] = {0.0, 0.0, 0.0};
     if (m < nt) {
       AngleC A = ang[m];
-      // |p_k - t| < h <= 0.7072 puts k within 0.71 of u = t + c - 1/2
+      // |p_k - t| < hs <= 1.2072 puts k within 1.21 of u = t + c - 1/2
       double u = x * A.cs + y * A.sn + (c - 0.5);
       long long kf = (long long)floor(u);
       for (long long k = kf - 2; k <= kf + 2; ++k) {
         if (k < 0 || k >= np) continue;
         double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
         if (chord_hit(A, pk, x, y)) {
-          if (nh < 2) {
+          if (nh < kMaxBins) {
             kh[nh] = (int)k;
-            if (kFill) Lh[nh] = chord_len(A, pk, x, y);
+            if (kFill) Lh[nh] = chord_len(A, model, pk, x, y);
           } else if (err) {
             atomicExch(err, 1);  // impossible by the bound above; reported, never written
           }
           ++nh;
         }
       }
-      nh = min(nh, 2);
+      nh = min(nh, kMaxBins);
     }
     if (!kFill) {
       total += nh;
@@ -378,7 +398,7 @@ __global__ void k_sell16_len(const int64_t *__restrict__ rp, const int32_t *__re
 // (offset | weight << 16) words and the segment bases; weights A_ij * a(theta)
 // recomputed in FP64 from the geometry.  Padding slots stay zero.
 template <bool kTranspose, typename W>
-__global__ void k_sell16_fill(const AngleC *__restrict__ ang, int nx, int ny, int np, double c,
+__global__ void k_sell16_fill(const AngleC *__restrict__ ang, int model, int nx, int ny, int np, double c,
                               const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t rows,
                               const int64_t *__restrict__ cpw, const int64_t *__restrict__ cpb,
                               uint32_t *__restrict__ ow, int32_t *__restrict__ base, int *__restrict__ err) {
@@ -404,7 +424,7 @@ __global__ void k_sell16_fill(const AngleC *__restrict__ ang, int nx, int ny, in
     int ix = pix % nx, iy = pix / nx;
     AngleC A = ang[m];
     double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
-    double w = __dmul_rn(chord_len(A, pk, coord(ix, nx), coord(iy, ny)), A.a);
+    double w = __dmul_rn(chord_len(A, model, pk, coord(ix, nx), coord(iy, ny)), A.a);
     uint16_t wbits;
     if constexpr (std::is_same<W, __nv_bfloat16>::value)
       wbits = __bfloat16_as_ushort(__double2bfloat16(w));
@@ -507,8 +527,8 @@ tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_
   TOMO_CUDA(cudaMemsetAsync(L.base, 0, sizeof(int32_t) * L.bases, st));
   const double c = h->center;
 #define TOMO_FILL16(TR, W)                                                                                      \
-  k_sell16_fill<TR, W><<<gr, 256, 0, st>>>(h->ang, h->nx, h->ny, h->np, c, M.rp, M.ci, M.rows, L.cpw, L.cpb, L.ow, \
-                                           L.base, scratch)
+  k_sell16_fill<TR, W><<<gr, 256, 0, st>>>(h->ang, h->model, h->nx, h->ny, h->np, c, M.rp, M.ci, M.rows, L.cpw,  \
+                                           L.cpb, L.ow, L.base, scratch)
   if (h->lp_dtype == TOMO_BF16) {
     if (transpose) TOMO_FILL16(true, __nv_bfloat16);
     else TOMO_FILL16(false, __nv_bfloat16);
@@ -605,6 +625,9 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
     return fail(TOMO_ERR_INVALID_ARG, "drop_csr needs a SELL form (FP32 SELL or 16-bit values)");
   double c = std::isnan(g->center) ? 0.5 * (double)g->n_p : g->center;
   if (!std::isfinite(c)) return fail(TOMO_ERR_INVALID_ARG, "center must be finite or NaN");
+  const int32_t model = o ? o->model : TOMO_MODEL_LINE;
+  if (model != TOMO_MODEL_LINE && model != TOMO_MODEL_STRIP)
+    return fail(TOMO_ERR_INVALID_ARG, "opts.model must be TOMO_MODEL_LINE or TOMO_MODEL_STRIP");
   const int nt = g->n_theta;
   std::vector<AngleC> ang(nt);
   std::vector<float> scale(nt);
@@ -623,6 +646,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
     A.ae = A.a * A.e;
     A.inv_cs = A.cs != 0.0 ? 1.0 / A.cs : 0.0;
     A.inv_sn = A.sn != 0.0 ? 1.0 / A.sn : 0.0;
+    A.hs = model == TOMO_MODEL_STRIP ? A.h + 0.5 : A.h;
     scale[m] = (float)(1.0 / A.a);
   }
 
@@ -639,6 +663,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   h->ny = g->n_y;
   h->np = g->n_p;
   h->nt = nt;
+  h->model = model;
   h->center = c;
   h->lp_dtype = lp;
   const int64_t rows = (int64_t)nt * g->n_p, cols = (int64_t)g->n_x * g->n_y;
@@ -672,7 +697,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   k_count_rays<<<grid_for_warps(rows), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, cnt);
   TOMO_CUDA(cudaGetLastError());
   TOMO_TRY(scan_counts(cnt, rows, h->A.rp, part, scratch + 1, st));
-  k_pixels<false><<<grid_for_warps(cols), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, cnt,
+  k_pixels<false><<<grid_for_warps(cols), kThreads, 0, st>>>(h->ang, model, h->nx, h->ny, h->np, nt, c, cnt,
                                                                nullptr, nullptr, nullptr, nullptr, scratch);
   TOMO_CUDA(cudaGetLastError());
   TOMO_TRY(scan_counts(cnt, cols, h->AT.rp, part, scratch + 2, st));
@@ -683,7 +708,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   TOMO_CUDA(cudaMemcpyAsync(&nnz_t, h->AT.rp + cols, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaMemcpyAsync(hs, scratch, sizeof(hs), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));
-  if (hs[0] != 0) return fail(TOMO_ERR_NUMERIC, "pixel enumeration found more than two bins per angle");
+  if (hs[0] != 0) return fail(TOMO_ERR_NUMERIC, "pixel enumeration found more bins per angle than the model allows");
   if (nnz_a != nnz_t)
     return fail(TOMO_ERR_NUMERIC, "ray-driven and pixel-driven entry counts differ: " + std::to_string(nnz_a) +
                                       " vs " + std::to_string(nnz_t));
@@ -704,10 +729,10 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   TOMO_TRY(dmalloc(&h->A.v, nnz_a));
   TOMO_TRY(dmalloc(&h->AT.ci, nnz_a));
   TOMO_TRY(dmalloc(&h->AT.v, nnz_a));
-  k_fill_rays<<<grid_for_warps(rows), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, h->A.rp,
+  k_fill_rays<<<grid_for_warps(rows), kThreads, 0, st>>>(h->ang, model, h->nx, h->ny, h->np, nt, c, h->A.rp,
                                                           h->A.ci, h->A.v, h->R);
   TOMO_CUDA(cudaGetLastError());
-  k_pixels<true><<<grid_for_warps(cols), kThreads, 0, st>>>(h->ang, h->nx, h->ny, h->np, nt, c, nullptr,
+  k_pixels<true><<<grid_for_warps(cols), kThreads, 0, st>>>(h->ang, model, h->nx, h->ny, h->np, nt, c, nullptr,
                                                              h->AT.rp, h->AT.ci, h->AT.v, h->C, scratch);
   TOMO_CUDA(cudaGetLastError());
   h->bytes_f32 = (rows + 1 + cols + 1) * 8 + nnz_a * 16;
@@ -732,7 +757,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   if (hs[0] == 2)
     return fail(TOMO_ERR_UNSUPPORTED, "a 16-entry chunk spans more than 65535 columns (geometry too large "
                                       "for 16-bit offsets)");
-  if (hs[0] != 0) return fail(TOMO_ERR_NUMERIC, "pixel enumeration found more than two bins per angle");
+  if (hs[0] != 0) return fail(TOMO_ERR_NUMERIC, "pixel enumeration found more bins per angle than the model allows");
   TOMO_TRY(build_ramp(h, st));
   guard.keep = true;
   *out = h;

@@ -19,6 +19,7 @@ namespace tomo {
 //   inv_a = 1/a, ae = a*e.  inv_cs / inv_sn only seed candidate searches.
 struct AngleC {
   double cs, sn, a, e, h, hm, inv_a, ae, inv_cs, inv_sn;
+  double hs;  // support half width: h (line model) or h + 1/2 (strip model)
 };
 
 struct Csr {
@@ -70,6 +71,7 @@ struct SellLp {
 
 struct tomo_matrix {
   int32_t nx = 0, ny = 0, np = 0, nt = 0;
+  int32_t model = TOMO_MODEL_LINE;
   double center = 0;
   int device = 0;
   tomo::AngleC *ang = nullptr;   // device [nt]
