@@ -27,8 +27,10 @@ constexpr int kMinBlocks = 6;  // fallback resident blocks per SM when occupancy
 // ---------------------------------------------------------------------------
 // SELL-32 kernels: grid-stride over row groups (see spmm.cuh)
 // ---------------------------------------------------------------------------
+// Six blocks (48 warps) per SM: at the unbounded 46 registers (5 blocks) the
+// B = 64 pass ran 37% slower (gathers in flight limit it, not bandwidth).
 template <int B, class Epi>
-__global__ void __launch_bounds__(kThreads) k_spmm_sell(const int64_t *__restrict__ cp,
+__global__ void __launch_bounds__(kThreads, 6) k_spmm_sell(const int64_t *__restrict__ cp,
                                                         const int32_t *__restrict__ rl,
                                                         const int2 *__restrict__ ent, int64_t rows,
                                                         const float *__restrict__ X, Epi epi,

@@ -253,18 +253,20 @@ __device__ __forceinline__ void sell_rowgroups(const int64_t *__restrict__ cp, c
     // entry pair (e, e+1), e even, of this row sits at p[(e/2)*32]
     const int4 *p = reinterpret_cast<const int4 *>(ent) + (__ldg(cp + (row >> 5)) >> 1) + (row & 31);
     int e = 0;
-    for (; e + 8 <= len; e += 8) {
-      int4 pr[4];
+    // two entry pairs (4 gathers) per step: at 6 blocks per SM (40 registers)
+    // this beat four pairs, which needs more registers than 6 blocks allow
+    for (; e + 4 <= len; e += 4) {
+      int4 pr[2];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pr[u] = __ldcs(p + (size_t)((e >> 1) + u) * 32);
-      Vec<V> xv[8];
+      for (int u = 0; u < 2; ++u) pr[u] = __ldcs(p + (size_t)((e >> 1) + u) * 32);
+      Vec<V> xv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 2; ++u) {
         xv[2 * u] = gather<V, kNC>(Xl + (size_t)pr[u].x * B);
         xv[2 * u + 1] = gather<V, kNC>(Xl + (size_t)pr[u].z * B);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 2; ++u) {
         const float w0 = __int_as_float(pr[u].y), w1 = __int_as_float(pr[u].w);
 #pragma unroll
         for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w0, xv[2 * u].v[t], acc.v[t]);
