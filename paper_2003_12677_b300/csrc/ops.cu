@@ -382,13 +382,22 @@ __global__ void __launch_bounds__(kThreads) k_cgls_dir(float *__restrict__ p, co
 
 // rf = P^T P r on every projection row: rf[m, k, :] = sum_j tap[|k - j|] r[m, j, :]
 // over the n_p bins of row m, j ascending (interleaved (rows, B) vectors).
-// Block (256 threads) = NG bin groups x Q slice groups of V slices; a thread
-// owns KB adjacent output bins and keeps the KB taps it needs in registers,
-// shifting them by one bin per step of j.  Grid: (ceil(n_p / TK), n_theta).
+// Block (256 threads) = 256/Q bin groups x Q slice groups of V slices; a
+// thread owns KB adjacent output bins and keeps the KB taps it needs in
+// registers, shifting them by one bin per step of j (the unrolled shift costs
+// no moves).  Grid: (ceil(n_p / TK), n_theta).
+constexpr int kRampKB = 8;  // output bins per thread
+
+// output bins one block of k_ramp_filter<B> covers
+template <int B>
+constexpr int ramp_tile_bins() {
+  return kRampKB * kThreads / (B >= 4 ? B / 4 : 1);
+}
+
 template <int B>
 __global__ void __launch_bounds__(kThreads) k_ramp_filter(const float *__restrict__ r, float *__restrict__ rf,
                                                           const float *__restrict__ tap, int np) {
-  constexpr int V = B >= 4 ? 4 : B, Q = B / V, KB = 4, NG = kThreads / Q, TK = NG * KB, TJ = 32;
+  constexpr int V = B >= 4 ? 4 : B, Q = B / V, KB = kRampKB, TK = ramp_tile_bins<B>(), TJ = 32;
   __shared__ __align__(16) float rs[TJ * B];
   const int q = threadIdx.x % Q, kg = threadIdx.x / Q;
   const int64_t m = blockIdx.y;
@@ -986,7 +995,7 @@ tomo_status bb_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, 
 
   const int gR = spmm_grid_of<B, EpiResidualNorm>(A);
   constexpr int PER = B >= 4 ? B / 4 : 1;
-  constexpr int TK = 4 * kThreads / PER;
+  constexpr int TK = ramp_tile_bins<B>();
   const int ge = elem_grid(cols * PER);
   const dim3 gf((unsigned)((h->np + TK - 1) / TK), (unsigned)h->nt);
   const double a0 = first_step > 0.0 ? first_step : 3.141592653589793 / (double)h->nt;
