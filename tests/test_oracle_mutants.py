@@ -65,6 +65,7 @@ def test_unmutated_variant_passes(tmp_path):
 # of Sec. 3.1 and its filter): a mutated copy of the package is put first on
 # the path, with the unmodified C library.
 PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
+FUB_SRC = os.path.join(ROOT, "oracle", "fubini.py")
 PY_MUTANTS = {
     "BB: first step not the FBP weight": ("a0 = math.pi / n_theta if first_step is None",
                                           "a0 = 1.0 / n_theta if first_step is None"),
@@ -87,18 +88,51 @@ def test_pins_catch_planted_python_mistake(name, tmp_path):
     assert r.returncode != 0, "pins did not catch: " + name
 
 
-def _run_python_variant(tmp_path, source):
+def _run_python_variant(tmp_path, source, fubini_source=None, pins=("test_oracle_pins.py", "bb or ramp or ramlak")):
     pkg = tmp_path / "oracle"
     pkg.mkdir()
     (pkg / "__init__.py").write_text(source)
+    (pkg / "fubini.py").write_text(fubini_source if fubini_source is not None else open(FUB_SRC).read())
     (pkg / "tomo_oracle.c").write_text(open(SRC).read())
     env = dict(os.environ, TOMO_ORACLE_LIB=oracle.build(), PYTHONPATH=str(tmp_path) + os.pathsep + ROOT)
-    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                           "-x", "-q", "-p", "no:cacheprovider", "-k", "bb or ramp or ramlak"], env=env,
-                          capture_output=True, text=True, cwd=str(tmp_path), timeout=600)
+    cmd = [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins[0]), "-x", "-q", "-p", "no:cacheprovider"]
+    if pins[1]:
+        cmd += ["-k", pins[1]]
+    return subprocess.run(cmd, env=env, capture_output=True, text=True, cwd=str(tmp_path), timeout=600)
 
 
 def test_unmutated_python_variant_passes(tmp_path):
     """Control: the copied package, unchanged, passes the same pins."""
     r = _run_python_variant(tmp_path, open(PY_SRC).read())
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+# Mistakes planted in the Fubini-Radon oracle (Sec. 3): the gridding phase,
+# the deapodization, the wrap sign, the radial transform and the FBP weight.
+FUB_MUTANTS = {
+    "fubini: grid phase conjugated": ("return np.exp(2j * math.pi * np.arange(G) * (G / 2.0 - 0.5) / G)",
+                                      "return np.exp(-2j * math.pi * np.arange(G) * (G / 2.0 - 0.5) / G)"),
+    "fubini: deapodization dropped": ("return 1.0 / kb_hat(fg.pix() / fg.G, fg.kw, fg.beta())",
+                                      "return np.ones(fg.n)"),
+    "fubini: wrap sign dropped": ("sx = np.where(((kx - kx % G) // G) % 2 != 0, -1.0, 1.0)",
+                                  "sx = np.where(((kx - kx % G) // G) % 2 != 0, 1.0, 1.0)"),
+    "fubini: radial transform sign": ("E = np.exp(2j * math.pi * np.multiply.outer(fg.omega(), fg.bins())) / fg.n_p",
+                                      "E = np.exp(-2j * math.pi * np.multiply.outer(fg.omega(), fg.bins())) / fg.n_p"),
+    "fubini: FBP angular weight": ("return (math.pi / fg.n_theta) * _adjoint_polar(fg, Pq, S)",
+                                   "return (1.0 / fg.n_theta) * _adjoint_polar(fg, Pq, S)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FUB_MUTANTS))
+def test_pins_catch_planted_fubini_mistake(name, tmp_path):
+    before, after = FUB_MUTANTS[name]
+    src = open(FUB_SRC).read()
+    assert src.count(before) == 1, name
+    r = _run_python_variant(tmp_path, open(PY_SRC).read(), src.replace(before, after),
+                            ("test_oracle_fubini.py", None))
+    assert r.returncode != 0, "pins did not catch: " + name
+
+
+def test_unmutated_fubini_variant_passes(tmp_path):
+    r = _run_python_variant(tmp_path, open(PY_SRC).read(), None, ("test_oracle_fubini.py", None))
     assert r.returncode == 0, r.stdout[-2000:]
