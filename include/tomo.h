@@ -368,6 +368,42 @@ TOMO_API tomo_status tomo_cgls_resume(const tomo_matrix *A, const float *sino, f
                                       const tomo_exec_opts *opts, void *workspace, size_t workspace_bytes,
                                       void *stream);
 
+/* ---------------------------------------------------------------------------
+ * The Fubini-Radon transform (Sec. 3, Eq. 2): the projector computed through
+ * the Fourier slice theorem.  Radon(u) = F1^-1 S^H F2 (k* o u): deapodize
+ * (k* = 1 / the Kaiser-Bessel window's transform), zero-pad the n x n image to
+ * a 2n x 2n grid, 2D FFT, interpolate the spectrum onto the polar samples
+ * (theta_m, w_q = (q - floor(n_p/2)) / n_p) with the sparse gridding matrix S
+ * (Kaiser-Bessel window of kw x kw grid points, shape beta = pi sqrt((kw/2)^2
+ * 1.5^2 - 0.8)), 1D inverse FFT along each radial line, real part.  It
+ * approximates, to the gridding error (about 3e-6 relative at kw = 6), the
+ * exact transform R[u](m,k) = Re((1/n_p) sum_q e^{2 pi i w_q p_k}
+ * sum_j u_j e^{-2 pi i w_q (x_j cos theta_m + y_j sin theta_m)}) with the pixel
+ * and bin coordinates of the line model.  S is real; the paper's phase ramp
+ * and FFT shifts are applied as diagonal phases beside the FFTs.  FFTs are
+ * cuFFT calls; S and its stored transpose are built on the device.
+ * ------------------------------------------------------------------------- */
+typedef struct tomo_fubini tomo_fubini; /* holds S, S^T, cuFFT plans and scratch: one call at a time */
+
+/* Build the operator for geom (n_x == n_y required; angles and center as for
+ * tomo_build_matrix) with a window of kw grid points (even, 2..16; 6 gives
+ * about 3e-6, 8 about 2e-8 relative error).  Synchronises `stream`. */
+TOMO_API tomo_status tomo_fubini_create(const tomo_geometry *geom, int32_t kw, void *stream, tomo_fubini **out);
+
+/* Free every device buffer and plan of the handle.  NULL is accepted. */
+TOMO_API tomo_status tomo_fubini_destroy(tomo_fubini *F);
+
+/* y (n_z, n_theta, n_p) = Radon(x) for x (n_z, n, n); DEVICE buffers,
+ * slice-major.  Calls on one handle must not overlap (shared scratch). */
+TOMO_API tomo_status tomo_fubini_project(tomo_fubini *F, const float *x, float *y, int32_t n_z, void *stream);
+
+/* x = the exact adjoint of tomo_fubini_project applied to y (filter 0), or the
+ * filtered backprojection iRadon (filter 1: the adjoint with the ramp density
+ * |w_q| on the polar samples, the DC sample weighted 1/(4 n_p), and the
+ * angular weight pi/n_theta; Sec. 3's D). */
+TOMO_API tomo_status tomo_fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t n_z, int32_t filter,
+                                             void *stream);
+
 /* Device-side status of `stream` (a stream of the CURRENT device; NULL = the
  * legacy default stream).  Calls queued without synchronising (tomo_cgls_batched
  * with opts->async) record the status of their bounded waits in one status

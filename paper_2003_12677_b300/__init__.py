@@ -8,7 +8,7 @@ torch.
 """
 _API = {"Matrix", "project", "backproject", "sirt", "cgls", "TomoProject", "radon", "tv_loss", "new_timing",
         "sirt_noalloc", "cgls_batched", "stream_status",
-        "sirt_bb"}
+        "sirt_bb", "Fubini"}
 
 
 def __getattr__(name):

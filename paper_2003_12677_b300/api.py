@@ -441,6 +441,62 @@ def stream_status(stream: Optional[torch.cuda.Stream] = None) -> str:
     return _lib.status_name(_lib.load().tomo_stream_status(ctypes.c_void_p(s.cuda_stream)))
 
 
+class Fubini:
+    """The Fubini-Radon transform (Fourier slice theorem with Kaiser-Bessel
+    gridding, one sparse matrix S and cuFFT) for an n x n image, n_theta
+    angles and n_p bins; kw is the window width in grid points."""
+
+    def __init__(self, n: int, n_theta: int, n_p: Optional[int] = None, angles=None,
+                 center: Optional[float] = None, kw: int = 6):
+        self._h = None
+        lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtomo needs a CUDA device")
+        self.n, self.n_theta = int(n), int(n_theta)
+        self.n_p = int(n if n_p is None else n_p)
+        g = _lib.Geometry()
+        g.n_x = g.n_y = self.n
+        g.n_p, g.n_theta = self.n_p, self.n_theta
+        self._angles = None
+        if angles is not None:
+            self._angles = np.ascontiguousarray(np.asarray(angles, np.float64))
+            if self._angles.shape != (self.n_theta,):
+                raise ValueError("angles must have n_theta entries")
+            g.angles = self._angles.ctypes.data
+        else:
+            g.angles = None
+        g.center = float("nan") if center is None else float(center)
+        h = ctypes.c_void_p()
+        _lib.check(lib.tomo_fubini_create(ctypes.byref(g), int(kw), _stream(), ctypes.byref(h)), "tomo_fubini_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.load().tomo_fubini_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def project(self, x: torch.Tensor) -> torch.Tensor:
+        _check_tensor(x, "x")
+        nz = _nz(x, self.n * self.n, "x")
+        y = torch.empty((nz, self.n_theta, self.n_p), device=x.device)
+        _lib.call("tomo_fubini_project", self._h, _ptr(x), _ptr(y), nz, _stream())
+        return y
+
+    def backproject(self, y: torch.Tensor, filtered: bool = False) -> torch.Tensor:
+        """The exact adjoint of project (filtered=False) or iRadon (True)."""
+        _check_tensor(y, "y")
+        nz = _nz(y, self.n_theta * self.n_p, "y")
+        x = torch.empty((nz, self.n, self.n), device=y.device)
+        _lib.call("tomo_fubini_backproject", self._h, _ptr(y), _ptr(x), nz, 1 if filtered else 0, _stream())
+        return x
+
+
 class TomoProject(torch.autograd.Function):
     """y = A x with the stored transpose as the backward: dL/dx = A^T dL/dy."""
 

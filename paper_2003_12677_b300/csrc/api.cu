@@ -260,6 +260,33 @@ tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo
   return run_autotune(A, n_z, allow_16bit != 0, best, rate, table, cap, n_table, (cudaStream_t)stream);
 }
 
+tomo_status tomo_fubini_create(const tomo_geometry *geom, int32_t kw, void *stream, tomo_fubini **out) {
+  return fubini_create(geom, kw, (cudaStream_t)stream, out);
+}
+
+tomo_status tomo_fubini_destroy(tomo_fubini *F) {
+  fubini_destroy(F);
+  return TOMO_OK;
+}
+
+tomo_status tomo_fubini_project(tomo_fubini *F, const float *x, float *y, int32_t n_z, void *stream) {
+  if (!F) return fail(TOMO_ERR_INVALID_ARG, "handle must be non-NULL");
+  TOMO_TRY(check_vec(x, "x"));
+  TOMO_TRY(check_vec(y, "y"));
+  if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
+  return fubini_project(F, x, y, n_z, (cudaStream_t)stream);
+}
+
+tomo_status tomo_fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t n_z, int32_t filter,
+                                    void *stream) {
+  if (!F) return fail(TOMO_ERR_INVALID_ARG, "handle must be non-NULL");
+  TOMO_TRY(check_vec(y, "y"));
+  TOMO_TRY(check_vec(x, "x"));
+  if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
+  if (filter != 0 && filter != 1) return fail(TOMO_ERR_INVALID_ARG, "filter must be 0 or 1");
+  return fubini_backproject(F, y, x, n_z, filter, (cudaStream_t)stream);
+}
+
 const char *tomo_status_string(tomo_status s) {
   switch (s) {
     case TOMO_OK: return "TOMO_OK";

@@ -544,6 +544,21 @@ tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_
 
 }  // namespace
 
+// Exclusive scan of n int32 counts into n+1 int64 offsets (other translation
+// units use it for their transposes).
+tomo_status exclusive_scan_i32(const int32_t *cnt, int64_t n, int64_t *out, cudaStream_t st) {
+  int64_t *part = nullptr;
+  int *maxv = nullptr;
+  TOMO_TRY(dmalloc(&part, n / kScanTile + 2));
+  DevBuf part_guard{part};
+  TOMO_TRY(dmalloc(&maxv, 1));
+  DevBuf max_guard{maxv};
+  TOMO_CUDA(cudaMemsetAsync(maxv, 0, sizeof(int), st));
+  TOMO_TRY(scan_counts(cnt, n, out, part, maxv, st));
+  TOMO_CUDA(cudaStreamSynchronize(st));  // the scratch is freed on return
+  return TOMO_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Taps of the preconditioning filter P^T P = F^dagger D F along the detector
 // (Sec. 2.1), used by the BB-step SIRT of Sec. 3.1.  On the N-point DFT grid

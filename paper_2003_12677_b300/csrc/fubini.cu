@@ -1,0 +1,444 @@
+// fubini.cu -- the Fubini-Radon transform (Sec. 3, Eq. 2) on the device.
+//
+// Radon(u) = F1^-1 S^H F2 (k* o u): deapodize the image, zero-pad it to a
+// G x G grid (G = 2n), 2D FFT, grid phase, interpolate the spectrum onto the
+// polar samples (angle m, radial frequency w_q = (q - floor(n_p/2)) / n_p)
+// with the sparse gridding matrix S (Kaiser-Bessel window of kw x kw grid
+// points), then a 1D inverse FFT along every radial line and the real part.
+// The adjoint runs the transposed steps with the stored transpose S^T; with
+// the ramp density on the polar samples and the weight pi/n_theta it is the
+// filtered backprojection (iRadon of Sec. 3).
+//
+// S is real here: the paper folds FFT shifts and the axis phase ramp into
+// complex entries of S; this build applies them as diagonal phase factors
+// next to the FFTs instead, so one real SpMM kernel serves complex data
+// stored as (re, im) column pairs.  The FFTs are cuFFT calls.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cufft.h>
+
+#include "internal.cuh"
+
+struct tomo_fubini {
+  int32_t n = 0, np = 0, nt = 0, kw = 0, G = 0, Bf = 0;
+  double center = 0, beta = 0;
+  int device = 0;
+  tomo::Csr S, ST;                // S: (nt*np) x (G*G); ST its transpose
+  float *deapod = nullptr;        // [n] 1 / phi_hat(x / G)
+  float *dens = nullptr;          // [np] ramp density of the filtered backprojection
+  cufftComplex *grid = nullptr;   // [Bf][G][G]
+  float *gridI = nullptr;         // [G*G][2 Bf] interleaved (re, im)
+  float *polI = nullptr;          // [nt*np][2 Bf]
+  cufftComplex *pol = nullptr;    // [Bf][nt][np]
+  cufftHandle plan2 = 0, plan1 = 0;
+  bool plans = false;
+};
+
+namespace tomo {
+
+tomo_status spmm_csr_store(const Csr &M, int B, const float *X, float *Y, cudaStream_t st);
+tomo_status exclusive_scan_i32(const int32_t *cnt, int64_t n, int64_t *out, cudaStream_t st);
+
+namespace {
+
+constexpr int kT = 256;
+
+// phi(t) = I0(beta sqrt(1 - (2t/kw)^2)) on |t| <= kw/2 (t in grid units)
+__device__ __forceinline__ double kb(double t, int kw, double beta) {
+  const double a = 1.0 - (2.0 * t / kw) * (2.0 * t / kw);
+  return a >= 0.0 ? cyl_bessel_i0(beta * sqrt(a)) : 0.0;
+}
+
+// One thread per polar sample r = m * np + q: its kw x kw window, in window
+// order (ky, then kx), columns wrapped modulo G with a factor -1 per wrap.
+__global__ void k_fub_fill_S(const double *cs, const double *sn, int nt, int np, int G, int kw, double beta,
+                             int64_t *rp, int32_t *ci, float *v) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (int64_t)nt * np) return;
+  const int m = (int)(r / np), q = (int)(r % np);
+  const double w = (double)(q - np / 2) / (double)np;
+  const double tx = (double)G * (w * cs[m]), ty = (double)G * (w * sn[m]);
+  const int64_t kx0 = (int64_t)floor(tx - 0.5 * kw) + 1, ky0 = (int64_t)floor(ty - 0.5 * kw) + 1;
+  const int64_t base = r * kw * kw;
+  if (r == 0) rp[0] = 0;
+  rp[r + 1] = base + (int64_t)kw * kw;
+  for (int a = 0; a < kw; ++a) {
+    const int64_t ky = ky0 + a;
+    const int64_t my = ((ky % G) + G) % G;
+    const double wy = kb(ty - (double)ky, kw, beta) * ((((ky - my) / G) & 1) ? -1.0 : 1.0);
+    for (int b = 0; b < kw; ++b) {
+      const int64_t kx = kx0 + b;
+      const int64_t mx = ((kx % G) + G) % G;
+      const double wx = kb(tx - (double)kx, kw, beta) * ((((kx - mx) / G) & 1) ? -1.0 : 1.0);
+      ci[base + a * kw + b] = (int32_t)(my * G + mx);
+      v[base + a * kw + b] = (float)(wy * wx);
+    }
+  }
+}
+
+// transpose: counts, scatter, then each row sorted by the polar sample index
+__global__ void k_fub_count(const int32_t *ci, int64_t nnz, int32_t *cnt) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(cnt + ci[e], 1);
+}
+
+__global__ void k_fub_scatter(const int32_t *ci, const float *v, int64_t rows, int per_row, const int64_t *rpT,
+                              int32_t *fill, int32_t *ciT, float *vT) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * per_row;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = ci[e];
+    const int64_t pos = rpT[c] + atomicAdd(fill + c, 1);
+    ciT[pos] = (int32_t)(e / per_row);
+    vT[pos] = v[e];
+  }
+}
+
+__global__ void k_fub_sort_rows(const int64_t *rpT, int64_t rows, int32_t *ciT, float *vT) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int64_t b = rpT[r], e = rpT[r + 1];
+  for (int64_t i = b + 1; i < e; ++i) {  // insertion sort; keys unique
+    const int32_t key = ciT[i];
+    const float val = vT[i];
+    int64_t j = i - 1;
+    while (j >= b && ciT[j] > key) {
+      ciT[j + 1] = ciT[j];
+      vT[j + 1] = vT[j];
+      --j;
+    }
+    ciT[j + 1] = key;
+    vT[j + 1] = val;
+  }
+}
+
+// 1 / phi_hat(x_i / G), phi_hat(s) = kw sinh(z)/z, z = sqrt(beta^2 - (pi kw s)^2)
+__global__ void k_fub_deapod(int n, int G, int kw, double beta, float *d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = ((double)i + 0.5 - 0.5 * n) / (double)G;
+  const double pk = 3.141592653589793 * kw * s;
+  const double z = sqrt(beta * beta - pk * pk);
+  d[i] = (float)(z / (kw * sinh(z)));
+}
+
+// e^{i pi r / G} for the integer r = (k (G - 1)) mod 2G: the grid phase
+// e^{2 pi i k (G/2 - 1/2) / G} with the argument reduced exactly
+__device__ __forceinline__ float2 grid_phase(int64_t k, int G) {
+  const int64_t r = (k * (G - 1)) % (2 * (int64_t)G);
+  double s, c;
+  sincospi((double)r / (double)G, &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// forward 1: grid[s][gy][gx] = x[s][iy][ix] d[iy] d[ix] in the centre, 0 elsewhere
+__global__ void k_fub_pad(const float *x, int cnt, int n, int G, const float *d, cufftComplex *grid, int Bf) {
+  const int64_t total = (int64_t)Bf * G * G;
+  const int o = (G - n) / 2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / ((int64_t)G * G));
+    const int gy = (int)((e / G) % G), gx = (int)(e % G);
+    const int iy = gy - o, ix = gx - o;
+    float val = 0.f;
+    if (s < cnt && iy >= 0 && iy < n && ix >= 0 && ix < n) val = x[((int64_t)s * n + iy) * n + ix] * d[iy] * d[ix];
+    grid[e] = make_float2(val, 0.f);
+  }
+}
+
+// forward 3 / adjoint 5: grid (slice-major, complex) <-> interleaved (re, im)
+// pairs, with the grid phase (forward) or its conjugate (adjoint)
+template <bool kToInterleaved>
+__global__ void k_fub_grid_phase(cufftComplex *grid, float *gI, int G, int Bf) {
+  const int64_t total = (int64_t)Bf * G * G;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = e / Bf;  // grid point (ky * G + kx)
+    const int s = (int)(e % Bf);
+    float2 ph = cmul(grid_phase(g / G, G), grid_phase(g % G, G));
+    if (kToInterleaved) {
+      const float2 w = cmul(grid[(int64_t)s * G * G + g], ph);
+      gI[2 * e] = w.x;
+      gI[2 * e + 1] = w.y;
+    } else {
+      ph.y = -ph.y;
+      grid[(int64_t)s * G * G + g] = cmul(make_float2(gI[2 * e], gI[2 * e + 1]), ph);
+    }
+  }
+}
+
+// radial phase e^{2 pi i (q - q0)(1/2 - c) / np} (argument in FP64)
+__device__ __forceinline__ float2 radial_phase(int q, int np, double c, double sign) {
+  double s, co;
+  sincospi(sign * 2.0 * (double)(q - np / 2) * (0.5 - c) / (double)np, &s, &co);
+  return make_float2((float)co, (float)s);
+}
+
+// e^{sign 2 pi i q0 k / np}, argument reduced exactly
+__device__ __forceinline__ float2 bin_phase(int k, int np, double sign) {
+  const int64_t r = ((int64_t)(np / 2) * k) % np;
+  double s, co;
+  sincospi(sign * 2.0 * (double)r / (double)np, &s, &co);
+  return make_float2((float)co, (float)s);
+}
+
+// forward 5: pol[s][m][q] = P[(m np + q)][s] * radial phase
+__global__ void k_fub_polar_in(const float *pI, cufftComplex *pol, int nt, int np, int Bf, double c) {
+  const int64_t total = (int64_t)Bf * nt * np;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Bf;
+    const int s = (int)(e % Bf);
+    const int q = (int)(r % np);
+    pol[(int64_t)s * nt * np + r] = cmul(make_float2(pI[2 * e], pI[2 * e + 1]), radial_phase(q, np, c, 1.0));
+  }
+}
+
+// forward 7: y[s][m][k] = Re(pol[s][m][k] e^{-2 pi i q0 k / np}) / np
+__global__ void k_fub_out(const cufftComplex *pol, float *y, int cnt, int nt, int np) {
+  const int64_t total = (int64_t)cnt * nt * np;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % np);
+    y[e] = cmul(pol[e], bin_phase(k, np, -1.0)).x / (float)np;
+  }
+}
+
+// adjoint 1: pol[s][m][k] = y[s][m][k] e^{+2 pi i q0 k / np}
+__global__ void k_fub_adj_in(const float *y, cufftComplex *pol, int cnt, int Bf, int nt, int np) {
+  const int64_t total = (int64_t)Bf * nt * np;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / ((int64_t)nt * np));
+    const int k = (int)(e % np);
+    const float val = s < cnt ? y[e] : 0.f;
+    const float2 ph = bin_phase(k, np, 1.0);
+    pol[e] = make_float2(val * ph.x, val * ph.y);
+  }
+}
+
+// adjoint 3: P[(m np + q)][s] = pol[s][m][q] * conj(radial phase) * w_q, with
+// w_q = 1/np (adjoint) or dens_q pi / (np n_theta) (filtered backprojection)
+__global__ void k_fub_polar_out(const cufftComplex *pol, float *pI, int nt, int np, int Bf, double c,
+                                const float *dens, float scale) {
+  const int64_t total = (int64_t)Bf * nt * np;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Bf;
+    const int s = (int)(e % Bf);
+    const int q = (int)(r % np);
+    const float wq = dens ? dens[q] * scale : scale;
+    const float2 v = cmul(pol[(int64_t)s * nt * np + r], radial_phase(q, np, c, -1.0));
+    pI[2 * e] = v.x * wq;
+    pI[2 * e + 1] = v.y * wq;
+  }
+}
+
+// adjoint 7: x[s][iy][ix] = Re(grid[s][iy + o][ix + o]) d[iy] d[ix]
+__global__ void k_fub_crop(const cufftComplex *grid, float *x, int cnt, int n, int G, const float *d) {
+  const int64_t total = (int64_t)cnt * n * n;
+  const int o = (G - n) / 2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / ((int64_t)n * n));
+    const int iy = (int)((e / n) % n), ix = (int)(e % n);
+    x[e] = grid[((int64_t)s * G + iy + o) * G + ix + o].x * d[iy] * d[ix];
+  }
+}
+
+__global__ void k_fub_dens(int np, float *dens) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  const int d = q - np / 2;
+  dens[q] = d == 0 ? (float)(1.0 / (4.0 * np)) : (float)(fabs((double)d) / (double)np);
+}
+
+int egrid(int64_t n) {
+  int64_t b = (n + kT - 1) / kT;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 16));
+}
+
+tomo_status cufft_check(cufftResult r, const char *what) {
+  if (r != CUFFT_SUCCESS) return fail(TOMO_ERR_CUDA, std::string("cuFFT ") + what + " failed: " + std::to_string((int)r));
+  return TOMO_OK;
+}
+
+template <class T>
+tomo_status dalloc(T **p, size_t count) {
+  if (cudaMalloc(p, sizeof(T) * std::max<size_t>(count, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(TOMO_ERR_OOM, "device allocation of " + std::to_string(sizeof(T) * count) + " bytes failed");
+  }
+  return TOMO_OK;
+}
+
+void free_fubini(tomo_fubini *F) {
+  if (!F) return;
+  if (F->plans) {
+    cufftDestroy(F->plan2);
+    cufftDestroy(F->plan1);
+  }
+  void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->ST.rp, F->ST.ci, F->ST.v, F->deapod, F->dens, F->grid, F->gridI,
+                  F->polI, F->pol};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete F;
+}
+
+}  // namespace
+
+tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, tomo_fubini **out) {
+  if (!g || !out) return fail(TOMO_ERR_INVALID_ARG, "geometry and out must be non-NULL");
+  *out = nullptr;
+  if (g->n_x <= 0 || g->n_x != g->n_y || g->n_p <= 0 || g->n_theta <= 0)
+    return fail(TOMO_ERR_INVALID_ARG, "the Fubini-Radon transform needs a square image (n_x == n_y > 0), n_p, n_theta > 0");
+  if (kw < 2 || kw > 16 || (kw & 1)) return fail(TOMO_ERR_INVALID_ARG, "kw must be even, 2..16");
+  const int64_t G = 2 * (int64_t)g->n_x;
+  if (G * G >= (int64_t)INT32_MAX || (int64_t)g->n_theta * g->n_p * kw * kw >= (int64_t)INT32_MAX * 4)
+    return fail(TOMO_ERR_INVALID_ARG, "geometry too large for the Fubini-Radon transform");
+  const double c = std::isnan(g->center) ? 0.5 * (double)g->n_p : g->center;
+  if (!std::isfinite(c)) return fail(TOMO_ERR_INVALID_ARG, "center must be finite or NaN");
+  std::vector<double> cs(g->n_theta), sn(g->n_theta);
+  for (int m = 0; m < g->n_theta; ++m) {
+    const double th = g->angles ? g->angles[m] : (double)m * M_PI / (double)g->n_theta;
+    if (!std::isfinite(th)) return fail(TOMO_ERR_INVALID_ARG, "angles must be finite");
+    cs[m] = std::cos(th);
+    sn[m] = std::sin(th);
+  }
+  tomo_fubini *F = new tomo_fubini();
+  struct Guard {
+    tomo_fubini *F;
+    bool keep = false;
+    ~Guard() {
+      if (!keep) free_fubini(F);
+    }
+  } guard{F};
+  cudaGetDevice(&F->device);
+  F->n = g->n_x;
+  F->np = g->n_p;
+  F->nt = g->n_theta;
+  F->kw = kw;
+  F->G = (int32_t)G;
+  F->center = c;
+  const double sigma = 2.0;
+  F->beta = M_PI * std::sqrt((kw / sigma) * (kw / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8);
+  // batch of slices per pass: 16, fewer when the grid would pass 2 GiB
+  F->Bf = 16;
+  while (F->Bf > 1 && (int64_t)G * G * F->Bf * 16 > (int64_t)2 << 30) F->Bf /= 2;
+
+  const int64_t rows = (int64_t)F->nt * F->np, cols = G * G, nnz = rows * kw * kw;
+  double *dcs = nullptr, *dsn = nullptr;
+  TOMO_TRY(dalloc(&dcs, F->nt));
+  TOMO_TRY(dalloc(&dsn, F->nt));
+  struct Tmp {
+    void *p[2];
+    ~Tmp() {
+      for (void *q : p)
+        if (q) cudaFree(q);
+    }
+  } tmp{{dcs, dsn}};
+  TOMO_CUDA(cudaMemcpyAsync(dcs, cs.data(), sizeof(double) * F->nt, cudaMemcpyHostToDevice, st));
+  TOMO_CUDA(cudaMemcpyAsync(dsn, sn.data(), sizeof(double) * F->nt, cudaMemcpyHostToDevice, st));
+  F->S.rows = rows;
+  F->S.cols = cols;
+  F->S.nnz = nnz;
+  F->S.max_len = (int64_t)kw * kw;
+  TOMO_TRY(dalloc(&F->S.rp, rows + 1));
+  TOMO_TRY(dalloc(&F->S.ci, nnz));
+  TOMO_TRY(dalloc(&F->S.v, nnz));
+  k_fub_fill_S<<<(unsigned)((rows + kT - 1) / kT), kT, 0, st>>>(dcs, dsn, F->nt, F->np, F->G, kw, F->beta, F->S.rp,
+                                                                 F->S.ci, F->S.v);
+  TOMO_CUDA(cudaGetLastError());
+  // S^T
+  F->ST.rows = cols;
+  F->ST.cols = rows;
+  F->ST.nnz = nnz;
+  TOMO_TRY(dalloc(&F->ST.rp, cols + 1));
+  TOMO_TRY(dalloc(&F->ST.ci, nnz));
+  TOMO_TRY(dalloc(&F->ST.v, nnz));
+  int32_t *cnt = nullptr;
+  TOMO_TRY(dalloc(&cnt, cols));
+  struct Tmp2 {
+    int32_t *p;
+    ~Tmp2() {
+      if (p) cudaFree(p);
+    }
+  } tmp2{cnt};
+  TOMO_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * cols, st));
+  k_fub_count<<<egrid(nnz), kT, 0, st>>>(F->S.ci, nnz, cnt);
+  TOMO_CUDA(cudaGetLastError());
+  TOMO_TRY(exclusive_scan_i32(cnt, cols, F->ST.rp, st));
+  TOMO_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * cols, st));
+  k_fub_scatter<<<egrid(nnz), kT, 0, st>>>(F->S.ci, F->S.v, rows, kw * kw, F->ST.rp, cnt, F->ST.ci, F->ST.v);
+  TOMO_CUDA(cudaGetLastError());
+  k_fub_sort_rows<<<(unsigned)((cols + kT - 1) / kT), kT, 0, st>>>(F->ST.rp, cols, F->ST.ci, F->ST.v);
+  TOMO_CUDA(cudaGetLastError());
+  // factors and buffers
+  TOMO_TRY(dalloc(&F->deapod, F->n));
+  k_fub_deapod<<<(F->n + kT - 1) / kT, kT, 0, st>>>(F->n, F->G, kw, F->beta, F->deapod);
+  TOMO_TRY(dalloc(&F->dens, F->np));
+  k_fub_dens<<<(F->np + kT - 1) / kT, kT, 0, st>>>(F->np, F->dens);
+  TOMO_CUDA(cudaGetLastError());
+  TOMO_TRY(dalloc(&F->grid, (size_t)G * G * F->Bf));
+  TOMO_TRY(dalloc(&F->gridI, (size_t)G * G * F->Bf * 2));
+  TOMO_TRY(dalloc(&F->polI, (size_t)rows * F->Bf * 2));
+  TOMO_TRY(dalloc(&F->pol, (size_t)rows * F->Bf));
+  // cuFFT plans: G x G 2D transforms and length-np 1D transforms, contiguous batches
+  int dims2[2] = {F->G, F->G};
+  TOMO_TRY(cufft_check(cufftPlanMany(&F->plan2, 2, dims2, nullptr, 1, F->G * F->G, nullptr, 1, F->G * F->G,
+                                     CUFFT_C2C, F->Bf), "plan 2D"));
+  int dims1[1] = {F->np};
+  cufftResult r1 = cufftPlanMany(&F->plan1, 1, dims1, nullptr, 1, F->np, nullptr, 1, F->np, CUFFT_C2C, F->nt * F->Bf);
+  if (r1 != CUFFT_SUCCESS) {
+    cufftDestroy(F->plan2);
+    return cufft_check(r1, "plan 1D");
+  }
+  F->plans = true;
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  guard.keep = true;
+  *out = F;
+  return TOMO_OK;
+}
+
+void fubini_destroy(tomo_fubini *F) { free_fubini(F); }
+
+tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz, cudaStream_t st) {
+  const int G = F->G, n = F->n, nt = F->nt, np = F->np, Bf = F->Bf;
+  const int64_t rows = (int64_t)nt * np;
+  TOMO_TRY(cufft_check(cufftSetStream(F->plan2, st), "set stream"));
+  TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
+  for (int32_t s0 = 0; s0 < nz; s0 += Bf) {
+    const int cnt = std::min<int32_t>(Bf, nz - s0);
+    k_fub_pad<<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(x + (int64_t)s0 * n * n, cnt, n, G, F->deapod, F->grid, Bf);
+    TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_FORWARD), "2D forward"));
+    k_fub_grid_phase<true><<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(F->grid, F->gridI, G, Bf);
+    TOMO_TRY(spmm_csr_store(F->S, 2 * Bf, F->gridI, F->polI, st));
+    k_fub_polar_in<<<egrid(rows * Bf), kT, 0, st>>>(F->polI, F->pol, nt, np, Bf, F->center);
+    TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_INVERSE), "1D inverse"));
+    k_fub_out<<<egrid(rows * cnt), kT, 0, st>>>(F->pol, y + (int64_t)s0 * rows, cnt, nt, np);
+    TOMO_CUDA(cudaGetLastError());
+  }
+  return TOMO_OK;
+}
+
+tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t nz, int filter, cudaStream_t st) {
+  const int G = F->G, n = F->n, nt = F->nt, np = F->np, Bf = F->Bf;
+  const int64_t rows = (int64_t)nt * np;
+  TOMO_TRY(cufft_check(cufftSetStream(F->plan2, st), "set stream"));
+  TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
+  const float scale = filter ? (float)(M_PI / ((double)np * nt)) : (float)(1.0 / np);
+  for (int32_t s0 = 0; s0 < nz; s0 += Bf) {
+    const int cnt = std::min<int32_t>(Bf, nz - s0);
+    k_fub_adj_in<<<egrid(rows * Bf), kT, 0, st>>>(y + (int64_t)s0 * rows, F->pol, cnt, Bf, nt, np);
+    TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_FORWARD), "1D forward"));
+    k_fub_polar_out<<<egrid(rows * Bf), kT, 0, st>>>(F->pol, F->polI, nt, np, Bf, F->center,
+                                                     filter ? F->dens : nullptr, scale);
+    TOMO_TRY(spmm_csr_store(F->ST, 2 * Bf, F->polI, F->gridI, st));
+    k_fub_grid_phase<false><<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(F->grid, F->gridI, G, Bf);
+    TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_INVERSE), "2D inverse"));
+    k_fub_crop<<<egrid((int64_t)cnt * n * n), kT, 0, st>>>(F->grid, x + (int64_t)s0 * n * n, cnt, n, G, F->deapod);
+    TOMO_CUDA(cudaGetLastError());
+  }
+  return TOMO_OK;
+}
+
+}  // namespace tomo

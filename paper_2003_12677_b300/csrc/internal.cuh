@@ -142,6 +142,11 @@ tomo_status run_sirt_bb(const tomo_matrix *h, const float *sino, float *x, int32
                         double first_step, double *hist, const tomo_bb_state *in, tomo_bb_state *out,
                         const Exec &ex, void *ws, cudaStream_t st);
 tomo_status batched_workspace(const tomo_request *reqs, int32_t n, const tomo_exec_opts *o, size_t *bytes);
+// Fubini-Radon transform (fubini.cu)
+tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, tomo_fubini **out);
+void fubini_destroy(tomo_fubini *F);
+tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz, cudaStream_t st);
+tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t nz, int filter, cudaStream_t st);
 // per-stream status word (status.cu)
 int *stream_status_word(cudaStream_t st);
 tomo_status fold_status(const int *src, cudaStream_t st);

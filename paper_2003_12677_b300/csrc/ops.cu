@@ -1247,6 +1247,26 @@ tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t 
   return dispatch<CglsF>(ex.B, h, sino, x, nz, iters, recompute, hist, in, out, ex, ws, st);
 }
 
+// Y = M X for an interleaved (rows, B) operand with the FP32 CSR kernels (the
+// Fubini-Radon gridding matrices use it).
+tomo_status spmm_csr_store(const Csr &M, int B, const float *X, float *Y, cudaStream_t st) {
+  Op op{};
+  op.m = &M;
+  op.format = TOMO_FMT_CSR;
+  switch (B) {
+    case 1: launch_spmm<1>(op, X, EpiStore{Y, 1}, nullptr, st); break;
+    case 2: launch_spmm<2>(op, X, EpiStore{Y, 2}, nullptr, st); break;
+    case 4: launch_spmm<4>(op, X, EpiStore{Y, 4}, nullptr, st); break;
+    case 8: launch_spmm<8>(op, X, EpiStore{Y, 8}, nullptr, st); break;
+    case 16: launch_spmm<16>(op, X, EpiStore{Y, 16}, nullptr, st); break;
+    case 32: launch_spmm<32>(op, X, EpiStore{Y, 32}, nullptr, st); break;
+    case 64: launch_spmm<64>(op, X, EpiStore{Y, 64}, nullptr, st); break;
+    default: return fail(TOMO_ERR_UNSUPPORTED, "SpMM width must be a power of two up to 64");
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
+}
+
 tomo_status run_sirt_bb(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
                         double first_step, double *hist, const tomo_bb_state *in, tomo_bb_state *out,
                         const Exec &ex, void *ws, cudaStream_t st) {
