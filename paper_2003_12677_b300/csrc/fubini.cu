@@ -28,6 +28,9 @@ struct tomo_fubini {
   tomo::Csr S, ST;                // S: (nt*np) x (G*G); ST its transpose
   float *deapod = nullptr;        // [n] 1 / phi_hat(x / G)
   float *dens = nullptr;          // [np] ramp density of the filtered backprojection
+  float2 *ph_grid = nullptr;      // [G]  e^{2 pi i k (G/2 - 1/2)/G}
+  float2 *ph_rad = nullptr;       // [np] e^{2 pi i (q - q0)(1/2 - c)/np}
+  float2 *ph_bin = nullptr;       // [np] e^{2 pi i q0 k / np}
   cufftComplex *grid = nullptr;   // [Bf][G][G]
   float *gridI = nullptr;         // [G*G][2 Bf] interleaved (re, im)
   float *polI = nullptr;          // [nt*np][2 Bf]
@@ -123,17 +126,29 @@ __global__ void k_fub_deapod(int n, int G, int kw, double beta, float *d) {
   d[i] = (float)(z / (kw * sinh(z)));
 }
 
-// e^{i pi r / G} for the integer r = (k (G - 1)) mod 2G: the grid phase
-// e^{2 pi i k (G/2 - 1/2) / G} with the argument reduced exactly
-__device__ __forceinline__ float2 grid_phase(int64_t k, int G) {
-  const int64_t r = (k * (G - 1)) % (2 * (int64_t)G);
-  double s, c;
-  sincospi((double)r / (double)G, &s, &c);
-  return make_float2((float)c, (float)s);
-}
-
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// Phase tables, FP64 arguments reduced exactly, rounded to FP32 once:
+//   grid  e^{i pi r / G},  r = (k (G - 1)) mod 2G  (= e^{2 pi i k (G/2 - 1/2)/G})
+//   rad   e^{2 pi i (q - q0)(1/2 - c)/np}
+//   bin   e^{2 pi i r / np}, r = (q0 k) mod np
+__global__ void k_fub_tables(int G, int np, double c, float2 *ph_grid, float2 *ph_rad, float2 *ph_bin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double s, co;
+  if (i < G) {
+    sincospi((double)(((int64_t)i * (G - 1)) % (2 * (int64_t)G)) / (double)G, &s, &co);
+    ph_grid[i] = make_float2((float)co, (float)s);
+  }
+  if (i < np) {
+    sincospi(2.0 * (double)(i - np / 2) * (0.5 - c) / (double)np, &s, &co);
+    ph_rad[i] = make_float2((float)co, (float)s);
+    sincospi(2.0 * (double)(((int64_t)(np / 2) * i) % np) / (double)np, &s, &co);
+    ph_bin[i] = make_float2((float)co, (float)s);
+  }
 }
 
 // forward 1: grid[s][gy][gx] = x[s][iy][ix] d[iy] d[ix] in the centre, 0 elsewhere
@@ -150,86 +165,71 @@ __global__ void k_fub_pad(const float *x, int cnt, int n, int G, const float *d,
   }
 }
 
-// forward 3 / adjoint 5: grid (slice-major, complex) <-> interleaved (re, im)
-// pairs, with the grid phase (forward) or its conjugate (adjoint)
-template <bool kToInterleaved>
-__global__ void k_fub_grid_phase(cufftComplex *grid, float *gI, int G, int Bf) {
-  const int64_t total = (int64_t)Bf * G * G;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = e / Bf;  // grid point (ky * G + kx)
-    const int s = (int)(e % Bf);
-    float2 ph = cmul(grid_phase(g / G, G), grid_phase(g % G, G));
-    if (kToInterleaved) {
-      const float2 w = cmul(grid[(int64_t)s * G * G + g], ph);
-      gI[2 * e] = w.x;
-      gI[2 * e + 1] = w.y;
-    } else {
-      ph.y = -ph.y;
-      grid[(int64_t)s * G * G + g] = cmul(make_float2(gI[2 * e], gI[2 * e + 1]), ph);
+// Slice-major complex data sm[s][i] (Bf x N) <-> interleaved (re, im) pairs
+// il[i][s], times a per-point factor: a tiled transpose through shared memory
+// so both sides are read and written coalesced.  kGrid: the factor is the grid
+// phase ph[i / G] ph[i % G]; else the radial phase ph[i % np] times
+// (w ? w[i % np] : 1) * scale.  kConj conjugates the phase (adjoint steps).
+constexpr int kTile = 32;
+
+template <bool kToIl, bool kGrid, bool kConj>
+__global__ void __launch_bounds__(256) k_fub_transpose(cufftComplex *sm, float2 *il, int64_t N, int Bf,
+                                                       const float2 *ph, int G, int np, const float *w, float scale) {
+  __shared__ float2 tile[16][kTile + 1];
+  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;  // 32 x 8
+  for (int64_t i0 = (int64_t)blockIdx.x * kTile; i0 < N; i0 += (int64_t)gridDim.x * kTile) {
+    const int64_t i = i0 + tx;
+    float2 f = make_float2(1.f, 0.f);
+    if (i < N) {
+      if (kGrid) {
+        f = cmul(ph[i / G], ph[i % G]);
+      } else {
+        f = ph[i % np];
+        const float sc = w ? w[i % np] * scale : scale;
+        f = make_float2(f.x * sc, f.y * sc);
+      }
+      if (kConj) f = conjf2(f);
     }
+    if (kToIl) {
+      for (int s = ty; s < Bf; s += 8)
+        if (i < N) tile[s][tx] = cmul(sm[(int64_t)s * N + i], f);
+      __syncthreads();
+      for (int l = threadIdx.x; l < kTile * Bf; l += 256) {
+        const int ii = l / Bf, s = l % Bf;
+        if (i0 + ii < N) il[(i0 + ii) * Bf + s] = tile[s][ii];
+      }
+    } else {
+      for (int l = threadIdx.x; l < kTile * Bf; l += 256) {
+        const int ii = l / Bf, s = l % Bf;
+        if (i0 + ii < N) tile[s][ii] = il[(i0 + ii) * Bf + s];
+      }
+      __syncthreads();
+      for (int s = ty; s < Bf; s += 8)
+        if (i < N) sm[(int64_t)s * N + i] = cmul(tile[s][tx], f);
+    }
+    __syncthreads();
   }
 }
 
-// radial phase e^{2 pi i (q - q0)(1/2 - c) / np} (argument in FP64)
-__device__ __forceinline__ float2 radial_phase(int q, int np, double c, double sign) {
-  double s, co;
-  sincospi(sign * 2.0 * (double)(q - np / 2) * (0.5 - c) / (double)np, &s, &co);
-  return make_float2((float)co, (float)s);
-}
-
-// e^{sign 2 pi i q0 k / np}, argument reduced exactly
-__device__ __forceinline__ float2 bin_phase(int k, int np, double sign) {
-  const int64_t r = ((int64_t)(np / 2) * k) % np;
-  double s, co;
-  sincospi(sign * 2.0 * (double)r / (double)np, &s, &co);
-  return make_float2((float)co, (float)s);
-}
-
-// forward 5: pol[s][m][q] = P[(m np + q)][s] * radial phase
-__global__ void k_fub_polar_in(const float *pI, cufftComplex *pol, int nt, int np, int Bf, double c) {
-  const int64_t total = (int64_t)Bf * nt * np;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / Bf;
-    const int s = (int)(e % Bf);
-    const int q = (int)(r % np);
-    pol[(int64_t)s * nt * np + r] = cmul(make_float2(pI[2 * e], pI[2 * e + 1]), radial_phase(q, np, c, 1.0));
-  }
-}
-
-// forward 7: y[s][m][k] = Re(pol[s][m][k] e^{-2 pi i q0 k / np}) / np
-__global__ void k_fub_out(const cufftComplex *pol, float *y, int cnt, int nt, int np) {
+// forward 7: y[s][m][k] = Re(pol[s][m][k] conj(ph_bin[k])) / np
+__global__ void k_fub_out(const cufftComplex *pol, float *y, int cnt, int nt, int np, const float2 *ph_bin) {
   const int64_t total = (int64_t)cnt * nt * np;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(e % np);
-    y[e] = cmul(pol[e], bin_phase(k, np, -1.0)).x / (float)np;
+    y[e] = cmul(pol[e], conjf2(ph_bin[k])).x / (float)np;
   }
 }
 
-// adjoint 1: pol[s][m][k] = y[s][m][k] e^{+2 pi i q0 k / np}
-__global__ void k_fub_adj_in(const float *y, cufftComplex *pol, int cnt, int Bf, int nt, int np) {
+// adjoint 1: pol[s][m][k] = y[s][m][k] ph_bin[k]
+__global__ void k_fub_adj_in(const float *y, cufftComplex *pol, int cnt, int Bf, int nt, int np,
+                             const float2 *ph_bin) {
   const int64_t total = (int64_t)Bf * nt * np;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int s = (int)(e / ((int64_t)nt * np));
     const int k = (int)(e % np);
     const float val = s < cnt ? y[e] : 0.f;
-    const float2 ph = bin_phase(k, np, 1.0);
+    const float2 ph = ph_bin[k];
     pol[e] = make_float2(val * ph.x, val * ph.y);
-  }
-}
-
-// adjoint 3: P[(m np + q)][s] = pol[s][m][q] * conj(radial phase) * w_q, with
-// w_q = 1/np (adjoint) or dens_q pi / (np n_theta) (filtered backprojection)
-__global__ void k_fub_polar_out(const cufftComplex *pol, float *pI, int nt, int np, int Bf, double c,
-                                const float *dens, float scale) {
-  const int64_t total = (int64_t)Bf * nt * np;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / Bf;
-    const int s = (int)(e % Bf);
-    const int q = (int)(r % np);
-    const float wq = dens ? dens[q] * scale : scale;
-    const float2 v = cmul(pol[(int64_t)s * nt * np + r], radial_phase(q, np, c, -1.0));
-    pI[2 * e] = v.x * wq;
-    pI[2 * e + 1] = v.y * wq;
   }
 }
 
@@ -249,6 +249,11 @@ __global__ void k_fub_dens(int np, float *dens) {
   if (q >= np) return;
   const int d = q - np / 2;
   dens[q] = d == 0 ? (float)(1.0 / (4.0 * np)) : (float)(fabs((double)d) / (double)np);
+}
+
+int tgrid(int64_t points) {
+  const int64_t b = (points + kTile - 1) / kTile;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 16));
 }
 
 int egrid(int64_t n) {
@@ -278,7 +283,7 @@ void free_fubini(tomo_fubini *F) {
     cufftDestroy(F->plan1);
   }
   void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->ST.rp, F->ST.ci, F->ST.v, F->deapod, F->dens, F->grid, F->gridI,
-                  F->polI, F->pol};
+                  F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete F;
@@ -377,6 +382,11 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
   k_fub_deapod<<<(F->n + kT - 1) / kT, kT, 0, st>>>(F->n, F->G, kw, F->beta, F->deapod);
   TOMO_TRY(dalloc(&F->dens, F->np));
   k_fub_dens<<<(F->np + kT - 1) / kT, kT, 0, st>>>(F->np, F->dens);
+  TOMO_TRY(dalloc(&F->ph_grid, F->G));
+  TOMO_TRY(dalloc(&F->ph_rad, F->np));
+  TOMO_TRY(dalloc(&F->ph_bin, F->np));
+  k_fub_tables<<<(std::max(F->G, F->np) + kT - 1) / kT, kT, 0, st>>>(F->G, F->np, c, F->ph_grid, F->ph_rad,
+                                                                      F->ph_bin);
   TOMO_CUDA(cudaGetLastError());
   TOMO_TRY(dalloc(&F->grid, (size_t)G * G * F->Bf));
   TOMO_TRY(dalloc(&F->gridI, (size_t)G * G * F->Bf * 2));
@@ -410,11 +420,13 @@ tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz,
     const int cnt = std::min<int32_t>(Bf, nz - s0);
     k_fub_pad<<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(x + (int64_t)s0 * n * n, cnt, n, G, F->deapod, F->grid, Bf);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_FORWARD), "2D forward"));
-    k_fub_grid_phase<true><<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(F->grid, F->gridI, G, Bf);
+    k_fub_transpose<true, true, false><<<tgrid((int64_t)G * G), 256, 0, st>>>(F->grid, (float2 *)F->gridI, (int64_t)G * G,
+                                                                         Bf, F->ph_grid, G, np, nullptr, 1.f);
     TOMO_TRY(spmm_csr_store(F->S, 2 * Bf, F->gridI, F->polI, st));
-    k_fub_polar_in<<<egrid(rows * Bf), kT, 0, st>>>(F->polI, F->pol, nt, np, Bf, F->center);
+    k_fub_transpose<false, false, false><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad,
+                                                               G, np, nullptr, 1.f);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_INVERSE), "1D inverse"));
-    k_fub_out<<<egrid(rows * cnt), kT, 0, st>>>(F->pol, y + (int64_t)s0 * rows, cnt, nt, np);
+    k_fub_out<<<egrid(rows * cnt), kT, 0, st>>>(F->pol, y + (int64_t)s0 * rows, cnt, nt, np, F->ph_bin);
     TOMO_CUDA(cudaGetLastError());
   }
   return TOMO_OK;
@@ -428,12 +440,13 @@ tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t
   const float scale = filter ? (float)(M_PI / ((double)np * nt)) : (float)(1.0 / np);
   for (int32_t s0 = 0; s0 < nz; s0 += Bf) {
     const int cnt = std::min<int32_t>(Bf, nz - s0);
-    k_fub_adj_in<<<egrid(rows * Bf), kT, 0, st>>>(y + (int64_t)s0 * rows, F->pol, cnt, Bf, nt, np);
+    k_fub_adj_in<<<egrid(rows * Bf), kT, 0, st>>>(y + (int64_t)s0 * rows, F->pol, cnt, Bf, nt, np, F->ph_bin);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_FORWARD), "1D forward"));
-    k_fub_polar_out<<<egrid(rows * Bf), kT, 0, st>>>(F->pol, F->polI, nt, np, Bf, F->center,
-                                                     filter ? F->dens : nullptr, scale);
+    k_fub_transpose<true, false, true><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad, G,
+                                                              np, filter ? F->dens : nullptr, scale);
     TOMO_TRY(spmm_csr_store(F->ST, 2 * Bf, F->polI, F->gridI, st));
-    k_fub_grid_phase<false><<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(F->grid, F->gridI, G, Bf);
+    k_fub_transpose<false, true, true><<<tgrid((int64_t)G * G), 256, 0, st>>>(F->grid, (float2 *)F->gridI, (int64_t)G * G,
+                                                                          Bf, F->ph_grid, G, np, nullptr, 1.f);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_INVERSE), "2D inverse"));
     k_fub_crop<<<egrid((int64_t)cnt * n * n), kT, 0, st>>>(F->grid, x + (int64_t)s0 * n * n, cnt, n, G, F->deapod);
     TOMO_CUDA(cudaGetLastError());

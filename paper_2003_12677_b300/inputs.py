@@ -227,6 +227,11 @@ def workload_case(name: str, slices: Optional[Sequence[int]] = None) -> Case:
 WORKLOADS["sirt_bb_512x360_b64"] = Workload("sirt_bb_512x360_b64", 512, 360, 64, "sirt_bb", 30,
                                            "poisson", 1e4, "ellipsoids3d", seed=12677 + 2)
 
+# the same data through the Fubini-Radon operator (Fourier slice theorem,
+# Kaiser-Bessel gridding, kw = 6): one forward and one adjoint per iteration
+WORKLOADS["fubini_512x360_b64"] = Workload("fubini_512x360_b64", 512, 360, 64, "fubini", 100,
+                                          "poisson", 1e4, "ellipsoids3d", seed=12677 + 2)
+
 WORKLOADS["uneven_256"] = Workload("uneven_256", 2048, 1024, 0, "cgls", 30, "poisson", 1e5, "ellipses2d",
                                   values="bf16", seed=12677 + 5)
 
