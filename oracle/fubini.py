@@ -190,7 +190,13 @@ def ramp_density(fg: FGeometry) -> np.ndarray:
     return d
 
 
-def fubini_fbp(fg: FGeometry, y, S: Optional[scipy.sparse.csr_matrix] = None) -> np.ndarray:
+def hamming_density(fg: FGeometry) -> np.ndarray:
+    """ramp_density times the Hamming window 0.54 + 0.46 cos(2 pi w_q)."""
+    return ramp_density(fg) * (0.54 + 0.46 * np.cos(2.0 * math.pi * fg.omega()))
+
+
+def fubini_fbp(fg: FGeometry, y, S: Optional[scipy.sparse.csr_matrix] = None,
+               density: Optional[np.ndarray] = None) -> np.ndarray:
     """Filtered backprojection (iRadon, Sec. 3): the adjoint with the density
     filter D on the polar samples and the angular weight pi/n_theta, i.e.
     (pi/n_theta) sum_m sum_q D_q (1/n_p) P_m(w_q) e^{2 pi i w_q (x . theta_m)},
@@ -198,5 +204,45 @@ def fubini_fbp(fg: FGeometry, y, S: Optional[scipy.sparse.csr_matrix] = None) ->
     S = gridding_matrix(fg) if S is None else S
     y = np.asarray(y, np.float64).reshape(-1, fg.n_theta, fg.n_p)
     Eh = np.exp(-2j * math.pi * np.multiply.outer(fg.bins(), fg.omega()))             # (k, q), no 1/n_p
-    Pq = (y @ Eh) * (ramp_density(fg) / fg.n_p)[None, None, :]
+    dens = ramp_density(fg) if density is None else density
+    Pq = (y @ Eh) * (dens / fg.n_p)[None, None, :]
     return (math.pi / fg.n_theta) * _adjoint_polar(fg, Pq, S)
+
+
+def fubini_sirt_bb(fg: FGeometry, b, iters: int, S: Optional[scipy.sparse.csr_matrix] = None):
+    """The paper's SIRT (Sec. 3.1: Hamming preconditioning, BB step) on its own
+    operator: per slice, r = b - R x (its norm is hist[k]), g = the filtered
+    backprojection of r with the Hamming-windowed ramp density
+    (= R^T W r for the symmetric PSD sinogram weight W the density defines),
+    x += alpha g; alpha = 1 on the first step (so x_1 = the filtered
+    backprojection of b), then the BB1 step <s,s>/<s,y> in FP64; a slice whose
+    <s,s> or <s,y> is not positive is frozen.  x0 = 0.  Returns (x, hist)."""
+    S = gridding_matrix(fg) if S is None else S
+    b = np.asarray(b, np.float64).reshape(-1, fg.n_theta * fg.n_p)
+    nz = b.shape[0]
+    dens = hamming_density(fg)
+    x = np.zeros((nz, fg.n * fg.n))
+    gp = None
+    alpha = np.zeros(nz)
+    frozen = np.zeros(nz, bool)
+    hist = np.zeros((iters, nz))
+    for k in range(iters):
+        r = b - fubini_project(fg, x, S)
+        hist[k] = np.sqrt(np.einsum("ij,ij->i", r, r))
+        g = fubini_fbp(fg, r, S, dens)
+        for s_ in range(nz):
+            if frozen[s_]:
+                a = 0.0
+            elif gp is None:
+                a = 1.0
+            else:
+                ss = alpha[s_] * alpha[s_] * float(np.dot(gp[s_], gp[s_]))
+                sy = -alpha[s_] * float(np.dot(gp[s_], g[s_] - gp[s_]))
+                if ss > 0.0 and sy > 0.0:
+                    a = ss / sy
+                else:
+                    a, frozen[s_] = 0.0, True
+            x[s_] += a * g[s_]
+            alpha[s_] = a
+        gp = g
+    return x, hist

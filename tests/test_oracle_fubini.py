@@ -107,3 +107,34 @@ def test_fbp_reconstructs_analytic_projections():
     xd = fb.fubini_fbp(fg, pd, S)[0].reshape(n, n)
     rr = np.sqrt(X ** 2 + Y ** 2)
     assert abs(xd[rr < 0.8 * R].mean() - 1.0) < 0.1
+
+
+def test_hamming_density_ends():
+    """The windowed density is the ramp density times 1 at DC and 0.08 at the
+    Nyquist sample (q = 0, w = -1/2)."""
+    fg = fb.FGeometry(16, 16, 4)
+    r, h = fb.ramp_density(fg), fb.hamming_density(fg)
+    assert h[fg.n_p // 2] == pytest.approx(r[fg.n_p // 2], rel=1e-15)
+    assert h[0] == pytest.approx(0.08 * r[0], rel=1e-12)
+
+
+def test_sirt_bb_first_step_is_the_fbp_and_it_solves_consistent_data():
+    """The first iterate is the Hamming-filtered backprojection of b.  On
+    consistent data b = R x_true of a smooth phantom (two Gaussian blobs), the
+    iteration drives the residual to 1e-3 of its start and the iterate to
+    x_true within 5e-3 in 30 steps (the FBP alone is 8% off): a descent
+    method with the right gradient; a wrong sign or step rule diverges or
+    stalls."""
+    n, nt = 32, 40
+    fg = fb.FGeometry(n, n, nt, kw=6)
+    S = fb.gridding_matrix(fg)
+    c = fg.pix()
+    X, Y = np.meshgrid(c, c)
+    xt = (np.exp(-((X - 3) ** 2 + (Y + 2) ** 2) / (2 * 3.0 ** 2))
+          + 0.5 * np.exp(-((X + 5) ** 2 + (Y - 4) ** 2) / (2 * 2.0 ** 2))).ravel()[None]
+    b = fb.fubini_project(fg, xt, S)
+    x1, _ = fb.fubini_sirt_bb(fg, b, 1, S)
+    np.testing.assert_allclose(x1, fb.fubini_fbp(fg, b, S, fb.hamming_density(fg)), rtol=1e-13, atol=1e-14)
+    x, hist = fb.fubini_sirt_bb(fg, b, 30, S)
+    assert hist[-1, 0] < 1e-3 * hist[0, 0]
+    assert np.linalg.norm(x - xt) < 5e-3 * np.linalg.norm(xt)

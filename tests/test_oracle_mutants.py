@@ -120,6 +120,9 @@ FUB_MUTANTS = {
                                       "E = np.exp(-2j * math.pi * np.multiply.outer(fg.omega(), fg.bins())) / fg.n_p"),
     "fubini: FBP angular weight": ("return (math.pi / fg.n_theta) * _adjoint_polar(fg, Pq, S)",
                                    "return (1.0 / fg.n_theta) * _adjoint_polar(fg, Pq, S)"),
+    "fubini SIRT: step along the gradient": ("            x[s_] += a * g[s_]", "            x[s_] -= a * g[s_]"),
+    "fubini SIRT: Hamming window dropped": ("return ramp_density(fg) * (0.54 + 0.46 * np.cos(2.0 * math.pi * fg.omega()))",
+                                            "return ramp_density(fg)"),
 }
 
 
