@@ -400,9 +400,20 @@ TOMO_API tomo_status tomo_fubini_project(tomo_fubini *F, const float *x, float *
 /* x = the exact adjoint of tomo_fubini_project applied to y (filter 0), or the
  * filtered backprojection iRadon (filter 1: the adjoint with the ramp density
  * |w_q| on the polar samples, the DC sample weighted 1/(4 n_p), and the
- * angular weight pi/n_theta; Sec. 3's D). */
+ * angular weight pi/n_theta; Sec. 3's D), or the same with the density times
+ * the Hamming window 0.54 + 0.46 cos(2 pi w_q) (filter 2). */
 TOMO_API tomo_status tomo_fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t n_z, int32_t filter,
                                              void *stream);
+
+/* The paper's SIRT (Sec. 3.1: Hamming preconditioning, BB step) on this
+ * operator: per slice from x = 0, r = b - Radon(x) (||r|| -> resnorm_hist
+ * [k * n_z + z], DEVICE, nullable), g = iRadon_Hamming(r) (filter 2), x += alpha
+ * g with alpha = 1 on the first step (x_1 = the filtered backprojection of b)
+ * and the BB1 step <s,s>/<s,y> after it (FP64 per slice; a slice whose <s,s>
+ * or <s,y> is not positive is frozen).  sino (n_z, n_theta, n_p) and x
+ * (n_z, n, n) DEVICE.  Scratch is allocated stream-ordered on `stream`. */
+TOMO_API tomo_status tomo_fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t n_z, int32_t iters,
+                                         double *resnorm_hist, void *stream);
 
 /* Device-side status of `stream` (a stream of the CURRENT device; NULL = the
  * legacy default stream).  Calls queued without synchronising (tomo_cgls_batched

@@ -488,13 +488,25 @@ class Fubini:
         _lib.call("tomo_fubini_project", self._h, _ptr(x), _ptr(y), nz, _stream())
         return y
 
-    def backproject(self, y: torch.Tensor, filtered: bool = False) -> torch.Tensor:
-        """The exact adjoint of project (filtered=False) or iRadon (True)."""
+    def backproject(self, y: torch.Tensor, filtered=False) -> torch.Tensor:
+        """The exact adjoint of project (filtered=False), iRadon with the ramp
+        density (True or "ramp") or with the Hamming-windowed one ("hamming")."""
         _check_tensor(y, "y")
         nz = _nz(y, self.n_theta * self.n_p, "y")
         x = torch.empty((nz, self.n, self.n), device=y.device)
-        _lib.call("tomo_fubini_backproject", self._h, _ptr(y), _ptr(x), nz, 1 if filtered else 0, _stream())
+        f = {False: 0, True: 1, "ramp": 1, "hamming": 2}[filtered]
+        _lib.call("tomo_fubini_backproject", self._h, _ptr(y), _ptr(x), nz, f, _stream())
         return x
+
+    def sirt_bb(self, sino: torch.Tensor, iters: int, history: bool = False):
+        """The paper's SIRT (Hamming preconditioning, BB step) on this operator,
+        from x = 0.  Returns x, and the ||b - R x_k|| history if asked."""
+        _check_tensor(sino, "sino")
+        nz = _nz(sino, self.n_theta * self.n_p, "sino")
+        x = torch.empty((nz, self.n, self.n), device=sino.device)
+        hist = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
+        _lib.call("tomo_fubini_sirt_bb", self._h, _ptr(sino), _ptr(x), nz, iters, _ptr(hist), _stream())
+        return (x, hist[:iters]) if history else x
 
 
 class TomoProject(torch.autograd.Function):

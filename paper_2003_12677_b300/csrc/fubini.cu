@@ -28,6 +28,7 @@ struct tomo_fubini {
   tomo::Csr S, ST;                // S: (nt*np) x (G*G); ST its transpose
   float *deapod = nullptr;        // [n] 1 / phi_hat(x / G)
   float *dens = nullptr;          // [np] ramp density of the filtered backprojection
+  float *dens_h = nullptr;        // [np] the same times the Hamming window
   float2 *ph_grid = nullptr;      // [G]  e^{2 pi i k (G/2 - 1/2)/G}
   float2 *ph_rad = nullptr;       // [np] e^{2 pi i (q - q0)(1/2 - c)/np}
   float2 *ph_bin = nullptr;       // [np] e^{2 pi i q0 k / np}
@@ -244,11 +245,86 @@ __global__ void k_fub_crop(const cufftComplex *grid, float *x, int cnt, int n, i
   }
 }
 
-__global__ void k_fub_dens(int np, float *dens) {
+// |w_q| with the DC sample weighted 1/(4 np) (the mean of |w| over its cell),
+// and the same times the Hamming window 0.54 + 0.46 cos(2 pi w_q)
+__global__ void k_fub_dens(int np, float *dens, float *dens_h) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= np) return;
   const int d = q - np / 2;
-  dens[q] = d == 0 ? (float)(1.0 / (4.0 * np)) : (float)(fabs((double)d) / (double)np);
+  const double r = d == 0 ? 1.0 / (4.0 * np) : fabs((double)d) / (double)np;
+  dens[q] = (float)r;
+  dens_h[q] = (float)(r * (0.54 + 0.46 * cospi(2.0 * (double)d / (double)np)));
+}
+
+// The paper's SIRT on this operator: per slice (one block each), FP64 sums.
+//   resid:  y = b - y, hist[k] = ||y||
+//   step:   P = <gp, gp>, Q = <gp, g - gp>; alpha = 1 on a slice's first step,
+//           else alpha_prev P / (-Q) (BB1; frozen when P or -Q is not
+//           positive); x += alpha g.  scal[s]: [0] alpha [1] frozen [2] stepped
+__device__ double fsb_block_sum(double v) {
+  __shared__ double red[kT];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kT / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kT) k_fsb_resid(const float *b, float *y, int64_t rows, double *hist, int k,
+                                                  int nz) {
+  const int s = blockIdx.x;
+  double ss = 0.0;
+  for (int64_t i = threadIdx.x; i < rows; i += kT) {
+    const float r = b[(int64_t)s * rows + i] - y[(int64_t)s * rows + i];
+    y[(int64_t)s * rows + i] = r;
+    ss += (double)r * (double)r;
+  }
+  ss = fsb_block_sum(ss);
+  if (hist && threadIdx.x == 0) hist[(int64_t)k * nz + s] = sqrt(ss);
+}
+
+__global__ void __launch_bounds__(kT) k_fsb_step(float *x, const float *g, const float *gp, int64_t cols,
+                                                 double *scal) {
+  const int s = blockIdx.x;
+  const float *gs = g + (int64_t)s * cols, *gps = gp + (int64_t)s * cols;
+  double P = 0.0, Q = 0.0;
+  const bool stepped = scal[s * 4 + 2] != 0.0;
+  if (stepped) {
+    for (int64_t i = threadIdx.x; i < cols; i += kT) {
+      const double a = gps[i];
+      P += a * a;
+      Q += a * ((double)gs[i] - a);
+    }
+  }
+  P = fsb_block_sum(P);
+  Q = fsb_block_sum(Q);
+  __shared__ float alpha_s;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    if (scal[s * 4 + 1] != 0.0) {
+      a = 0.0;
+    } else if (!stepped) {
+      a = 1.0;
+      scal[s * 4 + 2] = 1.0;
+    } else {
+      const double ap = scal[s * 4 + 0];
+      const double ss = ap * ap * P, sy = -ap * Q;
+      if (ss > 0.0 && sy > 0.0) {
+        a = ss / sy;
+      } else {
+        scal[s * 4 + 1] = 1.0;
+      }
+    }
+    scal[s * 4 + 0] = a;
+    alpha_s = (float)a;
+  }
+  __syncthreads();
+  const float a = alpha_s;
+  for (int64_t i = threadIdx.x; i < cols; i += kT) x[(int64_t)s * cols + i] = fmaf(a, gs[i], x[(int64_t)s * cols + i]);
 }
 
 int tgrid(int64_t points) {
@@ -282,7 +358,7 @@ void free_fubini(tomo_fubini *F) {
     cufftDestroy(F->plan2);
     cufftDestroy(F->plan1);
   }
-  void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->ST.rp, F->ST.ci, F->ST.v, F->deapod, F->dens, F->grid, F->gridI,
+  void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->ST.rp, F->ST.ci, F->ST.v, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
                   F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -381,7 +457,8 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
   TOMO_TRY(dalloc(&F->deapod, F->n));
   k_fub_deapod<<<(F->n + kT - 1) / kT, kT, 0, st>>>(F->n, F->G, kw, F->beta, F->deapod);
   TOMO_TRY(dalloc(&F->dens, F->np));
-  k_fub_dens<<<(F->np + kT - 1) / kT, kT, 0, st>>>(F->np, F->dens);
+  TOMO_TRY(dalloc(&F->dens_h, F->np));
+  k_fub_dens<<<(F->np + kT - 1) / kT, kT, 0, st>>>(F->np, F->dens, F->dens_h);
   TOMO_TRY(dalloc(&F->ph_grid, F->G));
   TOMO_TRY(dalloc(&F->ph_rad, F->np));
   TOMO_TRY(dalloc(&F->ph_bin, F->np));
@@ -438,18 +515,58 @@ tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t
   TOMO_TRY(cufft_check(cufftSetStream(F->plan2, st), "set stream"));
   TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
   const float scale = filter ? (float)(M_PI / ((double)np * nt)) : (float)(1.0 / np);
+  const float *dens = filter == 1 ? F->dens : (filter == 2 ? F->dens_h : nullptr);
   for (int32_t s0 = 0; s0 < nz; s0 += Bf) {
     const int cnt = std::min<int32_t>(Bf, nz - s0);
     k_fub_adj_in<<<egrid(rows * Bf), kT, 0, st>>>(y + (int64_t)s0 * rows, F->pol, cnt, Bf, nt, np, F->ph_bin);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_FORWARD), "1D forward"));
     k_fub_transpose<true, false, true><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad, G,
-                                                              np, filter ? F->dens : nullptr, scale);
+                                                              np, dens, scale);
     TOMO_TRY(spmm_csr_store(F->ST, 2 * Bf, F->polI, F->gridI, st));
     k_fub_transpose<false, true, true><<<tgrid((int64_t)G * G), 256, 0, st>>>(F->grid, (float2 *)F->gridI, (int64_t)G * G,
                                                                           Bf, F->ph_grid, G, np, nullptr, 1.f);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_INVERSE), "2D inverse"));
     k_fub_crop<<<egrid((int64_t)cnt * n * n), kT, 0, st>>>(F->grid, x + (int64_t)s0 * n * n, cnt, n, G, F->deapod);
     TOMO_CUDA(cudaGetLastError());
+  }
+  return TOMO_OK;
+}
+
+tomo_status fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t nz, int32_t iters, double *hist,
+                           cudaStream_t st) {
+  const int64_t rows = (int64_t)F->nt * F->np, cols = (int64_t)F->n * F->n;
+  float *y = nullptr, *g0 = nullptr, *g1 = nullptr;
+  double *scal = nullptr;
+  auto alloc = [&](void **p, size_t b) -> tomo_status {
+    if (cudaMallocAsync(p, b, st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TOMO_ERR_OOM, "workspace allocation of " + std::to_string(b) + " bytes failed");
+    }
+    return TOMO_OK;
+  };
+  struct Free {
+    void **p[4];
+    cudaStream_t st;
+    ~Free() {
+      for (void **q : p)
+        if (*q) cudaFreeAsync(*q, st);
+    }
+  } fr{{(void **)&y, (void **)&g0, (void **)&g1, (void **)&scal}, st};
+  TOMO_TRY(alloc((void **)&y, sizeof(float) * rows * nz));
+  TOMO_TRY(alloc((void **)&g0, sizeof(float) * cols * nz));
+  TOMO_TRY(alloc((void **)&g1, sizeof(float) * cols * nz));
+  TOMO_TRY(alloc((void **)&scal, sizeof(double) * 4 * nz));
+  TOMO_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * cols * nz, st));
+  TOMO_CUDA(cudaMemsetAsync(g1, 0, sizeof(float) * cols * nz, st));
+  TOMO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 4 * nz, st));
+  float *g = g0, *gp = g1;
+  for (int32_t k = 0; k < iters; ++k) {
+    TOMO_TRY(fubini_project(F, x, y, nz, st));
+    k_fsb_resid<<<nz, kT, 0, st>>>(sino, y, rows, hist, k, nz);
+    TOMO_TRY(fubini_backproject(F, y, g, nz, 2, st));
+    k_fsb_step<<<nz, kT, 0, st>>>(x, g, gp, cols, scal);
+    TOMO_CUDA(cudaGetLastError());
+    std::swap(g, gp);
   }
   return TOMO_OK;
 }

@@ -147,6 +147,8 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
 void fubini_destroy(tomo_fubini *F);
 tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz, cudaStream_t st);
 tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t nz, int filter, cudaStream_t st);
+tomo_status fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t nz, int32_t iters, double *hist,
+                           cudaStream_t st);
 // per-stream status word (status.cu)
 int *stream_status_word(cudaStream_t st);
 tomo_status fold_status(const int *src, cudaStream_t st);
