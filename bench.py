@@ -320,7 +320,7 @@ def run_alternate(args, w):
         print(json.dumps(line))
         return 0
     if w.solver == "sirt_bb":
-        fmt = args.format if args.format != "auto" else "csr"
+        fmt = args.format if args.format != "auto" else "sell"
         t0 = time.perf_counter()
         M = tomo.Matrix(w.n, w.n_theta)
         torch.cuda.synchronize()
