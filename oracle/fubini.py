@@ -246,3 +246,131 @@ def fubini_sirt_bb(fg: FGeometry, b, iters: int, S: Optional[scipy.sparse.csr_ma
             alpha[s_] = a
         gp = g
     return x, hist
+
+
+# ---------------------------------------------------------------------------
+# The normal operator (the Toeplitz route of the paper's outlook, Sec. 5):
+# the backprojection (or filtered backprojection) of the exact transform of
+# the image, N = R^T W R, in one operation.  The oracle is that composition
+# written out with exact double sums; `normal_taps` states the same operator
+# entry by entry (a Toeplitz part over pixel differences plus, for even n_p,
+# a Hankel part over pixel sums from the unpaired sample w = -1/2).
+
+def normal_weights(fg: FGeometry, filt: int):
+    """(kappa, D_q): the weight that the exact adjoint (filt 0: kappa = 1/n_p,
+    D = 1) or the filtered backprojection (filt 1 ramp, 2 Hamming-windowed ramp:
+    kappa = pi / (n_theta n_p)) puts on polar sample q."""
+    if filt == 0:
+        return 1.0 / fg.n_p, np.ones(fg.n_p)
+    if filt == 1:
+        return math.pi / (fg.n_theta * fg.n_p), ramp_density(fg)
+    if filt == 2:
+        return math.pi / (fg.n_theta * fg.n_p), hamming_density(fg)
+    raise ValueError("filt must be 0, 1 or 2")
+
+
+def fubini_direct_backproject(fg: FGeometry, y, filt: int = 0) -> np.ndarray:
+    """Exact adjoint (filt 0) or filtered backprojection (filt 1, 2) of the exact
+    transform as a double sum: g_j = kappa Re( sum_m sum_q D_q P_m(w_q)
+    e^{2 pi i w_q (x_j cos t_m + y_j sin t_m)} ), P_m(w_q) = sum_k y_mk
+    e^{-2 pi i w_q p_k}.  (nz, n_theta*n_p) -> (nz, n*n).  O(n^2 n_theta n_p)."""
+    kappa, D = normal_weights(fg, filt)
+    y = np.asarray(y, np.float64).reshape(-1, fg.n_theta, fg.n_p)
+    th = fg.theta()
+    x = fg.pix()
+    w = fg.omega()
+    Eh = np.exp(-2j * math.pi * np.multiply.outer(fg.bins(), w))        # (k, q)
+    out = np.zeros((y.shape[0], fg.n, fg.n))
+    for m in range(fg.n_theta):
+        P = (y[:, m, :] @ Eh) * (kappa * D)[None, :]                      # (z, q)
+        ex = np.exp(2j * math.pi * np.multiply.outer(w * math.cos(th[m]), x))   # (q, ix)
+        ey = np.exp(2j * math.pi * np.multiply.outer(w * math.sin(th[m]), x))   # (q, iy)
+        out += np.einsum("zq,qx,qy->zyx", P, ex, ey).real
+    return out.reshape(y.shape[0], -1)
+
+
+def fubini_normal(fg: FGeometry, u, filt: int = 0) -> np.ndarray:
+    """N u = (exact backprojection, filter filt) of (exact transform of u):
+    the definition, (nz, n*n) -> (nz, n*n)."""
+    return fubini_direct_backproject(fg, fubini_direct(fg, u), filt)
+
+
+def normal_taps(fg: FGeometry, d, s, filt: int = 0):
+    """Entries of N: N[j, l] = t(x_j - x_l) + h(x_j + x_l), x the pixel
+    centres (the differences and sums are integer vectors (dx, dy)).
+
+      t(d) = kappa sum_m sum_q nu_q cos(2 pi w_q (dx cos t_m + dy sin t_m))
+      h(s) = kappa (D_q0 / 2) sum_m cos(phi - pi (sx cos t_m + sy sin t_m)),
+             phi = 2 pi (1/2 - c), only for even n_p (q0 = 0, w_q0 = -1/2)
+
+    with nu_q = D_q, except nu_q0 = D_q0 / 2 for even n_p.  For real images
+    the transform's real part pairs every sample w with -w; the one sample
+    without a partner contributes half of its weight shift-invariantly (t) and
+    half through the mirror image (h).  d, s: integer arrays (k, 2) of (x, y)
+    components.  Returns (t (k,), h (k,))."""
+    kappa, D = normal_weights(fg, filt)
+    th = fg.theta()
+    w = fg.omega()
+    nu = D.copy()
+    even = fg.n_p % 2 == 0
+    if even:
+        nu[0] = D[0] / 2.0
+    d = np.asarray(d, np.float64).reshape(-1, 2)
+    s = np.asarray(s, np.float64).reshape(-1, 2)
+    t = np.zeros(d.shape[0])
+    h = np.zeros(s.shape[0])
+    phi = 2.0 * math.pi * (0.5 - fg.c())
+    for m in range(fg.n_theta):
+        pd = d[:, 0] * math.cos(th[m]) + d[:, 1] * math.sin(th[m])
+        t += np.cos(2.0 * math.pi * np.multiply.outer(pd, w)) @ nu
+        if even:
+            ps = s[:, 0] * math.cos(th[m]) + s[:, 1] * math.sin(th[m])
+            h += np.cos(phi - math.pi * ps)
+    return kappa * t, (kappa * D[0] / 2.0 * h if even else h)
+
+
+def normal_entry_vectors(fg: FGeometry, j, l):
+    """(d, s) integer vectors for pixel pairs j, l (flat indices iy * n + ix)."""
+    j = np.asarray(j, np.int64)
+    l = np.asarray(l, np.int64)
+    jx, jy, lx, ly = j % fg.n, j // fg.n, l % fg.n, l // fg.n
+    d = np.stack([jx - lx, jy - ly], axis=-1)
+    s = np.stack([jx + lx + 1 - fg.n, jy + ly + 1 - fg.n], axis=-1)
+    return d, s
+
+
+def fubini_sirt_bb_normal(fg: FGeometry, b, iters: int, S: Optional[scipy.sparse.csr_matrix] = None):
+    """The paper's SIRT (Sec. 3.1) with the normal operator in one step: per
+    slice, c = the Hamming-filtered backprojection of b (gridded, computed once),
+    g_k = c - N x_k (N = fubini_normal with the Hamming filter; ||g_k|| is
+    hist[k]), x += alpha g with alpha = 1 on the first step and the BB1 step
+    <s,s>/<s,y> after it, in FP64; a slice whose <s,s> or <s,y> is not positive
+    is frozen.  x0 = 0.  Returns (x, hist)."""
+    S = gridding_matrix(fg) if S is None else S
+    b = np.asarray(b, np.float64).reshape(-1, fg.n_theta * fg.n_p)
+    nz = b.shape[0]
+    c = fubini_fbp(fg, b, S, hamming_density(fg))
+    x = np.zeros((nz, fg.n * fg.n))
+    gp = None
+    alpha = np.zeros(nz)
+    frozen = np.zeros(nz, bool)
+    hist = np.zeros((iters, nz))
+    for k in range(iters):
+        g = c - fubini_normal(fg, x, 2)
+        hist[k] = np.sqrt(np.einsum("ij,ij->i", g, g))
+        for s_ in range(nz):
+            if frozen[s_]:
+                a = 0.0
+            elif gp is None:
+                a = 1.0
+            else:
+                ss = alpha[s_] * alpha[s_] * float(np.dot(gp[s_], gp[s_]))
+                sy = -alpha[s_] * float(np.dot(gp[s_], g[s_] - gp[s_]))
+                if ss > 0.0 and sy > 0.0:
+                    a = ss / sy
+                else:
+                    a, frozen[s_] = 0.0, True
+            x[s_] = x[s_] + a * g[s_]
+            alpha[s_] = a
+        gp = g
+    return x, hist

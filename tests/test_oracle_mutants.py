@@ -108,7 +108,9 @@ def test_unmutated_python_variant_passes(tmp_path):
 
 
 # Mistakes planted in the Fubini-Radon oracle (Sec. 3): the gridding phase,
-# the deapodization, the wrap sign, the radial transform and the FBP weight.
+# the deapodization, the wrap sign, the radial transform and the FBP weight;
+# and in its normal operator: the entry formula, the exact adjoint and the
+# SIRT that applies it.
 FUB_MUTANTS = {
     "fubini: grid phase conjugated": ("return np.exp(2j * math.pi * np.arange(G) * (G / 2.0 - 0.5) / G)",
                                       "return np.exp(-2j * math.pi * np.arange(G) * (G / 2.0 - 0.5) / G)"),
@@ -123,6 +125,13 @@ FUB_MUTANTS = {
     "fubini SIRT: step along the gradient": ("            x[s_] += a * g[s_]", "            x[s_] -= a * g[s_]"),
     "fubini SIRT: Hamming window dropped": ("return ramp_density(fg) * (0.54 + 0.46 * np.cos(2.0 * math.pi * fg.omega()))",
                                             "return ramp_density(fg)"),
+    "normal: Hankel part dropped": ("h += np.cos(phi - math.pi * ps)", "h += 0.0 * np.cos(phi - math.pi * ps)"),
+    "normal: unpaired sample at full weight": ("nu[0] = D[0] / 2.0", "nu[0] = D[0]"),
+    "direct adjoint: exponent sign": ("ex = np.exp(2j * math.pi * np.multiply.outer(w * math.cos(th[m]), x))",
+                                      "ex = np.exp(-2j * math.pi * np.multiply.outer(w * math.cos(th[m]), x))"),
+    "direct FBP: angular weight": ("return math.pi / (fg.n_theta * fg.n_p), ramp_density(fg)",
+                                   "return 1.0 / (fg.n_theta * fg.n_p), ramp_density(fg)"),
+    "normal SIRT: step along the gradient": ("x[s_] = x[s_] + a * g[s_]", "x[s_] = x[s_] - a * g[s_]"),
 }
 
 
