@@ -415,6 +415,35 @@ TOMO_API tomo_status tomo_fubini_backproject(tomo_fubini *F, const float *y, flo
 TOMO_API tomo_status tomo_fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t n_z, int32_t iters,
                                          double *resnorm_hist, void *stream);
 
+/* The normal operator in one step (the Toeplitz route of the outlook, Sec. 5):
+ * y = N x, N = R^T W R for the EXACT transform R above and the sinogram weight
+ * W of the exact adjoint (filter 0), of iRadon with the ramp density (1) or
+ * with the Hamming-windowed density (2) -- the same filters as
+ * tomo_fubini_backproject.  For real images
+ *   N[j,l] = t(x_j - x_l) + h(x_j + x_l),
+ *   t(d) = kappa sum_m sum_q nu_q cos(2 pi w_q (d . theta_m)),
+ *   h(s) = kappa (D_q0/2) sum_m cos(2 pi (1/2 - c) - pi (s . theta_m)),
+ * (kappa = 1/n_p for filter 0, pi/(n_theta n_p) otherwise; D_q the density,
+ * nu_q = D_q except nu_q0 = D_q0/2 and h = 0 unless n_p is even, q0 being the
+ * unpaired sample w = -1/2), applied as a circular convolution on the 2n x 2n
+ * grid: one FP32 real-to-complex FFT, one pointwise product, the inverse FFT;
+ * no gridding, no 1D transforms.  It agrees with
+ * tomo_fubini_backproject(tomo_fubini_project(x)) to the gridding error.  The
+ * first call per filter sums the taps in FP64 on the device and transforms
+ * them (O(n^2 n_theta n_p) work, synchronises `stream`).  x, y (n_z, n, n)
+ * DEVICE, slice-major, not overlapping. */
+TOMO_API tomo_status tomo_fubini_normal(tomo_fubini *F, const float *x, float *y, int32_t n_z, int32_t filter,
+                                        void *stream);
+
+/* The paper's SIRT of tomo_fubini_sirt_bb with the normal operator: per slice
+ * c = iRadon_Hamming(sino) once (gridded), then g_k = c - N x_k (filter 2;
+ * ||g_k|| -> gradnorm_hist[k * n_z + z], DEVICE, nullable), x += alpha g with
+ * alpha = 1 first and the BB1 step after it, as there.  One convolution per
+ * iteration instead of a projection and a backprojection.  n_z <= 65535.
+ * Scratch is allocated stream-ordered on `stream`. */
+TOMO_API tomo_status tomo_fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, int32_t n_z,
+                                                int32_t iters, double *gradnorm_hist, void *stream);
+
 /* Device-side status of `stream` (a stream of the CURRENT device; NULL = the
  * legacy default stream).  Calls queued without synchronising (tomo_cgls_batched
  * with opts->async) record the status of their bounded waits in one status

@@ -508,6 +508,26 @@ class Fubini:
         _lib.call("tomo_fubini_sirt_bb", self._h, _ptr(sino), _ptr(x), nz, iters, _ptr(hist), _stream())
         return (x, hist[:iters]) if history else x
 
+    def normal(self, x: torch.Tensor, filtered=False) -> torch.Tensor:
+        """N x = backproject(project(x), filtered) for the exact transform, in
+        one step (a convolution on the 2n x 2n grid)."""
+        _check_tensor(x, "x")
+        nz = _nz(x, self.n * self.n, "x")
+        y = torch.empty((nz, self.n, self.n), device=x.device)
+        f = {False: 0, True: 1, "ramp": 1, "hamming": 2}[filtered]
+        _lib.call("tomo_fubini_normal", self._h, _ptr(x), _ptr(y), nz, f, _stream())
+        return y
+
+    def sirt_bb_normal(self, sino: torch.Tensor, iters: int, history: bool = False):
+        """sirt_bb with the normal operator in one step per iteration.  Returns
+        x, and the ||g_k|| history (g_k = c - N x_k) if asked."""
+        _check_tensor(sino, "sino")
+        nz = _nz(sino, self.n_theta * self.n_p, "sino")
+        x = torch.empty((nz, self.n, self.n), device=sino.device)
+        hist = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
+        _lib.call("tomo_fubini_sirt_bb_normal", self._h, _ptr(sino), _ptr(x), nz, iters, _ptr(hist), _stream())
+        return (x, hist[:iters]) if history else x
+
 
 class TomoProject(torch.autograd.Function):
     """y = A x with the stored transpose as the backward: dL/dx = A^T dL/dy."""

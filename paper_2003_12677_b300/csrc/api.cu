@@ -297,6 +297,26 @@ tomo_status tomo_fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int
   return fubini_sirt_bb(F, sino, x, n_z, iters, resnorm_hist, (cudaStream_t)stream);
 }
 
+tomo_status tomo_fubini_normal(tomo_fubini *F, const float *x, float *y, int32_t n_z, int32_t filter, void *stream) {
+  if (!F) return fail(TOMO_ERR_INVALID_ARG, "handle must be non-NULL");
+  TOMO_TRY(check_vec(x, "x"));
+  TOMO_TRY(check_vec(y, "y"));
+  if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
+  if (filter < 0 || filter > 2) return fail(TOMO_ERR_INVALID_ARG, "filter must be 0, 1 or 2");
+  return fubini_normal(F, x, y, n_z, filter, (cudaStream_t)stream);
+}
+
+tomo_status tomo_fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, int32_t n_z, int32_t iters,
+                                       double *gradnorm_hist, void *stream) {
+  if (!F) return fail(TOMO_ERR_INVALID_ARG, "handle must be non-NULL");
+  TOMO_TRY(check_vec(sino, "sino"));
+  TOMO_TRY(check_vec(x, "x"));
+  if (n_z < 1 || iters < 0) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1 and iters >= 0");
+  if (n_z > 65535) return fail(TOMO_ERR_INVALID_ARG, "n_z must be <= 65535");
+  if (gradnorm_hist && ((uintptr_t)gradnorm_hist & 7u)) return fail(TOMO_ERR_INVALID_ARG, "gradnorm_hist misaligned");
+  return fubini_sirt_bb_normal(F, sino, x, n_z, iters, gradnorm_hist, (cudaStream_t)stream);
+}
+
 const char *tomo_status_string(tomo_status s) {
   switch (s) {
     case TOMO_OK: return "TOMO_OK";

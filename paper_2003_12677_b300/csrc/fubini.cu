@@ -17,28 +17,8 @@
 #include <cstring>
 #include <vector>
 
-#include <cufft.h>
+#include "fubini.cuh"
 
-#include "internal.cuh"
-
-struct tomo_fubini {
-  int32_t n = 0, np = 0, nt = 0, kw = 0, G = 0, Bf = 0;
-  double center = 0, beta = 0;
-  int device = 0;
-  tomo::Csr S, ST;                // S: (nt*np) x (G*G); ST its transpose
-  float *deapod = nullptr;        // [n] 1 / phi_hat(x / G)
-  float *dens = nullptr;          // [np] ramp density of the filtered backprojection
-  float *dens_h = nullptr;        // [np] the same times the Hamming window
-  float2 *ph_grid = nullptr;      // [G]  e^{2 pi i k (G/2 - 1/2)/G}
-  float2 *ph_rad = nullptr;       // [np] e^{2 pi i (q - q0)(1/2 - c)/np}
-  float2 *ph_bin = nullptr;       // [np] e^{2 pi i q0 k / np}
-  cufftComplex *grid = nullptr;   // [Bf][G][G]
-  float *gridI = nullptr;         // [G*G][2 Bf] interleaved (re, im)
-  float *polI = nullptr;          // [nt*np][2 Bf]
-  cufftComplex *pol = nullptr;    // [Bf][nt][np]
-  cufftHandle plan2 = 0, plan1 = 0;
-  bool plans = false;
-};
 
 namespace tomo {
 
@@ -358,8 +338,9 @@ void free_fubini(tomo_fubini *F) {
     cufftDestroy(F->plan2);
     cufftDestroy(F->plan1);
   }
+  free_normal(F);
   void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->ST.rp, F->ST.ci, F->ST.v, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
-                  F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin};
+                  F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin, F->cs, F->sn};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete F;
@@ -407,16 +388,9 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
   while (F->Bf > 1 && (int64_t)G * G * F->Bf * 16 > (int64_t)2 << 30) F->Bf /= 2;
 
   const int64_t rows = (int64_t)F->nt * F->np, cols = G * G, nnz = rows * kw * kw;
-  double *dcs = nullptr, *dsn = nullptr;
-  TOMO_TRY(dalloc(&dcs, F->nt));
-  TOMO_TRY(dalloc(&dsn, F->nt));
-  struct Tmp {
-    void *p[2];
-    ~Tmp() {
-      for (void *q : p)
-        if (q) cudaFree(q);
-    }
-  } tmp{{dcs, dsn}};
+  TOMO_TRY(dalloc(&F->cs, F->nt));
+  TOMO_TRY(dalloc(&F->sn, F->nt));
+  double *dcs = F->cs, *dsn = F->sn;
   TOMO_CUDA(cudaMemcpyAsync(dcs, cs.data(), sizeof(double) * F->nt, cudaMemcpyHostToDevice, st));
   TOMO_CUDA(cudaMemcpyAsync(dsn, sn.data(), sizeof(double) * F->nt, cudaMemcpyHostToDevice, st));
   F->S.rows = rows;

@@ -1,0 +1,53 @@
+// fubini.cuh -- the handle of the Fubini-Radon transform (Sec. 3, Eq. 2),
+// shared by the transform (fubini.cu) and its normal operator (normal.cu).
+#pragma once
+
+#include <cufft.h>
+
+#include "internal.cuh"
+
+namespace tomo {
+
+// The normal operator N = R^T W R of one filter, applied as a 2n x 2n
+// circular convolution: spectra of its Toeplitz taps (over pixel differences)
+// and of its Hankel taps (over pixel sums, times the phase that turns the
+// mirrored image's spectrum into the conjugate of the image's), each scaled
+// by 1 / L^2 for the unnormalised inverse transform.
+struct NormalKernel {
+  float2 *Kt = nullptr;  // [L][L/2+1]
+  float2 *Kh = nullptr;  // [L][L/2+1]; null when n_p is odd (no Hankel part)
+};
+
+}  // namespace tomo
+
+struct tomo_fubini {
+  int32_t n = 0, np = 0, nt = 0, kw = 0, G = 0, Bf = 0;
+  double center = 0, beta = 0;
+  int device = 0;
+  tomo::Csr S, ST;                // S: (nt*np) x (G*G); ST its transpose
+  double *cs = nullptr;           // [nt] cos theta_m
+  double *sn = nullptr;           // [nt] sin theta_m
+  float *deapod = nullptr;        // [n] 1 / phi_hat(x / G)
+  float *dens = nullptr;          // [np] ramp density of the filtered backprojection
+  float *dens_h = nullptr;        // [np] the same times the Hamming window
+  float2 *ph_grid = nullptr;      // [G]  e^{2 pi i k (G/2 - 1/2)/G}
+  float2 *ph_rad = nullptr;       // [np] e^{2 pi i (q - q0)(1/2 - c)/np}
+  float2 *ph_bin = nullptr;       // [np] e^{2 pi i q0 k / np}
+  cufftComplex *grid = nullptr;   // [Bf][G][G]
+  float *gridI = nullptr;         // [G*G][2 Bf] interleaved (re, im)
+  float *polI = nullptr;          // [nt*np][2 Bf]
+  cufftComplex *pol = nullptr;    // [Bf][nt][np]
+  cufftHandle plan2 = 0, plan1 = 0;
+  bool plans = false;
+  // normal operator (normal.cu), built on first use per filter
+  tomo::NormalKernel nk[3];
+  int32_t Bn = 0;                 // slices per convolution pass
+  float *nP = nullptr;            // [Bn][G][G] real padded image / result
+  float2 *nX = nullptr;           // [Bn][G][G/2+1] its half spectrum
+  cufftHandle planR = 0, planC = 0;
+  bool nplans = false;
+};
+
+namespace tomo {
+void free_normal(tomo_fubini *F);
+}

@@ -149,6 +149,10 @@ tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz,
 tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t nz, int filter, cudaStream_t st);
 tomo_status fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t nz, int32_t iters, double *hist,
                            cudaStream_t st);
+// its normal operator in one step (normal.cu)
+tomo_status fubini_normal(tomo_fubini *F, const float *x, float *y, int32_t nz, int filter, cudaStream_t st);
+tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, int32_t nz, int32_t iters,
+                                  double *hist, cudaStream_t st);
 // per-stream status word (status.cu)
 int *stream_status_word(cudaStream_t st);
 tomo_status fold_status(const int *src, cudaStream_t st);

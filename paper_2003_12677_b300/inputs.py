@@ -232,6 +232,11 @@ WORKLOADS["sirt_bb_512x360_b64"] = Workload("sirt_bb_512x360_b64", 512, 360, 64,
 WORKLOADS["fubini_512x360_b64"] = Workload("fubini_512x360_b64", 512, 360, 64, "fubini", 100,
                                           "poisson", 1e4, "ellipsoids3d", seed=12677 + 2)
 
+# the same data solved by the paper's SIRT on the Fubini-Radon operator with
+# its normal operator applied in one step (a 2n x 2n convolution), 30 iterations
+WORKLOADS["fubini_normal_512x360_b64"] = Workload("fubini_normal_512x360_b64", 512, 360, 64, "fubini_normal", 30,
+                                                 "poisson", 1e4, "ellipsoids3d", seed=12677 + 2)
+
 WORKLOADS["uneven_256"] = Workload("uneven_256", 2048, 1024, 0, "cgls", 30, "poisson", 1e5, "ellipses2d",
                                   values="bf16", seed=12677 + 5)
 
