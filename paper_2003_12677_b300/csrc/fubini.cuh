@@ -14,8 +14,10 @@ namespace tomo {
 // mirrored image's spectrum into the conjugate of the image's), each scaled
 // by 1 / L^2 for the unnormalised inverse transform.
 struct NormalKernel {
-  float2 *Kt = nullptr;  // [L][L/2+1]
-  float2 *Kh = nullptr;  // [L][L/2+1]; null when n_p is odd (no Hankel part)
+  float2 *Kt = nullptr;   // [L][L/2+1]
+  float2 *Kh = nullptr;   // [L][L/2+1]; null when n_p is odd (no Hankel part)
+  float2 *Kt2 = nullptr;  // [L/2+1][L]: the same, column-major (fused convolution)
+  float2 *Kh2 = nullptr;
 };
 
 }  // namespace tomo
@@ -46,6 +48,9 @@ struct tomo_fubini {
   float2 *nX = nullptr;           // [Bn][G][G/2+1] its half spectrum
   cufftHandle planR = 0, planC = 0;
   bool nplans = false;
+  float2 *twL = nullptr;          // [G] e^{-2 pi i t / G} (fused convolution)
+  float2 *H = nullptr;            // [Hc][n + 1][n] half spectra, column-major
+  int32_t Hc = 0;                 // slices per fused pass
 };
 
 namespace tomo {

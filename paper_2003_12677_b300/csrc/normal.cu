@@ -20,6 +20,7 @@
 // cosine series f), transformed once by a double-precision FFT and kept as
 // FP32 spectra; each application is an FP32 real-to-complex FFT, one
 // pointwise product and the inverse FFT.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -33,10 +34,8 @@ namespace {
 
 constexpr int kT = 256;
 
-int egrid(int64_t n) {
-  int64_t b = (n + kT - 1) / kT;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 16));
-}
+// sizes with the fused convolution (the 2n x 2n grid a power of two, 32..1024)
+bool fused_ok(int L) { return L >= 32 && L <= 1024 && (L & (L - 1)) == 0; }
 
 tomo_status cufft_ok(cufftResult r, const char *what) {
   if (r != CUFFT_SUCCESS) return fail(TOMO_ERR_CUDA, std::string("cuFFT ") + what + " failed: " + std::to_string((int)r));
@@ -129,22 +128,20 @@ __global__ void k_nrm_spec(const double2 *Ct, const double2 *Ch, int n, int L, f
   }
 }
 
-// P[s][gy][gx] = u[s][gy][gx] on the n x n corner, 0 elsewhere (s < cnt; the
-// pass's other slices are transformed too but never read)
-__global__ void k_nrm_pad(const float *u, int cnt, int n, int L, float *P) {
-  const int64_t total = (int64_t)cnt * L * L;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int s = (int)(e / ((int64_t)L * L));
-    const int gy = (int)((e / L) % L), gx = (int)(e % L);
-    P[e] = (gy < n && gx < n) ? u[((int64_t)s * n + gy) * n + gx] : 0.f;
-  }
+// P[s][gy][gx] = u[s][gy][gx] on the n x n corner, 0 elsewhere; grid (L rows,
+// cnt slices; the pass's other slices are transformed too but never read)
+__global__ void k_nrm_pad(const float *u, int n, int L, float *P) {
+  const int gy = blockIdx.x, s = blockIdx.y;
+  float *row = P + ((int64_t)s * L + gy) * L;
+  const float *src = u + ((int64_t)s * n + gy) * n;
+  for (int gx = threadIdx.x; gx < L; gx += blockDim.x) row[gx] = (gy < n && gx < n) ? src[gx] : 0.f;
 }
 
-// X = Kt X + Kh conj(X) on the half spectra of cnt slices
-__global__ void k_nrm_mul(float2 *X, int cnt, int64_t per, const float2 *Kt, const float2 *Kh) {
-  const int64_t total = (int64_t)cnt * per;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = e % per;
+// X = Kt X + Kh conj(X) on the half spectra; grid (ceil(per / kT), cnt slices)
+__global__ void k_nrm_mul(float2 *X, int per, const float2 *Kt, const float2 *Kh) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < per) {
+    const int64_t e = (int64_t)blockIdx.y * per + k;
     const float2 x = X[e], kt = Kt[k];
     float re = kt.x * x.x - kt.y * x.y, im = kt.x * x.y + kt.y * x.x;
     if (Kh) {
@@ -156,14 +153,12 @@ __global__ void k_nrm_mul(float2 *X, int cnt, int64_t per, const float2 *Kt, con
   }
 }
 
-// y[s][iy][ix] = P[s][iy][ix] on the n x n corner
-__global__ void k_nrm_crop(const float *P, int cnt, int n, int L, float *y) {
-  const int64_t total = (int64_t)cnt * n * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int s = (int)(e / ((int64_t)n * n));
-    const int iy = (int)((e / n) % n), ix = (int)(e % n);
-    y[e] = P[((int64_t)s * L + iy) * L + ix];
-  }
+// y[s][iy][ix] = P[s][iy][ix] on the n x n corner; grid (n rows, cnt slices)
+__global__ void k_nrm_crop(const float *P, int n, int L, float *y) {
+  const int iy = blockIdx.x, s = blockIdx.y;
+  const float *row = P + ((int64_t)s * L + iy) * L;
+  float *dst = y + ((int64_t)s * n + iy) * n;
+  for (int ix = threadIdx.x; ix < n; ix += blockDim.x) dst[ix] = row[ix];
 }
 
 // ---- the SIRT with N in one step --------------------------------------------
@@ -185,29 +180,48 @@ __device__ double nrm_block_sum(double v) {
 }
 
 // grid (NB, cnt): g = c - (P ? crop(P) : 0) for slices s0 .. s0 + cnt - 1;
-// part[(s0 + s) NB + b] = (<g,g>, <gp,gp>, <gp, g - gp>) of block b's range
+// block b takes image rows [b rpb, (b + 1) rpb), rpb = ceil(n / NB), NB <= n;
+// part[(s0 + s) NB + b] = (<g,g>, <gp,gp>, <gp, g - gp>) over those rows
 __global__ void __launch_bounds__(kT) k_nrm_grad(const float *P, const float *c, const float *gp, float *g, int s0,
                                                  int n, int L, int NB, double3 *part) {
   const int b = blockIdx.x, s = blockIdx.y;
-  const int64_t cols = (int64_t)n * n;
-  const int64_t per = (cols + NB - 1) / NB;
-  const int64_t lo = b * per, hi = lo + per < cols ? lo + per : cols;
-  const int64_t off = (int64_t)(s0 + s) * cols;
+  const int rpb = (n + NB - 1) / NB;
+  const int r0 = b * rpb, r1 = r0 + rpb < n ? r0 + rpb : n;
+  const int64_t off = (int64_t)(s0 + s) * n * n;
   double gg = 0.0, pp = 0.0, pq = 0.0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += kT) {
-    float nx = 0.f;
-    if (P) nx = P[((int64_t)s * L + i / n) * L + i % n];
-    const float gv = c[off + i] - nx;
-    g[off + i] = gv;
-    const double a = gp[off + i];
-    gg += (double)gv * (double)gv;
-    pp += a * a;
-    pq += a * ((double)gv - a);
+  for (int r = r0; r < r1; ++r) {
+    const float *prow = P ? P + ((int64_t)s * L + r) * L : nullptr;
+    const int64_t ro = off + (int64_t)r * n;
+    for (int col = threadIdx.x; col < n; col += kT) {
+      const float gv = c[ro + col] - (prow ? prow[col] : 0.f);
+      g[ro + col] = gv;
+      const double a = gp[ro + col];
+      gg += (double)gv * (double)gv;
+      pp += a * a;
+      pq += a * ((double)gv - a);
+    }
   }
   gg = nrm_block_sum(gg);
   pp = nrm_block_sum(pp);
   pq = nrm_block_sum(pq);
   if (threadIdx.x == 0) part[(int64_t)(s0 + s) * NB + b] = make_double3(gg, pp, pq);
+}
+
+// BB1 step of one slice from its sums (P = <gp,gp>, Q = <gp, g - gp>) and the
+// state (alpha, frozen, stepped): alpha = 1 on the first step, frozen slices 0
+__device__ __forceinline__ double bb_rule(double P, double Q, const double *in, double *frozen, double *stepped) {
+  const double ap = in[0];
+  *frozen = in[1];
+  *stepped = in[2];
+  if (*frozen != 0.0) return 0.0;
+  if (*stepped == 0.0) {
+    *stepped = 1.0;
+    return 1.0;
+  }
+  const double ss = ap * ap * P, sy = -ap * Q;
+  if (ss > 0.0 && sy > 0.0) return ss / sy;
+  *frozen = 1.0;
+  return 0.0;
 }
 
 // grid (NB, nz): alpha per slice from the partial sums (every block computes
@@ -225,21 +239,8 @@ __global__ void __launch_bounds__(kT) k_nrm_step(float *x, const float *g, int64
       P += v.y;
       Q += v.z;
     }
-    const double ap = sc_in[s * 4 + 0];
-    double frozen = sc_in[s * 4 + 1], stepped = sc_in[s * 4 + 2];
-    double a = 0.0;
-    if (frozen != 0.0) {
-      a = 0.0;
-    } else if (stepped == 0.0) {
-      a = 1.0;
-      stepped = 1.0;
-    } else {
-      const double ss = ap * ap * P, sy = -ap * Q;
-      if (ss > 0.0 && sy > 0.0)
-        a = ss / sy;
-      else
-        frozen = 1.0;
-    }
+    double frozen, stepped;
+    const double a = bb_rule(P, Q, sc_in + s * 4, &frozen, &stepped);
     if (b == 0) {
       sc_out[s * 4 + 0] = a;
       sc_out[s * 4 + 1] = frozen;
@@ -254,6 +255,335 @@ __global__ void __launch_bounds__(kT) k_nrm_step(float *x, const float *g, int64
   const int64_t lo = b * per, hi = lo + per < cols ? lo + per : cols;
   const int64_t off = (int64_t)s * cols;
   for (int64_t i = lo + threadIdx.x; i < hi; i += kT) x[off + i] = fmaf(a, g[off + i], x[off + i]);
+}
+
+// ---- fused convolution for L = 2n a power of two, 32 <= L <= 1024 ----------
+// Three passes over the half spectrum H[s][kx][j] (kx = 0..n, image row j < n;
+// column-major, so that the column pass reads each column contiguously):
+//   rows     image rows a = 2p and b = 2p + 1 as one complex FFT of length L
+//            (z = u_a + i u_b, zero-padded), split into the two half spectra;
+//   columns  per column kx: the FFT over its n rows (zero-padded to L),
+//            Kt V + Kh conj(V), the inverse FFT, rows < n kept;
+//   rows^-1  the half spectra of rows a, b joined as Y_a + i Y_b (Hermitian
+//            extension) and one inverse complex FFT: its real and imaginary
+//            parts are rows a and b of N u.
+// An FFT of length L = R1 R2 (R1 = R2 or 2 R2) runs on G = R2 lanes of one warp
+// by the four-step decomposition: R1-point DFTs in registers over
+// x[j1 R2 + j2], the twiddles W_L^{j2 k1}, a transpose through shared memory,
+// R2-point DFTs in registers; X[k1 + R1 k2] ends in lane k1 mod G.  The
+// inverse runs the same steps backwards with conjugate twiddles.
+
+struct Tw32 {
+  float2 w[32];  // e^{-2 pi i k / 32}
+};
+
+__host__ __device__ constexpr int rev8(int i) {
+  return ((i & 1) << 7) | ((i & 2) << 5) | ((i & 4) << 3) | ((i & 8) << 1) | ((i & 16) >> 1) | ((i & 32) >> 3) |
+         ((i & 64) >> 5) | ((i & 128) >> 7);
+}
+
+__host__ __device__ constexpr int ilog2(int R) { return R <= 1 ? 0 : 1 + ilog2(R / 2); }
+
+// bit reversal of i < R (R a power of two <= 256), loop-free so that unrolled
+// register indexing folds to constants
+template <int R>
+__host__ __device__ constexpr int bitrev(int i) {
+  return rev8(i) >> (8 - ilog2(R));
+}
+static_assert(bitrev<32>(1) == 16 && bitrev<32>(6) == 12 && bitrev<8>(3) == 6, "bit reversal");
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// in-register DFT of R <= 32 points, natural order in and out: radix-2
+// decimation in time on the bit-reversed sequence, one template level per
+// stage so that every loop unrolls; kInv: conjugate twiddles
+template <int R, int LEN, bool kInv>
+__device__ __forceinline__ void dft_stage(float2 *a, const Tw32 &tw) {
+#pragma unroll
+  for (int i = 0; i < R; i += LEN) {
+#pragma unroll
+    for (int j = 0; j < LEN / 2; ++j) {
+      const float2 u = a[i + j];
+      float2 t = a[i + j + LEN / 2];
+      if (j != 0) {
+        float2 w = tw.w[j * (32 / LEN)];
+        if (kInv) w.y = -w.y;
+        t = cmulf(w, t);
+      }
+      a[i + j] = make_float2(u.x + t.x, u.y + t.y);
+      a[i + j + LEN / 2] = make_float2(u.x - t.x, u.y - t.y);
+    }
+  }
+  if constexpr (LEN < R) dft_stage<R, 2 * LEN, kInv>(a, tw);
+}
+
+template <int R, bool kInv>
+__device__ __forceinline__ void dft_reg(float2 *v, const Tw32 &tw) {
+  float2 a[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[bitrev<R>(i)] = v[i];
+  dft_stage<R, 2, kInv>(a, tw);
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = a[i];
+}
+
+// forward: lane l holds v[j1] = x[j1 R2 + l]; on return w[t R2 + k2] =
+// X[(l + G t) + R1 k2].  S: the group's R1 x (R2 + 1) shared tile.
+template <int R1, int R2>
+__device__ __forceinline__ void fft_fwd(float2 *v, float2 *w, float2 *S, int l, const float2 *twL, const Tw32 &tw) {
+  constexpr int G = R2, T = R1 / G;
+  dft_reg<R1, false>(v, tw);
+#pragma unroll
+  for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulf(v[k1], __ldg(twL + l * k1));
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) S[k1 * (R2 + 1) + l] = v[k1];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int k1 = l + G * t;
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) w[t * R2 + j2] = S[k1 * (R2 + 1) + j2];
+    dft_reg<R2, false>(w + t * R2, tw);
+  }
+  __syncwarp();
+}
+
+// inverse (unnormalised) of fft_fwd: from w back to v[j1] = x[j1 R2 + l]
+template <int R1, int R2>
+__device__ __forceinline__ void fft_inv(float2 *w, float2 *v, float2 *S, int l, const float2 *twL, const Tw32 &tw) {
+  constexpr int G = R2, T = R1 / G;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int k1 = l + G * t;
+    dft_reg<R2, true>(w + t * R2, tw);
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) {
+      float2 tw1 = __ldg(twL + j2 * k1);
+      tw1.y = -tw1.y;
+      S[k1 * (R2 + 1) + j2] = cmulf(w[t * R2 + j2], tw1);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) v[k1] = S[k1 * (R2 + 1) + l];
+  __syncwarp();
+  dft_reg<R1, true>(v, tw);
+}
+
+constexpr int kCvThreads = 256;
+
+template <int R1, int R2>
+constexpr int cv_smem() {
+  return (kCvThreads / R2) * R1 * (R2 + 1) * (int)sizeof(float2);
+}
+
+// rows: FFT id f = s (n/2) + p over rows 2p, 2p + 1 of slice s; kStep: the
+// rows are x + alpha[s] g, written back to x first (the previous BB step)
+template <int R1, int R2, bool kStep>
+__global__ void __launch_bounds__(kCvThreads) k_cv_rows(const float *u, float *x, const float *g,
+                                                         const float *alpha, float2 *H, int nz, const float2 *twL,
+                                                         const __grid_constant__ Tw32 tw) {
+  constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
+  extern __shared__ float2 cv_sm[];
+  const int l = threadIdx.x % G;
+  float2 *S = cv_sm + (threadIdx.x / G) * R1 * (R2 + 1);
+  const int64_t f = ((int64_t)blockIdx.x * kCvThreads + threadIdx.x) / G;
+  const bool act = f < (int64_t)nz * (n / 2);
+  const int s = act ? (int)(f / (n / 2)) : 0, p = act ? (int)(f % (n / 2)) : 0;
+  const int64_t ra = ((int64_t)s * n + 2 * p) * n, rb = ra + n;
+  float2 v[R1], w[R1];
+  const float al = (kStep && act) ? alpha[s] : 0.f;
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) {
+    float a = 0.f, b = 0.f;
+    if (j1 < R1 / 2 && act) {
+      const int j = j1 * R2 + l;
+      if (kStep) {
+        a = fmaf(al, g[ra + j], x[ra + j]);
+        b = fmaf(al, g[rb + j], x[rb + j]);
+        x[ra + j] = a;
+        x[rb + j] = b;
+      } else {
+        a = u[ra + j];
+        b = u[rb + j];
+      }
+    }
+    v[j1] = make_float2(a, b);
+  }
+  fft_fwd<R1, R2>(v, w, S, l, twL, tw);
+  // Z in natural order through the tile, then A_k = (Z_k + conj Z_{L-k}) / 2,
+  // B_k = (Z_k - conj Z_{L-k}) / 2i for k = 0..n
+#pragma unroll
+  for (int t = 0; t < R1 / G; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) S[(l + G * t) + R1 * k2] = w[t * R2 + k2];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < R1 / G; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int k = (l + G * t) + R1 * k2;
+      if (k <= n && act) {
+        const float2 zk = w[t * R2 + k2], zm = S[(L - k) & (L - 1)];
+        const float4 o = make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y),
+                                     -0.5f * (zk.x - zm.x));
+        *reinterpret_cast<float4 *>(H + ((int64_t)s * W + k) * n + 2 * p) = o;
+      }
+    }
+}
+
+// columns: FFT id f = s W + kx; Kt2 / Kh2 in [kx][ky] order
+template <int R1, int R2>
+__global__ void __launch_bounds__(kCvThreads) k_cv_cols(float2 *H, int nz, const float2 *Kt2, const float2 *Kh2,
+                                                         const float2 *twL, const __grid_constant__ Tw32 tw) {
+  constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
+  extern __shared__ float2 cv_sm[];
+  const int l = threadIdx.x % G;
+  float2 *S = cv_sm + (threadIdx.x / G) * R1 * (R2 + 1);
+  const int64_t f = ((int64_t)blockIdx.x * kCvThreads + threadIdx.x) / G;
+  const bool act = f < (int64_t)nz * W;
+  const int kx = act ? (int)(f % W) : 0;
+  float2 *col = H + (act ? f : 0) * n;
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) v[j1] = (j1 < R1 / 2 && act) ? col[j1 * R2 + l] : make_float2(0.f, 0.f);
+  fft_fwd<R1, R2>(v, w, S, l, twL, tw);
+  const float2 *kt = Kt2 + (int64_t)kx * L, *kh = Kh2 ? Kh2 + (int64_t)kx * L : nullptr;
+#pragma unroll
+  for (int t = 0; t < R1 / G; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int ky = (l + G * t) + R1 * k2;
+      const float2 x = w[t * R2 + k2], a = __ldg(kt + ky);
+      float re = a.x * x.x - a.y * x.y, im = a.x * x.y + a.y * x.x;
+      if (kh) {
+        const float2 b = __ldg(kh + ky);  // times conj(x)
+        re += b.x * x.x + b.y * x.y;
+        im += b.y * x.x - b.x * x.y;
+      }
+      w[t * R2 + k2] = make_float2(re, im);
+    }
+  fft_inv<R1, R2>(w, v, S, l, twL, tw);
+  if (act) {
+#pragma unroll
+    for (int j1 = 0; j1 < R1 / 2; ++j1) col[j1 * R2 + l] = v[j1];
+  }
+}
+
+// rows^-1: FFT id f = s (n/2) + p.  kGrad: g = c - N u on rows 2p, 2p + 1 and
+// part[f] = (<g,g>, <gp,gp>, <gp, g - gp>) over them (the row-pair split of
+// k_nrm_grad with NB = n/2); else y = N u
+template <int R1, int R2, bool kGrad>
+__global__ void __launch_bounds__(kCvThreads) k_cv_rows_inv(const float2 *H, float *y, const float *c, const float *gp,
+                                                             double3 *part, int nz, const float2 *twL,
+                                                             const __grid_constant__ Tw32 tw) {
+  constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
+  extern __shared__ float2 cv_sm[];
+  const int l = threadIdx.x % G;
+  float2 *S = cv_sm + (threadIdx.x / G) * R1 * (R2 + 1);
+  const int64_t f = ((int64_t)blockIdx.x * kCvThreads + threadIdx.x) / G;
+  const bool act = f < (int64_t)nz * (n / 2);
+  const int s = act ? (int)(f / (n / 2)) : 0, p = act ? (int)(f % (n / 2)) : 0;
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int t = 0; t < R1 / G; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int k = (l + G * t) + R1 * k2;
+      const bool cj = k > n;
+      const int kk = cj ? L - k : k;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (act) q = *reinterpret_cast<const float4 *>(H + ((int64_t)s * W + kk) * n + 2 * p);
+      if (kk == 0 || kk == n) q.y = q.w = 0.f;  // real for real rows
+      if (cj) q.y = -q.y, q.w = -q.w;
+      w[t * R2 + k2] = make_float2(q.x - q.w, q.y + q.z);  // Y_a + i Y_b
+    }
+  fft_inv<R1, R2>(w, v, S, l, twL, tw);
+  const int64_t ra = ((int64_t)s * n + 2 * p) * n, rb = ra + n;
+  double gg = 0.0, pp = 0.0, pq = 0.0;
+  if (act) {
+#pragma unroll
+    for (int j1 = 0; j1 < R1 / 2; ++j1) {
+      const int j = j1 * R2 + l;
+      if (kGrad) {
+        const float ga = c[ra + j] - v[j1].x, gb = c[rb + j] - v[j1].y;
+        y[ra + j] = ga;
+        y[rb + j] = gb;
+        const double pa = gp[ra + j], pb = gp[rb + j];
+        gg += (double)ga * (double)ga + (double)gb * (double)gb;
+        pp += pa * pa + pb * pb;
+        pq += pa * ((double)ga - pa) + pb * ((double)gb - pb);
+      } else {
+        y[ra + j] = v[j1].x;
+        y[rb + j] = v[j1].y;
+      }
+    }
+  }
+  if (kGrad) {
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) {
+      gg += __shfl_xor_sync(0xffffffffu, gg, o);
+      pp += __shfl_xor_sync(0xffffffffu, pp, o);
+      pq += __shfl_xor_sync(0xffffffffu, pq, o);
+    }
+    if (act && l == 0) part[f] = make_double3(gg, pp, pq);
+  }
+}
+
+// one warp per slice: the NB partial sums in a fixed order, the BB step, the
+// state and ||g|| recorded, alpha[s] for the next pass
+__global__ void k_nrm_alpha(const double3 *part, int NB, const double *sc_in, double *sc_out, double *hist, int k,
+                            int nz, float *alpha) {
+  const int s = blockIdx.x, lane = threadIdx.x;
+  double gg = 0.0, P = 0.0, Q = 0.0;
+  for (int i = lane; i < NB; i += 32) {
+    const double3 v = part[(int64_t)s * NB + i];
+    gg += v.x;
+    P += v.y;
+    Q += v.z;
+  }
+  for (int o = 16; o; o >>= 1) {
+    gg += __shfl_xor_sync(0xffffffffu, gg, o);
+    P += __shfl_xor_sync(0xffffffffu, P, o);
+    Q += __shfl_xor_sync(0xffffffffu, Q, o);
+  }
+  if (lane == 0) {
+    double frozen, stepped;
+    const double a = bb_rule(P, Q, sc_in + s * 4, &frozen, &stepped);
+    sc_out[s * 4 + 0] = a;
+    sc_out[s * 4 + 1] = frozen;
+    sc_out[s * 4 + 2] = stepped;
+    if (hist) hist[(int64_t)k * nz + s] = sqrt(gg);
+    alpha[s] = (float)a;
+  }
+}
+
+// x += alpha[s] g; grid (blocks over a slice, nz)
+__global__ void k_nrm_axpy(float *x, const float *g, const float *alpha, int64_t cols) {
+  const float a = alpha[blockIdx.y];
+  const int64_t off = (int64_t)blockIdx.y * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cols; i += (int64_t)gridDim.x * blockDim.x)
+    x[off + i] = fmaf(a, g[off + i], x[off + i]);
+}
+
+// [L][W] -> [W][L] for the column pass
+__global__ void k_nrm_kT(const float2 *K, int L, float2 *KT) {
+  const int W = L / 2 + 1;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * W) return;
+  const int ky = (int)(e / W), kx = (int)(e % W);
+  KT[(int64_t)kx * L + ky] = K[e];
+}
+
+// e^{-2 pi i t / L}, t < L, FP64 arguments rounded once
+__global__ void k_nrm_twiddles(int L, float2 *tw) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L) return;
+  double s, c;
+  sincospi(-2.0 * (double)t / (double)L, &s, &c);
+  tw[t] = make_float2((float)c, (float)s);
 }
 
 // FP64 weights of the backprojection: kappa and the density at |w| = j / np
@@ -321,6 +651,15 @@ tomo_status build_kernel(tomo_fubini *F, int filter, cudaStream_t st) {
   }
   k_nrm_spec<<<(unsigned)((LW + kT - 1) / kT), kT, 0, st>>>(C, C + LW, n, L, K.Kt, K.Kh);
   TOMO_CUDA(cudaGetLastError());
+  if (fused_ok(L)) {  // the column pass reads the spectra column by column
+    TOMO_TRY(dalloc(&K.Kt2, LW));
+    k_nrm_kT<<<(unsigned)((LW + kT - 1) / kT), kT, 0, st>>>(K.Kt, L, K.Kt2);
+    if (even) {
+      TOMO_TRY(dalloc(&K.Kh2, LW));
+      k_nrm_kT<<<(unsigned)((LW + kT - 1) / kT), kT, 0, st>>>(K.Kh, L, K.Kh2);
+    }
+    TOMO_CUDA(cudaGetLastError());
+  }
   TOMO_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed on return
   return TOMO_OK;
 }
@@ -350,16 +689,95 @@ tomo_status ensure_plans(tomo_fubini *F) {
 // P (first cnt slices of the pass) = N u for slices u[0 .. cnt)
 tomo_status apply_pass(tomo_fubini *F, const NormalKernel &K, const float *u, int cnt, cudaStream_t st) {
   const int n = F->n, L = F->G, W = L / 2 + 1;
-  k_nrm_pad<<<egrid((int64_t)cnt * L * L), kT, 0, st>>>(u, cnt, n, L, F->nP);
+  k_nrm_pad<<<dim3(L, cnt), kT, 0, st>>>(u, n, L, F->nP);
   TOMO_TRY(cufft_ok(cufftExecR2C(F->planR, F->nP, (cufftComplex *)F->nX), "R2C"));
-  k_nrm_mul<<<egrid((int64_t)cnt * L * W), kT, 0, st>>>(F->nX, cnt, (int64_t)L * W, K.Kt, K.Kh);
+  k_nrm_mul<<<dim3((L * W + kT - 1) / kT, cnt), kT, 0, st>>>(F->nX, L * W, K.Kt, K.Kh);
   TOMO_TRY(cufft_ok(cufftExecC2R(F->planC, (cufftComplex *)F->nX, F->nP), "C2R"));
   TOMO_CUDA(cudaGetLastError());
   return TOMO_OK;
 }
 
+Tw32 tw32() {
+  Tw32 t;
+  for (int k = 0; k < 32; ++k)
+    t.w[k] = make_float2((float)std::cos(2.0 * M_PI * k / 32.0), (float)-std::sin(2.0 * M_PI * k / 32.0));
+  return t;
+}
+
+tomo_status ensure_fused(tomo_fubini *F, cudaStream_t st) {
+  if (F->H) return TOMO_OK;
+  const int L = F->G, n = F->n, W = n + 1;
+  // slices per fused pass: 64, fewer while the half spectrum would pass 1 GiB
+  int Hc = 64;
+  while (Hc > 1 && (int64_t)W * n * 8 * Hc > ((int64_t)1 << 30)) Hc /= 2;
+  if (!F->twL) {
+    TOMO_TRY(dalloc(&F->twL, L));
+    k_nrm_twiddles<<<(L + kT - 1) / kT, kT, 0, st>>>(L, F->twL);
+    TOMO_CUDA(cudaGetLastError());
+  }
+  TOMO_TRY(dalloc(&F->H, (size_t)W * n * Hc));
+  F->Hc = Hc;
+  return TOMO_OK;
+}
+
+// the pointers of one fused pass set over cnt slices
+struct CvArgs {
+  const float *u = nullptr;      // rows: input image (plain) ...
+  float *x = nullptr;            // ... or x += alpha g first (step)
+  const float *g = nullptr;
+  const float *alpha = nullptr;
+  float *y = nullptr;            // rows^-1: N u (plain) or the new gradient c - N u (grad)
+  const float *c = nullptr;
+  const float *gp = nullptr;
+  double3 *part = nullptr;
+  bool step = false, grad = false;
+};
+
+template <class Kern>
+tomo_status smem_attr(Kern k, int bytes) {
+  TOMO_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return TOMO_OK;
+}
+
+template <int R1, int R2>
+tomo_status cv_run(tomo_fubini *F, const NormalKernel &K, const CvArgs &a, int cnt, cudaStream_t st) {
+  constexpr int L = R1 * R2, n = L / 2, W = n + 1, per = kCvThreads / R2, sm = cv_smem<R1, R2>();
+  TOMO_TRY(smem_attr(k_cv_rows<R1, R2, true>, sm));
+  TOMO_TRY(smem_attr(k_cv_rows<R1, R2, false>, sm));
+  TOMO_TRY(smem_attr(k_cv_cols<R1, R2>, sm));
+  TOMO_TRY(smem_attr(k_cv_rows_inv<R1, R2, true>, sm));
+  TOMO_TRY(smem_attr(k_cv_rows_inv<R1, R2, false>, sm));
+  const Tw32 tw = tw32();
+  const unsigned gr = (unsigned)(((int64_t)cnt * (n / 2) + per - 1) / per);
+  const unsigned gc = (unsigned)(((int64_t)cnt * W + per - 1) / per);
+  if (a.step)
+    k_cv_rows<R1, R2, true><<<gr, kCvThreads, sm, st>>>(nullptr, a.x, a.g, a.alpha, F->H, cnt, F->twL, tw);
+  else
+    k_cv_rows<R1, R2, false><<<gr, kCvThreads, sm, st>>>(a.u, nullptr, nullptr, nullptr, F->H, cnt, F->twL, tw);
+  k_cv_cols<R1, R2><<<gc, kCvThreads, sm, st>>>(F->H, cnt, K.Kt2, K.Kh2, F->twL, tw);
+  if (a.grad)
+    k_cv_rows_inv<R1, R2, true><<<gr, kCvThreads, sm, st>>>(F->H, a.y, a.c, a.gp, a.part, cnt, F->twL, tw);
+  else
+    k_cv_rows_inv<R1, R2, false><<<gr, kCvThreads, sm, st>>>(F->H, a.y, nullptr, nullptr, nullptr, cnt, F->twL, tw);
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
+}
+
+tomo_status cv_dispatch(tomo_fubini *F, const NormalKernel &K, const CvArgs &a, int cnt, cudaStream_t st) {
+  switch (F->G) {
+    case 32: return cv_run<8, 4>(F, K, a, cnt, st);
+    case 64: return cv_run<8, 8>(F, K, a, cnt, st);
+    case 128: return cv_run<16, 8>(F, K, a, cnt, st);
+    case 256: return cv_run<16, 16>(F, K, a, cnt, st);
+    case 512: return cv_run<32, 16>(F, K, a, cnt, st);
+    case 1024: return cv_run<32, 32>(F, K, a, cnt, st);
+  }
+  return fail(TOMO_ERR_INVALID_ARG, "no fused convolution for this size");
+}
+
 tomo_status prepare(tomo_fubini *F, int filter, cudaStream_t st) {
   TOMO_TRY(build_kernel(F, filter, st));
+  if (fused_ok(F->G)) return ensure_fused(F, st);
   TOMO_TRY(ensure_plans(F));
   TOMO_TRY(cufft_ok(cufftSetStream(F->planR, st), "set stream"));
   TOMO_TRY(cufft_ok(cufftSetStream(F->planC, st), "set stream"));
@@ -370,10 +788,14 @@ tomo_status prepare(tomo_fubini *F, int filter, cudaStream_t st) {
 
 void free_normal(tomo_fubini *F) {
   for (NormalKernel &K : F->nk) {
-    if (K.Kt) cudaFree(K.Kt);
-    if (K.Kh) cudaFree(K.Kh);
+    for (float2 *q : {K.Kt, K.Kh, K.Kt2, K.Kh2})
+      if (q) cudaFree(q);
     K = NormalKernel{};
   }
+  if (F->twL) cudaFree(F->twL);
+  if (F->H) cudaFree(F->H);
+  F->twL = nullptr;
+  F->H = nullptr;
   if (F->nplans) {
     cufftDestroy(F->planR);
     cufftDestroy(F->planC);
@@ -389,10 +811,19 @@ tomo_status fubini_normal(tomo_fubini *F, const float *x, float *y, int32_t nz, 
   TOMO_TRY(prepare(F, filter, st));
   const NormalKernel &K = F->nk[filter];
   const int n = F->n, L = F->G;
+  if (fused_ok(L)) {
+    for (int32_t s0 = 0; s0 < nz; s0 += F->Hc) {
+      CvArgs a;
+      a.u = x + (int64_t)s0 * n * n;
+      a.y = y + (int64_t)s0 * n * n;
+      TOMO_TRY(cv_dispatch(F, K, a, std::min<int32_t>(F->Hc, nz - s0), st));
+    }
+    return TOMO_OK;
+  }
   for (int32_t s0 = 0; s0 < nz; s0 += F->Bn) {
     const int cnt = std::min<int32_t>(F->Bn, nz - s0);
     TOMO_TRY(apply_pass(F, K, x + (int64_t)s0 * n * n, cnt, st));
-    k_nrm_crop<<<egrid((int64_t)cnt * n * n), kT, 0, st>>>(F->nP, cnt, n, L, y + (int64_t)s0 * n * n);
+    k_nrm_crop<<<dim3(n, cnt), kT, 0, st>>>(F->nP, n, L, y + (int64_t)s0 * n * n);
     TOMO_CUDA(cudaGetLastError());
   }
   return TOMO_OK;
@@ -404,8 +835,10 @@ tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, i
   const NormalKernel &K = F->nk[2];
   const int n = F->n, L = F->G;
   const int64_t cols = (int64_t)n * n;
-  const int NB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (cols + 4095) / 4096));
-  float *c = nullptr, *g0 = nullptr, *g1 = nullptr;
+  const bool fused = fused_ok(L);
+  // partial sums per slice: the fused path sums row pairs (n/2 per slice)
+  const int NB = fused ? n / 2 : (int)std::max<int64_t>(1, std::min<int64_t>({32, (cols + 4095) / 4096, (int64_t)n}));
+  float *c = nullptr, *g0 = nullptr, *g1 = nullptr, *alpha = nullptr;
   double *scal = nullptr;
   double3 *part = nullptr;
   auto alloc = [&](void **p, size_t b) -> tomo_status {
@@ -416,13 +849,13 @@ tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, i
     return TOMO_OK;
   };
   struct Free {
-    void **p[5];
+    void **p[6];
     cudaStream_t st;
     ~Free() {
       for (void **q : p)
         if (*q) cudaFreeAsync(*q, st);
     }
-  } fr{{(void **)&c, (void **)&g0, (void **)&g1, (void **)&scal, (void **)&part}, st};
+  } fr{{(void **)&c, (void **)&g0, (void **)&g1, (void **)&scal, (void **)&part, (void **)&alpha}, st};
   TOMO_TRY(alloc((void **)&c, sizeof(float) * cols * nz));
   TOMO_TRY(alloc((void **)&g0, sizeof(float) * cols * nz));
   TOMO_TRY(alloc((void **)&g1, sizeof(float) * cols * nz));
@@ -434,6 +867,39 @@ tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, i
   TOMO_CUDA(cudaMemsetAsync(g1, 0, sizeof(float) * cols * nz, st));
   TOMO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 * nz, st));
   float *g = g0, *gp = g1;
+  if (fused && iters > 0) {
+    // per iteration k >= 1: alpha_{k-1} from the sums of g_{k-1}; then one fused
+    // set of passes takes x_k = x_{k-1} + alpha g_{k-1} into the rows pass and
+    // leaves g_k = c - N x_k and its sums after the inverse rows pass
+    TOMO_TRY(alloc((void **)&alpha, sizeof(float) * nz));
+    k_nrm_grad<<<dim3(NB, nz), kT, 0, st>>>(nullptr, c, gp, g, 0, n, L, NB, part);
+    for (int32_t k = 1; k <= iters; ++k) {
+      const int m = k - 1;  // the step taken now: from g_{k-1}
+      k_nrm_alpha<<<nz, 32, 0, st>>>(part, NB, scal + (m & 1) * 4 * nz, scal + ((m + 1) & 1) * 4 * nz, hist, m, nz,
+                                     alpha);
+      TOMO_CUDA(cudaGetLastError());
+      if (k == iters) {
+        const int per = (int)std::min<int64_t>(64, (cols + kT - 1) / kT);
+        k_nrm_axpy<<<dim3(per, nz), kT, 0, st>>>(x, g, alpha, cols);
+        TOMO_CUDA(cudaGetLastError());
+        break;
+      }
+      for (int32_t s0 = 0; s0 < nz; s0 += F->Hc) {
+        CvArgs a;
+        a.step = a.grad = true;
+        a.x = x + s0 * cols;
+        a.g = g + s0 * cols;
+        a.alpha = alpha + s0;
+        a.y = gp + s0 * cols;  // g_k into the buffer of g_{k-2}
+        a.c = c + s0 * cols;
+        a.gp = g + s0 * cols;
+        a.part = part + (int64_t)s0 * NB;
+        TOMO_TRY(cv_dispatch(F, K, a, std::min<int32_t>(F->Hc, nz - s0), st));
+      }
+      std::swap(g, gp);
+    }
+    return TOMO_OK;
+  }
   for (int32_t k = 0; k < iters; ++k) {
     if (k == 0) {
       k_nrm_grad<<<dim3(NB, nz), kT, 0, st>>>(nullptr, c, gp, g, 0, n, L, NB, part);

@@ -62,16 +62,30 @@ def test_normal_matches_oracle(geo, filt):
         assert per_slice_rel(got, ref).max() < 1e-5, (geo, filt, nz)
 
 
+@pytest.mark.parametrize("n,nt", [(32, 24), (64, 30), (128, 40), (256, 12)])
+def test_normal_fused_sizes_match_oracle(n, nt):
+    """The 2n x 2n grid a power of two (64 .. 512 here): the fused convolution
+    (register FFTs, no cuFFT); two slices per filter."""
+    fg, F = pair(n=n, nt=nt)
+    for filt in (0, 1, 2):
+        x = inputs.random_slices((2, n, n), 150 + n + filt)
+        got = F.normal(torch.from_numpy(x).cuda(), [False, True, "hamming"][filt]).cpu().numpy()
+        ref = fb.fubini_normal(fg, x.reshape(2, -1), filt)
+        assert per_slice_rel(got, ref).max() < 1e-5, (n, filt)
+
+
 def test_normal_spans_passes():
-    """33 slices: a full pass of 32 and a ragged pass of 1; every slice equal
-    to its single-slice result."""
-    fg, F = pair(n=16, nt=12)
-    x = inputs.random_slices((33, 16, 16), 131)
-    got = F.normal(torch.from_numpy(x).cuda(), "hamming").cpu().numpy()
-    ref = fb.fubini_normal(fg, x.reshape(33, -1), 2)
-    assert per_slice_rel(got, ref).max() < 1e-5
-    one = F.normal(torch.from_numpy(x[32:]).cuda(), "hamming").cpu().numpy()
-    np.testing.assert_array_equal(one[0], got[32])
+    """More slices than one pass holds (32 for the cuFFT path at n = 12, 64 for
+    the fused path at n = 16) and a ragged last pass; every slice equal to its
+    single-slice result."""
+    for n, nt, nz in ((12, 9, 33), (16, 12, 65)):
+        fg, F = pair(n=n, nt=nt)
+        x = inputs.random_slices((nz, n, n), 131 + n)
+        got = F.normal(torch.from_numpy(x).cuda(), "hamming").cpu().numpy()
+        ref = fb.fubini_normal(fg, x.reshape(nz, -1), 2)
+        assert per_slice_rel(got, ref).max() < 1e-5
+        one = F.normal(torch.from_numpy(x[nz - 1:]).cuda(), "hamming").cpu().numpy()
+        np.testing.assert_array_equal(one[0], got[nz - 1])
 
 
 def test_normal_full_size_columns_512x360():
@@ -129,16 +143,21 @@ def test_sirt_bb_normal_matches_oracle(geo):
     np.testing.assert_allclose(h.cpu().numpy(), href, rtol=1e-4)
 
 
-def test_sirt_bb_normal_spans_passes_and_zero_iterations():
-    fg, F = pair(n=16, nt=12)
-    c = inputs.make_case(16, 12, 33, seed=811, phantom="ellipses2d", noise="poisson", level=1e5)
+@pytest.mark.parametrize("n,nt,nz", [(12, 9, 33), (16, 12, 65)])
+def test_sirt_bb_normal_spans_passes_and_zero_iterations(n, nt, nz):
+    """The cuFFT path (n = 12) over two passes of 32 and the fused path (n =
+    16) over two passes of 64; 0 and 1 iterations."""
+    fg, F = pair(n=n, nt=nt)
+    c = inputs.make_case(n, nt, nz, seed=811, phantom="ellipses2d", noise="poisson", level=1e5)
     b = torch.from_numpy(c.sino).cuda()
     x, h = F.sirt_bb_normal(b, 6, history=True)
-    ref, href = fb.fubini_sirt_bb_normal(fg, c.sino.reshape(33, -1), 6)
+    ref, href = fb.fubini_sirt_bb_normal(fg, c.sino.reshape(nz, -1), 6)
     assert per_slice_rel(x.cpu().numpy(), ref).max() < 1e-4
     np.testing.assert_allclose(h.cpu().numpy(), href, rtol=1e-4)
     x0 = F.sirt_bb_normal(b[:2], 0)
     assert torch.count_nonzero(x0).item() == 0
+    x1 = F.sirt_bb_normal(b[:2], 1).cpu().numpy()
+    np.testing.assert_array_less(per_slice_rel(x1, F.backproject(b[:2], filtered="hamming").cpu().numpy()), 1e-6)
 
 
 def test_sirt_bb_normal_tracks_the_gridded_sirt():
