@@ -48,7 +48,7 @@ struct tomo_fubini {
   float2 *nX = nullptr;           // [Bn][G][G/2+1] its half spectrum
   cufftHandle planR = 0, planC = 0;
   bool nplans = false;
-  float2 *twL = nullptr;          // [G] e^{-2 pi i t / G} (fused convolution)
+  float2 *twL = nullptr;          // [2 G] W_G^{j2 k1} in both orders (fused convolution)
   float2 *H = nullptr;            // [Hc][n + 1][n] half spectra, column-major
   int32_t Hc = 0;                 // slices per fused pass
 };

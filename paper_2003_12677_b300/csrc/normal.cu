@@ -166,6 +166,19 @@ __global__ void k_nrm_crop(const float *P, int n, int L, float *y) {
 // step of the gridded SIRT; per-slice sums in FP64 over a fixed split of each
 // slice into NB blocks, reduced in a fixed order (deterministic).
 
+// compensated FP32 sum of a thread's own terms (Kahan): its error stays
+// near one FP32 rounding of the sum of magnitudes whatever the term count;
+// the threads' sums are then combined in FP64
+struct KSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 __device__ double nrm_block_sum(double v) {
   __shared__ double red[kT];
   red[threadIdx.x] = v;
@@ -188,22 +201,21 @@ __global__ void __launch_bounds__(kT) k_nrm_grad(const float *P, const float *c,
   const int rpb = (n + NB - 1) / NB;
   const int r0 = b * rpb, r1 = r0 + rpb < n ? r0 + rpb : n;
   const int64_t off = (int64_t)(s0 + s) * n * n;
-  double gg = 0.0, pp = 0.0, pq = 0.0;
+  KSum sg, sp, sq;
   for (int r = r0; r < r1; ++r) {
     const float *prow = P ? P + ((int64_t)s * L + r) * L : nullptr;
     const int64_t ro = off + (int64_t)r * n;
     for (int col = threadIdx.x; col < n; col += kT) {
       const float gv = c[ro + col] - (prow ? prow[col] : 0.f);
       g[ro + col] = gv;
-      const double a = gp[ro + col];
-      gg += (double)gv * (double)gv;
-      pp += a * a;
-      pq += a * ((double)gv - a);
+      const float a = gp[ro + col];
+      sg.add(gv * gv);
+      sp.add(a * a);
+      sq.add(a * gv);  // <gp, g - gp> = <gp, g> - <gp, gp>, formed in FP64 below
     }
   }
-  gg = nrm_block_sum(gg);
-  pp = nrm_block_sum(pp);
-  pq = nrm_block_sum(pq);
+  const double gg = nrm_block_sum(sg.value()), pp = nrm_block_sum(sp.value());
+  const double pq = nrm_block_sum(sq.value()) - pp;
   if (threadIdx.x == 0) part[(int64_t)(s0 + s) * NB + b] = make_double3(gg, pp, pq);
 }
 
@@ -330,13 +342,15 @@ __device__ __forceinline__ void dft_reg(float2 *v, const Tw32 &tw) {
 }
 
 // forward: lane l holds v[j1] = x[j1 R2 + l]; on return w[t R2 + k2] =
-// X[(l + G t) + R1 k2].  S: the group's R1 x (R2 + 1) shared tile.
+// X[(l + G t) + R1 k2].  S: the group's R1 x (R2 + 1) shared tile.  twL holds
+// W_L^{j2 k1} twice: [k1][j2] (first L entries) and [j2][k1], so that the
+// lanes of a group read consecutive entries in both directions.
 template <int R1, int R2>
 __device__ __forceinline__ void fft_fwd(float2 *v, float2 *w, float2 *S, int l, const float2 *twL, const Tw32 &tw) {
   constexpr int G = R2, T = R1 / G;
   dft_reg<R1, false>(v, tw);
 #pragma unroll
-  for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulf(v[k1], __ldg(twL + l * k1));
+  for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulf(v[k1], __ldg(twL + k1 * R2 + l));
 #pragma unroll
   for (int k1 = 0; k1 < R1; ++k1) S[k1 * (R2 + 1) + l] = v[k1];
   __syncwarp();
@@ -360,7 +374,7 @@ __device__ __forceinline__ void fft_inv(float2 *w, float2 *v, float2 *S, int l, 
     dft_reg<R2, true>(w + t * R2, tw);
 #pragma unroll
     for (int j2 = 0; j2 < R2; ++j2) {
-      float2 tw1 = __ldg(twL + j2 * k1);
+      float2 tw1 = __ldg(twL + R1 * R2 + j2 * R1 + k1);
       tw1.y = -tw1.y;
       S[k1 * (R2 + 1) + j2] = cmulf(w[t * R2 + j2], tw1);
     }
@@ -502,7 +516,7 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_rows_inv(const float2 *H, flo
     }
   fft_inv<R1, R2>(w, v, S, l, twL, tw);
   const int64_t ra = ((int64_t)s * n + 2 * p) * n, rb = ra + n;
-  double gg = 0.0, pp = 0.0, pq = 0.0;
+  KSum sg, sp, sq;
   if (act) {
 #pragma unroll
     for (int j1 = 0; j1 < R1 / 2; ++j1) {
@@ -511,10 +525,13 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_rows_inv(const float2 *H, flo
         const float ga = c[ra + j] - v[j1].x, gb = c[rb + j] - v[j1].y;
         y[ra + j] = ga;
         y[rb + j] = gb;
-        const double pa = gp[ra + j], pb = gp[rb + j];
-        gg += (double)ga * (double)ga + (double)gb * (double)gb;
-        pp += pa * pa + pb * pb;
-        pq += pa * ((double)ga - pa) + pb * ((double)gb - pb);
+        const float pa = gp[ra + j], pb = gp[rb + j];
+        sg.add(ga * ga);
+        sg.add(gb * gb);
+        sp.add(pa * pa);
+        sp.add(pb * pb);
+        sq.add(pa * ga);
+        sq.add(pb * gb);
       } else {
         y[ra + j] = v[j1].x;
         y[rb + j] = v[j1].y;
@@ -522,13 +539,14 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_rows_inv(const float2 *H, flo
     }
   }
   if (kGrad) {
+    double gg = sg.value(), pp = sp.value(), pq = sq.value();
 #pragma unroll
     for (int o = G / 2; o; o >>= 1) {
       gg += __shfl_xor_sync(0xffffffffu, gg, o);
       pp += __shfl_xor_sync(0xffffffffu, pp, o);
       pq += __shfl_xor_sync(0xffffffffu, pq, o);
     }
-    if (act && l == 0) part[f] = make_double3(gg, pp, pq);
+    if (act && l == 0) part[f] = make_double3(gg, pp, pq - pp);
   }
 }
 
@@ -577,13 +595,16 @@ __global__ void k_nrm_kT(const float2 *K, int L, float2 *KT) {
   KT[(int64_t)kx * L + ky] = K[e];
 }
 
-// e^{-2 pi i t / L}, t < L, FP64 arguments rounded once
-__global__ void k_nrm_twiddles(int L, float2 *tw) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= L) return;
+// W_L^{j2 k1} = e^{-2 pi i (j2 k1 mod L) / L} for L = R1 R2, FP64 arguments
+// rounded once: tw[k1 R2 + j2], then tw[L + j2 R1 + k1]
+__global__ void k_nrm_twiddles(int R1, int R2, float2 *tw) {
+  const int L = R1 * R2;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * L) return;
+  const int k1 = e < L ? e / R2 : (e - L) % R1, j2 = e < L ? e % R2 : (e - L) / R1;
   double s, c;
-  sincospi(-2.0 * (double)t / (double)L, &s, &c);
-  tw[t] = make_float2((float)c, (float)s);
+  sincospi(-2.0 * (double)(((int64_t)j2 * k1) % L) / (double)L, &s, &c);
+  tw[e] = make_float2((float)c, (float)s);
 }
 
 // FP64 weights of the backprojection: kappa and the density at |w| = j / np
@@ -711,8 +732,11 @@ tomo_status ensure_fused(tomo_fubini *F, cudaStream_t st) {
   int Hc = 64;
   while (Hc > 1 && (int64_t)W * n * 8 * Hc > ((int64_t)1 << 30)) Hc /= 2;
   if (!F->twL) {
-    TOMO_TRY(dalloc(&F->twL, L));
-    k_nrm_twiddles<<<(L + kT - 1) / kT, kT, 0, st>>>(L, F->twL);
+    int R2 = 1;
+    while (R2 * R2 < L) R2 *= 2;
+    if (R2 * R2 > L) R2 /= 2;  // L = R1 R2 with R1 = R2 or 2 R2, as in cv_dispatch
+    TOMO_TRY(dalloc(&F->twL, 2 * L));
+    k_nrm_twiddles<<<(2 * L + kT - 1) / kT, kT, 0, st>>>(L / R2, R2, F->twL);
     TOMO_CUDA(cudaGetLastError());
   }
   TOMO_TRY(dalloc(&F->H, (size_t)W * n * Hc));
