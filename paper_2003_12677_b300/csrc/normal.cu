@@ -388,21 +388,35 @@ __device__ __forceinline__ void fft_inv(float2 *w, float2 *v, float2 *S, int l, 
 
 constexpr int kCvThreads = 256;
 
+// a group's shared tile: R1 x (R2 + 1) plus one entry, so that the tiles of
+// consecutive groups start in different banks
+template <int R1, int R2>
+constexpr int cv_tile() {
+  return R1 * (R2 + 1) + 1;
+}
+
 template <int R1, int R2>
 constexpr int cv_smem() {
-  return (kCvThreads / R2) * R1 * (R2 + 1) * (int)sizeof(float2);
+  return (kCvThreads / R2) * cv_tile<R1, R2>() * (int)sizeof(float2);
+}
+
+// the rows passes move H through the tiles when a block's groups are
+// consecutive row pairs of one slice (n/2 a multiple of the groups per block)
+template <int R1, int R2>
+constexpr bool cv_stage() {
+  return (R1 * R2 / 4) % (kCvThreads / R2) == 0;
 }
 
 // rows: FFT id f = s (n/2) + p over rows 2p, 2p + 1 of slice s; kStep: the
 // rows are x + alpha[s] g, written back to x first (the previous BB step)
 template <int R1, int R2, bool kStep>
-__global__ void __launch_bounds__(kCvThreads) k_cv_rows(const float *u, float *x, const float *g,
+__global__ void __launch_bounds__(kCvThreads, 3) k_cv_rows(const float *u, float *x, const float *g,
                                                          const float *alpha, float2 *H, int nz, const float2 *twL,
                                                          const __grid_constant__ Tw32 tw) {
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
   extern __shared__ float2 cv_sm[];
   const int l = threadIdx.x % G;
-  float2 *S = cv_sm + (threadIdx.x / G) * R1 * (R2 + 1);
+  float2 *S = cv_sm + (threadIdx.x / G) * cv_tile<R1, R2>();
   const int64_t f = ((int64_t)blockIdx.x * kCvThreads + threadIdx.x) / G;
   const bool act = f < (int64_t)nz * (n / 2);
   const int s = act ? (int)(f / (n / 2)) : 0, p = act ? (int)(f % (n / 2)) : 0;
@@ -433,6 +447,23 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_rows(const float *u, float *x
   for (int t = 0; t < R1 / G; ++t)
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) S[(l + G * t) + R1 * k2] = w[t * R2 + k2];
+  if constexpr (cv_stage<R1, R2>()) {
+    // the block's NG row pairs together: row k of H gets NG consecutive pairs
+    constexpr int NG = kCvThreads / G;
+    __syncthreads();
+    const int64_t f0 = (int64_t)blockIdx.x * NG;
+    if (f0 < (int64_t)nz * (n / 2)) {
+      const int s0 = (int)(f0 / (n / 2)), p0 = (int)(f0 % (n / 2));
+      for (int e = threadIdx.x; e < W * NG; e += kCvThreads) {
+        const int k = e / NG, q = e % NG;
+        const float2 *Sq = cv_sm + q * cv_tile<R1, R2>();
+        const float2 zk = Sq[k], zm = Sq[(L - k) & (L - 1)];
+        *reinterpret_cast<float4 *>(H + ((int64_t)s0 * W + k) * n + 2 * (p0 + q)) =
+            make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      }
+    }
+    return;
+  }
   __syncwarp();
 #pragma unroll
   for (int t = 0; t < R1 / G; ++t)
@@ -455,7 +486,7 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_cols(float2 *H, int nz, const
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
   extern __shared__ float2 cv_sm[];
   const int l = threadIdx.x % G;
-  float2 *S = cv_sm + (threadIdx.x / G) * R1 * (R2 + 1);
+  float2 *S = cv_sm + (threadIdx.x / G) * cv_tile<R1, R2>();
   const int64_t f = ((int64_t)blockIdx.x * kCvThreads + threadIdx.x) / G;
   const bool act = f < (int64_t)nz * W;
   const int kx = act ? (int)(f % W) : 0;
@@ -490,17 +521,40 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_cols(float2 *H, int nz, const
 // part[f] = (<g,g>, <gp,gp>, <gp, g - gp>) over them (the row-pair split of
 // k_nrm_grad with NB = n/2); else y = N u
 template <int R1, int R2, bool kGrad>
-__global__ void __launch_bounds__(kCvThreads) k_cv_rows_inv(const float2 *H, float *y, const float *c, const float *gp,
+__global__ void __launch_bounds__(kCvThreads, 3) k_cv_rows_inv(const float2 *H, float *y, const float *c, const float *gp,
                                                              double3 *part, int nz, const float2 *twL,
                                                              const __grid_constant__ Tw32 tw) {
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
   extern __shared__ float2 cv_sm[];
   const int l = threadIdx.x % G;
-  float2 *S = cv_sm + (threadIdx.x / G) * R1 * (R2 + 1);
+  float2 *S = cv_sm + (threadIdx.x / G) * cv_tile<R1, R2>();
   const int64_t f = ((int64_t)blockIdx.x * kCvThreads + threadIdx.x) / G;
   const bool act = f < (int64_t)nz * (n / 2);
   const int s = act ? (int)(f / (n / 2)) : 0, p = act ? (int)(f % (n / 2)) : 0;
   float2 v[R1], w[R1];
+  if constexpr (cv_stage<R1, R2>()) {
+    // the block's NG row pairs together: Z_q[k] = Y_a + i Y_b and its
+    // Hermitian partner at L - k, written into the tiles in natural order
+    constexpr int NG = kCvThreads / G;
+    const int64_t f0 = (int64_t)blockIdx.x * NG;
+    if (f0 < (int64_t)nz * (n / 2)) {
+      const int s0 = (int)(f0 / (n / 2)), p0 = (int)(f0 % (n / 2));
+      for (int e = threadIdx.x; e < W * NG; e += kCvThreads) {
+        const int k = e / NG, q = e % NG;
+        float4 y4 = *reinterpret_cast<const float4 *>(H + ((int64_t)s0 * W + k) * n + 2 * (p0 + q));
+        if (k == 0 || k == n) y4.y = y4.w = 0.f;  // real for real rows
+        float2 *Sq = cv_sm + q * cv_tile<R1, R2>();
+        Sq[k] = make_float2(y4.x - y4.w, y4.y + y4.z);
+        if (k > 0 && k < n) Sq[L - k] = make_float2(y4.x + y4.w, y4.z - y4.y);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < R1 / G; ++t)
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) w[t * R2 + k2] = S[(l + G * t) + R1 * k2];
+    __syncwarp();
+  } else {
 #pragma unroll
   for (int t = 0; t < R1 / G; ++t)
 #pragma unroll
@@ -514,6 +568,7 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_rows_inv(const float2 *H, flo
       if (cj) q.y = -q.y, q.w = -q.w;
       w[t * R2 + k2] = make_float2(q.x - q.w, q.y + q.z);  // Y_a + i Y_b
     }
+  }
   fft_inv<R1, R2>(w, v, S, l, twL, tw);
   const int64_t ra = ((int64_t)s * n + 2 * p) * n, rb = ra + n;
   KSum sg, sp, sq;
@@ -576,6 +631,20 @@ __global__ void k_nrm_alpha(const double3 *part, int NB, const double *sc_in, do
     if (hist) hist[(int64_t)k * nz + s] = sqrt(gg);
     alpha[s] = (float)a;
   }
+}
+
+// part[s (n/2) + p] = (<c,c>, 0, 0) over rows 2p, 2p + 1: the sums of the
+// first gradient g_0 = c (no previous one); one warp per row pair, grid
+// (ceil(n / 16), nz)
+__global__ void k_nrm_sumsq(const float *c, int n, double3 *part) {
+  const int p = blockIdx.x * (kT / 32) + threadIdx.x / 32, s = blockIdx.y, lane = threadIdx.x & 31;
+  if (p >= n / 2) return;  // whole warps
+  const float *r = c + ((int64_t)s * n + 2 * p) * n;
+  KSum sg;
+  for (int j = lane; j < 2 * n; j += 32) sg.add(r[j] * r[j]);
+  double gg = sg.value();
+  for (int o = 16; o; o >>= 1) gg += __shfl_xor_sync(0xffffffffu, gg, o);
+  if (lane == 0) part[(int64_t)s * (n / 2) + p] = make_double3(gg, 0.0, 0.0);
 }
 
 // x += alpha[s] g; grid (blocks over a slice, nz)
@@ -888,15 +957,18 @@ tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, i
   // c = the Hamming-filtered backprojection of b (gridded), once
   TOMO_TRY(fubini_backproject(F, sino, c, nz, 2, st));
   TOMO_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * cols * nz, st));
-  TOMO_CUDA(cudaMemsetAsync(g1, 0, sizeof(float) * cols * nz, st));
+  if (!fused) TOMO_CUDA(cudaMemsetAsync(g1, 0, sizeof(float) * cols * nz, st));  // gp at k = 0
   TOMO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 * nz, st));
   float *g = g0, *gp = g1;
   if (fused && iters > 0) {
     // per iteration k >= 1: alpha_{k-1} from the sums of g_{k-1}; then one fused
     // set of passes takes x_k = x_{k-1} + alpha g_{k-1} into the rows pass and
     // leaves g_k = c - N x_k and its sums after the inverse rows pass
+    // g_0 = c itself; later gradients alternate between g0 and g1
     TOMO_TRY(alloc((void **)&alpha, sizeof(float) * nz));
-    k_nrm_grad<<<dim3(NB, nz), kT, 0, st>>>(nullptr, c, gp, g, 0, n, L, NB, part);
+    k_nrm_sumsq<<<dim3((n + 15) / 16, nz), kT, 0, st>>>(c, n, part);
+    g = c;
+    float *next = g0;
     for (int32_t k = 1; k <= iters; ++k) {
       const int m = k - 1;  // the step taken now: from g_{k-1}
       k_nrm_alpha<<<nz, 32, 0, st>>>(part, NB, scal + (m & 1) * 4 * nz, scal + ((m + 1) & 1) * 4 * nz, hist, m, nz,
@@ -914,13 +986,15 @@ tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, i
         a.x = x + s0 * cols;
         a.g = g + s0 * cols;
         a.alpha = alpha + s0;
-        a.y = gp + s0 * cols;  // g_k into the buffer of g_{k-2}
+        a.y = next + s0 * cols;  // g_k
         a.c = c + s0 * cols;
         a.gp = g + s0 * cols;
         a.part = part + (int64_t)s0 * NB;
         TOMO_TRY(cv_dispatch(F, K, a, std::min<int32_t>(F->Hc, nz - s0), st));
       }
-      std::swap(g, gp);
+      float *prev = g;
+      g = next;
+      next = prev == c ? g1 : prev;
     }
     return TOMO_OK;
   }
