@@ -79,21 +79,87 @@ __global__ void k_fub_scatter(const int32_t *ci, const float *v, int64_t rows, i
   }
 }
 
-__global__ void k_fub_sort_rows(const int64_t *rpT, int64_t rows, int32_t *ciT, float *vT) {
+// S^T is kept as two parts: rows of at most kLongRow entries (the short
+// part, long rows left empty) and the long rows (near the spectrum's centre,
+// where the samples of every angle meet) in a compact list.  Both sorted by
+// polar index within a row.
+constexpr int kLongRow = 64;
+
+__global__ void k_fub_split_count(const int64_t *rp, int64_t rows, int32_t *cnt_short, int32_t *is_long) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  const int64_t b = rpT[r], e = rpT[r + 1];
-  for (int64_t i = b + 1; i < e; ++i) {  // insertion sort; keys unique
-    const int32_t key = ciT[i];
-    const float val = vT[i];
-    int64_t j = i - 1;
-    while (j >= b && ciT[j] > key) {
-      ciT[j + 1] = ciT[j];
-      vT[j + 1] = vT[j];
+  const int64_t len = rp[r + 1] - rp[r];
+  cnt_short[r] = len <= kLongRow ? (int32_t)len : 0;
+  is_long[r] = len > kLongRow;
+}
+
+__global__ void k_fub_long_list(const int64_t *rp, const int64_t *lpos, int64_t rows, int32_t *rows_l,
+                                int32_t *cnt_l) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows || lpos[r + 1] == lpos[r]) return;
+  rows_l[lpos[r]] = (int32_t)r;
+  cnt_l[lpos[r]] = (int32_t)(rp[r + 1] - rp[r]);
+}
+
+// short rows: copy, then insertion sort by polar index (keys unique)
+__global__ void k_fub_copy_short(const int64_t *rp, const int32_t *ci, const float *v, int64_t rows,
+                                 const int64_t *rps, int32_t *cis, float *vs) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int64_t b = rps[r], len = rps[r + 1] - b, src = rp[r];
+  for (int64_t i = 0; i < len; ++i) {
+    const int32_t key = ci[src + i];
+    const float val = v[src + i];
+    int64_t j = b + i - 1;
+    while (j >= b && cis[j] > key) {
+      cis[j + 1] = cis[j];
+      vs[j + 1] = vs[j];
       --j;
     }
-    ciT[j + 1] = key;
-    vT[j + 1] = val;
+    cis[j + 1] = key;
+    vs[j + 1] = val;
+  }
+}
+
+// long rows, one block each: every entry goes to its rank among the row's keys
+__global__ void k_fub_copy_long(const int64_t *rp, const int32_t *ci, const float *v, const int32_t *rows_l,
+                                const int64_t *rpl, int32_t *cil, float *vl) {
+  const int64_t src = rp[rows_l[blockIdx.x]], dst = rpl[blockIdx.x];
+  const int len = (int)(rpl[blockIdx.x + 1] - dst);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const int32_t key = ci[src + i];
+    int rank = 0;
+    for (int j = 0; j < len; ++j) rank += ci[src + j] < key;
+    cil[dst + rank] = key;
+    vl[dst + rank] = v[src + i];
+  }
+}
+
+// Y[rows_l[b]] = (long row b of S^T) X for B interleaved columns: B/2 threads
+// per entry (two columns each), 512/B entries at a time, partial sums
+// combined in a fixed order (deterministic)
+template <int B>
+__global__ void __launch_bounds__(256) k_fub_long_spmm(const int64_t *rpl, const int32_t *cil, const float *vl,
+                                                       const int32_t *rows_l, const float *X, float *Y) {
+  constexpr int TPE = B / 2, SL = 256 / TPE;
+  const int t = threadIdx.x % TPE, slot = threadIdx.x / TPE;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int64_t e = rpl[blockIdx.x] + slot; e < rpl[blockIdx.x + 1]; e += SL) {
+    const float w = vl[e];
+    const float2 x = *reinterpret_cast<const float2 *>(X + (int64_t)cil[e] * B + 2 * t);
+    acc.x = fmaf(w, x.x, acc.x);
+    acc.y = fmaf(w, x.y, acc.y);
+  }
+  __shared__ float2 red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < TPE) {
+    float2 sum = make_float2(0.f, 0.f);
+    for (int k = 0; k < SL; ++k) {
+      sum.x += red[k * TPE + threadIdx.x].x;
+      sum.y += red[k * TPE + threadIdx.x].y;
+    }
+    *reinterpret_cast<float2 *>(Y + (int64_t)rows_l[blockIdx.x] * B + 2 * threadIdx.x) = sum;
   }
 }
 
@@ -339,11 +405,28 @@ void free_fubini(tomo_fubini *F) {
     cufftDestroy(F->plan1);
   }
   free_normal(F);
-  void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->ST.rp, F->ST.ci, F->ST.v, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
+  void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->STs.rp, F->STs.ci, F->STs.v, F->STl.rp, F->STl.ci, F->STl.v,
+                  F->rows_l, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
                   F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin, F->cs, F->sn};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete F;
+}
+
+tomo_status long_rows(tomo_fubini *F, const float *X, float *Y, cudaStream_t st) {
+  const unsigned nb = (unsigned)F->STl.rows;
+  if (nb == 0) return TOMO_OK;
+  const Csr &M = F->STl;
+  switch (2 * F->Bf) {
+    case 2: k_fub_long_spmm<2><<<nb, 256, 0, st>>>(M.rp, M.ci, M.v, F->rows_l, X, Y); break;
+    case 4: k_fub_long_spmm<4><<<nb, 256, 0, st>>>(M.rp, M.ci, M.v, F->rows_l, X, Y); break;
+    case 8: k_fub_long_spmm<8><<<nb, 256, 0, st>>>(M.rp, M.ci, M.v, F->rows_l, X, Y); break;
+    case 16: k_fub_long_spmm<16><<<nb, 256, 0, st>>>(M.rp, M.ci, M.v, F->rows_l, X, Y); break;
+    case 32: k_fub_long_spmm<32><<<nb, 256, 0, st>>>(M.rp, M.ci, M.v, F->rows_l, X, Y); break;
+    default: return fail(TOMO_ERR_UNSUPPORTED, "Fubini batch width must be 1..16 slices");
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
 }
 
 }  // namespace
@@ -403,30 +486,75 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
   k_fub_fill_S<<<(unsigned)((rows + kT - 1) / kT), kT, 0, st>>>(dcs, dsn, F->nt, F->np, F->G, kw, F->beta, F->S.rp,
                                                                  F->S.ci, F->S.v);
   TOMO_CUDA(cudaGetLastError());
-  // S^T
-  F->ST.rows = cols;
-  F->ST.cols = rows;
-  F->ST.nnz = nnz;
-  TOMO_TRY(dalloc(&F->ST.rp, cols + 1));
-  TOMO_TRY(dalloc(&F->ST.ci, nnz));
-  TOMO_TRY(dalloc(&F->ST.v, nnz));
-  int32_t *cnt = nullptr;
-  TOMO_TRY(dalloc(&cnt, cols));
-  struct Tmp2 {
-    int32_t *p;
-    ~Tmp2() {
-      if (p) cudaFree(p);
+  // S^T: counting-sort transpose, then split into its short and long rows
+  {
+    Csr T;  // the whole transpose, unsorted rows; freed here
+    int32_t *cnt = nullptr, *flag = nullptr, *cnt_l = nullptr;
+    int64_t *lpos = nullptr;
+    struct Tmp2 {
+      Csr *T;
+      int32_t **c, **f, **cl;
+      int64_t **lp;
+      ~Tmp2() {
+        for (void *q : {(void *)T->rp, (void *)T->ci, (void *)T->v, (void *)*c, (void *)*f, (void *)*cl, (void *)*lp})
+          if (q) cudaFree(q);
+      }
+    } tmp2{&T, &cnt, &flag, &cnt_l, &lpos};
+    TOMO_TRY(dalloc(&T.rp, cols + 1));
+    TOMO_TRY(dalloc(&T.ci, nnz));
+    TOMO_TRY(dalloc(&T.v, nnz));
+    TOMO_TRY(dalloc(&cnt, cols));
+    TOMO_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * cols, st));
+    k_fub_count<<<egrid(nnz), kT, 0, st>>>(F->S.ci, nnz, cnt);
+    TOMO_CUDA(cudaGetLastError());
+    TOMO_TRY(exclusive_scan_i32(cnt, cols, T.rp, st));
+    TOMO_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * cols, st));
+    k_fub_scatter<<<egrid(nnz), kT, 0, st>>>(F->S.ci, F->S.v, rows, kw * kw, T.rp, cnt, T.ci, T.v);
+    TOMO_CUDA(cudaGetLastError());
+    TOMO_TRY(dalloc(&flag, cols));
+    TOMO_TRY(dalloc(&lpos, cols + 1));
+    k_fub_split_count<<<(unsigned)((cols + kT - 1) / kT), kT, 0, st>>>(T.rp, cols, cnt, flag);
+    TOMO_CUDA(cudaGetLastError());
+    F->STs.rows = cols;
+    F->STs.cols = rows;
+    TOMO_TRY(dalloc(&F->STs.rp, cols + 1));
+    TOMO_TRY(exclusive_scan_i32(cnt, cols, F->STs.rp, st));
+    TOMO_TRY(exclusive_scan_i32(flag, cols, lpos, st));
+    int64_t nl = 0;
+    TOMO_CUDA(cudaMemcpyAsync(&F->STs.nnz, F->STs.rp + cols, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TOMO_CUDA(cudaMemcpyAsync(&nl, lpos + cols, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TOMO_CUDA(cudaStreamSynchronize(st));
+    F->STs.max_len = kLongRow;
+    TOMO_TRY(dalloc(&F->STs.ci, F->STs.nnz));
+    TOMO_TRY(dalloc(&F->STs.v, F->STs.nnz));
+    k_fub_copy_short<<<(unsigned)((cols + kT - 1) / kT), kT, 0, st>>>(T.rp, T.ci, T.v, cols, F->STs.rp, F->STs.ci,
+                                                                       F->STs.v);
+    TOMO_CUDA(cudaGetLastError());
+    F->STl.rows = nl;
+    F->STl.cols = rows;
+    TOMO_TRY(dalloc(&F->STl.rp, nl + 1));
+    TOMO_TRY(dalloc(&F->rows_l, nl));
+    TOMO_TRY(dalloc(&cnt_l, nl));
+    if (nl > 0) {
+      k_fub_long_list<<<(unsigned)((cols + kT - 1) / kT), kT, 0, st>>>(T.rp, lpos, cols, F->rows_l, cnt_l);
+      TOMO_CUDA(cudaGetLastError());
     }
-  } tmp2{cnt};
-  TOMO_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * cols, st));
-  k_fub_count<<<egrid(nnz), kT, 0, st>>>(F->S.ci, nnz, cnt);
-  TOMO_CUDA(cudaGetLastError());
-  TOMO_TRY(exclusive_scan_i32(cnt, cols, F->ST.rp, st));
-  TOMO_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * cols, st));
-  k_fub_scatter<<<egrid(nnz), kT, 0, st>>>(F->S.ci, F->S.v, rows, kw * kw, F->ST.rp, cnt, F->ST.ci, F->ST.v);
-  TOMO_CUDA(cudaGetLastError());
-  k_fub_sort_rows<<<(unsigned)((cols + kT - 1) / kT), kT, 0, st>>>(F->ST.rp, cols, F->ST.ci, F->ST.v);
-  TOMO_CUDA(cudaGetLastError());
+    if (nl > 0) {
+      TOMO_TRY(exclusive_scan_i32(cnt_l, nl, F->STl.rp, st));
+      TOMO_CUDA(cudaMemcpyAsync(&F->STl.nnz, F->STl.rp + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      TOMO_CUDA(cudaStreamSynchronize(st));
+    } else {
+      TOMO_CUDA(cudaMemsetAsync(F->STl.rp, 0, sizeof(int64_t), st));
+      F->STl.nnz = 0;
+    }
+    TOMO_TRY(dalloc(&F->STl.ci, F->STl.nnz));
+    TOMO_TRY(dalloc(&F->STl.v, F->STl.nnz));
+    if (nl > 0) {
+      k_fub_copy_long<<<(unsigned)nl, kT, 0, st>>>(T.rp, T.ci, T.v, F->rows_l, F->STl.rp, F->STl.ci, F->STl.v);
+      TOMO_CUDA(cudaGetLastError());
+    }
+    TOMO_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed here
+  }
   // factors and buffers
   TOMO_TRY(dalloc(&F->deapod, F->n));
   k_fub_deapod<<<(F->n + kT - 1) / kT, kT, 0, st>>>(F->n, F->G, kw, F->beta, F->deapod);
@@ -496,7 +624,8 @@ tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_FORWARD), "1D forward"));
     k_fub_transpose<true, false, true><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad, G,
                                                               np, dens, scale);
-    TOMO_TRY(spmm_csr_store(F->ST, 2 * Bf, F->polI, F->gridI, st));
+    TOMO_TRY(spmm_csr_store(F->STs, 2 * Bf, F->polI, F->gridI, st));  // long rows come out 0 ...
+    TOMO_TRY(long_rows(F, F->polI, F->gridI, st));                    // ... and are written here
     k_fub_transpose<false, true, true><<<tgrid((int64_t)G * G), 256, 0, st>>>(F->grid, (float2 *)F->gridI, (int64_t)G * G,
                                                                           Bf, F->ph_grid, G, np, nullptr, 1.f);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_INVERSE), "2D inverse"));

@@ -26,7 +26,10 @@ struct tomo_fubini {
   int32_t n = 0, np = 0, nt = 0, kw = 0, G = 0, Bf = 0;
   double center = 0, beta = 0;
   int device = 0;
-  tomo::Csr S, ST;                // S: (nt*np) x (G*G); ST its transpose
+  tomo::Csr S;                    // (nt*np) x (G*G)
+  tomo::Csr STs;                  // S^T with its long rows emptied (rows of <= 64 entries)
+  tomo::Csr STl;                  // the long rows of S^T, compact; rows_l[i] is row i's index
+  int32_t *rows_l = nullptr;
   double *cs = nullptr;           // [nt] cos theta_m
   double *sn = nullptr;           // [nt] sin theta_m
   float *deapod = nullptr;        // [n] 1 / phi_hat(x / G)
