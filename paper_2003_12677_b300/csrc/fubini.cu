@@ -17,6 +17,7 @@
 #include <cstring>
 #include <vector>
 
+#include "bbstep.cuh"
 #include "fubini.cuh"
 
 
@@ -302,77 +303,6 @@ __global__ void k_fub_dens(int np, float *dens, float *dens_h) {
   dens_h[q] = (float)(r * (0.54 + 0.46 * cospi(2.0 * (double)d / (double)np)));
 }
 
-// The paper's SIRT on this operator: per slice (one block each), FP64 sums.
-//   resid:  y = b - y, hist[k] = ||y||
-//   step:   P = <gp, gp>, Q = <gp, g - gp>; alpha = 1 on a slice's first step,
-//           else alpha_prev P / (-Q) (BB1; frozen when P or -Q is not
-//           positive); x += alpha g.  scal[s]: [0] alpha [1] frozen [2] stepped
-__device__ double fsb_block_sum(double v) {
-  __shared__ double red[kT];
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int o = kT / 2; o; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(kT) k_fsb_resid(const float *b, float *y, int64_t rows, double *hist, int k,
-                                                  int nz) {
-  const int s = blockIdx.x;
-  double ss = 0.0;
-  for (int64_t i = threadIdx.x; i < rows; i += kT) {
-    const float r = b[(int64_t)s * rows + i] - y[(int64_t)s * rows + i];
-    y[(int64_t)s * rows + i] = r;
-    ss += (double)r * (double)r;
-  }
-  ss = fsb_block_sum(ss);
-  if (hist && threadIdx.x == 0) hist[(int64_t)k * nz + s] = sqrt(ss);
-}
-
-__global__ void __launch_bounds__(kT) k_fsb_step(float *x, const float *g, const float *gp, int64_t cols,
-                                                 double *scal) {
-  const int s = blockIdx.x;
-  const float *gs = g + (int64_t)s * cols, *gps = gp + (int64_t)s * cols;
-  double P = 0.0, Q = 0.0;
-  const bool stepped = scal[s * 4 + 2] != 0.0;
-  if (stepped) {
-    for (int64_t i = threadIdx.x; i < cols; i += kT) {
-      const double a = gps[i];
-      P += a * a;
-      Q += a * ((double)gs[i] - a);
-    }
-  }
-  P = fsb_block_sum(P);
-  Q = fsb_block_sum(Q);
-  __shared__ float alpha_s;
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    if (scal[s * 4 + 1] != 0.0) {
-      a = 0.0;
-    } else if (!stepped) {
-      a = 1.0;
-      scal[s * 4 + 2] = 1.0;
-    } else {
-      const double ap = scal[s * 4 + 0];
-      const double ss = ap * ap * P, sy = -ap * Q;
-      if (ss > 0.0 && sy > 0.0) {
-        a = ss / sy;
-      } else {
-        scal[s * 4 + 1] = 1.0;
-      }
-    }
-    scal[s * 4 + 0] = a;
-    alpha_s = (float)a;
-  }
-  __syncthreads();
-  const float a = alpha_s;
-  for (int64_t i = threadIdx.x; i < cols; i += kT) x[(int64_t)s * cols + i] = fmaf(a, gs[i], x[(int64_t)s * cols + i]);
-}
-
 int tgrid(int64_t points) {
   const int64_t b = (points + kTile - 1) / kTile;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 16));
@@ -637,9 +567,16 @@ tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t
 
 tomo_status fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t nz, int32_t iters, double *hist,
                            cudaStream_t st) {
+  // The paper's SIRT on this operator, per slice: r = b - R x (||r|| ->
+  // hist[k]), g = iRadon_Hamming(r), the BB step from <gp,gp> and
+  // <gp, g - gp> (alpha = 1 first), x += alpha g.  Sums over a fixed split of
+  // each slice into NB blocks (bbstep.cuh).
   const int64_t rows = (int64_t)F->nt * F->np, cols = (int64_t)F->n * F->n;
-  float *y = nullptr, *g0 = nullptr, *g1 = nullptr;
+  constexpr int NB = 32;
+  if (nz > 65535) return fail(TOMO_ERR_INVALID_ARG, "n_z must be <= 65535");
+  float *y = nullptr, *g0 = nullptr, *g1 = nullptr, *alpha = nullptr;
   double *scal = nullptr;
+  double3 *part = nullptr;
   auto alloc = [&](void **p, size_t b) -> tomo_status {
     if (cudaMallocAsync(p, b, st) != cudaSuccess) {
       cudaGetLastError();
@@ -648,28 +585,34 @@ tomo_status fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t 
     return TOMO_OK;
   };
   struct Free {
-    void **p[4];
+    void **p[6];
     cudaStream_t st;
     ~Free() {
       for (void **q : p)
         if (*q) cudaFreeAsync(*q, st);
     }
-  } fr{{(void **)&y, (void **)&g0, (void **)&g1, (void **)&scal}, st};
+  } fr{{(void **)&y, (void **)&g0, (void **)&g1, (void **)&scal, (void **)&part, (void **)&alpha}, st};
   TOMO_TRY(alloc((void **)&y, sizeof(float) * rows * nz));
   TOMO_TRY(alloc((void **)&g0, sizeof(float) * cols * nz));
   TOMO_TRY(alloc((void **)&g1, sizeof(float) * cols * nz));
-  TOMO_TRY(alloc((void **)&scal, sizeof(double) * 4 * nz));
+  TOMO_TRY(alloc((void **)&scal, sizeof(double) * 8 * nz));
+  TOMO_TRY(alloc((void **)&part, sizeof(double3) * NB * nz));
+  TOMO_TRY(alloc((void **)&alpha, sizeof(float) * nz));
   TOMO_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * cols * nz, st));
-  TOMO_CUDA(cudaMemsetAsync(g1, 0, sizeof(float) * cols * nz, st));
-  TOMO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 4 * nz, st));
-  float *g = g0, *gp = g1;
+  TOMO_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 8 * nz, st));
+  float *g = g0, *gp = nullptr;
+  const int per = (int)std::min<int64_t>(64, (cols + kT - 1) / kT);
   for (int32_t k = 0; k < iters; ++k) {
     TOMO_TRY(fubini_project(F, x, y, nz, st));
-    k_fsb_resid<<<nz, kT, 0, st>>>(sino, y, rows, hist, k, nz);
+    k_bb_resid<<<dim3(NB, nz), kT, 0, st>>>(sino, y, rows, NB, part);
     TOMO_TRY(fubini_backproject(F, y, g, nz, 2, st));
-    k_fsb_step<<<nz, kT, 0, st>>>(x, g, gp, cols, scal);
+    k_bb_dots<<<dim3(NB, nz), kT, 0, st>>>(g, gp, cols, NB, part);
+    k_bb_alpha<<<nz, 32, 0, st>>>(part, NB, scal + (k & 1) * 4 * nz, scal + ((k + 1) & 1) * 4 * nz, hist, k, nz,
+                                  alpha);
+    k_bb_axpy<<<dim3(per, nz), kT, 0, st>>>(x, g, alpha, cols);
     TOMO_CUDA(cudaGetLastError());
-    std::swap(g, gp);
+    gp = g;
+    g = g == g0 ? g1 : g0;
   }
   return TOMO_OK;
 }

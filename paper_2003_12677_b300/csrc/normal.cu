@@ -24,6 +24,7 @@
 #include <cmath>
 #include <vector>
 
+#include "bbstep.cuh"
 #include "fubini.cuh"
 
 namespace tomo {
@@ -166,19 +167,6 @@ __global__ void k_nrm_crop(const float *P, int n, int L, float *y) {
 // step of the gridded SIRT; per-slice sums in FP64 over a fixed split of each
 // slice into NB blocks, reduced in a fixed order (deterministic).
 
-// compensated FP32 sum of a thread's own terms (Kahan): its error stays
-// near one FP32 rounding of the sum of magnitudes whatever the term count;
-// the threads' sums are then combined in FP64
-struct KSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = v - c, t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
 __device__ double nrm_block_sum(double v) {
   __shared__ double red[kT];
   red[threadIdx.x] = v;
@@ -217,23 +205,6 @@ __global__ void __launch_bounds__(kT) k_nrm_grad(const float *P, const float *c,
   const double gg = nrm_block_sum(sg.value()), pp = nrm_block_sum(sp.value());
   const double pq = nrm_block_sum(sq.value()) - pp;
   if (threadIdx.x == 0) part[(int64_t)(s0 + s) * NB + b] = make_double3(gg, pp, pq);
-}
-
-// BB1 step of one slice from its sums (P = <gp,gp>, Q = <gp, g - gp>) and the
-// state (alpha, frozen, stepped): alpha = 1 on the first step, frozen slices 0
-__device__ __forceinline__ double bb_rule(double P, double Q, const double *in, double *frozen, double *stepped) {
-  const double ap = in[0];
-  *frozen = in[1];
-  *stepped = in[2];
-  if (*frozen != 0.0) return 0.0;
-  if (*stepped == 0.0) {
-    *stepped = 1.0;
-    return 1.0;
-  }
-  const double ss = ap * ap * P, sy = -ap * Q;
-  if (ss > 0.0 && sy > 0.0) return ss / sy;
-  *frozen = 1.0;
-  return 0.0;
 }
 
 // grid (NB, nz): alpha per slice from the partial sums (every block computes
@@ -605,34 +576,6 @@ __global__ void __launch_bounds__(kCvThreads, 3) k_cv_rows_inv(const float2 *H, 
   }
 }
 
-// one warp per slice: the NB partial sums in a fixed order, the BB step, the
-// state and ||g|| recorded, alpha[s] for the next pass
-__global__ void k_nrm_alpha(const double3 *part, int NB, const double *sc_in, double *sc_out, double *hist, int k,
-                            int nz, float *alpha) {
-  const int s = blockIdx.x, lane = threadIdx.x;
-  double gg = 0.0, P = 0.0, Q = 0.0;
-  for (int i = lane; i < NB; i += 32) {
-    const double3 v = part[(int64_t)s * NB + i];
-    gg += v.x;
-    P += v.y;
-    Q += v.z;
-  }
-  for (int o = 16; o; o >>= 1) {
-    gg += __shfl_xor_sync(0xffffffffu, gg, o);
-    P += __shfl_xor_sync(0xffffffffu, P, o);
-    Q += __shfl_xor_sync(0xffffffffu, Q, o);
-  }
-  if (lane == 0) {
-    double frozen, stepped;
-    const double a = bb_rule(P, Q, sc_in + s * 4, &frozen, &stepped);
-    sc_out[s * 4 + 0] = a;
-    sc_out[s * 4 + 1] = frozen;
-    sc_out[s * 4 + 2] = stepped;
-    if (hist) hist[(int64_t)k * nz + s] = sqrt(gg);
-    alpha[s] = (float)a;
-  }
-}
-
 // part[s (n/2) + p] = (<c,c>, 0, 0) over rows 2p, 2p + 1: the sums of the
 // first gradient g_0 = c (no previous one); one warp per row pair, grid
 // (ceil(n / 16), nz)
@@ -645,14 +588,6 @@ __global__ void k_nrm_sumsq(const float *c, int n, double3 *part) {
   double gg = sg.value();
   for (int o = 16; o; o >>= 1) gg += __shfl_xor_sync(0xffffffffu, gg, o);
   if (lane == 0) part[(int64_t)s * (n / 2) + p] = make_double3(gg, 0.0, 0.0);
-}
-
-// x += alpha[s] g; grid (blocks over a slice, nz)
-__global__ void k_nrm_axpy(float *x, const float *g, const float *alpha, int64_t cols) {
-  const float a = alpha[blockIdx.y];
-  const int64_t off = (int64_t)blockIdx.y * cols;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cols; i += (int64_t)gridDim.x * blockDim.x)
-    x[off + i] = fmaf(a, g[off + i], x[off + i]);
 }
 
 // [L][W] -> [W][L] for the column pass
@@ -971,12 +906,12 @@ tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, i
     float *next = g0;
     for (int32_t k = 1; k <= iters; ++k) {
       const int m = k - 1;  // the step taken now: from g_{k-1}
-      k_nrm_alpha<<<nz, 32, 0, st>>>(part, NB, scal + (m & 1) * 4 * nz, scal + ((m + 1) & 1) * 4 * nz, hist, m, nz,
+      k_bb_alpha<<<nz, 32, 0, st>>>(part, NB, scal + (m & 1) * 4 * nz, scal + ((m + 1) & 1) * 4 * nz, hist, m, nz,
                                      alpha);
       TOMO_CUDA(cudaGetLastError());
       if (k == iters) {
         const int per = (int)std::min<int64_t>(64, (cols + kT - 1) / kT);
-        k_nrm_axpy<<<dim3(per, nz), kT, 0, st>>>(x, g, alpha, cols);
+        k_bb_axpy<<<dim3(per, nz), kT, 0, st>>>(x, g, alpha, cols);
         TOMO_CUDA(cudaGetLastError());
         break;
       }
