@@ -102,7 +102,7 @@ __global__ void k_fub_long_list(const int64_t *rp, const int64_t *lpos, int64_t 
   cnt_l[lpos[r]] = (int32_t)(rp[r + 1] - rp[r]);
 }
 
-// short rows: copy, then insertion sort by polar index (keys unique)
+// short rows: copy, then a stable insertion sort by polar index
 __global__ void k_fub_copy_short(const int64_t *rp, const int32_t *ci, const float *v, int64_t rows,
                                  const int64_t *rps, int32_t *cis, float *vs) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,7 +122,9 @@ __global__ void k_fub_copy_short(const int64_t *rp, const int32_t *ci, const flo
   }
 }
 
-// long rows, one block each: every entry goes to its rank among the row's keys
+// long rows, one block each: every entry goes to its stable rank among the
+// row's keys (a key repeats when the window is wider than the grid and wraps
+// onto the same point more than once)
 __global__ void k_fub_copy_long(const int64_t *rp, const int32_t *ci, const float *v, const int32_t *rows_l,
                                 const int64_t *rpl, int32_t *cil, float *vl) {
   const int64_t src = rp[rows_l[blockIdx.x]], dst = rpl[blockIdx.x];
@@ -130,7 +132,10 @@ __global__ void k_fub_copy_long(const int64_t *rp, const int32_t *ci, const floa
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
     const int32_t key = ci[src + i];
     int rank = 0;
-    for (int j = 0; j < len; ++j) rank += ci[src + j] < key;
+    for (int j = 0; j < len; ++j) {
+      const int32_t kj = ci[src + j];
+      rank += kj < key || (kj == key && j < i);
+    }
     cil[dst + rank] = key;
     vl[dst + rank] = v[src + i];
   }

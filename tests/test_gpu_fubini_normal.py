@@ -179,3 +179,19 @@ def test_normal_rejects_bad_arguments():
         _lib.call("tomo_fubini_normal", F._h, x.data_ptr(), y.data_ptr(), 1, 3, None)
     with pytest.raises(_lib.TomoError):
         _lib.call("tomo_fubini_normal", F._h, x.data_ptr(), y.data_ptr(), 0, 1, None)
+
+
+@pytest.mark.parametrize("n,n_p,nt", [(1, 1, 1), (2, 3, 2), (3, 2, 5), (1, 4, 3)])
+def test_degenerate_geometries(n, n_p, nt):
+    """One-pixel images, one bin, one angle: the transform, its adjoint and the
+    normal operator (cuFFT path, L = 2n < 32) against the oracle."""
+    fg, F = pair(n=n, nt=nt, n_p=n_p)
+    x = inputs.random_slices((2, n, n), 160 + n)
+    y = inputs.random_slices((2, nt, n_p), 161 + n)
+    gy = F.project(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert per_slice_rel(gy, fb.fubini_project(fg, x.reshape(2, -1))).max() < 1e-5
+    gb = F.backproject(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert per_slice_rel(gb, fb.fubini_backproject(fg, y.reshape(2, -1))).max() < 1e-5
+    for filt in (0, 1, 2):
+        got = F.normal(torch.from_numpy(x).cuda(), [False, True, "hamming"][filt]).cpu().numpy()
+        assert per_slice_rel(got, fb.fubini_normal(fg, x.reshape(2, -1), filt)).max() < 1e-5, filt
