@@ -162,6 +162,82 @@ def oracle_sample(w, slices=1, iters=1, steps=1, warmup=0, model="line"):
             "seconds": dt}
 
 
+def oracle_sample_bb(w, slices, iters):
+    """The oracle's BB-SIRT (Sec. 3.1) timed on a bounded sample of the workload."""
+    import oracle
+    from paper_2003_12677_b300 import inputs
+    g = oracle.Geometry(w.n, w.n, w.n, w.n_theta)
+    t0 = time.perf_counter()
+    A = oracle.build_matrix(g)
+    AT = A.transpose()
+    build_s = time.perf_counter() - t0
+    b = inputs.workload_case(w.name, slices=list(range(slices))).sino.reshape(slices, -1)
+    t0 = time.perf_counter()
+    oracle.sirt_bb(A, AT, w.n, b, iters)
+    dt = time.perf_counter() - t0
+    return {"value": slices * iters / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d slice(s) x %d BB-SIRT iteration(s) of the %s workload, FP64, matrix stored (oracle "
+                      "build %.1f s untimed)" % (slices, iters, w.name, build_s), "seconds": dt}
+
+
+def oracle_sample_fubini(w, slices, iters, solver):
+    """The Fubini-Radon oracle timed on a bounded sample: a forward + adjoint
+    pair per slice-iteration ("pair"), or its gridded BB-SIRT ("sirt")."""
+    import oracle
+    from oracle import fubini as fb
+    from paper_2003_12677_b300 import inputs
+    fg = fb.FGeometry(w.n, w.n, w.n_theta)
+    t0 = time.perf_counter()
+    S = fb.gridding_matrix(fg)
+    build_s = time.perf_counter() - t0
+    case = inputs.workload_case(w.name, slices=list(range(slices)))
+    t0 = time.perf_counter()
+    if solver == "pair":
+        x = case.phantom.reshape(slices, -1)
+        for _ in range(iters):
+            fb.fubini_backproject(fg, fb.fubini_project(fg, x, S), S)
+    else:
+        fb.fubini_sirt_bb(fg, case.sino.reshape(slices, -1), iters, S)
+    dt = time.perf_counter() - t0
+    what = ("forward + adjoint pair(s)" if solver == "pair" else
+            "iteration(s) of the oracle's gridded BB-SIRT (its SIRT with the exact normal operator sums the "
+            "exact transform: minutes per slice-iteration at this size, so the gridded one, equal up to the "
+            "gridding error, stands in)")
+    return {"value": slices * iters / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d slice(s) x %d %s of the %s workload, FP64 with numpy's FFT (gridding matrix %.1f s "
+                      "untimed)" % (slices, iters, what, w.name, build_s), "seconds": dt}
+
+
+def spmm_roofline(M, B, fmt, tm, kinds, torch, local, clk):
+    """Roofline of the dominant SpMM pass from the per-kernel CUDA-event
+    timing tm: algorithmic bytes (matrix once, gathered vector once, the
+    epilogue's own reads and writes, kinds[k] = (name, extra vector bytes per
+    row-or-column of the output, per slice)) over its average launch time."""
+    kind = 0 if tm.ms[0] >= tm.ms[1] else 1
+    avg_ms = tm.ms[kind] / max(tm.launches[kind], 1)
+    rows, cols, nnz = M.rows, M.cols, M.nnz
+    bnnz = 4.25 if fmt == "sell16" else 8
+    mat_bytes = (rows + 1 if kind == 0 else cols + 1) * 8 + nnz * bnnz
+    gathered_len, out_len = (cols, rows) if kind == 0 else (rows, cols)
+    name, out_vecs = kinds[kind]
+    alg = mat_bytes + gathered_len * B * 4 + out_vecs * out_len * B * 4
+    peak, src = measured_peaks()
+    achieved = alg / (avg_ms / 1000.0) / 1e9
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or 2032.0
+    gathered = nnz * B * 4
+    roof = {"bound": "hbm", "kernel": name % (KERNEL[fmt], B), "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": src + " (burst copy)",
+            "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
+            "kernel_share": tm.ms[kind] / max(sum(tm.ms[k] for k in range(3)), 1e-12)}
+    ceil = {"operand_delivery": {"achieved": gathered / (avg_ms / 1000.0) / 1e9, "unit": "GB/s",
+                                 "peak": sms * 128 * mhz * 1e6 / 1e9, "bytes_per_launch": gathered,
+                                 "peak_source": "128 B/clk/SM x %d SMs x median SM clock" % sms}}
+    for c in ceil.values():
+        c["frac"] = c["achieved"] / c["peak"]
+    return roof, ceil
+
+
 KERNEL = {"sell": "sell", "sell16": "sell16", "csr": "f32"}
 
 
@@ -317,6 +393,24 @@ def run_alternate(args, w):
                      "clocks": clk, "build_s": build_s, "fbp": {"ms_per_64_slices": fbp_ms,
                                                                "slices_per_s": w.n_z / (fbp_ms / 1000.0)},
                      "gpu_launches": args.steps * iters * 2 * 7 * math.ceil(w.n_z / 16)})
+        # whole-pair roofline over modelled bytes: every kernel's compulsory reads
+        # and writes per slice, each cuFFT 2D transform as two passes over the
+        # complex G x G grid, 1D transforms as one pass, S / S^T read once per
+        # 16-slice group
+        G, rows_p = 2 * w.n, w.n_theta * w.n
+        grid_c, pol_c = G * G * 8, rows_p * 8
+        per_slice_dir = (w.n * w.n * 4 + grid_c) + 4 * grid_c + 2 * grid_c + grid_c + pol_c \
+            + 2 * pol_c + 2 * pol_c + (pol_c + rows_p * 4)
+        mat = 2 * (rows_p * 36 * 8) / 16
+        bytes_step = iters * w.n_z * (2 * per_slice_dir + mat)
+        peak, src = measured_peaks()
+        ach = bytes_step / (ms / 1000.0) / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": "forward + adjoint, all kernels (modelled bytes)",
+                            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                            "peak_source": src + " (burst copy)", "alg_bytes_per_slice_iter": bytes_step / (
+                                iters * w.n_z)}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample_fubini(w, slices=16, iters=6, solver="pair")
         print(json.dumps(line))
         return 0
     if w.solver == "fubini_normal":
@@ -362,6 +456,29 @@ def run_alternate(args, w):
                      # kernel per pass of 32 slices (none at x = 0) and one step kernel
                      "gpu_launches": args.steps * (5 * math.ceil(w.n_z / 16) + 2
                                                    + (iters - 1) * (3 * math.ceil(w.n_z / 32) + 1))})
+        # roofline of one application of N (the three fused passes) over the
+        # compulsory bytes: rows (image read, half spectrum H written), columns
+        # (H read and written), inverse rows (H read, result written); and the
+        # FFT arithmetic, 5 L log2 L flops per length-L complex transform
+        n = w.n
+        L = 2 * n
+        H = (n + 1) * n * 8
+        nbytes = w.n_z * (n * n * 4 + H + 2 * H + H + n * n * 4)
+        nflops = w.n_z * (n // 2 + 2 * (n + 1) + n // 2) * 5 * L * math.log2(L)
+        peak, src = measured_peaks()
+        ach = nbytes / (n_ms / 1000.0) / 1e9
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2032.0
+        fpeak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        line["roofline"] = {"bound": "hbm", "kernel": "normal operator: k_cv_rows + k_cv_cols + k_cv_rows_inv",
+                            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                            "peak_source": src + " (burst copy)", "alg_bytes_per_launch": nbytes,
+                            "avg_launch_ms": n_ms}
+        line["ceilings"] = {"fp32": {"achieved": nflops / (n_ms / 1000.0) / 1e12, "unit": "TFLOP/s",
+                                     "peak": fpeak, "peak_source": "128 FP32 FMA/clk/SM",
+                                     "frac": nflops / (n_ms / 1000.0) / 1e12 / fpeak}}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample_fubini(w, slices=8, iters=12, solver="sirt")
         print(json.dumps(line))
         return 0
     if w.solver == "sirt_bb":
@@ -397,11 +514,18 @@ def run_alternate(args, w):
                      "clocks": clk, "build_s": build_s, "nnz": M.nnz, "gpu_launches": args.steps * int(
                          sum(tm.launches[k] for k in range(3))),
                      "time_split": {"A": tm.ms[0] / tot, "A^T": tm.ms[1] / tot, "filter+vector+scalar": tm.ms[2] / tot},
+                     # A pass: r = b - A x (b read, r written); A^T pass: g = A^T P^T P r (g written)
+                     **dict(zip(("roofline", "ceilings"), spmm_roofline(
+                         M, B, fmt, tm, [("k_spmm_%s<%d, EpiResidual> (A pass)", 2),
+                                         ("k_spmm_%s<%d, EpiStore> (A^T pass)", 1)], torch,
+                         torch.cuda.current_device(), clk))),
                      "convergence": {"classical_sirt_100_resid_median": float(r100.median()),
                                      "bb_iters_to_reach_it": {"median": sorted(reached)[len(reached) // 2]
                                                               if reached else None,
                                                               "max": max(reached) if reached else None,
                                                               "slices_reached": len(reached)}}})
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample_bb(w, slices=8, iters=20)
         print(json.dumps(line))
         return 0
     if w.solver == "cgls":
