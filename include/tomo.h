@@ -415,6 +415,16 @@ TOMO_API tomo_status tomo_fubini_backproject(tomo_fubini *F, const float *y, flo
 TOMO_API tomo_status tomo_fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t n_z, int32_t iters,
                                          double *resnorm_hist, void *stream);
 
+/* The TV prior of the model-based objective (Sec. 2.1), value and gradient in
+ * one pass: per slice s of x (n_z, n_y, n_x), DEVICE, slice-major,
+ *   loss[s] = sum_{iy,ix} sqrt(Dx^2 + Dy^2 + eps^2)   (FP64, DEVICE, n_z values)
+ * with forward differences Dx = x[iy][ix+1] - x[iy][ix], Dy = x[iy+1][ix] -
+ * x[iy][ix] (0 on the last column / row), and grad (same shape as x, DEVICE)
+ * = d loss[s] / d x_s.  The value is summed in FP64 in a fixed order
+ * (deterministic).  eps > 0; n_z <= 65535. */
+TOMO_API tomo_status tomo_tv(const float *x, int32_t n_z, int32_t n_y, int32_t n_x, float eps, double *loss,
+                             float *grad, void *stream);
+
 /* The normal operator in one step (the Toeplitz route of the outlook, Sec. 5):
  * y = N x, N = R^T W R for the EXACT transform R above and the sinogram weight
  * W of the exact adjoint (filter 0), of iRadon with the ramp density (1) or

@@ -20,7 +20,7 @@ EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo
            "tomo_sirt", "tomo_cgls", "tomo_cgls_resume", "tomo_cgls_batched", "tomo_cgls_batched_workspace",
            "tomo_sirt_noalloc", "tomo_autotune", "tomo_stream_status", "tomo_sirt_bb",
            "tomo_fubini_create", "tomo_fubini_destroy", "tomo_fubini_project", "tomo_fubini_backproject",
-           "tomo_fubini_sirt_bb", "tomo_fubini_normal", "tomo_fubini_sirt_bb_normal",
+           "tomo_fubini_sirt_bb", "tomo_fubini_normal", "tomo_fubini_sirt_bb_normal", "tomo_tv",
            "tomo_status_string", "tomo_last_error"]
 
 
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "tomo_fubini_backproject": [P, P, P, I32, I32, P],
         "tomo_fubini_sirt_bb": [P, P, P, I32, I32, P, P],
         "tomo_fubini_normal": [P, P, P, I32, I32, P],
+        "tomo_tv": [P, I32, I32, I32, ctypes.c_float, P, P, P],
         "tomo_fubini_sirt_bb_normal": [P, P, P, I32, I32, P, P],
         "tomo_sirt_bb": [P, P, P, I32, I32, ctypes.c_double, P, ctypes.POINTER(BbState), ctypes.POINTER(BbState),
                          ctypes.POINTER(ExecOpts), P, SZ, P],

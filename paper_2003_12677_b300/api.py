@@ -548,10 +548,31 @@ def radon(x: torch.Tensor, M: Matrix, batch_width: int = 0, fmt="sell") -> torch
     return TomoProject.apply(x, M, batch_width, fmt)
 
 
+class TomoTV(torch.autograd.Function):
+    """TV_eps(x) summed over slices (tomo_tv); the gradient comes out of the
+    same pass and is kept for the backward."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, eps: float):
+        x = x.contiguous()
+        _check_tensor(x, "x")
+        if x.dim() < 2:
+            raise ValueError("x must be (..., n_y, n_x)")
+        ny, nx = x.shape[-2], x.shape[-1]
+        nz = x.numel() // (ny * nx)
+        loss = torch.empty(nz, dtype=torch.float64, device=x.device)
+        grad = torch.empty_like(x)
+        _lib.call("tomo_tv", _ptr(x), nz, ny, nx, float(eps), _ptr(loss), _ptr(grad), _stream())
+        ctx.save_for_backward(grad)
+        return loss.sum().to(x.dtype)
+
+    @staticmethod
+    def backward(ctx, go: torch.Tensor):
+        grad, = ctx.saved_tensors
+        return go * grad, None
+
+
 def tv_loss(x: torch.Tensor, eps: float = 1e-3) -> torch.Tensor:
-    """Isotropic TV with forward differences (0 on the last row / column), per slice."""
-    dx = torch.zeros_like(x)
-    dy = torch.zeros_like(x)
-    dx[..., :, :-1] = x[..., :, 1:] - x[..., :, :-1]
-    dy[..., :-1, :] = x[..., 1:, :] - x[..., :-1, :]
-    return torch.sqrt(dx * dx + dy * dy + eps * eps).sum()
+    """Isotropic TV with forward differences (0 on the last row / column),
+    summed over the slices of x (..., n_y, n_x); differentiable."""
+    return TomoTV.apply(x, eps)

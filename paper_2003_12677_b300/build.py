@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtomo.so")
-SOURCES = ["build.cu", "ops.cu", "api.cu", "noalloc.cu", "persistent.cu", "status.cu", "fubini.cu", "normal.cu"]
+SOURCES = ["build.cu", "ops.cu", "api.cu", "noalloc.cu", "persistent.cu", "status.cu", "fubini.cu", "normal.cu", "tv.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr", "-I", INCLUDE]

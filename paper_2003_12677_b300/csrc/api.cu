@@ -297,6 +297,17 @@ tomo_status tomo_fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int
   return fubini_sirt_bb(F, sino, x, n_z, iters, resnorm_hist, (cudaStream_t)stream);
 }
 
+tomo_status tomo_tv(const float *x, int32_t n_z, int32_t n_y, int32_t n_x, float eps, double *loss, float *grad,
+                    void *stream) {
+  TOMO_TRY(check_vec(x, "x"));
+  TOMO_TRY(check_vec(grad, "grad"));
+  if (!loss || ((uintptr_t)loss & 7u)) return fail(TOMO_ERR_INVALID_ARG, "loss must be non-NULL and 8-byte aligned");
+  if (n_z < 1 || n_z > 65535 || n_y < 1 || n_x < 1)
+    return fail(TOMO_ERR_INVALID_ARG, "need 1 <= n_z <= 65535, n_y >= 1, n_x >= 1");
+  if (!(eps > 0.f) || !std::isfinite(eps)) return fail(TOMO_ERR_INVALID_ARG, "eps must be positive and finite");
+  return tv_loss_grad(x, n_z, n_y, n_x, eps, loss, grad, (cudaStream_t)stream);
+}
+
 tomo_status tomo_fubini_normal(tomo_fubini *F, const float *x, float *y, int32_t n_z, int32_t filter, void *stream) {
   if (!F) return fail(TOMO_ERR_INVALID_ARG, "handle must be non-NULL");
   TOMO_TRY(check_vec(x, "x"));

@@ -149,6 +149,9 @@ tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz,
 tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t nz, int filter, cudaStream_t st);
 tomo_status fubini_sirt_bb(tomo_fubini *F, const float *sino, float *x, int32_t nz, int32_t iters, double *hist,
                            cudaStream_t st);
+// TV prior value and gradient (tv.cu)
+tomo_status tv_loss_grad(const float *x, int32_t nz, int32_t ny, int32_t nx, float eps, double *loss, float *grad,
+                         cudaStream_t st);
 // its normal operator in one step (normal.cu)
 tomo_status fubini_normal(tomo_fubini *F, const float *x, float *y, int32_t nz, int filter, cudaStream_t st);
 tomo_status fubini_sirt_bb_normal(tomo_fubini *F, const float *sino, float *x, int32_t nz, int32_t iters,
