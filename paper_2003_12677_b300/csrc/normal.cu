@@ -35,8 +35,8 @@ namespace {
 
 constexpr int kT = 256;
 
-// sizes with the fused convolution (the 2n x 2n grid a power of two, 32..1024)
-bool fused_ok(int L) { return L >= 32 && L <= 1024 && (L & (L - 1)) == 0; }
+// sizes with the fused convolution (the 2n x 2n grid a power of two, 32..2048)
+bool fused_ok(int L) { return L >= 32 && L <= 2048 && (L & (L - 1)) == 0; }
 
 tomo_status cufft_ok(cufftResult r, const char *what) {
   if (r != CUFFT_SUCCESS) return fail(TOMO_ERR_CUDA, std::string("cuFFT ") + what + " failed: " + std::to_string((int)r));
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kT) k_nrm_step(float *x, const float *g, int64
 // inverse runs the same steps backwards with conjugate twiddles.
 
 struct Tw32 {
-  float2 w[32];  // e^{-2 pi i k / 32}
+  float2 w[64];  // e^{-2 pi i k / 64}
 };
 
 __host__ __device__ constexpr int rev8(int i) {
@@ -279,7 +279,7 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// in-register DFT of R <= 32 points, natural order in and out: radix-2
+// in-register DFT of R <= 64 points, natural order in and out: radix-2
 // decimation in time on the bit-reversed sequence, one template level per
 // stage so that every loop unrolls; kInv: conjugate twiddles
 template <int R, int LEN, bool kInv>
@@ -291,7 +291,7 @@ __device__ __forceinline__ void dft_stage(float2 *a, const Tw32 &tw) {
       const float2 u = a[i + j];
       float2 t = a[i + j + LEN / 2];
       if (j != 0) {
-        float2 w = tw.w[j * (32 / LEN)];
+        float2 w = tw.w[j * (64 / LEN)];
         if (kInv) w.y = -w.y;
         t = cmulf(w, t);
       }
@@ -381,7 +381,7 @@ constexpr bool cv_stage() {
 // rows: FFT id f = s (n/2) + p over rows 2p, 2p + 1 of slice s; kStep: the
 // rows are x + alpha[s] g, written back to x first (the previous BB step)
 template <int R1, int R2, bool kStep>
-__global__ void __launch_bounds__(kCvThreads, 3) k_cv_rows(const float *u, float *x, const float *g,
+__global__ void __launch_bounds__(kCvThreads, (R1 <= 32 ? 3 : 1)) k_cv_rows(const float *u, float *x, const float *g,
                                                          const float *alpha, float2 *H, int nz, const float2 *twL,
                                                          const __grid_constant__ Tw32 tw) {
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_cols(float2 *H, int nz, const
 // part[f] = (<g,g>, <gp,gp>, <gp, g - gp>) over them (the row-pair split of
 // k_nrm_grad with NB = n/2); else y = N u
 template <int R1, int R2, bool kGrad>
-__global__ void __launch_bounds__(kCvThreads, 3) k_cv_rows_inv(const float2 *H, float *y, const float *c, const float *gp,
+__global__ void __launch_bounds__(kCvThreads, (R1 <= 32 ? 3 : 1)) k_cv_rows_inv(const float2 *H, float *y, const float *c, const float *gp,
                                                              double3 *part, int nz, const float2 *twL,
                                                              const __grid_constant__ Tw32 tw) {
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
@@ -724,8 +724,8 @@ tomo_status apply_pass(tomo_fubini *F, const NormalKernel &K, const float *u, in
 
 Tw32 tw32() {
   Tw32 t;
-  for (int k = 0; k < 32; ++k)
-    t.w[k] = make_float2((float)std::cos(2.0 * M_PI * k / 32.0), (float)-std::sin(2.0 * M_PI * k / 32.0));
+  for (int k = 0; k < 64; ++k)
+    t.w[k] = make_float2((float)std::cos(2.0 * M_PI * k / 64.0), (float)-std::sin(2.0 * M_PI * k / 64.0));
   return t;
 }
 
@@ -799,6 +799,7 @@ tomo_status cv_dispatch(tomo_fubini *F, const NormalKernel &K, const CvArgs &a, 
     case 256: return cv_run<16, 16>(F, K, a, cnt, st);
     case 512: return cv_run<32, 16>(F, K, a, cnt, st);
     case 1024: return cv_run<32, 32>(F, K, a, cnt, st);
+    case 2048: return cv_run<64, 32>(F, K, a, cnt, st);
   }
   return fail(TOMO_ERR_INVALID_ARG, "no fused convolution for this size");
 }

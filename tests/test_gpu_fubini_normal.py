@@ -195,3 +195,29 @@ def test_degenerate_geometries(n, n_p, nt):
     for filt in (0, 1, 2):
         got = F.normal(torch.from_numpy(x).cuda(), [False, True, "hamming"][filt]).cpu().numpy()
         assert per_slice_rel(got, fb.fubini_normal(fg, x.reshape(2, -1), filt)).max() < 1e-5, filt
+
+
+def test_normal_fused_2048_columns():
+    """1024 x 1024 (2n = 2048: 64-point register DFTs, one block per SM):
+    columns N e_l at three impulses against the oracle's entry formula (48
+    sampled entries each, 1e-5 of the peak), and N against the gridded
+    composition."""
+    n, nt = 1024, 60
+    fg, F = pair(n=n, nt=nt)
+    ls = [n * (n // 2) + n // 2, 5, n * 900 + 1000]
+    e = np.zeros((3, n * n), np.float32)
+    for i, l in enumerate(ls):
+        e[i, l] = 1.0
+    rng = np.random.default_rng(171)
+    for filt in (0, 2):
+        col = F.normal(torch.from_numpy(e.reshape(3, n, n)).cuda(), [False, True, "hamming"][filt])
+        col = col.reshape(3, -1).cpu().numpy().astype(np.float64)
+        for i, l in enumerate(ls):
+            j = np.concatenate([[l], rng.integers(0, n * n, 47)])
+            d, s = fb.normal_entry_vectors(fg, j, np.full(j.shape, l))
+            t, h = fb.normal_taps(fg, d, s, filt)
+            assert np.abs(col[i, j] - (t + h)).max() <= 1e-5 * np.abs(col[i]).max(), (filt, l)
+    x = torch.from_numpy(inputs.random_slices((2, n, n), 172)).cuda()
+    got = F.normal(x, "hamming").cpu().numpy()
+    ref = F.backproject(F.project(x), "hamming").cpu().numpy()
+    assert per_slice_rel(got, ref).max() < 1e-4
