@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "bbstep.cuh"
+#include "regfft.cuh"
 #include "fubini.cuh"
 
 
@@ -308,6 +309,88 @@ __global__ void k_fub_dens(int np, float *dens, float *dens_h) {
   dens_h[q] = (float)(r * (0.54 + 0.46 * cospi(2.0 * (double)d / (double)np)));
 }
 
+// ---- the adjoint's last steps on power-of-two grids: the inverse 2D transform
+// of the gridded spectrum, cropped to the image, in two register-FFT passes
+// (regfft.cuh) that read and write only what the crop keeps:
+//   columns  per (kx, 8 slices): c[ky] = gridI[ky G + kx][s] conj(ph[ky] ph[kx]),
+//            inverse FFT over ky, rows gy in [o, o + n) -> T[s][kx][gy - o]
+//   rows     per (slice, 8 image rows r): T[s][kx][r] over kx, inverse FFT,
+//            columns gx in [o, o + n): x[s][r][gx - o] = Re(.) d[r] d[gx - o]
+// Inputs are staged through shared memory so that global reads are whole rows.
+constexpr int kFaSlices = 8;
+
+template <int R1, int R2>
+constexpr int fa_smem() {
+  constexpr int stage = R1 * R2 * (kFaSlices + 1);
+  constexpr int tiles = kFaSlices * (R1 * (R2 + 1) + 1);
+  return (stage > tiles ? stage : tiles) * (int)sizeof(float2);
+}
+
+template <int R1, int R2>
+__global__ void __launch_bounds__(kFaSlices *R2) k_fa_cols(const float2 *gridI, int Bf, int cnt, int n,
+                                                           const float2 *ph, float2 *T, const float2 *twL,
+                                                           const __grid_constant__ Tw64 tw) {
+  constexpr int G = R1 * R2;
+  extern __shared__ float2 fa_sm[];
+  const int kx = blockIdx.x, q = threadIdx.x / R2, l = threadIdx.x % R2;
+  const int s0 = blockIdx.y * kFaSlices, o = (G - n) / 2;
+  for (int e = threadIdx.x; e < G * kFaSlices; e += blockDim.x) {
+    const int ky = e / kFaSlices, qq = e % kFaSlices;
+    fa_sm[ky * (kFaSlices + 1) + qq] =
+        s0 + qq < cnt ? gridI[((int64_t)ky * G + kx) * Bf + s0 + qq] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const float2 pkx = conjf2(ph[kx]);
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) {
+    const int ky = j1 * R2 + l;
+    v[j1] = cmul(fa_sm[ky * (kFaSlices + 1) + q], cmul(conjf2(ph[ky]), pkx));
+  }
+  __syncthreads();
+  fft_fwd<R1, R2, true>(v, w, fa_sm + q * (R1 * (R2 + 1) + 1), l, twL, tw);
+  const int s = s0 + q;
+  if (s >= cnt) return;
+#pragma unroll
+  for (int t = 0; t < R1 / R2; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int gy = (l + R2 * t) + R1 * k2;
+      if (gy >= o && gy < o + n) T[((int64_t)s * G + kx) * n + gy - o] = w[t * R2 + k2];
+    }
+}
+
+template <int R1, int R2>
+__global__ void __launch_bounds__(kFaSlices *R2) k_fa_rows(const float2 *T, int n, const float *d, float *x,
+                                                           const float2 *twL, const __grid_constant__ Tw64 tw) {
+  constexpr int G = R1 * R2;
+  extern __shared__ float2 fa_sm[];
+  const int s = blockIdx.y, r0 = blockIdx.x * kFaSlices, q = threadIdx.x / R2, l = threadIdx.x % R2;
+  const int o = (G - n) / 2;
+  for (int e = threadIdx.x; e < G * kFaSlices; e += blockDim.x) {
+    const int kx = e / kFaSlices, qq = e % kFaSlices;
+    fa_sm[kx * (kFaSlices + 1) + qq] =
+        r0 + qq < n ? T[((int64_t)s * G + kx) * n + r0 + qq] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) v[j1] = fa_sm[(j1 * R2 + l) * (kFaSlices + 1) + q];
+  __syncthreads();
+  fft_fwd<R1, R2, true>(v, w, fa_sm + q * (R1 * (R2 + 1) + 1), l, twL, tw);
+  const int r = r0 + q;
+  if (r >= n) return;
+  const float dr = d[r];
+  float *xr = x + ((int64_t)s * n + r) * n;
+#pragma unroll
+  for (int t = 0; t < R1 / R2; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int gx = (l + R2 * t) + R1 * k2;
+      if (gx >= o && gx < o + n) xr[gx - o] = w[t * R2 + k2].x * dr * d[gx - o];
+    }
+}
+
 int tgrid(int64_t points) {
   const int64_t b = (points + kTile - 1) / kTile;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 16));
@@ -341,7 +424,7 @@ void free_fubini(tomo_fubini *F) {
   }
   free_normal(F);
   void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->STs.rp, F->STs.ci, F->STs.v, F->STl.rp, F->STl.ci, F->STl.v,
-                  F->rows_l, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
+                  F->rows_l, F->faT, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
                   F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin, F->cs, F->sn};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -362,6 +445,34 @@ tomo_status long_rows(tomo_fubini *F, const float *X, float *Y, cudaStream_t st)
   }
   TOMO_CUDA(cudaGetLastError());
   return TOMO_OK;
+}
+
+template <int R1, int R2>
+tomo_status fa_run(tomo_fubini *F, int cnt, float *x, cudaStream_t st) {
+  constexpr int G = R1 * R2, sm = fa_smem<R1, R2>();
+  TOMO_CUDA(cudaFuncSetAttribute(k_fa_cols<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  TOMO_CUDA(cudaFuncSetAttribute(k_fa_rows<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  const Tw64 tw = tw64();
+  k_fa_cols<R1, R2><<<dim3(G, (cnt + kFaSlices - 1) / kFaSlices), kFaSlices * R2, sm, st>>>(
+      (const float2 *)F->gridI, F->Bf, cnt, F->n, F->ph_grid, F->faT, F->twL, tw);
+  k_fa_rows<R1, R2><<<dim3((F->n + kFaSlices - 1) / kFaSlices, cnt), kFaSlices * R2, sm, st>>>(
+      F->faT, F->n, F->deapod, x, F->twL, tw);
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
+}
+
+// the adjoint's inverse 2D transform and crop by register FFTs (G a power of two, 32..2048)
+tomo_status fa_dispatch(tomo_fubini *F, int cnt, float *x, cudaStream_t st) {
+  switch (F->G) {
+    case 32: return fa_run<8, 4>(F, cnt, x, st);
+    case 64: return fa_run<8, 8>(F, cnt, x, st);
+    case 128: return fa_run<16, 8>(F, cnt, x, st);
+    case 256: return fa_run<16, 16>(F, cnt, x, st);
+    case 512: return fa_run<32, 16>(F, cnt, x, st);
+    case 1024: return fa_run<32, 32>(F, cnt, x, st);
+    case 2048: return fa_run<64, 32>(F, cnt, x, st);
+  }
+  return fail(TOMO_ERR_INVALID_ARG, "no register-FFT adjoint for this grid");
 }
 
 }  // namespace
@@ -506,6 +617,10 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
   TOMO_TRY(dalloc(&F->gridI, (size_t)G * G * F->Bf * 2));
   TOMO_TRY(dalloc(&F->polI, (size_t)rows * F->Bf * 2));
   TOMO_TRY(dalloc(&F->pol, (size_t)rows * F->Bf));
+  if (fused_ok(F->G)) {  // the adjoint's inverse 2D transform by register FFTs
+    TOMO_TRY(ensure_twiddles(F, st));
+    TOMO_TRY(dalloc(&F->faT, (size_t)F->Bf * F->G * F->n));
+  }
   // cuFFT plans: G x G 2D transforms and length-np 1D transforms, contiguous batches
   int dims2[2] = {F->G, F->G};
   TOMO_TRY(cufft_check(cufftPlanMany(&F->plan2, 2, dims2, nullptr, 1, F->G * F->G, nullptr, 1, F->G * F->G,
@@ -561,6 +676,10 @@ tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t
                                                               np, dens, scale);
     TOMO_TRY(spmm_csr_store(F->STs, 2 * Bf, F->polI, F->gridI, st));  // long rows come out 0 ...
     TOMO_TRY(long_rows(F, F->polI, F->gridI, st));                    // ... and are written here
+    if (F->faT) {
+      TOMO_TRY(fa_dispatch(F, cnt, x + (int64_t)s0 * n * n, st));
+      continue;
+    }
     k_fub_transpose<false, true, true><<<tgrid((int64_t)G * G), 256, 0, st>>>(F->grid, (float2 *)F->gridI, (int64_t)G * G,
                                                                           Bf, F->ph_grid, G, np, nullptr, 1.f);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_INVERSE), "2D inverse"));

@@ -42,6 +42,7 @@ struct tomo_fubini {
   float *gridI = nullptr;         // [G*G][2 Bf] interleaved (re, im)
   float *polI = nullptr;          // [nt*np][2 Bf]
   cufftComplex *pol = nullptr;    // [Bf][nt][np]
+  float2 *faT = nullptr;          // [Bf][G][n] the adjoint's column-transformed grid (register-FFT path)
   cufftHandle plan2 = 0, plan1 = 0;
   bool plans = false;
   // normal operator (normal.cu), built on first use per filter
@@ -58,4 +59,8 @@ struct tomo_fubini {
 
 namespace tomo {
 void free_normal(tomo_fubini *F);
+// the W_L^{j2 k1} tables of regfft.cuh for L = G (built once per handle)
+tomo_status ensure_twiddles(tomo_fubini *F, cudaStream_t st);
+// grids with the register-FFT passes (G a power of two, 32..2048)
+inline bool fused_ok(int L) { return L >= 32 && L <= 2048 && (L & (L - 1)) == 0; }
 }

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "bbstep.cuh"
+#include "regfft.cuh"
 #include "fubini.cuh"
 
 namespace tomo {
@@ -35,8 +36,6 @@ namespace {
 
 constexpr int kT = 256;
 
-// sizes with the fused convolution (the 2n x 2n grid a power of two, 32..2048)
-bool fused_ok(int L) { return L >= 32 && L <= 2048 && (L & (L - 1)) == 0; }
 
 tomo_status cufft_ok(cufftResult r, const char *what) {
   if (r != CUFFT_SUCCESS) return fail(TOMO_ERR_CUDA, std::string("cuFFT ") + what + " failed: " + std::to_string((int)r));
@@ -256,107 +255,6 @@ __global__ void __launch_bounds__(kT) k_nrm_step(float *x, const float *g, int64
 // R2-point DFTs in registers; X[k1 + R1 k2] ends in lane k1 mod G.  The
 // inverse runs the same steps backwards with conjugate twiddles.
 
-struct Tw32 {
-  float2 w[64];  // e^{-2 pi i k / 64}
-};
-
-__host__ __device__ constexpr int rev8(int i) {
-  return ((i & 1) << 7) | ((i & 2) << 5) | ((i & 4) << 3) | ((i & 8) << 1) | ((i & 16) >> 1) | ((i & 32) >> 3) |
-         ((i & 64) >> 5) | ((i & 128) >> 7);
-}
-
-__host__ __device__ constexpr int ilog2(int R) { return R <= 1 ? 0 : 1 + ilog2(R / 2); }
-
-// bit reversal of i < R (R a power of two <= 256), loop-free so that unrolled
-// register indexing folds to constants
-template <int R>
-__host__ __device__ constexpr int bitrev(int i) {
-  return rev8(i) >> (8 - ilog2(R));
-}
-static_assert(bitrev<32>(1) == 16 && bitrev<32>(6) == 12 && bitrev<8>(3) == 6, "bit reversal");
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// in-register DFT of R <= 64 points, natural order in and out: radix-2
-// decimation in time on the bit-reversed sequence, one template level per
-// stage so that every loop unrolls; kInv: conjugate twiddles
-template <int R, int LEN, bool kInv>
-__device__ __forceinline__ void dft_stage(float2 *a, const Tw32 &tw) {
-#pragma unroll
-  for (int i = 0; i < R; i += LEN) {
-#pragma unroll
-    for (int j = 0; j < LEN / 2; ++j) {
-      const float2 u = a[i + j];
-      float2 t = a[i + j + LEN / 2];
-      if (j != 0) {
-        float2 w = tw.w[j * (64 / LEN)];
-        if (kInv) w.y = -w.y;
-        t = cmulf(w, t);
-      }
-      a[i + j] = make_float2(u.x + t.x, u.y + t.y);
-      a[i + j + LEN / 2] = make_float2(u.x - t.x, u.y - t.y);
-    }
-  }
-  if constexpr (LEN < R) dft_stage<R, 2 * LEN, kInv>(a, tw);
-}
-
-template <int R, bool kInv>
-__device__ __forceinline__ void dft_reg(float2 *v, const Tw32 &tw) {
-  float2 a[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) a[bitrev<R>(i)] = v[i];
-  dft_stage<R, 2, kInv>(a, tw);
-#pragma unroll
-  for (int i = 0; i < R; ++i) v[i] = a[i];
-}
-
-// forward: lane l holds v[j1] = x[j1 R2 + l]; on return w[t R2 + k2] =
-// X[(l + G t) + R1 k2].  S: the group's R1 x (R2 + 1) shared tile.  twL holds
-// W_L^{j2 k1} twice: [k1][j2] (first L entries) and [j2][k1], so that the
-// lanes of a group read consecutive entries in both directions.
-template <int R1, int R2>
-__device__ __forceinline__ void fft_fwd(float2 *v, float2 *w, float2 *S, int l, const float2 *twL, const Tw32 &tw) {
-  constexpr int G = R2, T = R1 / G;
-  dft_reg<R1, false>(v, tw);
-#pragma unroll
-  for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulf(v[k1], __ldg(twL + k1 * R2 + l));
-#pragma unroll
-  for (int k1 = 0; k1 < R1; ++k1) S[k1 * (R2 + 1) + l] = v[k1];
-  __syncwarp();
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int k1 = l + G * t;
-#pragma unroll
-    for (int j2 = 0; j2 < R2; ++j2) w[t * R2 + j2] = S[k1 * (R2 + 1) + j2];
-    dft_reg<R2, false>(w + t * R2, tw);
-  }
-  __syncwarp();
-}
-
-// inverse (unnormalised) of fft_fwd: from w back to v[j1] = x[j1 R2 + l]
-template <int R1, int R2>
-__device__ __forceinline__ void fft_inv(float2 *w, float2 *v, float2 *S, int l, const float2 *twL, const Tw32 &tw) {
-  constexpr int G = R2, T = R1 / G;
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int k1 = l + G * t;
-    dft_reg<R2, true>(w + t * R2, tw);
-#pragma unroll
-    for (int j2 = 0; j2 < R2; ++j2) {
-      float2 tw1 = __ldg(twL + R1 * R2 + j2 * R1 + k1);
-      tw1.y = -tw1.y;
-      S[k1 * (R2 + 1) + j2] = cmulf(w[t * R2 + j2], tw1);
-    }
-  }
-  __syncwarp();
-#pragma unroll
-  for (int k1 = 0; k1 < R1; ++k1) v[k1] = S[k1 * (R2 + 1) + l];
-  __syncwarp();
-  dft_reg<R1, true>(v, tw);
-}
-
 constexpr int kCvThreads = 256;
 
 // a group's shared tile: R1 x (R2 + 1) plus one entry, so that the tiles of
@@ -383,7 +281,7 @@ constexpr bool cv_stage() {
 template <int R1, int R2, bool kStep>
 __global__ void __launch_bounds__(kCvThreads, (R1 <= 32 ? 3 : 1)) k_cv_rows(const float *u, float *x, const float *g,
                                                          const float *alpha, float2 *H, int nz, const float2 *twL,
-                                                         const __grid_constant__ Tw32 tw) {
+                                                         const __grid_constant__ Tw64 tw) {
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
   extern __shared__ float2 cv_sm[];
   const int l = threadIdx.x % G;
@@ -453,7 +351,7 @@ __global__ void __launch_bounds__(kCvThreads, (R1 <= 32 ? 3 : 1)) k_cv_rows(cons
 // columns: FFT id f = s W + kx; Kt2 / Kh2 in [kx][ky] order
 template <int R1, int R2>
 __global__ void __launch_bounds__(kCvThreads) k_cv_cols(float2 *H, int nz, const float2 *Kt2, const float2 *Kh2,
-                                                         const float2 *twL, const __grid_constant__ Tw32 tw) {
+                                                         const float2 *twL, const __grid_constant__ Tw64 tw) {
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
   extern __shared__ float2 cv_sm[];
   const int l = threadIdx.x % G;
@@ -494,7 +392,7 @@ __global__ void __launch_bounds__(kCvThreads) k_cv_cols(float2 *H, int nz, const
 template <int R1, int R2, bool kGrad>
 __global__ void __launch_bounds__(kCvThreads, (R1 <= 32 ? 3 : 1)) k_cv_rows_inv(const float2 *H, float *y, const float *c, const float *gp,
                                                              double3 *part, int nz, const float2 *twL,
-                                                             const __grid_constant__ Tw32 tw) {
+                                                             const __grid_constant__ Tw64 tw) {
   constexpr int L = R1 * R2, n = L / 2, G = R2, W = n + 1;
   extern __shared__ float2 cv_sm[];
   const int l = threadIdx.x % G;
@@ -597,18 +495,6 @@ __global__ void k_nrm_kT(const float2 *K, int L, float2 *KT) {
   if (e >= (int64_t)L * W) return;
   const int ky = (int)(e / W), kx = (int)(e % W);
   KT[(int64_t)kx * L + ky] = K[e];
-}
-
-// W_L^{j2 k1} = e^{-2 pi i (j2 k1 mod L) / L} for L = R1 R2, FP64 arguments
-// rounded once: tw[k1 R2 + j2], then tw[L + j2 R1 + k1]
-__global__ void k_nrm_twiddles(int R1, int R2, float2 *tw) {
-  const int L = R1 * R2;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 2 * L) return;
-  const int k1 = e < L ? e / R2 : (e - L) % R1, j2 = e < L ? e % R2 : (e - L) / R1;
-  double s, c;
-  sincospi(-2.0 * (double)(((int64_t)j2 * k1) % L) / (double)L, &s, &c);
-  tw[e] = make_float2((float)c, (float)s);
 }
 
 // FP64 weights of the backprojection: kappa and the density at |w| = j / np
@@ -722,27 +608,13 @@ tomo_status apply_pass(tomo_fubini *F, const NormalKernel &K, const float *u, in
   return TOMO_OK;
 }
 
-Tw32 tw32() {
-  Tw32 t;
-  for (int k = 0; k < 64; ++k)
-    t.w[k] = make_float2((float)std::cos(2.0 * M_PI * k / 64.0), (float)-std::sin(2.0 * M_PI * k / 64.0));
-  return t;
-}
-
 tomo_status ensure_fused(tomo_fubini *F, cudaStream_t st) {
   if (F->H) return TOMO_OK;
-  const int L = F->G, n = F->n, W = n + 1;
+  const int n = F->n, W = n + 1;
   // slices per fused pass: 64, fewer while the half spectrum would pass 1 GiB
   int Hc = 64;
   while (Hc > 1 && (int64_t)W * n * 8 * Hc > ((int64_t)1 << 30)) Hc /= 2;
-  if (!F->twL) {
-    int R2 = 1;
-    while (R2 * R2 < L) R2 *= 2;
-    if (R2 * R2 > L) R2 /= 2;  // L = R1 R2 with R1 = R2 or 2 R2, as in cv_dispatch
-    TOMO_TRY(dalloc(&F->twL, 2 * L));
-    k_nrm_twiddles<<<(2 * L + kT - 1) / kT, kT, 0, st>>>(L / R2, R2, F->twL);
-    TOMO_CUDA(cudaGetLastError());
-  }
+  TOMO_TRY(ensure_twiddles(F, st));
   TOMO_TRY(dalloc(&F->H, (size_t)W * n * Hc));
   F->Hc = Hc;
   return TOMO_OK;
@@ -775,7 +647,7 @@ tomo_status cv_run(tomo_fubini *F, const NormalKernel &K, const CvArgs &a, int c
   TOMO_TRY(smem_attr(k_cv_cols<R1, R2>, sm));
   TOMO_TRY(smem_attr(k_cv_rows_inv<R1, R2, true>, sm));
   TOMO_TRY(smem_attr(k_cv_rows_inv<R1, R2, false>, sm));
-  const Tw32 tw = tw32();
+  const Tw64 tw = tw64();
   const unsigned gr = (unsigned)(((int64_t)cnt * (n / 2) + per - 1) / per);
   const unsigned gc = (unsigned)(((int64_t)cnt * W + per - 1) / per);
   if (a.step)
@@ -814,6 +686,19 @@ tomo_status prepare(tomo_fubini *F, int filter, cudaStream_t st) {
 }
 
 }  // namespace
+
+tomo_status ensure_twiddles(tomo_fubini *F, cudaStream_t st) {
+  if (F->twL) return TOMO_OK;
+  const int L = F->G, R2 = fft_r2(L);
+  if (cudaMalloc(&F->twL, sizeof(float2) * 2 * L) != cudaSuccess) {
+    cudaGetLastError();
+    F->twL = nullptr;
+    return fail(TOMO_ERR_OOM, "twiddle table allocation failed");
+  }
+  k_fft_twiddles<<<(2 * L + kT - 1) / kT, kT, 0, st>>>(L / R2, R2, F->twL);
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
+}
 
 void free_normal(tomo_fubini *F) {
   for (NormalKernel &K : F->nk) {
