@@ -391,6 +391,74 @@ __global__ void __launch_bounds__(kFaSlices *R2) k_fa_rows(const float2 *T, int 
     }
 }
 
+// ---- the forward transform's first steps on power-of-two grids: deapodize,
+// zero-pad and transform the image in two register-FFT passes that touch only
+// the image's rows and write the grid straight into the SpMM layout:
+//   rows     per (slice, 8 image rows iy): u[iy][gx - o] d[iy] d[gx - o] over the
+//            padded row, FFT -> T[s][kx][iy]
+//   columns  per (kx, 8 slices): T[s][kx][gy - o] over the padded column, FFT,
+//            the grid phase ph[ky] ph[kx] -> gridI[ky G + kx][s]
+// Outputs are staged through shared memory so that global writes are whole rows.
+template <int R1, int R2>
+__global__ void __launch_bounds__(kFaSlices *R2) k_ff_rows(const float *u, int n, const float *d, float2 *T,
+                                                           const float2 *twL, const __grid_constant__ Tw64 tw) {
+  constexpr int G = R1 * R2;
+  extern __shared__ float2 fa_sm[];
+  const int s = blockIdx.y, iy0 = blockIdx.x * kFaSlices, q = threadIdx.x / R2, l = threadIdx.x % R2;
+  const int o = (G - n) / 2, iy = iy0 + q;
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) {
+    const int gx = j1 * R2 + l;
+    float val = 0.f;
+    if (iy < n && gx >= o && gx < o + n) val = u[((int64_t)s * n + iy) * n + gx - o] * d[iy] * d[gx - o];
+    v[j1] = make_float2(val, 0.f);
+  }
+  fft_fwd<R1, R2, false>(v, w, fa_sm + q * (R1 * (R2 + 1) + 1), l, twL, tw);
+  __syncthreads();  // every group is done with its tile: the staging area overlaps them
+#pragma unroll
+  for (int t = 0; t < R1 / R2; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) fa_sm[((l + R2 * t) + R1 * k2) * (kFaSlices + 1) + q] = w[t * R2 + k2];
+  __syncthreads();
+  for (int e = threadIdx.x; e < G * kFaSlices; e += blockDim.x) {
+    const int kx = e / kFaSlices, qq = e % kFaSlices;
+    if (iy0 + qq < n) T[((int64_t)s * G + kx) * n + iy0 + qq] = fa_sm[kx * (kFaSlices + 1) + qq];
+  }
+}
+
+// grid (G, ceil(Bf / 8)): slices cnt .. Bf - 1 of the pass get zero columns
+template <int R1, int R2>
+__global__ void __launch_bounds__(kFaSlices *R2) k_ff_cols(const float2 *T, int Bf, int cnt, int n,
+                                                           const float2 *ph, float2 *gridI, const float2 *twL,
+                                                           const __grid_constant__ Tw64 tw) {
+  constexpr int G = R1 * R2;
+  extern __shared__ float2 fa_sm[];
+  const int kx = blockIdx.x, s0 = blockIdx.y * kFaSlices, q = threadIdx.x / R2, l = threadIdx.x % R2;
+  const int o = (G - n) / 2, s = s0 + q;
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) {
+    const int gy = j1 * R2 + l;
+    v[j1] = (s < cnt && gy >= o && gy < o + n) ? T[((int64_t)s * G + kx) * n + gy - o] : make_float2(0.f, 0.f);
+  }
+  fft_fwd<R1, R2, false>(v, w, fa_sm + q * (R1 * (R2 + 1) + 1), l, twL, tw);
+  const float2 pkx = ph[kx];
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < R1 / R2; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int ky = (l + R2 * t) + R1 * k2;
+      fa_sm[ky * (kFaSlices + 1) + q] = cmul(w[t * R2 + k2], cmul(ph[ky], pkx));
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < G * kFaSlices; e += blockDim.x) {
+    const int ky = e / kFaSlices, qq = e % kFaSlices;
+    if (s0 + qq < Bf) gridI[((int64_t)ky * G + kx) * Bf + s0 + qq] = fa_sm[ky * (kFaSlices + 1) + qq];
+  }
+}
+
 int tgrid(int64_t points) {
   const int64_t b = (points + kTile - 1) / kTile;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 16));
@@ -459,6 +527,34 @@ tomo_status fa_run(tomo_fubini *F, int cnt, float *x, cudaStream_t st) {
       F->faT, F->n, F->deapod, x, F->twL, tw);
   TOMO_CUDA(cudaGetLastError());
   return TOMO_OK;
+}
+
+template <int R1, int R2>
+tomo_status ff_run(tomo_fubini *F, int cnt, const float *u, cudaStream_t st) {
+  constexpr int G = R1 * R2, sm = fa_smem<R1, R2>();
+  TOMO_CUDA(cudaFuncSetAttribute(k_ff_rows<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  TOMO_CUDA(cudaFuncSetAttribute(k_ff_cols<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  const Tw64 tw = tw64();
+  k_ff_rows<R1, R2><<<dim3((F->n + kFaSlices - 1) / kFaSlices, cnt), kFaSlices * R2, sm, st>>>(
+      u, F->n, F->deapod, F->faT, F->twL, tw);
+  k_ff_cols<R1, R2><<<dim3(G, (F->Bf + kFaSlices - 1) / kFaSlices), kFaSlices * R2, sm, st>>>(
+      F->faT, F->Bf, cnt, F->n, F->ph_grid, (float2 *)F->gridI, F->twL, tw);
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
+}
+
+// the forward transform's deapodize, pad and 2D FFT by register FFTs (G a power of two, 32..2048)
+tomo_status ff_dispatch(tomo_fubini *F, int cnt, const float *u, cudaStream_t st) {
+  switch (F->G) {
+    case 32: return ff_run<8, 4>(F, cnt, u, st);
+    case 64: return ff_run<8, 8>(F, cnt, u, st);
+    case 128: return ff_run<16, 8>(F, cnt, u, st);
+    case 256: return ff_run<16, 16>(F, cnt, u, st);
+    case 512: return ff_run<32, 16>(F, cnt, u, st);
+    case 1024: return ff_run<32, 32>(F, cnt, u, st);
+    case 2048: return ff_run<64, 32>(F, cnt, u, st);
+  }
+  return fail(TOMO_ERR_INVALID_ARG, "no register-FFT forward for this grid");
 }
 
 // the adjoint's inverse 2D transform and crop by register FFTs (G a power of two, 32..2048)
@@ -647,10 +743,15 @@ tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz,
   TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
   for (int32_t s0 = 0; s0 < nz; s0 += Bf) {
     const int cnt = std::min<int32_t>(Bf, nz - s0);
-    k_fub_pad<<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(x + (int64_t)s0 * n * n, cnt, n, G, F->deapod, F->grid, Bf);
-    TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_FORWARD), "2D forward"));
-    k_fub_transpose<true, true, false><<<tgrid((int64_t)G * G), 256, 0, st>>>(F->grid, (float2 *)F->gridI, (int64_t)G * G,
-                                                                         Bf, F->ph_grid, G, np, nullptr, 1.f);
+    if (F->faT) {
+      TOMO_TRY(ff_dispatch(F, cnt, x + (int64_t)s0 * n * n, st));
+    } else {
+      k_fub_pad<<<egrid((int64_t)Bf * G * G), kT, 0, st>>>(x + (int64_t)s0 * n * n, cnt, n, G, F->deapod, F->grid,
+                                                            Bf);
+      TOMO_TRY(cufft_check(cufftExecC2C(F->plan2, F->grid, F->grid, CUFFT_FORWARD), "2D forward"));
+      k_fub_transpose<true, true, false><<<tgrid((int64_t)G * G), 256, 0, st>>>(
+          F->grid, (float2 *)F->gridI, (int64_t)G * G, Bf, F->ph_grid, G, np, nullptr, 1.f);
+    }
     TOMO_TRY(spmm_csr_store(F->S, 2 * Bf, F->gridI, F->polI, st));
     k_fub_transpose<false, false, false><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad,
                                                                G, np, nullptr, 1.f);
