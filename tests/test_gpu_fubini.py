@@ -117,3 +117,18 @@ def test_sirt_bb_matches_oracle():
     ref, href = fb.fubini_sirt_bb(fg, c.sino.reshape(3, -1), 10, S)
     assert per_slice_rel(x.cpu().numpy(), ref).max() < 1e-4
     np.testing.assert_allclose(h.cpu().numpy(), href, rtol=1e-4)
+
+
+@pytest.mark.parametrize("n,nt", [(16, 12), (32, 20), (256, 40), (1024, 30)])
+def test_register_fft_grids_match_oracle(n, nt):
+    """Every power-of-two grid split of the register-FFT passes (G = 2n = 32 ..
+    2048): forward, adjoint and the Hamming iRadon against the oracle."""
+    fg, S, F = pair(n=n, nt=nt)
+    x = inputs.random_slices((3, n, n), 60 + n)
+    y = inputs.random_slices((3, nt, n), 61 + n)
+    gy = F.project(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert per_slice_rel(gy, fb.fubini_project(fg, x.reshape(3, -1), S)).max() < 1e-5
+    gx = F.backproject(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert per_slice_rel(gx, fb.fubini_backproject(fg, y.reshape(3, -1), S)).max() < 1e-5
+    gf = F.backproject(torch.from_numpy(y).cuda(), filtered="hamming").cpu().numpy()
+    assert per_slice_rel(gf, fb.fubini_fbp(fg, y.reshape(3, -1), S, fb.hamming_density(fg))).max() < 1e-5
