@@ -380,8 +380,10 @@ TOMO_API tomo_status tomo_cgls_resume(const tomo_matrix *A, const float *sino, f
  * exact transform R[u](m,k) = Re((1/n_p) sum_q e^{2 pi i w_q p_k}
  * sum_j u_j e^{-2 pi i w_q (x_j cos theta_m + y_j sin theta_m)}) with the pixel
  * and bin coordinates of the line model.  S is real; the paper's phase ramp
- * and FFT shifts are applied as diagonal phases beside the FFTs.  FFTs are
- * cuFFT calls; S and its stored transpose are built on the device.
+ * and FFT shifts are applied as diagonal phases beside the FFTs.  The 2D
+ * FFTs are hand-written register FFTs when 2n is a power of two up to 2048
+ * (cuFFT otherwise), the 1D ones cuFFT calls; S and its stored transpose are
+ * built on the device.
  * ------------------------------------------------------------------------- */
 typedef struct tomo_fubini tomo_fubini; /* holds S, S^T, cuFFT plans and scratch: one call at a time */
 
@@ -436,7 +438,9 @@ TOMO_API tomo_status tomo_tv(const float *x, int32_t n_z, int32_t n_y, int32_t n
  * (kappa = 1/n_p for filter 0, pi/(n_theta n_p) otherwise; D_q the density,
  * nu_q = D_q except nu_q0 = D_q0/2 and h = 0 unless n_p is even, q0 being the
  * unpaired sample w = -1/2), applied as a circular convolution on the 2n x 2n
- * grid: one FP32 real-to-complex FFT, one pointwise product, the inverse FFT;
+ * grid: an FP32 FFT of the padded image, one pointwise product, the inverse FFT
+ * (hand-written register FFTs when 2n is a power of two up to 2048, cuFFT
+ * otherwise);
  * no gridding, no 1D transforms.  It agrees with
  * tomo_fubini_backproject(tomo_fubini_project(x)) to the gridding error.  The
  * first call per filter sums the taps in FP64 on the device and transforms

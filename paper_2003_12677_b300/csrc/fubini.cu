@@ -12,7 +12,10 @@
 // S is real here: the paper folds FFT shifts and the axis phase ramp into
 // complex entries of S; this build applies them as diagonal phase factors
 // next to the FFTs instead, so one real SpMM kernel serves complex data
-// stored as (re, im) column pairs.  The FFTs are cuFFT calls.
+// stored as (re, im) column pairs.  On power-of-two grids (32..2048) the 2D
+// transforms are register-FFT passes (regfft.cuh) fused with the padding,
+// cropping, phases and layout changes around them; the 1D radial transforms
+// and other grid sizes use cuFFT.
 #include <cmath>
 #include <cstring>
 #include <vector>

@@ -18,8 +18,10 @@
 // (for real u the mirrored image's spectrum is that phase times conj(U)).
 // The taps are summed on the device in FP64 (Clenshaw's recurrence for the
 // cosine series f), transformed once by a double-precision FFT and kept as
-// FP32 spectra; each application is an FP32 real-to-complex FFT, one
-// pointwise product and the inverse FFT.
+// FP32 spectra.  Each application is then a forward FFT of the padded image,
+// one pointwise product and the inverse FFT: three fused register-FFT passes
+// (regfft.cuh) when L is a power of two up to 2048, else cuFFT R2C / C2R with
+// pad, product and crop kernels around them.
 #include <algorithm>
 #include <cmath>
 #include <vector>
