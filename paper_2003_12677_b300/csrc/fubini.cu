@@ -335,8 +335,10 @@ __global__ void __launch_bounds__(kFaSlices *R2) k_fa_cols(const float2 *gridI, 
                                                            const __grid_constant__ Tw64 tw) {
   constexpr int G = R1 * R2;
   extern __shared__ float2 fa_sm[];
-  const int kx = blockIdx.x, q = threadIdx.x / R2, l = threadIdx.x % R2;
-  const int s0 = blockIdx.y * kFaSlices, o = (G - n) / 2;
+  // grid (slice groups, G): the groups of one column run next to each other,
+  // so the second reads the other half of each 128-byte row from L2
+  const int kx = blockIdx.y, q = threadIdx.x / R2, l = threadIdx.x % R2;
+  const int s0 = blockIdx.x * kFaSlices, o = (G - n) / 2;
   for (int e = threadIdx.x; e < G * kFaSlices; e += blockDim.x) {
     const int ky = e / kFaSlices, qq = e % kFaSlices;
     fa_sm[ky * (kFaSlices + 1) + qq] =
@@ -430,14 +432,14 @@ __global__ void __launch_bounds__(kFaSlices *R2) k_ff_rows(const float *u, int n
   }
 }
 
-// grid (G, ceil(Bf / 8)): slices cnt .. Bf - 1 of the pass get zero columns
+// grid (ceil(Bf / 8), G): slices cnt .. Bf - 1 of the pass get zero columns
 template <int R1, int R2>
 __global__ void __launch_bounds__(kFaSlices *R2) k_ff_cols(const float2 *T, int Bf, int cnt, int n,
                                                            const float2 *ph, float2 *gridI, const float2 *twL,
                                                            const __grid_constant__ Tw64 tw) {
   constexpr int G = R1 * R2;
   extern __shared__ float2 fa_sm[];
-  const int kx = blockIdx.x, s0 = blockIdx.y * kFaSlices, q = threadIdx.x / R2, l = threadIdx.x % R2;
+  const int kx = blockIdx.y, s0 = blockIdx.x * kFaSlices, q = threadIdx.x / R2, l = threadIdx.x % R2;
   const int o = (G - n) / 2, s = s0 + q;
   float2 v[R1], w[R1];
 #pragma unroll
@@ -524,7 +526,7 @@ tomo_status fa_run(tomo_fubini *F, int cnt, float *x, cudaStream_t st) {
   TOMO_CUDA(cudaFuncSetAttribute(k_fa_cols<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   TOMO_CUDA(cudaFuncSetAttribute(k_fa_rows<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   const Tw64 tw = tw64();
-  k_fa_cols<R1, R2><<<dim3(G, (cnt + kFaSlices - 1) / kFaSlices), kFaSlices * R2, sm, st>>>(
+  k_fa_cols<R1, R2><<<dim3((cnt + kFaSlices - 1) / kFaSlices, G), kFaSlices * R2, sm, st>>>(
       (const float2 *)F->gridI, F->Bf, cnt, F->n, F->ph_grid, F->faT, F->twL, tw);
   k_fa_rows<R1, R2><<<dim3((F->n + kFaSlices - 1) / kFaSlices, cnt), kFaSlices * R2, sm, st>>>(
       F->faT, F->n, F->deapod, x, F->twL, tw);
@@ -540,7 +542,7 @@ tomo_status ff_run(tomo_fubini *F, int cnt, const float *u, cudaStream_t st) {
   const Tw64 tw = tw64();
   k_ff_rows<R1, R2><<<dim3((F->n + kFaSlices - 1) / kFaSlices, cnt), kFaSlices * R2, sm, st>>>(
       u, F->n, F->deapod, F->faT, F->twL, tw);
-  k_ff_cols<R1, R2><<<dim3(G, (F->Bf + kFaSlices - 1) / kFaSlices), kFaSlices * R2, sm, st>>>(
+  k_ff_cols<R1, R2><<<dim3((F->Bf + kFaSlices - 1) / kFaSlices, G), kFaSlices * R2, sm, st>>>(
       F->faT, F->Bf, cnt, F->n, F->ph_grid, (float2 *)F->gridI, F->twL, tw);
   TOMO_CUDA(cudaGetLastError());
   return TOMO_OK;
