@@ -330,7 +330,7 @@ constexpr int fa_smem() {
 }
 
 template <int R1, int R2>
-__global__ void __launch_bounds__(kFaSlices *R2) k_fa_cols(const float2 *gridI, int Bf, int cnt, int n,
+__global__ void __launch_bounds__(kFaSlices *R2, (R1 <= 32 ? 3 : 1)) k_fa_cols(const float2 *gridI, int Bf, int cnt, int n,
                                                            const float2 *ph, float2 *T, const float2 *twL,
                                                            const __grid_constant__ Tw64 tw) {
   constexpr int G = R1 * R2;
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kFaSlices *R2) k_fa_cols(const float2 *gridI, 
 }
 
 template <int R1, int R2>
-__global__ void __launch_bounds__(kFaSlices *R2) k_fa_rows(const float2 *T, int n, const float *d, float *x,
+__global__ void __launch_bounds__(kFaSlices *R2, (R1 <= 32 ? 3 : 1)) k_fa_rows(const float2 *T, int n, const float *d, float *x,
                                                            const float2 *twL, const __grid_constant__ Tw64 tw) {
   constexpr int G = R1 * R2;
   extern __shared__ float2 fa_sm[];
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kFaSlices *R2) k_fa_rows(const float2 *T, int 
 //            the grid phase ph[ky] ph[kx] -> gridI[ky G + kx][s]
 // Outputs are staged through shared memory so that global writes are whole rows.
 template <int R1, int R2>
-__global__ void __launch_bounds__(kFaSlices *R2) k_ff_rows(const float *u, int n, const float *d, float2 *T,
+__global__ void __launch_bounds__(kFaSlices *R2, (R1 <= 32 ? 3 : 1)) k_ff_rows(const float *u, int n, const float *d, float2 *T,
                                                            const float2 *twL, const __grid_constant__ Tw64 tw) {
   constexpr int G = R1 * R2;
   extern __shared__ float2 fa_sm[];
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kFaSlices *R2) k_ff_rows(const float *u, int n
 
 // grid (ceil(Bf / 8), G): slices cnt .. Bf - 1 of the pass get zero columns
 template <int R1, int R2>
-__global__ void __launch_bounds__(kFaSlices *R2) k_ff_cols(const float2 *T, int Bf, int cnt, int n,
+__global__ void __launch_bounds__(kFaSlices *R2, (R1 <= 32 ? 3 : 1)) k_ff_cols(const float2 *T, int Bf, int cnt, int n,
                                                            const float2 *ph, float2 *gridI, const float2 *twL,
                                                            const __grid_constant__ Tw64 tw) {
   constexpr int G = R1 * R2;
