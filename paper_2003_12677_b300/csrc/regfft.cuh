@@ -47,8 +47,20 @@ __device__ __forceinline__ void dft_stage(float2 *a, const Tw64 &tw) {
     for (int j = 0; j < LEN / 2; ++j) {
       const float2 u = a[i + j];
       float2 t = a[i + j + LEN / 2];
-      if (j != 0) {
-        float2 w = tw.w[j * (64 / LEN)];
+      // the twiddle e^{-+2 pi i idx / 64}: multiplications by -+i are swaps,
+      // the two diagonal ones take two multiplies, the rest a full product
+      const int idx = j * (64 / LEN);
+      if (idx == 16) {
+        t = kInv ? make_float2(-t.y, t.x) : make_float2(t.y, -t.x);
+      } else if (idx == 8 || idx == 24) {
+        const float h = tw.w[8].x;  // cos(pi/4), as the table holds it
+        const float p = h * (t.x + t.y), m = h * (t.x - t.y);
+        if (idx == 8)
+          t = kInv ? make_float2(m, p) : make_float2(p, -m);
+        else
+          t = kInv ? make_float2(-p, m) : make_float2(-m, -p);
+      } else if (idx != 0) {
+        float2 w = tw.w[idx];
         if (kInv) w.y = -w.y;
         t = cmulf(w, t);
       }
