@@ -440,8 +440,15 @@ __global__ void __launch_bounds__(kCvThreads, (R1 <= 32 ? 3 : 1)) k_cv_rows_inv(
       w[t * R2 + k2] = make_float2(q.x - q.w, q.y + q.z);  // Y_a + i Y_b
     }
   }
-  fft_inv<R1, R2>(w, v, S, l, twL, tw);
   const int64_t ra = ((int64_t)s * n + 2 * p) * n, rb = ra + n;
+  if (kGrad && act) {
+    // the epilogue's c and gp rows (2 x n floats each) towards L2 while the FFT runs
+    for (int j = 32 * l; j < 2 * n; j += 32 * R2) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(c + ra + j));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(gp + ra + j));
+    }
+  }
+  fft_inv<R1, R2>(w, v, S, l, twL, tw);
   KSum sg, sp, sq;
   if (act) {
 #pragma unroll
