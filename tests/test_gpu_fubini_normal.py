@@ -221,3 +221,16 @@ def test_normal_fused_2048_columns():
     got = F.normal(x, "hamming").cpu().numpy()
     ref = F.backproject(F.project(x), "hamming").cpu().numpy()
     assert per_slice_rel(got, ref).max() < 1e-4
+
+
+def test_both_sirts_are_deterministic():
+    """Fixed-order sums everywhere (BB sums, the long rows of S^T, the row-pair
+    partials): two runs give the same bits, for the gridded SIRT and the SIRT
+    with N."""
+    fg, F = pair(n=64, nt=90)
+    c = inputs.make_case(64, 90, 5, seed=831, phantom="ellipses2d", noise="poisson", level=1e5)
+    b = torch.from_numpy(c.sino).cuda()
+    for run in (lambda: F.sirt_bb(b, 8, history=True), lambda: F.sirt_bb_normal(b, 8, history=True)):
+        x1, h1 = run()
+        x2, h2 = run()
+        assert torch.equal(x1, x2) and torch.equal(h1, h2)
