@@ -183,6 +183,14 @@ TOMO_API tomo_status tomo_matrix_export_rows(const tomo_matrix *A, int32_t trans
                                              int64_t row_end, int64_t *row_ptr, int32_t *col, float *val,
                                              int64_t cap);
 
+/* Copy the whole CSR form of A (transpose = 0) or of its stored transpose
+ * (transpose = 1) to HOST buffers: row_ptr (rows + 1 offsets), col and val
+ * (nnz entries each; sizes from tomo_matrix_info).  Enqueued on `stream` and
+ * synchronised before return.  UNSUPPORTED when the handle dropped its CSR
+ * form.  For parity checks of the stored structure. */
+TOMO_API tomo_status tomo_matrix_export_csr(const tomo_matrix *A, int32_t transpose, int64_t *row_ptr, int32_t *col,
+                                            float *val, void *stream);
+
 /* Copy the SIRT normalisers to HOST buffers (R: rows floats, C: cols floats;
  * either may be NULL).  Synchronous. */
 TOMO_API tomo_status tomo_matrix_export_norms(const tomo_matrix *A, float *R, float *C);

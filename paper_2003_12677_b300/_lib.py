@@ -16,6 +16,7 @@ SLICE_MAJOR, INTERLEAVED = 0, 1
 
 # every entry point include/tomo.h declares
 EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo_matrix_export_rows",
+           "tomo_matrix_export_csr",
            "tomo_matrix_export_norms", "tomo_workspace_size", "tomo_project", "tomo_backproject",
            "tomo_sirt", "tomo_cgls", "tomo_cgls_resume", "tomo_cgls_batched", "tomo_cgls_batched_workspace",
            "tomo_sirt_noalloc", "tomo_autotune", "tomo_stream_status", "tomo_sirt_bb",
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
         "tomo_matrix_destroy": [P],
         "tomo_matrix_info": [P, ctypes.POINTER(MatrixInfo)],
         "tomo_matrix_export_rows": [P, I32, I64, I64, P, P, P, I64],
+        "tomo_matrix_export_csr": [P, I32, P, P, P, P],
         "tomo_matrix_export_norms": [P, P, P],
         "tomo_workspace_size": [P, I32, I32, ctypes.POINTER(ExecOpts), ctypes.POINTER(SZ)],
         "tomo_project": [P, P, P, I32, I32, ctypes.POINTER(ExecOpts), P, SZ, P],

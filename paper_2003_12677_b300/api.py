@@ -147,8 +147,14 @@ class Matrix:
         return rp, col[:need], val[:need]
 
     def export_csr(self, transpose: bool = False):
+        """The whole CSR form of A (or of its stored transpose) on the host."""
         n = self.cols if transpose else self.rows
-        return self.export_rows(0, n, transpose)
+        rp = np.empty(n + 1, np.int64)
+        col = np.empty(max(self.nnz, 1), np.int32)
+        val = np.empty(max(self.nnz, 1), np.float32)
+        _lib.call("tomo_matrix_export_csr", self._h, int(transpose), rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                  _stream())
+        return rp, col[:self.nnz], val[:self.nnz]
 
     def export_norms(self) -> Tuple[np.ndarray, np.ndarray]:
         R = np.empty(self.rows, np.float32)

@@ -105,6 +105,22 @@ tomo_status tomo_matrix_export_rows(const tomo_matrix *A, int32_t transpose, int
   return TOMO_OK;
 }
 
+tomo_status tomo_matrix_export_csr(const tomo_matrix *A, int32_t transpose, int64_t *row_ptr, int32_t *col, float *val,
+                                   void *stream) {
+  if (!A || !row_ptr || !col || !val) return fail(TOMO_ERR_INVALID_ARG, "matrix, row_ptr, col and val must be non-NULL");
+  const Csr &M = transpose ? A->AT : A->A;
+  if (!M.ci) return fail(TOMO_ERR_UNSUPPORTED, "matrix was built with drop_csr: nothing to export");
+  DeviceGuard dg(A->device);
+  const cudaStream_t st = (cudaStream_t)stream;
+  TOMO_CUDA(cudaMemcpyAsync(row_ptr, M.rp, sizeof(int64_t) * (M.rows + 1), cudaMemcpyDeviceToHost, st));
+  if (M.nnz > 0) {
+    TOMO_CUDA(cudaMemcpyAsync(col, M.ci, sizeof(int32_t) * M.nnz, cudaMemcpyDeviceToHost, st));
+    TOMO_CUDA(cudaMemcpyAsync(val, M.v, sizeof(float) * M.nnz, cudaMemcpyDeviceToHost, st));
+  }
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  return TOMO_OK;
+}
+
 tomo_status tomo_matrix_export_norms(const tomo_matrix *A, float *R, float *C) {
   if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
   DeviceGuard dg(A->device);
