@@ -1,0 +1,45 @@
+"""bench.py's contract, checked without a GPU: the reference arm (the FP64
+oracle timed on the host cores) prints one JSON line with every key the
+driver reads, and the stored DRAM counters belong to the current sources of
+the SpMM kernels (so the GPU line reports `traffic` rather than null)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["config"]["workload"] == "sirt_512x360_b64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_stored_traffic_matches_the_spmm_sources():
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        tj = json.load(f)
+    assert tj["kernel_hash"] == bench.kernel_hash()
+    for k in ("sirt_512x360_b64/B64/sell/k0", "sirt_512x360_b64/B64/sell/k1"):
+        assert tj["per_launch_bytes"][k] > 1e9
+
+
+def test_peaks_come_from_the_measured_file():
+    peak, src = bench.measured_peaks()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert src == "measured" and peak > 1000
+    else:
+        assert src == "fallback" and peak == 6400.0
