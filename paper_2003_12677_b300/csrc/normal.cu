@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kT) k_nrm_step(float *x, const float *g, int64
   for (int64_t i = lo + threadIdx.x; i < hi; i += kT) x[off + i] = fmaf(a, g[off + i], x[off + i]);
 }
 
-// ---- fused convolution for L = 2n a power of two, 32 <= L <= 1024 ----------
+// ---- fused convolution for L = 2n a power of two, 32 <= L <= 2048 ----------
 // Three passes over the half spectrum H[s][kx][j] (kx = 0..n, image row j < n;
 // column-major, so that the column pass reads each column contiguously):
 //   rows     image rows a = 2p and b = 2p + 1 as one complex FFT of length L

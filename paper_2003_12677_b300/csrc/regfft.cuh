@@ -82,7 +82,8 @@ __device__ __forceinline__ void dft_reg(float2 *v, const Tw64 &tw) {
 }
 
 // forward (kInv: the unnormalised inverse DFT, conjugate twiddles): lane l
-// holds v[j1] = x[j1 R2 + l]; on return w[t R2 + k2] = X[(l + G t) + R1 k2].  S: the group's R1 x (R2 + 1) shared tile.  twL holds
+// holds v[j1] = x[j1 R2 + l]; on return w[t R2 + k2] = X[(l + G t) + R1 k2].
+// S: the group's R1 x (R2 + 1) shared tile.  twL holds
 // W_L^{j2 k1} twice: [k1][j2] (first L entries) and [j2][k1], so that the
 // lanes of a group read consecutive entries in both directions.
 template <int R1, int R2, bool kInv = false>
