@@ -606,6 +606,7 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
   } guard{F};
   cudaGetDevice(&F->device);
   F->n = g->n_x;
+  F->default_angles = g->angles == nullptr;
   F->np = g->n_p;
   F->nt = g->n_theta;
   F->kw = kw;

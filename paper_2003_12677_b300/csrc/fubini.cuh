@@ -30,6 +30,7 @@ struct tomo_fubini {
   tomo::Csr STs;                  // S^T with its long rows emptied (rows of <= 64 entries)
   tomo::Csr STl;                  // the long rows of S^T, compact; rows_l[i] is row i's index
   int32_t *rows_l = nullptr;
+  bool default_angles = false;    // theta_m = m pi / nt (no user angles)
   double *cs = nullptr;           // [nt] cos theta_m
   double *sn = nullptr;           // [nt] sin theta_m
   float *deapod = nullptr;        // [n] 1 / phi_hat(x / G)

@@ -68,17 +68,19 @@ __device__ __forceinline__ bool tap_offset(int i, int n, int L, int *d) {
 //   a[0..J]: cosine-series coefficients of f (nu_q paired with its mirror
 //   folded: a_0 = D_0, a_j = 2 D_j, and for even n_p a_{n_p/2} = D_q0 / 2);
 //   hc = kappa D_q0 / 2 (0: no Hankel part); cphi, sphi = cos, sin phi.
+// with_t = false: h only (t from k_nrm_taps8, ct cleared beforehand).
 __global__ void k_nrm_taps(int n, int L, int np, int nt, const double *cs, const double *sn, const double *a, int J,
-                           double kappa, double hc, double cphi, double sphi, double *ct, double *ch) {
+                           double kappa, double hc, double cphi, double sphi, double *ct, double *ch, bool with_t) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)L * L) return;
   const int iy = (int)(e / L), ix = (int)(e % L);
   int dy, dx;
   if (!tap_offset(iy, n, L, &dy) || !tap_offset(ix, n, L, &dx)) {
-    ct[e] = 0.0;
+    if (with_t) ct[e] = 0.0;
     if (ch) ch[e] = 0.0;
     return;
   }
+  if (!with_t && !ch) return;
   if (dy < 0 || (dy == 0 && dx < 0)) return;  // written by the mirror thread
   const int64_t em = (int64_t)((L - iy) % L) * L + (L - ix) % L;
   double t = 0.0, hp = 0.0, hm = 0.0;
@@ -86,16 +88,18 @@ __global__ void k_nrm_taps(int n, int L, int np, int nt, const double *cs, const
   for (int m = 0; m < nt; ++m) {
     const double c = cs[m], s = sn[m];
     const double p = (double)dx * c + (double)dy * s;
-    // f(p) = sum_j a_j cos(j th), th = 2 pi p / np: Clenshaw, b_k = a_k + 2 cos(th) b_{k+1} - b_{k+2}
-    const double c1 = cospi(p * inv);
-    const double c2 = 2.0 * c1;
-    double b1 = 0.0, b2 = 0.0;
-    for (int j = J; j >= 1; --j) {
-      const double b0 = fma(c2, b1, __ldg(a + j) - b2);
-      b2 = b1;
-      b1 = b0;
+    if (with_t) {
+      // f(p) = sum_j a_j cos(j th), th = 2 pi p / np: Clenshaw, b_k = a_k + 2 cos(th) b_{k+1} - b_{k+2}
+      const double c1 = cospi(p * inv);
+      const double c2 = 2.0 * c1;
+      double b1 = 0.0, b2 = 0.0;
+      for (int j = J; j >= 1; --j) {
+        const double b0 = fma(c2, b1, __ldg(a + j) - b2);
+        b2 = b1;
+        b1 = b0;
+      }
+      t += fma(-c1, b1, __ldg(a) + c2 * b1 - b2);  // b_0 - cos(th) b_1
     }
-    t += fma(-c1, b1, __ldg(a) + c2 * b1 - b2);  // b_0 - cos(th) b_1
     if (ch) {
       // s = x_j + x_l for the pair at offset (dx, dy) from the mirrored image: h(d) and h(-d)
       double sp, cp;
@@ -104,13 +108,49 @@ __global__ void k_nrm_taps(int n, int L, int np, int nt, const double *cs, const
       hm += fma(cphi, cp, -sphi * sp);  // cos(phi + pi p)
     }
   }
-  t *= kappa;
-  ct[e] = t;
-  ct[em] = t;
+  if (with_t) {
+    t *= kappa;
+    ct[e] = t;
+    ct[em] = t;
+  }
   if (ch) {
     ch[e] = hc * hp;
     ch[em] = hc * hm;
   }
+}
+
+// t for the default angles m pi / n_theta with n_theta even: t is then
+// invariant under the eight symmetries of the square (reflection: m ->
+// n_theta - m; quarter turn: m -> m + n_theta / 2, f being even), so one thread
+// per offset 0 <= ay <= ax < n sums it and writes all eight images.  Grid
+// (ceil(n / 64), n) of 64 threads: one thread per (ax, ay).
+__global__ void k_nrm_taps8(int n, int L, int np, int nt, const double *cs, const double *sn, const double *a, int J,
+                            double kappa, double *ct) {
+  const int ax = blockIdx.x * blockDim.x + threadIdx.x, ay = blockIdx.y;
+  if (ax >= n || ay > ax) return;
+  double t = 0.0;
+  const double inv = 2.0 / (double)np;
+  for (int m = 0; m < nt; ++m) {
+    const double p = (double)ax * cs[m] + (double)ay * sn[m];
+    const double c1 = cospi(p * inv);
+    const double c2 = 2.0 * c1;
+    double b1 = 0.0, b2 = 0.0;
+    for (int j = J; j >= 1; --j) {
+      const double b0 = fma(c2, b1, __ldg(a + j) - b2);
+      b2 = b1;
+      b1 = b0;
+    }
+    t += fma(-c1, b1, __ldg(a) + c2 * b1 - b2);
+  }
+  t *= kappa;
+  const int u[2] = {ax, ay};
+  for (int sw = 0; sw < 2; ++sw)
+    for (int sx = -1; sx <= 1; sx += 2)
+      for (int sy = -1; sy <= 1; sy += 2) {
+        const int dx = sx * u[sw], dy = sy * u[1 - sw];
+        const int ix = dx >= 0 ? dx : dx + L, iy = dy >= 0 ? dy : dy + L;
+        ct[(int64_t)iy * L + ix] = t;
+      }
 }
 
 // Kt = C_t / L^2; Kh = C_h e^{-2 pi i ((kx + ky)(n - 1) mod L) / L} / L^2
@@ -552,8 +592,14 @@ tomo_status build_kernel(tomo_fubini *F, int filter, cudaStream_t st) {
   TOMO_CUDA(cudaMemcpyAsync(da, a.data(), sizeof(double) * (J + 1), cudaMemcpyHostToDevice, st));
   double *ch = even ? ct + LL : nullptr;
   if (!even) TOMO_CUDA(cudaMemsetAsync(ct + LL, 0, sizeof(double) * LL, st));
+  // default angles, n_theta even: t from one octant of offsets (k_nrm_taps8)
+  const bool sym8 = F->default_angles && (nt % 2) == 0;
+  if (sym8) {
+    TOMO_CUDA(cudaMemsetAsync(ct, 0, sizeof(double) * LL, st));
+    k_nrm_taps8<<<dim3((n + 63) / 64, n), 64, 0, st>>>(n, L, np, nt, F->cs, F->sn, da, J, kappa, ct);
+  }
   k_nrm_taps<<<(unsigned)((LL + kT - 1) / kT), kT, 0, st>>>(n, L, np, nt, F->cs, F->sn, da, J, kappa, hc,
-                                                             std::cos(phi), std::sin(phi), ct, ch);
+                                                             std::cos(phi), std::sin(phi), ct, ch, !sym8);
   TOMO_CUDA(cudaGetLastError());
   int dims[2] = {L, L};
   TOMO_TRY(cufft_ok(cufftPlanMany(&pd, 2, dims, nullptr, 1, (int)LL, nullptr, 1, (int)LW, CUFFT_D2Z, 2), "plan D2Z"));
