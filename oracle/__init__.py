@@ -12,6 +12,7 @@ Function map (paper: "Sparse Matrix-Based HPC Tomography"):
   project / backproject   y = A x, x' = A^T y per slice (Sec. 3, SpMV / SpMM)
   project_mf / backproject_mf   the same without storing A
   sirt / cgls       Sec. 2.1 iterative solvers (classical SIRT, textbook CGLS)
+  cgls_mf / cgls_resume_mf      the same CGLS without storing A
   loss_grad         Sec. 2.1 model-based objective with a TV prior
   ramp_response / ramp_filter   Sec. 2.1 preconditioner P = F^dagger D^(1/2) F
                     along the detector, D a Hamming-windowed ramp
@@ -289,6 +290,36 @@ def cgls_resume(A: CSR, AT: CSR, x, r, p, gamma, frozen, iters: int):
     _load().oracle_cgls_resume(_i64(A.rows), _i64(A.cols), _p(A.row_ptr), _p(A.col), _p(A.val),
                                _p(AT.row_ptr), _p(AT.col), _p(AT.val), _i32(nz), _p(x), _p(r), _p(p),
                                _p(gamma), _p(frozen), _i32(iters), _p(hist))
+    return x, r, p, gamma, frozen, hist[:iters]
+
+
+def cgls_mf(g: Geometry, b, iters: int):
+    """cgls without a stored matrix (products generated on the fly, in the
+    stored form's summation order, so the iterates are the same bits).
+    Returns (x (nz, cols), hist (iters, nz) of ||r|| after each iteration)."""
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1, g.rows))
+    nz = b.shape[0]
+    cs, sn = g.trig()
+    x = np.zeros((nz, g.cols))
+    hist = np.zeros((max(iters, 1), nz))
+    _load().oracle_cgls_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()), _p(cs), _p(sn),
+                           _i32(g.model_id()), _i32(nz), _p(b), _p(x), _i32(iters), _p(hist))
+    return x, hist[:iters]
+
+
+def cgls_resume_mf(g: Geometry, x, r, p, gamma, frozen, iters: int):
+    """cgls_resume without a stored matrix; returns (x, r, p, gamma, frozen, hist)."""
+    x = np.ascontiguousarray(np.array(x, np.float64).reshape(-1, g.cols))
+    nz = x.shape[0]
+    r = np.ascontiguousarray(np.array(r, np.float64).reshape(nz, g.rows))
+    p = np.ascontiguousarray(np.array(p, np.float64).reshape(nz, g.cols))
+    gamma = np.ascontiguousarray(np.array(gamma, np.float64).reshape(nz))
+    frozen = np.ascontiguousarray(np.array(frozen, np.int32).reshape(nz))
+    cs, sn = g.trig()
+    hist = np.zeros((max(iters, 1), nz))
+    _load().oracle_cgls_resume_mf(_i32(g.nx), _i32(g.ny), _i32(g.n_p), _i32(g.n_theta), _dbl(g.c()), _p(cs),
+                                  _p(sn), _i32(g.model_id()), _i32(nz), _p(x), _p(r), _p(p), _p(gamma),
+                                  _p(frozen), _i32(iters), _p(hist))
     return x, r, p, gamma, frozen, hist[:iters]
 
 

@@ -347,6 +347,33 @@ static double dot(int64_t n, const double *a, const double *b) {
   return s;
 }
 
+/* The two products CGLS takes, q = A p and s = A^T r, for one slice: from the
+ * stored CSR pair, or generated on the fly (matrix-free, for geometries whose
+ * matrix does not fit in host memory).  Both forms sum every row's terms in
+ * the same order, so they give the same bits. */
+typedef struct {
+  const int64_t *arp, *trp;
+  const int32_t *aci, *tci;
+  const double *av, *tv;
+  int32_t mf, nx, ny, np_, nt, model;
+  double c;
+  const double *cs, *sn;
+} cgls_ops;
+
+static void cgls_A(const cgls_ops *o, int64_t rows, int64_t cols, const double *p, double *q) {
+  if (o->mf)
+    oracle_project_mf(o->nx, o->ny, o->np_, o->nt, o->c, o->cs, o->sn, 1, p, q, o->model);
+  else
+    oracle_spmv(rows, cols, o->arp, o->aci, o->av, 1, p, q);
+}
+
+static void cgls_AT(const cgls_ops *o, int64_t rows, int64_t cols, const double *r, double *s) {
+  if (o->mf)
+    oracle_backproject_mf(o->nx, o->ny, o->np_, o->nt, o->c, o->cs, o->sn, 1, r, s, o->model);
+  else
+    oracle_spmv(cols, rows, o->trp, o->tci, o->tv, 1, r, s);
+}
+
 /* CGLS (Sec. 2.1; Hestenes-Stiefel form for min ||A x - b||), independently per
  * slice.  One iteration from the state (x, r = b - A x, p, gamma = ||A^T r||^2):
  *   q = A p, alpha = gamma/||q||^2, x += alpha p, r -= alpha q,
@@ -355,13 +382,12 @@ static double dot(int64_t n, const double *a, const double *b) {
  * hist (nullable, iters x nz) receives ||r|| after each iteration.
  * Pinned: iterate k equals the minimiser of ||A x - b|| over the Krylov space
  * K_k(A^T A, A^T b); after rank-many steps it equals the lstsq solution. */
-static void cgls_iterate(int64_t rows, int64_t cols, const int64_t *arp, const int32_t *aci, const double *av,
-                         const int64_t *trp, const int32_t *tci, const double *tv, double *xz, double *r,
+static void cgls_iterate(const cgls_ops *o, int64_t rows, int64_t cols, double *xz, double *r,
                          double *p, double *gamma, int32_t *frozen, int32_t iters, double *hist, int32_t nz,
                          int32_t z, double *q, double *s) {
   for (int32_t it = 0; it < iters; ++it) {
     if (!*frozen) {
-      oracle_spmv(rows, cols, arp, aci, av, 1, p, q);
+      cgls_A(o, rows, cols, p, q);
       double qq = dot(rows, q, q);
       if (*gamma == 0.0 || qq == 0.0) {
         *frozen = 1;
@@ -369,7 +395,7 @@ static void cgls_iterate(int64_t rows, int64_t cols, const int64_t *arp, const i
         double alpha = *gamma / qq;
         for (int64_t j = 0; j < cols; ++j) xz[j] += alpha * p[j];
         for (int64_t i = 0; i < rows; ++i) r[i] -= alpha * q[i];
-        oracle_spmv(cols, rows, trp, tci, tv, 1, r, s);
+        cgls_AT(o, rows, cols, r, s);
         double gnew = dot(cols, s, s);
         double beta = gnew / *gamma;
         for (int64_t j = 0; j < cols; ++j) p[j] = s[j] + beta * p[j];
@@ -380,12 +406,10 @@ static void cgls_iterate(int64_t rows, int64_t cols, const int64_t *arp, const i
   }
 }
 
-/* CGLS from x0 = 0: r = b, s = A^T r, p = s, gamma = ||s||^2, then `iters`
- * iterations (see cgls_iterate). */
-void oracle_cgls(int64_t rows, int64_t cols,
-                 const int64_t *arp, const int32_t *aci, const double *av,
-                 const int64_t *trp, const int32_t *tci, const double *tv,
-                 int32_t nz, const double *b, double *x, int32_t iters, double *hist) {
+/* CGLS from x0 = 0 for every slice: r = b, s = A^T r, p = s, gamma = ||s||^2,
+ * then `iters` iterations (see cgls_iterate). */
+static void cgls_run(const cgls_ops *o, int64_t rows, int64_t cols, int32_t nz, const double *b, double *x,
+                     int32_t iters, double *hist) {
   double *r = (double *)malloc(sizeof(double) * rows);
   double *q = (double *)malloc(sizeof(double) * rows);
   double *s = (double *)malloc(sizeof(double) * cols);
@@ -394,11 +418,11 @@ void oracle_cgls(int64_t rows, int64_t cols,
     double *xz = x + (int64_t)z * cols;
     memset(xz, 0, sizeof(double) * cols);
     memcpy(r, b + (int64_t)z * rows, sizeof(double) * rows);
-    oracle_spmv(cols, rows, trp, tci, tv, 1, r, s);
+    cgls_AT(o, rows, cols, r, s);
     memcpy(p, s, sizeof(double) * cols);
     double gamma = dot(cols, s, s);
     int32_t frozen = 0;
-    cgls_iterate(rows, cols, arp, aci, av, trp, tci, tv, xz, r, p, &gamma, &frozen, iters, hist, nz, z, q, s);
+    cgls_iterate(o, rows, cols, xz, r, p, &gamma, &frozen, iters, hist, nz, z, q, s);
   }
   free(r);
   free(q);
@@ -408,18 +432,66 @@ void oracle_cgls(int64_t rows, int64_t cols,
 
 /* CGLS continued from a given state: x (nz, cols), r (nz, rows), p (nz, cols),
  * gamma (nz), frozen (nz), all updated in place by `iters` iterations. */
+static void cgls_resume_run(const cgls_ops *o, int64_t rows, int64_t cols, int32_t nz, double *x, double *r,
+                            double *p, double *gamma, int32_t *frozen, int32_t iters, double *hist) {
+  double *q = (double *)malloc(sizeof(double) * rows);
+  double *s = (double *)malloc(sizeof(double) * cols);
+  for (int32_t z = 0; z < nz; ++z)
+    cgls_iterate(o, rows, cols, x + (int64_t)z * cols, r + (int64_t)z * rows, p + (int64_t)z * cols, gamma + z,
+                 frozen + z, iters, hist, nz, z, q, s);
+  free(q);
+  free(s);
+}
+
+static cgls_ops stored_ops(const int64_t *arp, const int32_t *aci, const double *av, const int64_t *trp,
+                           const int32_t *tci, const double *tv) {
+  cgls_ops o;
+  memset(&o, 0, sizeof(o));
+  o.arp = arp; o.aci = aci; o.av = av;
+  o.trp = trp; o.tci = tci; o.tv = tv;
+  return o;
+}
+
+static cgls_ops mf_ops(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c, const double *cs,
+                       const double *sn, int32_t model) {
+  cgls_ops o;
+  memset(&o, 0, sizeof(o));
+  o.mf = 1;
+  o.nx = nx; o.ny = ny; o.np_ = np_; o.nt = nt; o.c = c; o.cs = cs; o.sn = sn; o.model = model;
+  return o;
+}
+
+void oracle_cgls(int64_t rows, int64_t cols,
+                 const int64_t *arp, const int32_t *aci, const double *av,
+                 const int64_t *trp, const int32_t *tci, const double *tv,
+                 int32_t nz, const double *b, double *x, int32_t iters, double *hist) {
+  cgls_ops o = stored_ops(arp, aci, av, trp, tci, tv);
+  cgls_run(&o, rows, cols, nz, b, x, iters, hist);
+}
+
 void oracle_cgls_resume(int64_t rows, int64_t cols,
                         const int64_t *arp, const int32_t *aci, const double *av,
                         const int64_t *trp, const int32_t *tci, const double *tv,
                         int32_t nz, double *x, double *r, double *p, double *gamma, int32_t *frozen,
                         int32_t iters, double *hist) {
-  double *q = (double *)malloc(sizeof(double) * rows);
-  double *s = (double *)malloc(sizeof(double) * cols);
-  for (int32_t z = 0; z < nz; ++z)
-    cgls_iterate(rows, cols, arp, aci, av, trp, tci, tv, x + (int64_t)z * cols, r + (int64_t)z * rows,
-                 p + (int64_t)z * cols, gamma + z, frozen + z, iters, hist, nz, z, q, s);
-  free(q);
-  free(s);
+  cgls_ops o = stored_ops(arp, aci, av, trp, tci, tv);
+  cgls_resume_run(&o, rows, cols, nz, x, r, p, gamma, frozen, iters, hist);
+}
+
+/* The same two CGLS calls with the matrix-free projector pair: the iterates
+ * equal those of the stored form bit for bit. */
+void oracle_cgls_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c, const double *cs,
+                    const double *sn, int32_t model, int32_t nz, const double *b, double *x, int32_t iters,
+                    double *hist) {
+  cgls_ops o = mf_ops(nx, ny, np_, nt, c, cs, sn, model);
+  cgls_run(&o, (int64_t)nt * np_, (int64_t)nx * ny, nz, b, x, iters, hist);
+}
+
+void oracle_cgls_resume_mf(int32_t nx, int32_t ny, int32_t np_, int32_t nt, double c, const double *cs,
+                           const double *sn, int32_t model, int32_t nz, double *x, double *r, double *p,
+                           double *gamma, int32_t *frozen, int32_t iters, double *hist) {
+  cgls_ops o = mf_ops(nx, ny, np_, nt, c, cs, sn, model);
+  cgls_resume_run(&o, (int64_t)nt * np_, (int64_t)nx * ny, nz, x, r, p, gamma, frozen, iters, hist);
 }
 
 /* TV term of the model-based objective: adds mu * sum sqrt(Dx^2 + Dy^2 + eps^2)
