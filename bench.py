@@ -1,17 +1,26 @@
 #!/usr/bin/env python
-"""Throughput of batched projection + backprojection inside SIRT.
+"""Throughput of batched projection + backprojection inside the iterative solvers.
 
-Workload (default): 64 slices of 512x512 pixels, 360 angles over [0, pi), 512
-detector bins; seeded random-ellipsoid phantom with analytic projections and
-Poisson noise at 1e4 photons/ray; SIRT, 100 iterations per solve.  One step is
-one full SIRT solve of the 64-slice batch (interleave, 100 iterations of the
-fused A / A^T passes replayed from a CUDA graph, de-interleave).  The matrix is
-built once before timing (its build time is reported separately).
+Workload (default, cgls_2048x1024_b16): 16 slices of 2048x2048 pixels, 1024
+angles over [0, pi), 2048 detector bins; a seeded random-ellipsoid phantom with
+analytic projections and 5% Gaussian noise; CGLS, 50 iterations per solve,
+matrix values in BF16 with 16-bit column offsets (4.25 bytes per nonzero),
+FP32 vectors and accumulation, FP64 dots and step scalars, the residual
+recomputed every 10 iterations.  One step is one full CGLS solve of the
+16-slice batch (interleave, 50 iterations replayed from CUDA graphs,
+de-interleave).  The matrix is built once before timing (its build time is
+reported separately).  `--workload sirt_512x360_b64` gives the SIRT line:
+64 slices of 512x512, 360 angles, Poisson noise at 1e4 photons/ray, SIRT 100.
 
 Metric: slice-iterations per second (one slice-iteration = one application of
-A and of A^T to one slice plus the SIRT update), summed over all ranks.
+A and of A^T to one slice plus the solver update), summed over all ranks.
 
-Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+The line also carries the roofline of the dominant SpMM pass, the plain FP32
+CSR SpMV comparator, the end-to-end rate with host copies, the CPU oracle as a
+baseline and (CGLS) the iterations each form needs to reach the FP64 oracle's
+50-iteration data fit.
+
+Run: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 Multi-GPU: one process per GPU (torchrun); every rank solves its own batch
 (weak scaling, no collective on the data path).
 """
@@ -34,6 +43,8 @@ METRIC = "proj+backproj slice-iters/s"
 UNIT = "slice-iters/s"
 DATA = ("synthetic: seeded random ellipsoids (16 per volume), analytic line integrals, "
         "Poisson noise at 1e4 photons/ray")
+DATA_OF = {"sirt": DATA,
+           "cgls": "synthetic: seeded random ellipsoids (16 per volume), analytic line integrals, 5% Gaussian noise"}
 
 
 def parse():
@@ -42,12 +53,21 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="sirt_512x360_b64")
+    p.add_argument("--workload", default="cgls_2048x1024_b16")
     p.add_argument("--batch-width", type=int, default=0, help="0 = autotuned")
     p.add_argument("--format", default="auto", choices=["auto", "sell", "sell16", "csr"],
-                   help="matrix storage streamed by the kernels (auto = autotuned over FP32 formats)")
+                   help="matrix storage streamed by the kernels (auto: the workload's 16-bit form for CGLS, "
+                        "autotuned over FP32 formats for SIRT)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip e2e / plain-CSR legs")
+    p.add_argument("--col-blocks", type=int, default=-1,
+                   help="16-bit A stored as this many bands of image rows (-1: enough bands that one band of "
+                        "the gathered image batch fits in 48 MB of L2)")
+    p.add_argument("--order", default="auto", choices=["auto", "rows", "tiles"],
+                   help="row-group order of the A^T passes (same bits, different speed)")
+    p.add_argument("--no-csr", action="store_true",
+                   help="CGLS: build without the FP32 CSR pair (implies --no-extras: the comparators and the "
+                        "accuracy leg need it); for hardware-counter captures in a few GB")
     p.add_argument("--iters", type=int, default=0, help="override the solver iterations (profiling runs)")
     p.add_argument("--no-graph", action="store_true", help="launch kernels directly (profiling runs)")
     p.add_argument("--model", default="line", choices=["line", "strip"],
@@ -162,6 +182,77 @@ def oracle_sample(w, slices=1, iters=1, steps=1, warmup=0, model="line"):
             "seconds": dt}
 
 
+def oracle_sample_cgls(w, angle_stride=1, steps=1, warmup=0):
+    """The oracle's matrix-free CGLS (its stored matrix would not fit in host
+    memory at this size) timed on one slice: each step is one CGLS iteration
+    (A p, A^T r and the vector updates) over every angle_stride-th angle of the
+    workload, i.e. 1/angle_stride of a slice-iteration."""
+    import numpy as np
+    import oracle
+    from paper_2003_12677_b300 import inputs
+    th = np.arange(w.n_theta) * math.pi / w.n_theta
+    sel = np.arange(0, w.n_theta, angle_stride)
+    g = oracle.Geometry(w.n, w.n, w.n, len(sel), angles=th[sel] if angle_stride > 1 else None)
+    case = inputs.workload_case(w.name, slices=[0])
+    b = case.sino.reshape(w.n_theta, w.n)[sel].reshape(1, -1).astype(np.float64)
+    p = case.phantom.reshape(1, -1).astype(np.float64)       # any search direction costs the same
+    state = [np.zeros_like(p), b, p, np.ones(1), np.zeros(1, np.int32)]
+    for _ in range(warmup):
+        oracle.cgls_resume_mf(g, *state, 1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.cgls_resume_mf(g, *state, 1)
+    dt = time.perf_counter() - t0
+    share = len(sel) / w.n_theta
+    return {"value": steps * share / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d step(s) of one matrix-free FP64 CGLS iteration of slice 0 of the %s workload over %d of "
+                      "its %d angles (%.3g slice-iterations per step)" % (steps, w.name, len(sel), w.n_theta, share),
+            "seconds": dt}
+
+
+def oracle_sample_gd(w, slices=1):
+    """The oracle's matrix-free loss and gradient (one projection and one
+    backprojection per slice: one slice-iteration) timed on a bounded sample."""
+    import numpy as np
+    import oracle
+    from paper_2003_12677_b300 import inputs
+    g = oracle.Geometry(w.n, w.n, w.n, w.n_theta)
+    case = inputs.workload_case(w.name, slices=list(range(slices)))
+    x = np.zeros((slices, g.cols))
+    b = case.sino.reshape(slices, -1)
+    t0 = time.perf_counter()
+    oracle.loss_grad_mf(g, x, b)
+    dt = time.perf_counter() - t0
+    return {"value": slices / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d slice(s) x one matrix-free FP64 loss-and-gradient evaluation (A x, A^T r, TV) of the %s "
+                      "workload" % (slices, w.name), "seconds": dt}
+
+
+def oracle_sample_uneven(reqs):
+    """The oracle's matrix-free CGLS, one iteration of the first slice of one
+    request of each image size in the batch (its per-slice work spans 64x)."""
+    import numpy as np
+    import oracle
+    from paper_2003_12677_b300 import inputs
+    picks = {}
+    for r in reqs:
+        picks.setdefault(r.n, r)
+    t, done = 0.0, []
+    for n in sorted(picks):
+        r = picks[n]
+        g = oracle.Geometry(r.n, r.n, r.n, r.n_theta)
+        b = inputs.make_case(r.n, r.n_theta, 1, r.seed, "ellipses2d", "poisson", 1e5).sino.reshape(1, -1)
+        p = np.ones((1, g.cols))
+        state = [np.zeros((1, g.cols)), b.astype(np.float64), p, np.ones(1), np.zeros(1, np.int32)]
+        t0 = time.perf_counter()
+        oracle.cgls_resume_mf(g, *state, 1)
+        t += time.perf_counter() - t0
+        done.append("%dx%d" % (r.n, r.n_theta))
+    return {"value": len(done) / t, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "one matrix-free FP64 CGLS iteration of one slice of one request per image size (%s); the "
+                      "batch's per-slice work varies with the size" % ", ".join(done), "seconds": t}
+
+
 def oracle_sample_bb(w, slices, iters):
     """The oracle's BB-SIRT (Sec. 3.1) timed on a bounded sample of the workload."""
     import oracle
@@ -252,11 +343,18 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    res = oracle_sample(w, slices=4, iters=2, steps=args.steps, warmup=args.warmup, model=args.model)
+    if w.solver == "cgls":
+        # a whole CGLS iteration of one slice takes ~20 s on 16 host cores, so each
+        # step samples one eighth of its angles
+        res = oracle_sample_cgls(w, angle_stride=8, steps=args.steps, warmup=args.warmup)
+        cfg = workload_config(w, min(16, w.n_z), "sell16" if w.values != "f32" else "sell", args.model)
+    else:
+        res = oracle_sample(w, slices=4, iters=2, steps=args.steps, warmup=args.warmup, model=args.model)
+        cfg = workload_config(w, 0, "sell", args.model)
     line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * res["seconds"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": DATA, "config": workload_config(w, 0, "sell", args.model),
+            "data": DATA_OF.get(w.solver, DATA), "config": cfg,
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -357,6 +455,25 @@ def run_alternate(args, w):
                                 "workspace_bytes": ws["ws"].numel(),
                                 "device_bytes_in_use": torch.cuda.mem_get_info()[1] - torch.cuda.mem_get_info()[0]},
                      "clocks": clk, "build_s": build_s, "gpu_launches": args.steps})
+        # roofline of the persistent launch over its algorithmic bytes: per
+        # iteration and packed batch of 16 slices, both 16-bit matrices once
+        # (4.25 B/nnz) and the CGLS vectors (q, r, p, s, x streams of 4 B)
+        per_geo = {}
+        for r in reqs:
+            per_geo[(r.n, r.n_theta)] = per_geo.get((r.n, r.n_theta), 0) + r.n_z
+        alg = 0.0
+        for g, nzs in per_geo.items():
+            M_ = mats[g]
+            batches = math.ceil(nzs / 16)
+            alg += iters * batches * (2 * M_.nnz * 4.25 + (5 * M_.rows + 7 * M_.cols) * 16 * 4)
+        peak, src = measured_peaks()
+        ach = alg / (ms / 1000.0) / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": "k_cgls_persistent<16, SELL16> (the whole batched solve)",
+                            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                            "peak_source": src + " (burst copy)", "alg_bytes_per_launch": alg,
+                            "avg_launch_ms": ms}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample_uneven(reqs)
         print(json.dumps(line))
         return 0
 
@@ -528,42 +645,6 @@ def run_alternate(args, w):
             line["cpu_baseline"] = oracle_sample_bb(w, slices=8, iters=20)
         print(json.dumps(line))
         return 0
-    if w.solver == "cgls":
-        fmt = args.format if args.format != "auto" else "sell16"
-        t0 = time.perf_counter()
-        M = tomo.Matrix(w.n, w.n_theta, values=w.values, fp32_sell=False)
-        torch.cuda.synchronize()
-        build_s = time.perf_counter() - t0
-        B = args.batch_width or 16
-        iters = args.iters or w.iters
-        x = torch.empty((w.n_z, w.n, w.n), device="cuda")
-        wsb = torch.empty(M.workspace_size(3, w.n_z, B, fmt), dtype=torch.uint8, device="cuda")
-
-        def step():
-            tomo.cgls(M, sino, iters, recompute_every=10, batch_width=B, fmt=fmt, out=x, workspace=wsb)
-
-        ms, clk = _timed(step, args.steps, args.warmup)
-        value = w.n_z * iters / (ms / 1000.0)
-        # FP32 comparators on the same GPU: CSR at the same width, and the plain SpMV form
-        xc = torch.empty_like(x)
-        wsc = torch.empty(M.workspace_size(3, w.n_z, B, "csr"), dtype=torch.uint8, device="cuda")
-        mc, _ = _timed(lambda: tomo.cgls(M, sino, 5, batch_width=B, fmt="csr", out=xc, workspace=wsc), 1, 1)
-        x1 = torch.empty((1, w.n, w.n), device="cuda")
-        ws1 = torch.empty(M.workspace_size(3, 1, 1, "csr"), dtype=torch.uint8, device="cuda")
-        m1, _ = _timed(lambda: tomo.cgls(M, sino[:1].contiguous(), 3, batch_width=1, fmt="csr", out=x1, workspace=ws1),
-                       1, 1)
-        line.update({"value": value, "ms_per_step": ms, "dtype": "f32-accumulate/%s-values" % w.values,
-                     "data": "synthetic: seeded random ellipsoids, analytic line integrals, 5% Gaussian noise",
-                     "config": {"workload": w.name, "n": w.n, "n_theta": w.n_theta, "slices": w.n_z, "iters": iters,
-                                "solver": "cgls, residual recomputed every 10", "batch_width": B, "format": fmt},
-                     "clocks": clk, "build_s": build_s, "nnz": M.nnz,
-                     "fp32_csr_same_width": {"value": w.n_z * 5 / (mc / 1000.0), "unit": UNIT},
-                     "plain_f32_csr": {"value": 3 / (m1 / 1000.0), "unit": UNIT,
-                                       "form": "FP32 CSR SpMV (batch width 1, warp per row)"}})
-        line["speedup_vs_plain_f32_csr"] = value / line["plain_f32_csr"]["value"]
-        print(json.dumps(line))
-        return 0
-
     # gradient descent on ||A x - b||^2 + mu TV(x) through the autograd Function
     t0 = time.perf_counter()
     M = tomo.Matrix(w.n, w.n_theta)
@@ -598,6 +679,18 @@ def run_alternate(args, w):
                             "solver": "gradient descent on ||Ax-b||^2 + 1e-3 TV through torch.autograd",
                             "batch_width": B, "format": "sell", "step": eta},
                  "clocks": clk, "build_s": build_s, "nnz": M.nnz})
+    # roofline of the dominant SpMM pass: the autograd step runs one projection
+    # (forward) and one backprojection (backward) per iteration, the same
+    # kernels as this timed pair on the same batch
+    tm = tomo.new_timing()
+    yy = tomo.project(M, x, batch_width=B, timing=tm)
+    tomo.backproject(M, yy, batch_width=B, timing=tm)
+    line["roofline"], line["ceilings"] = spmm_roofline(
+        M, B, "sell", tm, [("k_spmm_%s<%d, EpiStore> (A pass, forward)", 1),
+                           ("k_spmm_%s<%d, EpiStore> (A^T pass, backward)", 1)], torch, torch.cuda.current_device(), clk)
+    line["gpu_launches"] = args.steps * iters * 2 * (3 * math.ceil(w.n_z / B)) + args.steps * iters
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample_gd(w, slices=1)
     print(json.dumps(line))
     return 0
 
@@ -648,22 +741,82 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def main():
-    args = parse()
-    from paper_2003_12677_b300 import inputs
-    w = inputs.WORKLOADS[args.workload]
-    if args.iters:
-        import dataclasses
-        w = dataclasses.replace(w, iters=args.iters)
-    if args.impl == "reference":
-        return run_reference(args, w)
+def kernel_names(solver, fmt, B):
+    """(name template, output vectors read or written per output row and slice) of the
+    A pass (kind 0) and the A^T pass (kind 1) of a solver's iteration."""
+    if solver == "sirt":   # r = R o (b - A x): b read, r written; x += lam C o A^T r: x read + written
+        return [("k_spmm_%s<%d, EpiSirtResidual> (A pass)", 2),
+                ("k_spmm_%s<%d, EpiSirtUpdate> (A^T pass)", 2)]
+    # CGLS: q = A p and s = A^T r, each written once with its squared norm
+    return [("k_spmm_%s<%d, EpiStoreNorm> (A pass, q = A p)", 1),
+            ("k_spmm_%s<%d, EpiStoreNorm> (A^T pass, s = A^T r)", 1)]
 
+
+def golden_fit(w):
+    """The oracle's stored data-fit history of slice 0 (tests/golden), if any."""
+    path = os.path.join(ROOT, "tests", "golden", "%s_slice0.json" % w.name.rsplit("_", 1)[0])
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+def accuracy_leg(tomo, torch, M, w, sino, B, fmt, rate, plain_rate, max_iters=90):
+    """Iterations each form needs to reach the FP64 oracle's 50-iteration data
+    fit ||b - A x_50|| of slice 0 (stored by tests/golden/make_cgls_2048.py),
+    to 1e-4: the benchmarked batch (slice 0 of it) and the plain FP32 CSR
+    SpMV form.  The data fit of every GPU iterate is tomo_residual_norm (FP64
+    accumulation).  CGLS iterates are not reproducible one by one past the
+    first few in any precision (FP32 runs lag the FP64 one by a few
+    iterations), so the forms are compared at equal data fit."""
+    gold = golden_fit(w)
+    if gold is None:
+        return {"error": "no stored oracle data fit for %s" % w.name}
+    k50 = 50
+    target = gold["resnorm"][k50 - 1] * (1 + 1e-4)
+    b0 = sino[:1].contiguous()
+    rws = M._workspace(5, 1, 0, "sell")
+    idx = torch.tensor(gold["sample_index"], device="cuda", dtype=torch.int64)
+
+    def walk(sino_in, bw, f, recompute):
+        x, st = tomo.cgls(M, sino_in, 0, batch_width=bw, fmt=f, return_state=True)
+        fits, samples = [], {}
+        for k in range(1, max_iters + 1):
+            rc = recompute if (recompute and k % 10 == 0) else 0
+            x, st = tomo.cgls(M, sino_in, 1, recompute_every=rc, batch_width=bw, fmt=f, resume=st,
+                              return_state=True)
+            fit = float(tomo.residual_norm(M, b0, x[:1].contiguous(), workspace=rws)[0])
+            fits.append(fit)
+            if str(k) in gold.get("samples", {}):
+                ref = torch.tensor([float(v) for v in gold["samples"][str(k)]], device="cuda", dtype=torch.float64)
+                got = x[0].reshape(-1)[idx].double()
+                samples[str(k)] = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+            if fit <= target and k >= k50:
+                return k, fits, samples
+        return None, fits, samples
+
+    k_b, fits_b, samp_b = walk(sino, B, fmt, 1)          # the benchmarked batch and form (recompute every 10)
+    k_p, fits_p, samp_p = walk(b0, 1, "csr", 0)          # the plain FP32 CSR SpMV form, one slice
+    out = {"target": "FP64 oracle's data fit ||b - A x_50|| of slice 0, to 1e-4 (matrix-free oracle, stored)",
+           "target_fit": target, "oracle_fit_by_iter": {str(k): gold["resnorm"][k - 1] for k in (1, 10, 25, 50)},
+           "iters_to_target": {"%s_b%d" % (fmt, B): k_b, "plain_f32_csr": k_p},
+           "fit_at_50": {"%s_b%d" % (fmt, B): fits_b[k50 - 1] if len(fits_b) >= k50 else None,
+                         "plain_f32_csr": fits_p[k50 - 1] if len(fits_p) >= k50 else None},
+           "first_iterates_rel_l2_sampled": {"%s_b%d" % (fmt, B): samp_b, "plain_f32_csr": samp_p,
+                                             "pixels": len(gold["sample_index"])}}
+    if k_b and k_p:
+        t_b, t_p = k_b / rate, k_p / plain_rate
+        out["seconds_per_slice_to_target"] = {"%s_b%d" % (fmt, B): t_b, "plain_f32_csr": t_p}
+        out["speedup_at_same_accuracy"] = t_p / t_b
+    return out
+
+
+def run_main(args, w):
+    """SIRT or CGLS over the workload's slice batch: the metric line."""
     import torch
     import torch.distributed as dist
     import paper_2003_12677_b300 as tomo
-
-    if w.solver != "sirt" or args.workload == "uneven_256":
-        return run_alternate(args, w)
+    from paper_2003_12677_b300 import inputs
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -674,15 +827,34 @@ def main():
         if world > 1:
             dist.barrier()
 
+    cgls = w.solver == "cgls"
+    tomo.set_launch(order=args.order)
     fmt = args.format
+    if cgls and fmt == "auto":
+        fmt = "sell16" if w.values != "f32" else "sell"
     values = (w.values if w.values != "f32" else "bf16") if fmt == "sell16" else "f32"
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    M = tomo.Matrix(w.n, w.n_theta, values=values, model=args.model)
+    if cgls:   # the 16-bit pair streamed by the solve, the FP32 CSR pair for the comparators and the data fit
+        if args.no_csr:
+            args.no_extras = True
+        bw = args.batch_width or min(16, w.n_z)
+        bands = args.col_blocks if args.col_blocks >= 0 else (
+            max(1, math.ceil(w.n * w.n * bw * 4 / (48 << 20))) if fmt == "sell16" else 0)
+        M = tomo.Matrix(w.n, w.n_theta, values=values, fp32_sell=fmt == "sell", keep_csr=not args.no_csr,
+                        model=args.model, col_blocks=min(bands, 64, w.n) if fmt == "sell16" else 0)
+    else:
+        M = tomo.Matrix(w.n, w.n_theta, values=values, model=args.model)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     tune = None
-    if args.batch_width == 0 or fmt == "auto":
+    if cgls:
+        if fmt == "sell16" and args.batch_width == 0:
+            tune = M.autotune(w.n_z, allow_16bit="only")   # the workload's 16-bit values
+            B = tune["batch_width"]
+        else:
+            B = args.batch_width or min(16, w.n_z)
+    elif args.batch_width == 0 or fmt == "auto":
         tune = M.autotune(w.n_z)
         B = args.batch_width or tune["batch_width"]
         if fmt == "auto":
@@ -693,12 +865,21 @@ def main():
     case = inputs.workload_case(args.workload)
     sino = torch.from_numpy(case.sino).cuda()
     x = torch.zeros((w.n_z, w.n, w.n), device="cuda")
-    wsb = torch.empty(M.workspace_size(2, w.n_z, B, fmt), dtype=torch.uint8, device="cuda")
-
+    op = 3 if cgls else 2
+    wsb = torch.empty(M.workspace_size(op, w.n_z, B, fmt), dtype=torch.uint8, device="cuda")
     graph = not args.no_graph
+    recompute = 10 if cgls else 0
+
+    def solve(sn, out, timing=None):
+        if cgls:
+            tomo.cgls(M, sn, w.iters, recompute_every=recompute, batch_width=B, fmt=fmt, out=out, workspace=wsb,
+                      use_graph=graph, timing=timing)
+        else:
+            tomo.sirt(M, sn, w.iters, batch_width=B, fmt=fmt, out=out, workspace=wsb, use_graph=graph,
+                      timing=timing)
 
     def step():
-        tomo.sirt(M, sino, w.iters, batch_width=B, fmt=fmt, out=x, workspace=wsb, use_graph=graph)
+        solve(sino, x)
 
     for _ in range(args.warmup):
         step()
@@ -725,63 +906,54 @@ def main():
     units_per_step = world * w.n_z * w.iters
     value = units_per_step / (ms / 1000.0)
 
+    dtype = "f32" if fmt != "sell16" else "f32-accumulate/%s-values" % values
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if fmt != "sell16" else "f32-accumulate/%s-values" % values,
-            "data": DATA, "config": workload_config(w, B, fmt, args.model), "clocks": clk,
-            "build_s": build_s, "nnz": M.nnz}
+            "vs_baseline": None, "dtype": dtype, "data": DATA_OF[w.solver],
+            "config": workload_config(w, B, fmt, args.model), "clocks": clk, "build_s": build_s, "nnz": M.nnz}
+    if cgls:
+        line["config"]["solver"] = "cgls, FP64 dots and step scalars, residual recomputed every %d" % recompute
+        if fmt == "sell16":
+            line["config"]["col_blocks"] = min(bands, 64, w.n)
     if tune is not None:
-        line["autotune"] = {"chosen": [tune["batch_width"], tune["format"]],
-                            "table": [[t["batch_width"], t["format"], round(t["slice_iters_per_s"])]
-                                      for t in tune["table"]]}
+        line["autotune"] = {"chosen": [tune["batch_width"], tune["format"], tune["order"], tune["blocks_per_sm"]],
+                            "columns": ["batch_width", "format", "A^T order", "blocks per SM (0 = all)",
+                                        "slice-iters/s of a SIRT pair"],
+                            "table": [[t["batch_width"], t["format"], t["order"], t["blocks_per_sm"],
+                                       round(t["slice_iters_per_s"])] for t in tune["table"]]}
 
     # per-kernel device time of one extra solve (CUDA events around every launch)
     tm = tomo.new_timing()
-    tomo.sirt(M, sino, w.iters, batch_width=B, fmt=fmt, out=x, workspace=wsb, timing=tm)
+    solve(sino, x, tm)
     launches = int(sum(tm.launches[k] for k in range(3)))
     line["gpu_launches"] = launches * args.steps
+    tot = sum(tm.ms[k] for k in range(3))
+    line["time_split"] = {"A": tm.ms[0] / tot, "A^T": tm.ms[1] / tot, "vector+scalar": tm.ms[2] / tot}
+    kinds = kernel_names(w.solver, fmt, B)
+    roof, ceil = spmm_roofline(M, B, fmt, tm, kinds, torch, local, clk)
     kind = 0 if tm.ms[0] >= tm.ms[1] else 1
-    avg_ms = tm.ms[kind] / max(tm.launches[kind], 1)
-    rows, cols, nnz = M.rows, M.cols, M.nnz
-    bnnz = 4.25 if fmt == "sell16" else 8
-    mat_bytes = (rows + 1 if kind == 0 else cols + 1) * 8 + nnz * bnnz
-    if kind == 0:   # r = R o (b - A x): matrix, x gathered once, b, R, r
-        vec_bytes = cols * B * 4 + 2 * rows * B * 4 + rows * 4
-        kname = "k_spmm_%s<%d, EpiSirtResidual> (A pass)" % (KERNEL[fmt], B)
-    else:           # x += lambda C o A^T r: matrix, r gathered once, x read+write, C
-        vec_bytes = rows * B * 4 + 2 * cols * B * 4 + cols * 4
-        kname = "k_spmm_%s<%d, EpiSirtUpdate> (A^T pass)" % (KERNEL[fmt], B)
-    alg = mat_bytes + vec_bytes
-    peak, src = measured_peaks()
-    achieved = alg / (avg_ms / 1000.0) / 1e9
-    traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
         key = "%s/B%d/%s/k%d" % (w.name, B, fmt, kind)
-        if tj.get("kernel_hash") == kernel_hash() and key in tj.get("per_launch_bytes", {}):
-            traffic = tj["per_launch_bytes"][key]
-    line["roofline"] = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": traffic, "peak_source": src + " (burst copy)",
-                        "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
-                        "kernel_share": tm.ms[kind] / max(sum(tm.ms[k] for k in range(3)), 1e-12)}
-    # the two on-chip ceilings beside HBM: gathered-operand delivery (each
-    # nonzero brings B*4 bytes of the gathered vector row through L1, at most
-    # 128 B per clock per SM) and FP32 FMA (2 flops per nonzero per slice)
+        if key in tj.get("per_launch_bytes", {}):
+            if tj.get("kernel_hash") == kernel_hash():
+                roof["traffic"] = tj["per_launch_bytes"][key]
+            else:
+                sys.stderr.write("bench: stored DRAM counters (profiles/traffic.json) predate the current SpMM "
+                                 "sources: roofline traffic reported as null\n")
+                roof["traffic_note"] = "stored DRAM counters predate the current kernels"
+    line["roofline"] = roof
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = (clk or {}).get("sm_mhz") or 2032.0
-    gathered = nnz * B * 4
-    line["ceilings"] = {
-        "operand_delivery": {"achieved": gathered / (avg_ms / 1000.0) / 1e9, "unit": "GB/s",
-                             "peak": sms * 128 * mhz * 1e6 / 1e9, "bytes_per_launch": gathered,
-                             "peak_source": "128 B/clk/SM x %d SMs x median SM clock" % sms},
-        "fma": {"achieved": 2.0 * nnz * B / (avg_ms / 1000.0) / 1e12, "unit": "TFLOP/s",
-                "peak": sms * 128 * 2 * mhz * 1e6 / 1e12, "peak_source": "128 FP32 FMA/clk/SM"}}
-    for c in line["ceilings"].values():
-        c["frac"] = c["achieved"] / c["peak"]
-    step_bytes = w.iters * ((rows + cols + 2) * 8 + 2 * nnz * bnnz
-                            + (3 * rows + 3 * cols) * B * 4) * math.ceil(w.n_z / B)
+    ceil["fma"] = {"achieved": 2.0 * M.nnz * B / (roof["avg_launch_ms"] / 1000.0) / 1e12, "unit": "TFLOP/s",
+                   "peak": sms * 128 * 2 * mhz * 1e6 / 1e12, "peak_source": "128 FP32 FMA/clk/SM"}
+    ceil["fma"]["frac"] = ceil["fma"]["achieved"] / ceil["fma"]["peak"]
+    line["ceilings"] = ceil
+    bnnz = 4.25 if fmt == "sell16" else 8
+    vec = (3 * M.rows + 3 * M.cols) if not cgls else (5 * M.rows + 7 * M.cols)
+    step_bytes = w.iters * ((M.rows + M.cols + 2) * 8 + 2 * M.nnz * bnnz + vec * B * 4) * math.ceil(w.n_z / B)
     line["hbm_gbs_step"] = step_bytes / (ms / 1000.0) / 1e9
 
     if not args.no_extras:
@@ -792,7 +964,7 @@ def main():
 
         def e2e_step():
             sd.copy_(sino_h, non_blocking=True)
-            tomo.sirt(M, sd, w.iters, batch_width=B, fmt=fmt, out=x, workspace=wsb)
+            solve(sd, x)
             x_h.copy_(x, non_blocking=True)
 
         e2e_step()
@@ -808,29 +980,43 @@ def main():
                        "ms_per_step": ems}
 
         # the plain FP32 CSR SpMV form (one slice per pass) on the same GPU
-        nzp, itp = 4, 10
+        nzp, itp = (1, 5) if cgls else (4, 10)
         xp = torch.zeros((nzp, w.n, w.n), device="cuda")
-        wsp = torch.empty(M.workspace_size(2, nzp, 1, "csr"), dtype=torch.uint8, device="cuda")
         sp = sino[:nzp].contiguous()
-        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp, fmt="csr")
+        wsp = torch.empty(M.workspace_size(op, nzp, 1, "csr"), dtype=torch.uint8, device="cuda")
+
+        def plain():
+            if cgls:
+                tomo.cgls(M, sp, itp, batch_width=1, out=xp, workspace=wsp, fmt="csr")
+            else:
+                tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp, fmt="csr")
+
+        plain()
         torch.cuda.synchronize()
         e0.record()
-        tomo.sirt(M, sp, itp, batch_width=1, out=xp, workspace=wsp, fmt="csr")
+        plain()
         e1.record()
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1)
         line["plain_f32_csr"] = {"value": world * nzp * itp / (pms / 1000.0), "unit": UNIT,
                                  "form": "FP32 CSR SpMV (batch width 1, warp per row)",
-                                 "sample": "%d slices x %d SIRT iterations" % (nzp, itp)}
+                                 "sample": "%d slice(s) x %d %s iterations" % (nzp, itp, w.solver.upper())}
         line["speedup_vs_plain_f32_csr"] = value / line["plain_f32_csr"]["value"]
-        try:
-            line["cusparse_f32_csr"] = cusparse_leg(M, B, torch)
-        except Exception as e:  # context only, never fatal for the GPU number
-            line["cusparse_f32_csr"] = {"error": str(e)}
+        if cgls and rank == 0:
+            line["accuracy"] = accuracy_leg(tomo, torch, M, w, sino, B, fmt, value / world,
+                                            line["plain_f32_csr"]["value"] / world)
+        if not cgls:
+            try:
+                line["cusparse_f32_csr"] = cusparse_leg(M, B, torch)
+            except Exception as e:  # context only, never fatal for the GPU number
+                line["cusparse_f32_csr"] = {"error": str(e)}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = oracle_sample(w, slices=8, iters=48, steps=1, model=args.model)
+            if cgls:
+                line["cpu_baseline"] = oracle_sample_cgls(w, angle_stride=1)
+            else:
+                line["cpu_baseline"] = oracle_sample(w, slices=8, iters=48, steps=1, model=args.model)
         except Exception as e:  # reported, never fatal for the GPU number
             line["cpu_baseline"] = {"error": str(e)}
 
@@ -839,6 +1025,20 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def main():
+    args = parse()
+    from paper_2003_12677_b300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    if args.iters:
+        import dataclasses
+        w = dataclasses.replace(w, iters=args.iters)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    if w.solver in ("sirt", "cgls") and args.workload != "uneven_256":
+        return run_main(args, w)
+    return run_alternate(args, w)
 
 
 if __name__ == "__main__":

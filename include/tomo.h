@@ -95,7 +95,13 @@ typedef struct {
                             per operand); export calls and TOMO_FMT_CSR then report UNSUPPORTED.
                             Needs at least one SELL form. */
   int32_t model;         /* tomo_model (default TOMO_MODEL_LINE) */
-  int32_t reserved[4];
+  int32_t col_blocks;    /* 16-bit values only: store the 16-bit A as this many column bands (bands of
+                            consecutive image rows, each its own 16-bit SELL-32 matrix) instead of one;
+                            a projection then runs one pass per band and adds the bands' partial sums
+                            in a workspace buffer, so that each pass gathers only its band of the image
+                            (which can stay in L2 when the whole image stack cannot).  0 or 1: one band;
+                            at most min(64, n_y).  tomo_cgls_batched rejects banded matrices. */
+  int32_t reserved[3];
 } tomo_matrix_opts;
 
 /* Device time of the kernels one call launched, filled when a call is given
@@ -132,7 +138,19 @@ typedef struct {
                           synchronising; the launch's device status then goes to the stream's
                           status word (tomo_stream_status).  Sinograms, tomograms, states and
                           the workspace must stay valid until the stream passes the launch. */
-  int32_t reserved[2];
+  int32_t recompute_fp32; /* tomo_cgls / tomo_cgls_resume with TOMO_FMT_SELL16: non-zero computes
+                          the periodic residual r = b - A x with the FP32 values of A (the FP32
+                          SELL form when built, else CSR) instead of the 16-bit ones */
+  int32_t order;       /* order in which the SELL A^T passes visit their rows (pixels): 0 = auto
+                          (image tiles when the gathered sinogram batch exceeds 64 MB, else row
+                          order), 1 = row order, 2 = image tiles (blocks of 8 image rows, tiles of
+                          128 rows, so a block's rays share sinogram rows in L1 and a tile's stay
+                          in L2).  The results are the same bits either way.  After
+                          tomo_autotune for this slice count, 0 selects the tuned order. */
+  int32_t blocks_per_sm; /* resident blocks per SM the SpMM launches use: 0 = all that fit (or the
+                          tuned count after tomo_autotune for this slice count), else at most this
+                          many.  The results are the same bits either way. */
+  int32_t reserved[3];
 } tomo_exec_opts;
 
 typedef struct tomo_matrix tomo_matrix; /* opaque, immutable after build */
@@ -152,7 +170,8 @@ typedef enum {
   TOMO_OP_BACKPROJECT = 1,
   TOMO_OP_SIRT = 2,
   TOMO_OP_CGLS = 3,
-  TOMO_OP_SIRT_BB = 4
+  TOMO_OP_SIRT_BB = 4,
+  TOMO_OP_RESIDUAL = 5
 } tomo_op;
 
 /* Build A and A^T on the current device (Sec. 3.1: entries generated from the
@@ -226,12 +245,28 @@ TOMO_API tomo_status tomo_sirt(const tomo_matrix *A, const float *sino, float *x
 /* CGLS (Sec. 2.1) for min ||A x - b|| per slice from x0 = 0: vectors FP32,
  * inner products, norms and the step scalars alpha / beta in FP64 on the
  * device.  Every `recompute_every` iterations (0 = never) the residual is
- * recomputed as r = b - A x.  A slice whose ||s||^2 or ||q||^2 reaches 0 stops
+ * recomputed as r = b - A x (with the format's own values, or with the FP32
+ * ones when opts->recompute_fp32 is set).  A slice whose ||s||^2 or ||q||^2 reaches 0 stops
  * changing.  resnorm_hist (DEVICE, nullable) receives ||r|| per iteration and
  * slice, laid out (iters, n_z).  x: (n_z, n_y, n_x) output. */
 TOMO_API tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x, int32_t n_z, int32_t iters,
                                int32_t recompute_every, double *resnorm_hist, const tomo_exec_opts *opts,
                                void *workspace, size_t workspace_bytes, void *stream);
+
+/* The data fit ||b - A x|| of every slice (the objective CGLS minimises,
+ * Sec. 2.1) with FP64 accumulation: the product of an FP32 value and an FP32
+ * operand is exact in FP64 and every sum is FP64, so the result is the data
+ * fit of the FP32-valued operator to about 1e-15 relative, whatever the row
+ * length (an FP32 SpMM loses ~1e-6 of ||b|| to rounding, which is a large part
+ * of a small residual).  For stopping rules and for comparing solves of
+ * different precision at equal data fit.  sino (n_z, n_theta, n_p) and x
+ * (n_z, n_y, n_x) are DEVICE, slice-major; norms (DEVICE, 8-byte aligned)
+ * receives n_z doubles.  Uses the FP32 CSR form of A (UNSUPPORTED when the
+ * handle dropped it).  Workspace: tomo_workspace_size with TOMO_OP_RESIDUAL
+ * (NULL: allocated stream-ordered by the call).  Deterministic: the sums run
+ * in a fixed order. */
+TOMO_API tomo_status tomo_residual_norm(const tomo_matrix *A, const float *sino, const float *x, int32_t n_z,
+                                        double *norms, void *workspace, size_t workspace_bytes, void *stream);
 
 /* SIRT exactly as tomo_sirt, for callers that cannot allocate GPU memory at
  * all.  The paper has no counterpart; this entry point exists for programs
@@ -243,8 +278,10 @@ TOMO_API tomo_status tomo_cgls(const tomo_matrix *A, const float *sino, float *x
  *
  * The call allocates nothing.  Its scratch is a 16 MiB array compiled into
  * the library; every GPU that loads the library reserves it until the process
- * exits.  The first call on a device looks up that array's device address;
- * make that first call before any stream capture on that device.  Batch width
+ * exits.  The call looks up that array's device address on the current
+ * device each time (a device reset may move it), except while `stream` is
+ * being captured, when it takes the address an earlier call on that device
+ * found: make the first call on a device before any stream capture.  Batch width
  * is chosen internally (the widest of 16, 8, 4, 2, 1, not above n_z, whose
  * scratch fits); a geometry whose residual alone exceeds 16 MiB (more than
  * 4,194,304 rays) is rejected with TOMO_ERR_INVALID_ARG and a message giving
@@ -342,21 +379,28 @@ TOMO_API tomo_status tomo_cgls_batched_workspace(const tomo_request *reqs, int32
 /* One timed candidate of tomo_autotune. */
 typedef struct {
   int32_t batch_width, format;
+  int32_t order;             /* row-group order of the A^T pass (1 rows, 2 image tiles) */
+  int32_t blocks_per_sm;     /* resident blocks per SM (0 = all that fit) */
   double ms_per_iter;        /* one SIRT iteration (A pass + A^T pass) over one batch of batch_width slices */
   double slice_iters_per_s;  /* for n_z slices: n_z / (ceil(n_z / batch_width) * ms_per_iter) */
 } tomo_tune_entry;
 
-/* Autotuner (batch width and matrix storage; the row block of a warp follows
- * from the width).  The paper picks no such parameters; it relies on library
- * SpMV.  Times one SIRT iteration (the A pass with the residual epilogue and
- * the A^T pass with the update epilogue, the same kernels tomo_sirt replays)
- * on device scratch for every width 1..64 not above n_z rounded up to a
- * power of two, and for TOMO_FMT_SELL, TOMO_FMT_CSR and, when allow_16bit is
- * non-zero and the matrix has a 16-bit encoding, TOMO_FMT_SELL16.  Writes up
+/* Autotuner of the SpMM launch shape.  The paper picks no such parameters; it
+ * relies on library SpMV.  Times one SIRT iteration (the A pass with the
+ * residual epilogue and the A^T pass with the update epilogue, the same
+ * kernels tomo_sirt replays) on device scratch.  Stage 1: every batch width
+ * 1..64 not above n_z rounded up to a power of two (the width fixes the row
+ * block of a warp: 32 / max(1, width / 4) rows), every format (TOMO_FMT_SELL,
+ * TOMO_FMT_CSR and, when allow_16bit is non-zero and the matrix has a 16-bit
+ * encoding, TOMO_FMT_SELL16; allow_16bit = 2 searches TOMO_FMT_SELL16 alone),
+ * and for the SELL formats both row-group orders
+ * of the A^T pass (rows, image tiles).  Stage 2: the best stage-1 shape with
+ * fewer resident blocks per SM (all that fit minus 1 and minus 2).  Writes up
  * to `cap` candidates to `table` (nullable) and their count to *n_table,
- * returns the fastest in *best (batch_width, format) with its rate in *rate,
- * and remembers it in the handle for later calls with that n_z that pass
- * batch_width = 0 or format = TOMO_FMT_AUTO.  Allocates its scratch with
+ * returns the fastest in *best (batch_width, format, order, blocks_per_sm)
+ * with its rate in *rate, and remembers it in the handle for later calls with
+ * that n_z (up to 8 slice counts) that pass batch_width = 0, format =
+ * TOMO_FMT_AUTO, order = 0 or blocks_per_sm = 0.  Allocates its scratch with
  * cudaMalloc and synchronises `stream`.  Not to be called while other calls
  * on the same handle are being queued from another thread. */
 TOMO_API tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo_exec_opts *best,
@@ -431,7 +475,8 @@ TOMO_API tomo_status tomo_fubini_sirt_bb(tomo_fubini *F, const float *sino, floa
  * with forward differences Dx = x[iy][ix+1] - x[iy][ix], Dy = x[iy+1][ix] -
  * x[iy][ix] (0 on the last column / row), and grad (same shape as x, DEVICE)
  * = d loss[s] / d x_s.  The value is summed in FP64 in a fixed order
- * (deterministic).  eps > 0; n_z <= 65535. */
+ * (deterministic).  eps > 0 with eps^2 a normal FP32 number (eps >= 1.1e-19);
+ * n_z <= 65535. */
 TOMO_API tomo_status tomo_tv(const float *x, int32_t n_z, int32_t n_y, int32_t n_x, float eps, double *loss,
                              float *grad, void *stream);
 

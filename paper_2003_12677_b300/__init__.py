@@ -8,7 +8,7 @@ torch.
 """
 _API = {"Matrix", "project", "backproject", "sirt", "cgls", "TomoProject", "radon", "tv_loss", "new_timing",
         "sirt_noalloc", "cgls_batched", "stream_status",
-        "sirt_bb", "Fubini"}
+        "sirt_bb", "Fubini", "residual_norm", "set_launch"}
 
 
 def __getattr__(name):

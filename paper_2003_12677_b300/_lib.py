@@ -11,7 +11,7 @@ TOMO_OK = 0
 STATUS = {0: "TOMO_OK", 1: "TOMO_ERR_INVALID_ARG", 2: "TOMO_ERR_OOM", 3: "TOMO_ERR_CUDA",
           4: "TOMO_ERR_TIMEOUT", 5: "TOMO_ERR_UNSUPPORTED", 6: "TOMO_ERR_NUMERIC", 7: "TOMO_ERR_IO"}
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
-OP_PROJECT, OP_BACKPROJECT, OP_SIRT, OP_CGLS, OP_SIRT_BB = 0, 1, 2, 3, 4
+OP_PROJECT, OP_BACKPROJECT, OP_SIRT, OP_CGLS, OP_SIRT_BB, OP_RESIDUAL = 0, 1, 2, 3, 4, 5
 SLICE_MAJOR, INTERLEAVED = 0, 1
 
 # every entry point include/tomo.h declares
@@ -22,7 +22,7 @@ EXPORTS = ["tomo_build_matrix", "tomo_matrix_destroy", "tomo_matrix_info", "tomo
            "tomo_sirt_noalloc", "tomo_autotune", "tomo_stream_status", "tomo_sirt_bb",
            "tomo_fubini_create", "tomo_fubini_destroy", "tomo_fubini_project", "tomo_fubini_backproject",
            "tomo_fubini_sirt_bb", "tomo_fubini_normal", "tomo_fubini_sirt_bb_normal", "tomo_tv",
-           "tomo_status_string", "tomo_last_error"]
+           "tomo_residual_norm", "tomo_status_string", "tomo_last_error"]
 
 
 class TomoError(RuntimeError):
@@ -38,7 +38,7 @@ class Geometry(ctypes.Structure):
 
 class MatrixOpts(ctypes.Structure):
     _fields_ = [("values", ctypes.c_int32), ("no_fp32_sell", ctypes.c_int32), ("drop_csr", ctypes.c_int32),
-                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("model", ctypes.c_int32), ("col_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Timing(ctypes.Structure):
@@ -49,11 +49,13 @@ class ExecOpts(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("format", ctypes.c_int32), ("timeout_s", ctypes.c_float),
                 ("timing", ctypes.POINTER(Timing)), ("test_flags", ctypes.c_int32),
-                ("async_", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("async_", ctypes.c_int32), ("recompute_fp32", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class TuneEntry(ctypes.Structure):
     _fields_ = [("batch_width", ctypes.c_int32), ("format", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("ms_per_iter", ctypes.c_double), ("slice_iters_per_s", ctypes.c_double)]
 
 
@@ -106,6 +108,7 @@ def load(path: str = LIB_PATH):
         "tomo_cgls_resume": [P, P, P, I32, I32, I32, P, ctypes.POINTER(CglsState), ctypes.POINTER(CglsState),
                              ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_sirt_noalloc": [P, P, P, I32, I32, ctypes.c_float, P],
+        "tomo_residual_norm": [P, P, P, I32, P, P, SZ, P],
         "tomo_cgls_batched": [ctypes.POINTER(Request), I32, I32, ctypes.POINTER(ExecOpts), P, SZ, P],
         "tomo_cgls_batched_workspace": [ctypes.POINTER(Request), I32, ctypes.POINTER(ExecOpts),
                                         ctypes.POINTER(SZ)],

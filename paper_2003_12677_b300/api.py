@@ -47,11 +47,31 @@ def _fmt(fmt) -> int:
     return FORMATS[fmt]
 
 
-def _exec(batch_width: int = 0, use_graph: bool = True, fmt="sell", timing=None) -> _lib.ExecOpts:
+ORDERS = {"auto": 0, "rows": 1, "tiles": 2}
+_launch = {"order": "auto", "blocks_per_sm": 0}
+
+
+def set_launch(order: str = "auto", blocks_per_sm: int = 0):
+    """Launch shape of the SpMM passes of later calls: the row-group order of
+    the A^T passes ("auto", "rows" or "tiles") and the resident blocks per SM
+    (0: all that fit).  "auto" / 0 take tomo_autotune's choice for the slice
+    count when there is one.  The results are the same bits either way."""
+    if order not in ORDERS:
+        raise ValueError("order must be one of %s" % sorted(ORDERS))
+    if blocks_per_sm < 0:
+        raise ValueError("blocks_per_sm must be >= 0")
+    _launch["order"], _launch["blocks_per_sm"] = order, int(blocks_per_sm)
+
+
+def _exec(batch_width: int = 0, use_graph: bool = True, fmt="sell", timing=None,
+          recompute_fp32: bool = False) -> _lib.ExecOpts:
     o = _lib.ExecOpts()
     o.batch_width = batch_width
     o.use_graph = 1 if use_graph else 0
     o.format = _fmt(fmt)
+    o.recompute_fp32 = 1 if recompute_fp32 else 0
+    o.order = ORDERS[_launch["order"]]
+    o.blocks_per_sm = _launch["blocks_per_sm"]
     if timing is not None:
         o.timing = ctypes.pointer(timing)
     return o
@@ -72,12 +92,14 @@ class Matrix:
     m*pi/n_theta; center defaults to n_p/2.  values in {"f32", "bf16", "f16"}
     also builds the 16-bit encoding used with fmt="sell16"; fp32_sell=False
     skips the FP32 SELL-32 copy and keep_csr=False frees the CSR pair after
-    the SELL forms are built (memory for very large geometries).
+    the SELL forms are built (memory for very large geometries).  col_blocks
+    > 1 stores the 16-bit A as that many bands of image rows, so that each
+    projection pass gathers one band (which can stay in L2).
     """
 
     def __init__(self, n: int, n_theta: int, n_p: Optional[int] = None, n_y: Optional[int] = None,
                  angles=None, center: Optional[float] = None, values: str = "f32", fp32_sell: bool = True,
-                 keep_csr: bool = True, model: str = "line"):
+                 keep_csr: bool = True, model: str = "line", col_blocks: int = 0):
         self._h = None
         lib = _lib.load()
         if not torch.cuda.is_available():
@@ -102,6 +124,7 @@ class Matrix:
         o.no_fp32_sell = 0 if fp32_sell else 1
         o.drop_csr = 0 if keep_csr else 1
         o.model = MODELS[model]
+        o.col_blocks = int(col_blocks)
         h = ctypes.c_void_p()
         _lib.check(lib.tomo_build_matrix(ctypes.byref(g), ctypes.byref(o), _stream(), ctypes.byref(h)),
                    "tomo_build_matrix")
@@ -162,18 +185,28 @@ class Matrix:
         _lib.call("tomo_matrix_export_norms", self.handle, R.ctypes.data, C.ctypes.data)
         return R, C
 
-    def autotune(self, n_z: int, allow_16bit: bool = False) -> dict:
-        """Time every (batch width, format) for n_z slices on the device; the
-        fastest is remembered for calls with batch_width=0 / fmt="auto"."""
+    def autotune(self, n_z: int, allow_16bit=None) -> dict:
+        """Time the SpMM launch shapes for n_z slices on the device (batch
+        width, format, row-group order of the A^T pass, then resident blocks
+        per SM); the fastest is remembered for calls with batch_width=0,
+        fmt="auto" and the default order / blocks.  allow_16bit: include the
+        16-bit format (default: when the matrix has one); "only": search it
+        alone."""
+        if allow_16bit is None:
+            allow_16bit = self.values != "f32"
+        mode = 2 if allow_16bit == "only" else int(bool(allow_16bit))
         best = _lib.ExecOpts()
         rate = ctypes.c_double()
-        table = (_lib.TuneEntry * 32)()
+        table = (_lib.TuneEntry * 64)()
         n = ctypes.c_int32()
-        _lib.call("tomo_autotune", self.handle, n_z, int(allow_16bit), ctypes.byref(best), ctypes.byref(rate),
-                  table, 32, ctypes.byref(n), _stream())
-        rows = [{"batch_width": t.batch_width, "format": FORMAT_NAMES[t.format], "ms_per_iter": t.ms_per_iter,
-                 "slice_iters_per_s": t.slice_iters_per_s} for t in table[:min(n.value, 32)]]
+        _lib.call("tomo_autotune", self.handle, n_z, mode, ctypes.byref(best), ctypes.byref(rate),
+                  table, 64, ctypes.byref(n), _stream())
+        names = {1: "rows", 2: "tiles"}
+        rows = [{"batch_width": t.batch_width, "format": FORMAT_NAMES[t.format], "order": names.get(t.order, "auto"),
+                 "blocks_per_sm": t.blocks_per_sm, "ms_per_iter": t.ms_per_iter,
+                 "slice_iters_per_s": t.slice_iters_per_s} for t in table[:min(n.value, 64)]]
         return {"batch_width": best.batch_width, "format": FORMAT_NAMES[best.format],
+                "order": names.get(best.order, "auto"), "blocks_per_sm": best.blocks_per_sm,
                 "slice_iters_per_s": rate.value, "table": rows}
 
     def workspace_size(self, op: int, n_z: int, batch_width: int = 0, fmt="sell") -> int:
@@ -279,11 +312,12 @@ def _state_struct(st: dict) -> _lib.CglsState:
 def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, history: bool = False,
          batch_width: int = 0, fmt="sell", use_graph: bool = True, out: Optional[torch.Tensor] = None,
          workspace: Optional[torch.Tensor] = None, timing=None, resume: Optional[dict] = None,
-         return_state: bool = False):
+         return_state: bool = False, recompute_fp32: bool = False):
     """CGLS per slice.  Starts from x0 = 0, or from `resume` (a dict with the
     iterate "x" and the state "r", "p", "gamma", "frozen" as returned with
     return_state=True).  Returns x, then the ||r|| history (iters, n_z) if
-    history, then the final state dict if return_state."""
+    history, then the final state dict if return_state.  recompute_fp32: with
+    fmt="sell16", the residual recompute uses the FP32 values of A."""
     _check_tensor(sino, "sino")
     nz = _nz(sino, M.rows, "sino")
     if resume is not None:
@@ -293,7 +327,7 @@ def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, hi
     _check_tensor(x, "out", (nz, M.n_y, M.n_x))
     hist = torch.zeros((max(iters, 1), nz), device=sino.device, dtype=torch.float64) if history else None
     ws = workspace if workspace is not None else M._workspace(_lib.OP_CGLS, nz, batch_width, fmt)
-    o = _exec(batch_width, use_graph, fmt, timing)
+    o = _exec(batch_width, use_graph, fmt, timing, recompute_fp32)
     sin = None
     if resume is not None:
         for k in ("r", "p"):
@@ -317,6 +351,22 @@ def cgls(M: Matrix, sino: torch.Tensor, iters: int, recompute_every: int = 0, hi
         state["x"] = x.clone()
         res.append(state)
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def residual_norm(M: Matrix, sino: torch.Tensor, x: torch.Tensor,
+                  workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """||b - A x|| per slice (float64, on the device) with FP64 accumulation
+    (tomo_residual_norm): the data fit of the FP32-valued operator to ~1e-15."""
+    _check_tensor(sino, "sino")
+    _check_tensor(x, "x")
+    nz = _nz(sino, M.rows, "sino")
+    if _nz(x, M.cols, "x") != nz:
+        raise ValueError("sino and x hold different slice counts")
+    out = torch.empty(nz, dtype=torch.float64, device=sino.device)
+    ws = workspace if workspace is not None else M._workspace(_lib.OP_RESIDUAL, nz, 0, "sell")
+    _lib.call("tomo_residual_norm", M.handle, _ptr(sino), _ptr(x), nz, _ptr(out), _ptr(ws),
+              0 if ws is None else ws.numel(), _stream())
+    return out
 
 
 def sirt_bb(M: Matrix, sino: torch.Tensor, iters: int, first_step: float = 0.0, history: bool = False,

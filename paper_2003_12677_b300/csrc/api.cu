@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" boundary of libtomo (declared in include/tomo.h).
 // Argument checking, device selection and error strings live here; every
 // computation is queued by build.cu / ops.cu.
+#include <cfloat>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -135,7 +136,11 @@ tomo_status tomo_workspace_size(const tomo_matrix *A, int32_t op, int32_t n_z, c
                                 size_t *bytes) {
   if (!A || !bytes) return fail(TOMO_ERR_INVALID_ARG, "matrix and bytes must be non-NULL");
   if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
-  if (op < TOMO_OP_PROJECT || op > TOMO_OP_SIRT_BB) return fail(TOMO_ERR_INVALID_ARG, "unknown op");
+  if (op < TOMO_OP_PROJECT || op > TOMO_OP_RESIDUAL) return fail(TOMO_ERR_INVALID_ARG, "unknown op");
+  if (op == TOMO_OP_RESIDUAL) {
+    *bytes = sizeof(double) * (size_t)residual_parts();
+    return TOMO_OK;
+  }
   Exec ex;
   TOMO_TRY(resolve_exec(A, opts, n_z, &ex));
   *bytes = workspace_bytes(A, op, n_z, ex);
@@ -187,6 +192,24 @@ tomo_status tomo_sirt(const tomo_matrix *A, const float *sino, float *x, int32_t
   TOMO_TRY(check_ws(A, TOMO_OP_SIRT, n_z, ex, workspace, workspace_bytes));
   if (iters == 0) return TOMO_OK;
   return run_sirt(A, sino, x, n_z, iters, lambda, ex, workspace, (cudaStream_t)stream);
+}
+
+tomo_status tomo_residual_norm(const tomo_matrix *A, const float *sino, const float *x, int32_t n_z, double *norms,
+                               void *workspace, size_t workspace_bytes, void *stream) {
+  if (!A) return fail(TOMO_ERR_INVALID_ARG, "matrix must be non-NULL");
+  TOMO_TRY(check_vec(sino, "sino"));
+  TOMO_TRY(check_vec(x, "x"));
+  if (!norms || ((uintptr_t)norms & 7u)) return fail(TOMO_ERR_INVALID_ARG, "norms must be non-NULL and 8-byte aligned");
+  if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
+  if (!A->A.ci) return fail(TOMO_ERR_UNSUPPORTED, "matrix was built with drop_csr");
+  DeviceGuard dg(A->device);
+  if (workspace) {
+    if (!aligned16(workspace)) return fail(TOMO_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    if (workspace_bytes < sizeof(double) * (size_t)residual_parts())
+      return fail(TOMO_ERR_INVALID_ARG,
+                  "workspace too small: need " + std::to_string(sizeof(double) * (size_t)residual_parts()));
+  }
+  return run_residual_norm(A, sino, x, n_z, norms, workspace, (cudaStream_t)stream);
 }
 
 static tomo_status check_state(const tomo_cgls_state *s, const char *name) {
@@ -273,7 +296,7 @@ tomo_status tomo_autotune(tomo_matrix *A, int32_t n_z, int32_t allow_16bit, tomo
   if (n_z < 1) return fail(TOMO_ERR_INVALID_ARG, "n_z must be >= 1");
   if (cap < 0 || (cap > 0 && !table)) return fail(TOMO_ERR_INVALID_ARG, "table must hold cap entries");
   DeviceGuard dg(A->device);
-  return run_autotune(A, n_z, allow_16bit != 0, best, rate, table, cap, n_table, (cudaStream_t)stream);
+  return run_autotune(A, n_z, allow_16bit, best, rate, table, cap, n_table, (cudaStream_t)stream);
 }
 
 tomo_status tomo_fubini_create(const tomo_geometry *geom, int32_t kw, void *stream, tomo_fubini **out) {
@@ -321,6 +344,8 @@ tomo_status tomo_tv(const float *x, int32_t n_z, int32_t n_y, int32_t n_x, float
   if (n_z < 1 || n_z > 65535 || n_y < 1 || n_x < 1)
     return fail(TOMO_ERR_INVALID_ARG, "need 1 <= n_z <= 65535, n_y >= 1, n_x >= 1");
   if (!(eps > 0.f) || !std::isfinite(eps)) return fail(TOMO_ERR_INVALID_ARG, "eps must be positive and finite");
+  // the kernel works with eps^2 in FP32: below ~1.1e-19 it underflows, and flat regions would divide by 0
+  if (eps * eps < FLT_MIN) return fail(TOMO_ERR_INVALID_ARG, "eps must be at least 1.1e-19 (eps^2 is a normal FP32)");
   return tv_loss_grad(x, n_z, n_y, n_x, eps, loss, grad, (cudaStream_t)stream);
 }
 

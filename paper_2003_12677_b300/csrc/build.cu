@@ -378,8 +378,9 @@ __global__ void __launch_bounds__(kThreads) k_sell_fill(const int64_t *__restric
 // early (padded with zero-weight entries) when the next column lies more than
 // 65535 past its base, which happens where a pixel is seen by two separate
 // ranges of angles (image corners).
+// Only the entries with column in [c0, c1) are taken (one band of a banded A).
 __global__ void k_sell16_len(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t rows,
-                             int32_t *__restrict__ rl16) {
+                             int32_t *__restrict__ rl16, int32_t c0, int32_t c1) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   int64_t b = rp[r], len = rp[r + 1] - b;
@@ -387,6 +388,7 @@ __global__ void k_sell16_len(const int64_t *__restrict__ rp, const int32_t *__re
   int32_t cb = 0;
   for (int64_t e = 0; e < len; ++e) {
     int32_t col = ci[b + e];
+    if (col < c0 || col >= c1) continue;
     if ((slot & 15) != 0 && (int64_t)col - cb > 65535) slot = (slot + 15) / 16 * 16;
     if ((slot & 15) == 0) cb = col;
     ++slot;
@@ -401,7 +403,8 @@ template <bool kTranspose, typename W>
 __global__ void k_sell16_fill(const AngleC *__restrict__ ang, int model, int nx, int ny, int np, double c,
                               const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t rows,
                               const int64_t *__restrict__ cpw, const int64_t *__restrict__ cpb,
-                              uint32_t *__restrict__ ow, int32_t *__restrict__ base, int *__restrict__ err) {
+                              uint32_t *__restrict__ ow, int32_t *__restrict__ base, int *__restrict__ err,
+                              int32_t c0, int32_t c1) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   int64_t b = rp[r], len = rp[r + 1] - b;
@@ -411,6 +414,7 @@ __global__ void k_sell16_fill(const AngleC *__restrict__ ang, int model, int nx,
   int32_t cb = 0;
   for (int64_t e = 0; e < len; ++e) {
     int32_t col = ci[b + e];
+    if (col < c0 || col >= c1) continue;
     if ((slot & 15) != 0 && (int64_t)col - cb > 65535) slot = (slot + 15) / 16 * 16;
     if ((slot & 15) == 0) {
       cb = col;
@@ -503,17 +507,17 @@ tomo_status build_sell(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t 
   return TOMO_OK;
 }
 
+// The 16-bit SELL-32 form of A (or A^T) restricted to columns [c0, c1), into L.
 tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t *cnt, int64_t *part,
-                         int *scratch) {
+                         int *scratch, SellLp &L, int32_t c0, int32_t c1) {
   const Csr &M = transpose ? h->AT : h->A;
-  SellLp &L = transpose ? h->lpAT : h->lpA;
   L.rows = M.rows;
   L.chunks = (M.rows + 31) / 32;
   TOMO_TRY(dmalloc(&L.rl, M.rows));
   TOMO_TRY(dmalloc(&L.cpw, L.chunks + 1));
   TOMO_TRY(dmalloc(&L.cpb, L.chunks + 1));
   const unsigned gr = (unsigned)((M.rows + 255) / 256), gc = (unsigned)((L.chunks + 255) / 256);
-  k_sell16_len<<<gr, 256, 0, st>>>(M.rp, M.ci, M.rows, L.rl);
+  k_sell16_len<<<gr, 256, 0, st>>>(M.rp, M.ci, M.rows, L.rl, c0, c1);
   int32_t *cntb = cnt + L.chunks;  // cnt holds enough entries for two per-chunk arrays
   k_chunk_sizes_rl<<<gc, 256, 0, st>>>(L.rl, M.rows, cnt, cntb);
   TOMO_TRY(scan_counts(cnt, L.chunks, L.cpw, part, scratch + 3, st));
@@ -528,7 +532,7 @@ tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_
   const double c = h->center;
 #define TOMO_FILL16(TR, W)                                                                                      \
   k_sell16_fill<TR, W><<<gr, 256, 0, st>>>(h->ang, h->model, h->nx, h->ny, h->np, c, M.rp, M.ci, M.rows, L.cpw,  \
-                                           L.cpb, L.ow, L.base, scratch)
+                                           L.cpb, L.ow, L.base, scratch, c0, c1)
   if (h->lp_dtype == TOMO_BF16) {
     if (transpose) TOMO_FILL16(true, __nv_bfloat16);
     else TOMO_FILL16(false, __nv_bfloat16);
@@ -615,6 +619,9 @@ tomo_status build_ramp(tomo_matrix *h, cudaStream_t st) {
 
 void free_matrix(tomo_matrix *h) {
   if (!h) return;
+  for (SellLp &L : h->lpAb)
+    for (void *p : {(void *)L.cpw, (void *)L.cpb, (void *)L.rl, (void *)L.ow, (void *)L.base})
+      if (p) cudaFree(p);
   void *ptrs[] = {h->ang,      h->ang_scale, h->A.rp,     h->A.ci,     h->A.v,       h->AT.rp,
                   h->AT.ci,    h->AT.v,      h->R,        h->C,        h->sA.cp,     h->sA.rl,
                   h->sA.ent,   h->sAT.cp,    h->sAT.rl,   h->sAT.ent,  h->lpA.cpw,   h->lpA.cpb,
@@ -643,6 +650,11 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   const int32_t model = o ? o->model : TOMO_MODEL_LINE;
   if (model != TOMO_MODEL_LINE && model != TOMO_MODEL_STRIP)
     return fail(TOMO_ERR_INVALID_ARG, "opts.model must be TOMO_MODEL_LINE or TOMO_MODEL_STRIP");
+  const int32_t bands = o ? o->col_blocks : 0;
+  if (bands < 0 || bands > 64 || bands > g->n_y)
+    return fail(TOMO_ERR_INVALID_ARG, "opts.col_blocks must be in [0, min(64, n_y)]");
+  if (bands > 1 && lp == TOMO_F32)
+    return fail(TOMO_ERR_INVALID_ARG, "opts.col_blocks > 1 needs 16-bit values (TOMO_BF16 or TOMO_F16)");
   const int nt = g->n_theta;
   std::vector<AngleC> ang(nt);
   std::vector<float> scale(nt);
@@ -757,8 +769,17 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
     TOMO_TRY(build_sell(h, true, st, cnt, part, scratch));
   }
   if (lp != TOMO_F32) {
-    TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch));
-    TOMO_TRY(build_sell16(h, true, st, cnt, part, scratch));
+    if (bands > 1) {
+      // band b holds the image rows [b n_y / bands, (b + 1) n_y / bands)
+      h->lpAb.resize(bands);
+      for (int b = 0; b < bands; ++b) {
+        const int32_t y0 = (int32_t)((int64_t)g->n_y * b / bands), y1 = (int32_t)((int64_t)g->n_y * (b + 1) / bands);
+        TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch, h->lpAb[b], y0 * g->n_x, y1 * g->n_x));
+      }
+    } else {
+      TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch, h->lpA, 0, INT32_MAX));
+    }
+    TOMO_TRY(build_sell16(h, true, st, cnt, part, scratch, h->lpAT, 0, INT32_MAX));
   }
   TOMO_CUDA(cudaMemcpyAsync(hs, scratch, sizeof(hs), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "tomo.h"
 
@@ -82,9 +83,16 @@ struct tomo_matrix {
   int32_t lp_dtype = TOMO_F32;
   tomo::Sell sA, sAT;
   tomo::SellLp lpA, lpAT;
+  // 16-bit A stored as column bands (bands of image rows, each its own 16-bit
+  // SELL-32 matrix over all rows of A) when built with col_blocks > 1; lpA is
+  // then empty
+  std::vector<tomo::SellLp> lpAb;
   int64_t bytes_f32 = 0, bytes_lp = 0;
-  // last tomo_autotune result (0 / -1: none)
-  int32_t tuned_nz = 0, tuned_B = 0, tuned_fmt = -1;
+  // tomo_autotune's choice per slice count (most recent first)
+  struct Tuned {
+    int32_t nz, B, fmt, order, blocks;
+  };
+  std::vector<Tuned> tuned;
 };
 
 namespace tomo {
@@ -128,6 +136,9 @@ struct Exec {
   bool graph = true;
   int format = TOMO_FMT_SELL;
   tomo_timing *timing = nullptr;
+  bool recompute_fp32 = false;  // CGLS on 16-bit values: residual recompute with the FP32 values
+  int order = 0;                // A^T row-group order: 0 auto, 1 rows, 2 image tiles
+  int blocks = 0;               // SpMM blocks per SM (0: all that fit)
 };
 tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t nz, Exec *ex);
 size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex);
@@ -138,6 +149,10 @@ tomo_status run_sirt(const tomo_matrix *h, const float *sino, float *x, int32_t 
 tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
                      int32_t recompute, double *hist, const tomo_cgls_state *in, tomo_cgls_state *out,
                      const Exec &ex, void *ws, cudaStream_t st);
+// ||b - A x|| per slice with FP64 accumulation (ops.cu); ws: residual_parts() doubles
+int residual_parts();
+tomo_status run_residual_norm(const tomo_matrix *h, const float *sino, const float *x, int32_t nz, double *norms,
+                              void *ws, cudaStream_t st);
 tomo_status run_sirt_bb(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters,
                         double first_step, double *hist, const tomo_bb_state *in, tomo_bb_state *out,
                         const Exec &ex, void *ws, cudaStream_t st);
@@ -162,7 +177,7 @@ tomo_status fold_status(const int *src, cudaStream_t st);
 tomo_status read_stream_status(cudaStream_t st);
 tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters, const tomo_exec_opts *o,
                              void *ws, size_t ws_bytes, cudaStream_t st);
-tomo_status run_autotune(tomo_matrix *h, int32_t nz, bool allow16, tomo_exec_opts *best, double *rate,
+tomo_status run_autotune(tomo_matrix *h, int32_t nz, int allow16, tomo_exec_opts *best, double *rate,
                          tomo_tune_entry *table, int32_t cap, int32_t *n_table, cudaStream_t st);
 
 }  // namespace tomo

@@ -12,9 +12,9 @@
 // memory, reserved on every GPU that loads the library and held until the
 // process exits.
 //
-// Its address is looked up once per device with cudaGetSymbolAddress (host
-// code cannot use the array's name as a device pointer) and passed to the
-// existing SIRT kernels as their workspace.
+// Its address is looked up with cudaGetSymbolAddress on the calling device
+// (host code cannot use the array's name as a device pointer) and passed to
+// the existing SIRT kernels as their workspace.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -31,32 +31,49 @@ static __device__ __align__(256) unsigned char g_sirt_scratch[kScratchBytes];
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_sirt_scratch on the current device (looked up once).
-tomo_status scratch_address(void **out) {
+// Device address of g_sirt_scratch on the current device.  It is looked up
+// again on every call made outside stream capture (a device reset or a new
+// primary context may load the module at another address) and remembered for
+// calls made while `stream` is being captured, which may not query it.
+tomo_status scratch_address(cudaStream_t stream, void **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return tomo::fail(TOMO_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return tomo::fail(TOMO_ERR_UNSUPPORTED, "device ordinal out of range");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cs);
+  if (e != cudaSuccess)
+    return tomo::fail(TOMO_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_sirt_scratch);
     if (e != cudaSuccess || !p)
       return tomo::fail(TOMO_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") +
                                            cudaGetErrorString(e));
     g_scratch_addr[dev] = p;
+  } else if (!g_scratch_addr[dev]) {
+    return tomo::fail(TOMO_ERR_UNSUPPORTED,
+                      "the first tomo_sirt_noalloc call on a device must come before any stream capture");
   }
   *out = g_scratch_addr[dev];
   return TOMO_OK;
 }
 
+// Makes `dev` current for the duration of the call and restores the previous device.
 struct CurrentDevice {
   int prev = -1;
+  cudaError_t err = cudaSuccess;
   explicit CurrentDevice(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
-      cudaSetDevice(dev);
-    else
+    err = cudaGetDevice(&prev);
+    if (err != cudaSuccess) {
       prev = -1;
+    } else if (prev != dev) {
+      err = cudaSetDevice(dev);
+      if (err != cudaSuccess) prev = -1;
+    } else {
+      prev = -1;
+    }
   }
   ~CurrentDevice() {
     if (prev >= 0) cudaSetDevice(prev);
@@ -76,6 +93,8 @@ extern "C" tomo_status tomo_sirt_noalloc(const tomo_matrix *A, const float *sino
     return fail(TOMO_ERR_INVALID_ARG, "lambda must be finite");
   if (!A->sA.ent) return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without the FP32 SELL form");
   CurrentDevice cd(A->device);
+  if (cd.err != cudaSuccess)
+    return fail(TOMO_ERR_CUDA, std::string("selecting the matrix's device: ") + cudaGetErrorString(cd.err));
   // widest batch (at most 16, at most the slice count) whose scratch fits
   Exec ex;
   ex.graph = false;
@@ -92,7 +111,9 @@ extern "C" tomo_status tomo_sirt_noalloc(const tomo_matrix *A, const float *sino
                                           std::to_string(kScratchBytes) + " bytes");
   }
   void *scratch = nullptr;
-  TOMO_TRY(scratch_address(&scratch));
+  TOMO_TRY(scratch_address((cudaStream_t)stream, &scratch));
+  // never NULL here: run_sirt would otherwise allocate a workspace itself
+  if (!scratch) return fail(TOMO_ERR_CUDA, "static scratch has no device address");
   if (iters == 0) return TOMO_OK;
   // every scratch word SIRT reads (residual, interleaved copies with zero
   // padding) is written earlier in the same call, so stale contents left by

@@ -29,28 +29,36 @@ constexpr int kMinBlocks = 6;  // fallback resident blocks per SM when occupancy
 // ---------------------------------------------------------------------------
 // Six blocks (48 warps) per SM: at the unbounded 46 registers (5 blocks) the
 // B = 64 pass ran 37% slower (gathers in flight limit it, not bandwidth).
-template <int B, class Epi>
+// kTile: visit the row groups in image tiles (map) rather than in row order;
+// a separate instantiation, so that the row-order kernels carry no mapping
+template <int B, class Epi, bool kTile = false>
 __global__ void __launch_bounds__(kThreads, 6) k_spmm_sell(const int64_t *__restrict__ cp,
                                                         const int32_t *__restrict__ rl,
                                                         const int2 *__restrict__ ent, int64_t rows,
                                                         const float *__restrict__ X, Epi epi,
-                                                        double *__restrict__ part) {
+                                                        double *__restrict__ part, TileMap map) {
   constexpr int V = Lanes<B>::V, G = Lanes<B>::G, L = Lanes<B>::L;
   double *ss = norm_slots<V, Epi>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  sell_rowgroups<B>(cp, rl, ent, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
+  if constexpr (kTile)
+    sell_rowgroups<B>(cp, rl, ent, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss, map);
+  else
+    sell_rowgroups<B>(cp, rl, ent, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
   if constexpr (Epi::kNorm) block_norms<V>(ss, ((threadIdx.x & 31) % L) * V, B, part);
 }
 
-template <int B, bool kBf16, bool kTrans, class Epi>
+template <int B, bool kBf16, bool kTrans, class Epi, bool kPre = false, bool kTile = false>
 __global__ void __launch_bounds__(kThreads) k_spmm_sell16(Sell16View M, int64_t rows, const float *__restrict__ X,
-                                                          Epi epi, double *__restrict__ part) {
+                                                          Epi epi, double *__restrict__ part, TileMap map) {
   constexpr int V = Lanes<B>::V, G = Lanes<B>::G, L = Lanes<B>::L;
   double *ss = norm_slots<V, Epi>();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  sell16_rowgroups<B, kBf16, kTrans>(M, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
+  if constexpr (kTile)
+    sell16_rowgroups<B, kBf16, kTrans, Epi, true, kPre>(M, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss, map);
+  else
+    sell16_rowgroups<B, kBf16, kTrans, Epi, true, kPre>(M, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
   if constexpr (Epi::kNorm) block_norms<V>(ss, ((threadIdx.x & 31) % L) * V, B, part);
 }
 
@@ -192,6 +200,54 @@ __global__ void __launch_bounds__(kThreads) k_spmv_f32(const int64_t *__restrict
 }
 
 // ---------------------------------------------------------------------------
+// Data fit ||b - A x|| of one slice with FP64 accumulation.  The product of an
+// FP32 value and an FP32 operand is exact in FP64 (24 + 24 significand bits),
+// so the only rounding left is the FP64 summation: the result is the data fit
+// of the FP32-valued operator to about 1e-15 relative, whatever the row
+// length.  A warp per row (lanes split its entries), slice-major vectors;
+// per-block partials of r^2 in a fixed order, summed by k_sum_parts.
+// ---------------------------------------------------------------------------
+constexpr int kResidBlocksPerSm = 4;
+
+__global__ void __launch_bounds__(kThreads) k_resid_f64(const int64_t *__restrict__ rp,
+                                                        const int32_t *__restrict__ ci,
+                                                        const float *__restrict__ val, int64_t rows,
+                                                        const float *__restrict__ x, const float *__restrict__ b,
+                                                        double *__restrict__ part) {
+  __shared__ double red[kWarps];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double ss = 0.0;
+  for (int64_t row = warp; row < rows; row += nwarps) {
+    double acc = 0.0;
+    const int64_t end = __ldg(rp + row + 1);
+    for (int64_t e = __ldg(rp + row) + lane; e < end; e += 32)
+      acc = fma((double)__ldg(val + e), (double)__ldg(x + __ldg(ci + e)), acc);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const double r = (double)__ldg(b + row) - acc;
+    ss = fma(r, r, ss);
+  }
+  if (lane == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// out = sqrt(sum of part[0 .. n)), summed in index order by one thread
+__global__ void k_sum_parts(const double *__restrict__ part, int n, double *__restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += part[i];
+    *out = sqrt(t);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Layout: slice-major (n_z, n) <-> interleaved (n, B), through shared memory.
 // ---------------------------------------------------------------------------
 template <int B>
@@ -313,12 +369,15 @@ __global__ void k_cgls_save(const double *scal, double *gamma, int32_t *frozen, 
 }
 
 // x += alpha p (cols); r -= alpha q (rows), optional ||r||^2 partials
+// rs (nullable): also write r times 1/a(theta) of each row's angle (scale, per
+// angle; np bins per angle), the operand of the 16-bit A^T pass
 template <int B>
 __global__ void __launch_bounds__(kThreads) k_cgls_step(float *__restrict__ x, const float *__restrict__ p,
                                                         int64_t ncols, float *__restrict__ r,
                                                         const float *__restrict__ q, int64_t nrows,
                                                         const double *__restrict__ scal,
-                                                        double *__restrict__ part_r) {
+                                                        double *__restrict__ part_r, float *__restrict__ rs,
+                                                        const float *__restrict__ scale, int np) {
   constexpr int V = B >= 4 ? 4 : B;
   constexpr int PER = B / V;  // vectors per row
   const int64_t nvx = ncols * PER, nvr = nrows * PER;
@@ -346,8 +405,23 @@ __global__ void __launch_bounds__(kThreads) k_cgls_step(float *__restrict__ x, c
       ss[t] += (double)rv.v[t] * (double)rv.v[t];
     }
     st_vec<V>(r + i * V, rv);
+    if (rs) {
+      const float sc = __ldg(scale + (i / PER) / np);
+#pragma unroll
+      for (int t = 0; t < V; ++t) rv.v[t] *= sc;
+      st_vec<V>(rs + i * V, rv);
+    }
   }
   if (part_r) block_norms<V>(ss, s0, B, part_r);
+}
+
+// dst = src times 1/a(theta) of each row's angle, (rows, B) interleaved (dst may be src)
+template <int B>
+__global__ void __launch_bounds__(kThreads) k_scale_rows(const float *src, float *dst, int64_t nrows,
+                                                         const float *__restrict__ scale, int np) {
+  const int64_t n = nrows * B;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i] * __ldg(scale + (i / B) / np);
 }
 
 // p = s + beta p (cols); advances the iteration counter
@@ -394,9 +468,12 @@ constexpr int ramp_tile_bins() {
   return kRampKB * kThreads / (B >= 4 ? B / 4 : 1);
 }
 
+// scale (nullable): multiply projection row m's output by scale[m] (1/a(theta_m),
+// for the 16-bit A^T pass that follows)
 template <int B>
 __global__ void __launch_bounds__(kThreads) k_ramp_filter(const float *__restrict__ r, float *__restrict__ rf,
-                                                          const float *__restrict__ tap, int np) {
+                                                          const float *__restrict__ tap, int np,
+                                                          const float *__restrict__ scale) {
   constexpr int V = B >= 4 ? 4 : B, Q = B / V, KB = kRampKB, TK = ramp_tile_bins<B>(), TJ = 32;
   __shared__ __align__(16) float rs[TJ * B];
   const int q = threadIdx.x % Q, kg = threadIdx.x / Q;
@@ -431,12 +508,13 @@ __global__ void __launch_bounds__(kThreads) k_ramp_filter(const float *__restric
       w[0] = tapv(k0 - (j0 + jj) - 1);
     }
   }
+  const float sc = scale ? __ldg(scale + m) : 1.0f;
 #pragma unroll
   for (int i = 0; i < KB; ++i) {
     if (k0 + i >= np) break;
     Vec<V> o;
 #pragma unroll
-    for (int t = 0; t < V; ++t) o.v[t] = acc[i][t];
+    for (int t = 0; t < V; ++t) o.v[t] = acc[i][t] * sc;
     st_vec<V>(rf + (m * np + k0 + i) * B + q * V, o);
   }
 }
@@ -553,7 +631,25 @@ struct Op {  // one SpMM operand (A or A^T) in the selected storage
   bool bf16;
   const float *scale;
   int np;
+  bool pre = false;  // 16-bit A^T: the operand already carries 1/a(theta) per row
+  int nx = 0, ny = 0;  // image shape (A^T rows are its pixels)
+  const std::vector<SellLp> *bands = nullptr;  // 16-bit A stored as column bands
+  float *partial = nullptr;                     // (rows, B) sums of the bands before the last
+  int order = 0;                                // A^T row-group order (Exec::order)
+  int blocks = 0;                               // resident blocks per SM to launch (0: all that fit)
 };
+
+// blocks per SM a launch of the op uses: all that fit, or fewer when asked
+inline int op_res(const Op &op, int res) { return op.blocks > 0 ? std::min(res, op.blocks) : res; }
+
+// Row-group order of a SELL pass: row order for A; for A^T image tiles (see
+// TileMap) when asked, or by default when the gathered batch of sinograms
+// (rows of A times B floats) exceeds half of the L2.
+inline TileMap tile_map(const Op &op, int G, int B) {
+  if (!op.trans || op.order == 1 || op.nx % G != 0 || op.ny % 8 != 0) return TileMap{0, 0};
+  if (op.order == 0 && op.m->cols * (int64_t)B * 4 <= (int64_t)(64 << 20)) return TileMap{0, 0};
+  return TileMap{op.nx / G, op.ny / 8};
+}
 
 // rows one warp handles in the SpMM kernels of a format / width
 inline int rows_per_warp(int format, int B) {
@@ -595,58 +691,119 @@ void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream
   const int64_t rows = op.m->rows;
   if (op.format == TOMO_FMT_SELL) {
     const Sell &S = *op.sell;
-    static const int res = resident_blocks(k_spmm_sell<B, Epi>);
-    k_spmm_sell<B, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(S.cp, S.rl, S.ent, rows, X, epi, part);
+    const TileMap map = tile_map(op, G, B);
+    if (map.gx) {
+      static const int res = resident_blocks(k_spmm_sell<B, Epi, true>);
+      k_spmm_sell<B, Epi, true><<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(S.cp, S.rl, S.ent, rows, X,
+                                                                                           epi, part, map);
+    } else {
+      static const int res = resident_blocks(k_spmm_sell<B, Epi>);
+      k_spmm_sell<B, Epi><<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(S.cp, S.rl, S.ent, rows, X, epi,
+                                                                                    part, map);
+    }
+  } else if (op.format == TOMO_FMT_SELL16 && op.bands) {
+    // one pass per column band; the bands' partial sums meet in op.partial
+    const float inv_np = 1.0f / (float)op.np;
+    const int K = (int)op.bands->size();
+    for (int b = 0; b < K; ++b) {
+      const SellLp &L = (*op.bands)[b];
+      const Sell16View view{L.cpw, L.cpb, L.rl, L.ow, L.base, op.scale, op.np, inv_np};
+      if (b < K - 1) {
+        const EpiBandPartial ep{op.partial, B, b == 0};
+        if (op.bf16) {
+          static const int res = resident_blocks(k_spmm_sell16<B, true, false, EpiBandPartial>);
+          k_spmm_sell16<B, true, false, EpiBandPartial>
+              <<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(view, rows, X, ep, nullptr, TileMap{0, 0});
+        } else {
+          static const int res = resident_blocks(k_spmm_sell16<B, false, false, EpiBandPartial>);
+          k_spmm_sell16<B, false, false, EpiBandPartial>
+              <<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(view, rows, X, ep, nullptr, TileMap{0, 0});
+        }
+      } else {
+        const EpiBandLast<Epi> el{op.partial, B, epi};
+        if (op.bf16) {
+          static const int res = resident_blocks(k_spmm_sell16<B, true, false, EpiBandLast<Epi>>);
+          k_spmm_sell16<B, true, false, EpiBandLast<Epi>>
+              <<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(view, rows, X, el, part, TileMap{0, 0});
+        } else {
+          static const int res = resident_blocks(k_spmm_sell16<B, false, false, EpiBandLast<Epi>>);
+          k_spmm_sell16<B, false, false, EpiBandLast<Epi>>
+              <<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(view, rows, X, el, part, TileMap{0, 0});
+        }
+      }
+    }
   } else if (op.format == TOMO_FMT_SELL16) {
     const SellLp &L = *op.lp;
     const float inv_np = 1.0f / (float)op.np;
     const Sell16View view{L.cpw, L.cpb, L.rl, L.ow, L.base, op.scale, op.np, inv_np};
-#define TOMO_SELL16(BF, TR)                                                                                    \
+    const TileMap map = tile_map(op, G, B);
+#define TOMO_SELL16(BF, TR, PRE)                                                                               \
   do {                                                                                                         \
-    static const int res = resident_blocks(k_spmm_sell16<B, BF, TR, Epi>);                                     \
-    k_spmm_sell16<B, BF, TR, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(view, rows, X, epi, part);    \
+    if (TR && map.gx) {                                                                                        \
+      static const int res = resident_blocks(k_spmm_sell16<B, BF, TR, Epi, PRE, true>);                        \
+      k_spmm_sell16<B, BF, TR, Epi, PRE, true>                                                                 \
+          <<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(view, rows, X, epi, part, map);          \
+    } else {                                                                                                   \
+      static const int res = resident_blocks(k_spmm_sell16<B, BF, TR, Epi, PRE>);                              \
+      k_spmm_sell16<B, BF, TR, Epi, PRE>                                                                       \
+          <<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(view, rows, X, epi, part, map);          \
+    }                                                                                                          \
   } while (0)
     if (op.bf16) {
-      if (op.trans) TOMO_SELL16(true, true);
-      else TOMO_SELL16(true, false);
+      if (op.trans && op.pre) TOMO_SELL16(true, true, true);
+      else if (op.trans) TOMO_SELL16(true, true, false);
+      else TOMO_SELL16(true, false, false);
     } else {
-      if (op.trans) TOMO_SELL16(false, true);
-      else TOMO_SELL16(false, false);
+      if (op.trans && op.pre) TOMO_SELL16(false, true, true);
+      else if (op.trans) TOMO_SELL16(false, true, false);
+      else TOMO_SELL16(false, false, false);
     }
 #undef TOMO_SELL16
   } else {
     if constexpr (B >= 4) {
       static const int res = std::min(resident_blocks(csr_kernel<B, Epi>()), kCsrMaxBlocks);
-      csr_kernel<B, Epi>()<<<spmm_grid(rows, G, res), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X, epi,
+      csr_kernel<B, Epi>()<<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X, epi,
                                                                         part);
     } else {
       static const int res = resident_blocks(k_spmv_f32<B, 32, Epi>);
-      k_spmv_f32<B, 32, Epi><<<spmm_grid(rows, G, res), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X,
+      k_spmv_f32<B, 32, Epi><<<spmm_grid(rows, G, op_res(op, res)), kThreads, 0, st>>>(op.m->rp, op.m->ci, op.m->v, rows, X,
                                                                             epi, part);
     }
   }
 }
 
-// grid the SpMM of (op, B, Epi) will use; CGLS sizes its norm reductions with it
+// grid the SpMM of (op, B, Epi) will use (the same instantiation launch_spmm
+// picks); CGLS sizes its norm reductions with it
 template <int B, class Epi>
 int spmm_grid_of(const Op &op) {
   const int G = rows_per_warp(op.format, B);
+  const bool tile = tile_map(op, G, B).gx != 0;
   int res = kMinBlocks;
   if (op.format == TOMO_FMT_SELL) {
-    res = resident_blocks(k_spmm_sell<B, Epi>);
-  } else if (op.format == TOMO_FMT_SELL16) {
+    res = tile ? resident_blocks(k_spmm_sell<B, Epi, true>) : resident_blocks(k_spmm_sell<B, Epi>);
+  } else if (op.format == TOMO_FMT_SELL16 && op.bands) {  // the last band's pass reduces the norms
+    res = op.bf16 ? resident_blocks(k_spmm_sell16<B, true, false, EpiBandLast<Epi>>)
+                  : resident_blocks(k_spmm_sell16<B, false, false, EpiBandLast<Epi>>);
+  } else if (op.format == TOMO_FMT_SELL16 && op.trans) {
     if (op.bf16)
-      res = op.trans ? resident_blocks(k_spmm_sell16<B, true, true, Epi>)
-                     : resident_blocks(k_spmm_sell16<B, true, false, Epi>);
+      res = op.pre ? (tile ? resident_blocks(k_spmm_sell16<B, true, true, Epi, true, true>)
+                           : resident_blocks(k_spmm_sell16<B, true, true, Epi, true>))
+                   : (tile ? resident_blocks(k_spmm_sell16<B, true, true, Epi, false, true>)
+                           : resident_blocks(k_spmm_sell16<B, true, true, Epi>));
     else
-      res = op.trans ? resident_blocks(k_spmm_sell16<B, false, true, Epi>)
-                     : resident_blocks(k_spmm_sell16<B, false, false, Epi>);
+      res = op.pre ? (tile ? resident_blocks(k_spmm_sell16<B, false, true, Epi, true, true>)
+                           : resident_blocks(k_spmm_sell16<B, false, true, Epi, true>))
+                   : (tile ? resident_blocks(k_spmm_sell16<B, false, true, Epi, false, true>)
+                           : resident_blocks(k_spmm_sell16<B, false, true, Epi>));
+  } else if (op.format == TOMO_FMT_SELL16) {
+    res = op.bf16 ? resident_blocks(k_spmm_sell16<B, true, false, Epi>)
+                  : resident_blocks(k_spmm_sell16<B, false, false, Epi>);
   } else if constexpr (B >= 4) {
     res = std::min(resident_blocks(csr_kernel<B, Epi>()), kCsrMaxBlocks);
   } else {
     res = resident_blocks(k_spmv_f32<B, 32, Epi>);
   }
-  return spmm_grid(op.m->rows, G, res);
+  return spmm_grid(op.m->rows, G, op_res(op, res));
 }
 
 inline int elem_grid(int64_t n_vec) {
@@ -756,6 +913,11 @@ Op make_op(const tomo_matrix *h, bool trans, const Exec &ex) {
   op.bf16 = h->lp_dtype == TOMO_BF16;
   op.scale = h->ang_scale;
   op.np = h->np;
+  op.nx = h->nx;
+  op.ny = h->ny;
+  op.order = ex.order;
+  op.blocks = ex.blocks;
+  if (!trans && ex.format == TOMO_FMT_SELL16 && !h->lpAb.empty()) op.bands = &h->lpAb;
   return op;
 }
 
@@ -769,6 +931,10 @@ tomo_status project_t(const tomo_matrix *h, bool trans, const float *in, float *
   Timer tm{ex.timing};
   const int kind = trans ? kAT : kA;
   const int64_t nin = op.m->cols, nout = op.m->rows;
+  Carver cv{(char *)ws};
+  float *xi = B > 1 ? cv.take<float>(nin * B) : nullptr;
+  float *yi = B > 1 ? cv.take<float>(nout * B) : nullptr;
+  if (op.bands) op.partial = cv.take<float>(nout * B);  // sums of the column bands
   if (layout == TOMO_INTERLEAVED || B == 1) {
     // interleaved with n_z == B (or a single slice per pass): operate in place
     for (int32_t s0 = 0; s0 < nz; s0 += B)
@@ -777,12 +943,14 @@ tomo_status project_t(const tomo_matrix *h, bool trans, const float *in, float *
     TOMO_CUDA(cudaGetLastError());
     return tm.finish(st);
   }
-  Carver cv{(char *)ws};
-  float *xi = cv.take<float>(nin * B);
-  float *yi = cv.take<float>(nout * B);
+  // the 16-bit A^T pass gathers an operand scaled by 1/a(theta) per row (its own copy here)
+  op.pre = trans && op.format == TOMO_FMT_SELL16;
   for (int32_t s0 = 0; s0 < nz; s0 += B) {
     int cnt = std::min<int32_t>(B, nz - s0);
     TIMED(tm, st, kOther, interleave<B>(in + (int64_t)s0 * nin, nin, cnt, xi, st));
+    if (op.pre)
+      TIMED(tm, st, kOther,
+            (k_scale_rows<B><<<elem_grid(nin * B), kThreads, 0, st>>>(xi, xi, nin, h->ang_scale, h->np)));
     TIMED(tm, st, kind, launch_spmm<B>(op, xi, EpiStore{yi, B}, nullptr, st));
     TIMED(tm, st, kOther, deinterleave<B>(yi, nout, cnt, out + (int64_t)s0 * nout, st));
   }
@@ -797,11 +965,15 @@ template <int B>
 tomo_status sirt_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, int32_t iters, float lam,
                    const Exec &ex, void *ws, cudaStream_t st) {
   Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
+  // 16-bit values: the residual is written times 1/a(theta), so A^T needs no per-entry scale
+  AT.pre = ex.format == TOMO_FMT_SELL16;
+  const float *rscale = AT.pre ? h->ang_scale : nullptr;
   const int64_t rows = h->A.rows, cols = h->A.cols;
   Carver cv{(char *)ws};
   float *r = cv.take<float>(rows * B);
   float *bi = B > 1 ? cv.take<float>(rows * B) : nullptr;
   float *xi = B > 1 ? cv.take<float>(cols * B) : nullptr;
+  if (A.bands) A.partial = cv.take<float>(rows * B);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   TOMO_CUDA(cudaStreamIsCapturing(st, &cs));
   Timer tm{ex.timing};
@@ -818,7 +990,10 @@ tomo_status sirt_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
       xx = xi;
     }
     auto one_iter = [&](cudaStream_t s) {
-      TIMED(tm, s, kA, launch_spmm<B>(A, xx, EpiSirtResidual{r, bb, h->R, B}, nullptr, s));
+      if (rscale)
+        TIMED(tm, s, kA, launch_spmm<B>(A, xx, EpiSirtResidualScaled{r, bb, h->R, B, rscale, h->np}, nullptr, s));
+      else
+        TIMED(tm, s, kA, launch_spmm<B>(A, xx, EpiSirtResidual{r, bb, h->R, B}, nullptr, s));
       TIMED(tm, s, kAT, launch_spmm<B>(AT, r, EpiSirtUpdate{xx, h->C, lam, B}, nullptr, s));
     };
     if (use_graph) {
@@ -863,9 +1038,24 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
   int *itc = cv.take<int>(4);
   float *bi = B > 1 ? cv.take<float>(rows * B) : nullptr;
   float *xi = B > 1 ? cv.take<float>(cols * B) : nullptr;
+  // 16-bit values: A^T gathers rs = r times 1/a(theta) (written beside r), not r
+  AT.pre = ex.format == TOMO_FMT_SELL16;
+  float *rs = AT.pre ? cv.take<float>(rows * B) : r;
+  const float *rsc = AT.pre ? h->ang_scale : nullptr;
+  if (A.bands) A.partial = cv.take<float>(rows * B);
 
-  const int gA = spmm_grid_of<B, EpiStoreNorm>(A);     // q = A p
-  const int gR = spmm_grid_of<B, EpiResidualNorm>(A);  // r = b - A x
+  // the periodic residual r = b - A x: the solve's own values, or the FP32 ones
+  Op Arec = A;
+  if (ex.recompute_fp32 && ex.format == TOMO_FMT_SELL16) {
+    Exec e32 = ex;
+    e32.format = h->sA.ent ? TOMO_FMT_SELL : TOMO_FMT_CSR;
+    Arec = make_op(h, false, e32);
+  } else {
+    Arec.partial = A.partial;
+  }
+  const int gA = spmm_grid_of<B, EpiStoreNorm>(A);        // q = A p
+  const int gR = AT.pre ? spmm_grid_of<B, EpiResidualNormScaled>(Arec)   // r = b - A x
+                        : spmm_grid_of<B, EpiResidualNorm>(Arec);
   const int gT = spmm_grid_of<B, EpiStoreNorm>(AT);    // s = A^T r
   constexpr int PER = B >= 4 ? B / 4 : 1;
   const int ge = elem_grid((rows > cols ? rows : cols) * PER);
@@ -900,7 +1090,9 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
       // x = 0, r = b, s = A^T r, p = s, gamma = ||s||^2
       TOMO_CUDA(cudaMemsetAsync(xx, 0, sizeof(float) * cols * B, st));
       TOMO_CUDA(cudaMemcpyAsync(r, bb, sizeof(float) * rows * B, cudaMemcpyDeviceToDevice, st));
-      TIMED(tm, st, kAT, launch_spmm<B>(AT, r, EpiStoreNorm{s, B}, part_b, st));
+      if (AT.pre)
+        TIMED(tm, st, kOther, (k_scale_rows<B><<<elem_grid(rows * B), kThreads, 0, st>>>(r, rs, rows, rsc, h->np)));
+      TIMED(tm, st, kAT, launch_spmm<B>(AT, rs, EpiStoreNorm{s, B}, part_b, st));
       TOMO_CUDA(cudaMemcpyAsync(p, s, sizeof(float) * cols * B, cudaMemcpyDeviceToDevice, st));
       TIMED(tm, st, kOther, (k_cgls_init<<<B, kThreads, 0, st>>>(part_b, gT, B, scal, itc)));
     }
@@ -915,11 +1107,15 @@ tomo_status cgls_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz
       TIMED(tm, sm, kOther, (k_cgls_alpha<<<B, kThreads, 0, sm>>>(part_a, gA, B, scal)));
       // x += alpha p, r -= alpha q
       TIMED(tm, sm, kOther,
-            (k_cgls_step<B><<<ge, kThreads, 0, sm>>>(xx, p, cols, r, q, rows, scal, hist ? part_r : nullptr)));
+            (k_cgls_step<B><<<ge, kThreads, 0, sm>>>(xx, p, cols, r, q, rows, scal, hist ? part_r : nullptr,
+                                                     AT.pre && !recomp ? rs : nullptr, rsc, h->np)));
       // every `recompute` iterations: r = b - A x
-      if (recomp) TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidualNorm{r, bb, B}, part_r, sm));
+      if (recomp && AT.pre)
+        TIMED(tm, sm, kA, launch_spmm<B>(Arec, xx, EpiResidualNormScaled{r, bb, B, rs, rsc, h->np}, part_r, sm));
+      else if (recomp)
+        TIMED(tm, sm, kA, launch_spmm<B>(Arec, xx, EpiResidualNorm{r, bb, B}, part_r, sm));
       // s = A^T r, ||s||^2
-      TIMED(tm, sm, kAT, launch_spmm<B>(AT, r, EpiStoreNorm{s, B}, part_b, sm));
+      TIMED(tm, sm, kAT, launch_spmm<B>(AT, rs, EpiStoreNorm{s, B}, part_b, sm));
       // beta = ||s||^2 / gamma, residual history
       TIMED(tm, sm, kOther,
             (k_cgls_beta<<<B, kThreads, 0, sm>>>(part_b, gT, hist ? part_r : nullptr, recomp ? gR : ge, B, scal,
@@ -979,6 +1175,7 @@ tomo_status bb_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, 
                  double *hist, const tomo_bb_state *sin, tomo_bb_state *sout, const Exec &ex, void *ws,
                  cudaStream_t st) {
   Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
+  AT.pre = ex.format == TOMO_FMT_SELL16;  // the filter writes P^T P r times 1/a(theta)
   const int64_t rows = h->A.rows, cols = h->A.cols;
   const int pg = max_spmm_grid();
   Carver cv{(char *)ws};
@@ -992,6 +1189,7 @@ tomo_status bb_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, 
   int *itc = cv.take<int>(4);
   float *bi = B > 1 ? cv.take<float>(rows * B) : nullptr;
   float *xi = B > 1 ? cv.take<float>(cols * B) : nullptr;
+  if (A.bands) A.partial = cv.take<float>(rows * B);
 
   const int gR = spmm_grid_of<B, EpiResidualNorm>(A);
   constexpr int PER = B >= 4 ? B / 4 : 1;
@@ -1038,7 +1236,8 @@ tomo_status bb_t(const tomo_matrix *h, const float *sino, float *x, int32_t nz, 
         TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidualNorm{r, bb, B}, part_r, sm));
       else
         TIMED(tm, sm, kA, launch_spmm<B>(A, xx, EpiResidual{r, bb, B}, nullptr, sm));
-      TIMED(tm, sm, kOther, (k_ramp_filter<B><<<gf, kThreads, 0, sm>>>(r, rf, h->ramp, h->np)));
+      TIMED(tm, sm, kOther,
+            (k_ramp_filter<B><<<gf, kThreads, 0, sm>>>(r, rf, h->ramp, h->np, AT.pre ? h->ang_scale : nullptr)));
       TIMED(tm, sm, kAT, launch_spmm<B>(AT, rf, EpiStore{g, B}, nullptr, sm));
       TIMED(tm, sm, kOther, (k_bb_dots<B><<<ge, kThreads, 0, sm>>>(gp, g, cols, part_p, part_q)));
       TIMED(tm, sm, kOther,
@@ -1135,13 +1334,19 @@ tomo_status with_ws(const tomo_matrix *h, int op, int32_t nz, const Exec &ex, vo
 
 tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t nz, Exec *ex) {
   Exec e;
-  const bool tuned = h->tuned_B > 0 && h->tuned_nz == nz;
+  const tomo_matrix::Tuned *tc = nullptr;  // tomo_autotune's choice for this slice count
+  for (const auto &t : h->tuned)
+    if (t.nz == nz) {
+      tc = &t;
+      break;
+    }
+  const bool tuned = tc != nullptr;
   int req = o ? o->batch_width : 0;
   if (req != 0 && !valid_width(req))
     return fail(TOMO_ERR_UNSUPPORTED, "batch_width must be 0, 1, 2, 4, 8, 16, 32 or 64");
   if (req == 0) {
     if (tuned) {
-      req = h->tuned_B;
+      req = tc->B;
     } else {
       int b = 1;
       while (b < nz && b < 16) b <<= 1;
@@ -1152,7 +1357,7 @@ tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t 
   e.graph = o ? o->use_graph != 0 : true;
   e.timing = o ? o->timing : nullptr;
   e.format = o ? o->format : TOMO_FMT_SELL;
-  if (e.format == TOMO_FMT_AUTO) e.format = tuned ? h->tuned_fmt : TOMO_FMT_SELL;
+  if (e.format == TOMO_FMT_AUTO) e.format = tuned ? tc->fmt : TOMO_FMT_SELL;
   if (e.format != TOMO_FMT_SELL && e.format != TOMO_FMT_SELL16 && e.format != TOMO_FMT_CSR)
     return fail(TOMO_ERR_INVALID_ARG, "format must be a tomo_format value");
   if (e.format == TOMO_FMT_SELL16 && h->lp_dtype == TOMO_F32)
@@ -1161,6 +1366,15 @@ tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t 
     return fail(TOMO_ERR_UNSUPPORTED, "matrix was built without the FP32 SELL form (no_fp32_sell)");
   if (e.format == TOMO_FMT_CSR && !h->A.ci)
     return fail(TOMO_ERR_UNSUPPORTED, "matrix was built with drop_csr");
+  e.recompute_fp32 = o ? o->recompute_fp32 != 0 : false;
+  e.order = o ? o->order : 0;
+  if (e.order < 0 || e.order > 2) return fail(TOMO_ERR_INVALID_ARG, "order must be 0, 1 or 2");
+  if (e.order == 0 && tuned) e.order = tc->order;
+  e.blocks = o ? o->blocks_per_sm : 0;
+  if (e.blocks < 0) return fail(TOMO_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
+  if (e.blocks == 0 && tuned) e.blocks = tc->blocks;
+  if (e.recompute_fp32 && !h->sA.ent && !h->A.ci)
+    return fail(TOMO_ERR_UNSUPPORTED, "recompute_fp32 needs an FP32 form of A (FP32 SELL or CSR)");
   *ex = e;
   return TOMO_OK;
 }
@@ -1169,6 +1383,8 @@ size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex)
   (void)nz;
   const int64_t rows = h->A.rows, cols = h->A.cols;
   const int B = ex.B;
+  // the 16-bit A stored as column bands sums its bands in a (rows, B) buffer
+  const bool banded = ex.format == TOMO_FMT_SELL16 && !h->lpAb.empty();
   Carver cv{nullptr};
   switch (op) {
     case TOMO_OP_PROJECT:
@@ -1177,6 +1393,7 @@ size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex)
         cv.take<float>(cols * B);
         cv.take<float>(rows * B);
       }
+      if (banded && op == TOMO_OP_PROJECT) cv.take<float>(rows * B);
       break;
     case TOMO_OP_SIRT:
       cv.take<float>(rows * B);
@@ -1184,6 +1401,7 @@ size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex)
         cv.take<float>(rows * B);
         cv.take<float>(cols * B);
       }
+      if (banded) cv.take<float>(rows * B);
       break;
     case TOMO_OP_CGLS: {
       const int pg = max_spmm_grid();
@@ -1200,6 +1418,8 @@ size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex)
         cv.take<float>(rows * B);
         cv.take<float>(cols * B);
       }
+      if (ex.format == TOMO_FMT_SELL16) cv.take<float>(rows * B);  // r times 1/a(theta)
+      if (banded) cv.take<float>(rows * B);
       break;
     }
     case TOMO_OP_SIRT_BB: {
@@ -1217,6 +1437,7 @@ size_t workspace_bytes(const tomo_matrix *h, int op, int32_t nz, const Exec &ex)
         cv.take<float>(rows * B);
         cv.take<float>(cols * B);
       }
+      if (banded) cv.take<float>(rows * B);
       break;
     }
     default:
@@ -1245,6 +1466,31 @@ tomo_status run_cgls(const tomo_matrix *h, const float *sino, float *x, int32_t 
   WsHolder hold;
   TOMO_TRY(with_ws(h, TOMO_OP_CGLS, nz, ex, ws, hold, st));
   return dispatch<CglsF>(ex.B, h, sino, x, nz, iters, recompute, hist, in, out, ex, ws, st);
+}
+
+int residual_parts() { return num_sms() * kResidBlocksPerSm; }
+
+tomo_status run_residual_norm(const tomo_matrix *h, const float *sino, const float *x, int32_t nz, double *norms,
+                              void *ws, cudaStream_t st) {
+  const Csr &A = h->A;
+  const int nb = residual_parts();
+  double *part = static_cast<double *>(ws);
+  WsHolder hold;
+  if (!part) {
+    if (cudaMallocAsync(&hold.p, sizeof(double) * nb, st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TOMO_ERR_OOM, "workspace allocation failed");
+    }
+    hold.st = st;
+    part = static_cast<double *>(hold.p);
+  }
+  for (int32_t s = 0; s < nz; ++s) {
+    k_resid_f64<<<nb, kThreads, 0, st>>>(A.rp, A.ci, A.v, A.rows, x + (int64_t)s * A.cols,
+                                         sino + (int64_t)s * A.rows, part);
+    k_sum_parts<<<1, 32, 0, st>>>(part, nb, norms + s);
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
 }
 
 // Y = M X for an interleaved (rows, B) operand with the FP32 CSR kernels (the
@@ -1281,14 +1527,22 @@ tomo_status run_sirt_bb(const tomo_matrix *h, const float *sino, float *x, int32
 namespace {
 
 template <int B>
-tomo_status time_sirt_pair(const tomo_matrix *h, int format, float *x, float *r, float *b, cudaStream_t st,
-                           double *ms_out) {
+tomo_status time_sirt_pair(const tomo_matrix *h, int format, int order, int blocks, float *x, float *r, float *b,
+                           float *partial, cudaStream_t st, double *ms_out) {
   Exec ex;
   ex.B = B;
   ex.format = format;
+  ex.order = order;
+  ex.blocks = blocks;
   Op A = make_op(h, false, ex), AT = make_op(h, true, ex);
+  A.partial = partial;
+  AT.pre = format == TOMO_FMT_SELL16;
+  const float *rscale = AT.pre ? h->ang_scale : nullptr;
   auto pair = [&]() {
-    launch_spmm<B>(A, x, EpiSirtResidual{r, b, h->R, B}, nullptr, st);
+    if (rscale)
+      launch_spmm<B>(A, x, EpiSirtResidualScaled{r, b, h->R, B, rscale, h->np}, nullptr, st);
+    else
+      launch_spmm<B>(A, x, EpiSirtResidual{r, b, h->R, B}, nullptr, st);
     launch_spmm<B>(AT, r, EpiSirtUpdate{x, h->C, 0.0f, B}, nullptr, st);
   };
   for (int i = 0; i < 2; ++i) pair();
@@ -1310,6 +1564,18 @@ tomo_status time_sirt_pair(const tomo_matrix *h, int format, float *x, float *r,
   return TOMO_OK;
 }
 
+// blocks per SM that the SIRT A pass of (B, format) fits (the autotuner's stage 2 starts below it)
+template <int B>
+int resident_of(const tomo_matrix *h, const Exec &ex) {
+  const Op A = make_op(h, false, ex);
+  const int G = rows_per_warp(ex.format, B);
+  const int grid = spmm_grid_of<B, EpiSirtResidual>(A);
+  const int64_t groups = (A.m->rows + G - 1) / G;
+  const int64_t full = (groups + kWarps - 1) / kWarps;
+  if (grid < full) return std::max(1, grid / num_sms());
+  return std::max(1, (int)((full + num_sms() - 1) / num_sms()));
+}
+
 template <int B>
 struct TimeF {
   template <typename... A>
@@ -1318,54 +1584,96 @@ struct TimeF {
 
 }  // namespace
 
-tomo_status run_autotune(tomo_matrix *h, int32_t nz, bool allow16, tomo_exec_opts *best, double *rate,
+tomo_status run_autotune(tomo_matrix *h, int32_t nz, int allow16, tomo_exec_opts *best, double *rate,
                          tomo_tune_entry *table, int32_t cap, int32_t *n_table, cudaStream_t st) {
   int bmax = 1;
   while (bmax < nz && bmax < 64) bmax <<= 1;
-  if (!h->sA.ent && !h->A.ci && !(allow16 && h->lp_dtype != TOMO_F32))
-    return fail(TOMO_ERR_UNSUPPORTED, "no FP32 form to tune (built with no_fp32_sell and drop_csr)");
+  const bool lp16 = allow16 != 0 && h->lp_dtype != TOMO_F32;
   std::vector<int> fmts;
-  if (h->sA.ent) fmts.push_back(TOMO_FMT_SELL);
-  if (h->A.ci) fmts.push_back(TOMO_FMT_CSR);
-  if (allow16 && h->lp_dtype != TOMO_F32) fmts.push_back(TOMO_FMT_SELL16);
+  if (allow16 != 2) {
+    if (h->sA.ent) fmts.push_back(TOMO_FMT_SELL);
+    if (h->A.ci) fmts.push_back(TOMO_FMT_CSR);
+  }
+  if (lp16) fmts.push_back(TOMO_FMT_SELL16);
+  if (fmts.empty())
+    return fail(TOMO_ERR_UNSUPPORTED, allow16 == 2 ? "matrix was built without 16-bit values"
+                                                   : "no FP32 form to tune (built with no_fp32_sell and drop_csr)");
   const int64_t rows = h->A.rows, cols = h->A.cols;
-  float *x = nullptr, *r = nullptr, *b = nullptr;
+  float *x = nullptr, *r = nullptr, *b = nullptr, *partial = nullptr;
   struct Free {
-    float **p[3];
+    float **p[4];
     ~Free() {
       for (auto q : p)
         if (*q) cudaFree(*q);
     }
-  } guard{{&x, &r, &b}};
+  } guard{{&x, &r, &b, &partial}};
   TOMO_CUDA(cudaMalloc(&x, sizeof(float) * cols * bmax));
   TOMO_CUDA(cudaMalloc(&r, sizeof(float) * rows * bmax));
   TOMO_CUDA(cudaMalloc(&b, sizeof(float) * rows * bmax));
+  if (!h->lpAb.empty()) TOMO_CUDA(cudaMalloc(&partial, sizeof(float) * rows * bmax));
   TOMO_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * cols * bmax, st));
   TOMO_CUDA(cudaMemsetAsync(b, 0, sizeof(float) * rows * bmax, st));
   int n = 0;
   double best_rate = -1.0;
+  tomo_tune_entry bestc{};
+  auto run = [&](int B, int f, int order, int blocks) -> tomo_status {
+    double ms = 0.0;
+    TOMO_TRY(dispatch<TimeF>(B, h, f, order, blocks, x, r, b, partial, st, &ms));
+    const double chunks = (double)((nz + B - 1) / B);
+    const double rt = ms > 0 ? nz / (chunks * ms) * 1000.0 : 0.0;
+    const tomo_tune_entry ent{B, f, order, blocks, ms, rt};
+    if (table && n < cap) table[n] = ent;
+    ++n;
+    if (rt > best_rate) {
+      best_rate = rt;
+      bestc = ent;
+    }
+    return TOMO_OK;
+  };
+  // stage 1: width x format x A^T order
   for (int f : fmts) {
     for (int B = 1; B <= bmax; B <<= 1) {
-      double ms = 0.0;
-      TOMO_TRY(dispatch<TimeF>(B, h, f, x, r, b, st, &ms));
-      const double chunks = (double)((nz + B - 1) / B);
-      const double rt = ms > 0 ? nz / (chunks * ms) * 1000.0 : 0.0;
-      if (table && n < cap) table[n] = tomo_tune_entry{B, f, ms, rt};
-      ++n;
-      if (rt > best_rate) {
-        best_rate = rt;
-        std::memset(best, 0, sizeof(*best));
-        best->batch_width = B;
-        best->format = f;
-        best->use_graph = 1;
-      }
+      const int G = rows_per_warp(f, B);
+      const bool tileable = f != TOMO_FMT_CSR && h->nx % G == 0 && h->ny % 8 == 0;
+      TOMO_TRY(run(B, f, 1, 0));
+      if (tileable) TOMO_TRY(run(B, f, 2, 0));
     }
+  }
+  // stage 2: the best shape with fewer resident blocks per SM
+  {
+    Exec ex;
+    ex.B = bestc.batch_width;
+    ex.format = bestc.format;
+    int res = 0;
+    switch (ex.B) {  // blocks per SM the SIRT A pass of that shape fits
+      case 1: res = resident_of<1>(h, ex); break;
+      case 2: res = resident_of<2>(h, ex); break;
+      case 4: res = resident_of<4>(h, ex); break;
+      case 8: res = resident_of<8>(h, ex); break;
+      case 16: res = resident_of<16>(h, ex); break;
+      case 32: res = resident_of<32>(h, ex); break;
+      default: res = resident_of<64>(h, ex); break;
+    }
+    const tomo_tune_entry s1 = bestc;
+    for (int k = 1; k <= 2; ++k)
+      if (res - k >= 1) TOMO_TRY(run(s1.batch_width, s1.format, s1.order, res - k));
   }
   if (n_table) *n_table = n;
   if (rate) *rate = best_rate;
-  h->tuned_nz = nz;
-  h->tuned_B = best->batch_width;
-  h->tuned_fmt = best->format;
+  std::memset(best, 0, sizeof(*best));
+  best->batch_width = bestc.batch_width;
+  best->format = bestc.format;
+  best->order = bestc.order;
+  best->blocks_per_sm = bestc.blocks_per_sm;
+  best->use_graph = 1;
+  auto &tl = h->tuned;
+  for (size_t k = 0; k < tl.size(); ++k)
+    if (tl[k].nz == nz) {
+      tl.erase(tl.begin() + k);
+      break;
+    }
+  tl.insert(tl.begin(), tomo_matrix::Tuned{nz, bestc.batch_width, bestc.format, bestc.order, bestc.blocks_per_sm});
+  if (tl.size() > 8) tl.pop_back();
   return TOMO_OK;
 }
 

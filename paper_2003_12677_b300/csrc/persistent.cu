@@ -493,6 +493,8 @@ tomo_status check_requests(const tomo_request *reqs, int32_t n, int B, int fmt) 
       if (q.A->lp_dtype == TOMO_F32) return fail(TOMO_ERR_UNSUPPORTED, "a matrix was built without 16-bit values");
       if (lp == -2) lp = q.A->lp_dtype;
       if (q.A->lp_dtype != lp) return fail(TOMO_ERR_UNSUPPORTED, "requests mix bf16 and f16 matrices");
+      if (!q.A->lpAb.empty())
+        return fail(TOMO_ERR_UNSUPPORTED, "a matrix stores its 16-bit A as column bands (col_blocks > 1)");
     }
   }
   return TOMO_OK;

@@ -94,6 +94,26 @@ struct EpiSirtResidual {  // r = R o (b - acc)
   }
 };
 
+// the same, times 1/a(theta) of the row's angle: the operand the 16-bit A^T
+// pass gathers without a per-entry scale (separate type, so the FP32 kernels
+// keep their register budget)
+struct EpiSirtResidualScaled {
+  static constexpr bool kNorm = false;
+  float *r;
+  const float *b, *R;
+  int ld;
+  const float *scale;  // per angle
+  int np;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
+    const float w = __ldg(R + row) * __ldg(scale + row / np);
+    Vec<V> bv = ldg_vec<V>(b + row * ld + s0);
+#pragma unroll
+    for (int t = 0; t < V; ++t) a.v[t] = w * (bv.v[t] - a.v[t]);
+    st_vec<V>(r + row * ld + s0, a);
+  }
+};
+
 struct EpiSirtUpdate {  // x += lambda C o acc
   static constexpr bool kNorm = false;
   float *x;
@@ -153,6 +173,67 @@ struct EpiResidualNorm {  // r = b - acc, ss += r^2
   }
 };
 
+// the same, also writing rs = r times 1/a(theta) of the row's angle (the
+// operand of the 16-bit A^T pass)
+struct EpiResidualNormScaled {
+  static constexpr bool kNorm = true;
+  float *r;
+  const float *b;
+  int ld;
+  float *rs;
+  const float *scale;
+  int np;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *ss) const {
+    Vec<V> bv = ldg_vec<V>(b + row * ld + s0);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      a.v[t] = bv.v[t] - a.v[t];
+      ss[t] += (double)a.v[t] * (double)a.v[t];
+    }
+    st_vec<V>(r + row * ld + s0, a);
+    const float sc = __ldg(scale + row / np);
+#pragma unroll
+    for (int t = 0; t < V; ++t) a.v[t] *= sc;
+    st_vec<V>(rs + row * ld + s0, a);
+  }
+};
+
+// Column bands of A (the image cut into bands of rows, each band stored as a
+// matrix of its own): the pass over band b < last adds its sums into P (band 0
+// stores them); the last band's pass adds P and hands the total to the real
+// epilogue, which alone reduces norms.
+struct EpiBandPartial {
+  static constexpr bool kNorm = false;
+  float *P;
+  int ld;
+  bool first;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *) const {
+    if (!first) {
+      const Vec<V> p = ld_vec<V>(P + row * ld + s0);
+#pragma unroll
+      for (int t = 0; t < V; ++t) a.v[t] += p.v[t];
+    }
+    st_vec<V>(P + row * ld + s0, a);
+  }
+};
+
+template <class Epi>
+struct EpiBandLast {
+  static constexpr bool kNorm = Epi::kNorm;
+  const float *P;
+  int ld;
+  Epi epi;
+  template <int V>
+  __device__ void operator()(int64_t row, int s0, Vec<V> &a, double *ss) const {
+    const Vec<V> p = ld_vec<V>(P + row * ld + s0);
+#pragma unroll
+    for (int t = 0; t < V; ++t) a.v[t] += p.v[t];
+    epi.template operator()<V>(row, s0, a, ss);
+  }
+};
+
 // Deterministic per-block reduction of ss[V] (slices s0..s0+V-1 of each thread)
 // into out[s], s < B.
 // The reduction array doubles as the per-thread accumulators of the norm
@@ -206,6 +287,45 @@ __device__ void block_norms(const double *ss, int s0, int B, double *part) {
   block_norms_to<V>(ss, s0, B, part + (int64_t)blockIdx.x * B);
 }
 
+// Order in which a pass visits its row groups.  IdentityMap: row order.
+// TileMap (A^T, whose rows are pixels): the grid-stride schedule t is mapped
+// so that the 8 warps of a block take 8 image rows x G pixels (a compact cell:
+// rays through it hit few distinct bins, so their gathered residual rows are
+// shared in L1) and consecutive blocks walk the image in tiles of 16 x 16
+// cells (128 image rows x 16 G pixels: the residual rows that a tile's rays
+// touch stay in L2 while the tile is in flight, instead of every angle's whole
+// detector).  A bijection of [0, n_y n_x / G) when n_x % G == 0 and
+// n_y % 8 == 0; gx = 0 selects row order.
+struct IdentityMap {
+  __device__ __forceinline__ int64_t operator()(int64_t t) const { return t; }
+};
+
+struct TileMap {
+  int64_t gx;  // row groups per image row (n_x / G), 0 = row order
+  int64_t cy;  // cell rows (n_y / 8)
+  __device__ __forceinline__ int64_t operator()(int64_t t) const {
+    if (gx == 0) return t;
+    constexpr int64_t kTy = 16, kTx = 16;  // tile of kTy x kTx cells
+    const int64_t w = t & 7, T = t >> 3;   // image row within the cell; cell in tiled order
+    const int64_t band_cells = kTy * gx;
+    const int64_t band = T / band_cells, r = T - band * band_cells;
+    const int64_t ty = min(kTy, cy - band * kTy);
+    const int64_t full = gx / kTx, tile_cells = ty * kTx;
+    const int64_t ct = r / tile_cells;
+    int64_t cyi, cxi;
+    if (ct < full) {
+      const int64_t u = r - ct * tile_cells;
+      cyi = u / kTx;
+      cxi = ct * kTx + u % kTx;
+    } else {  // the narrower last tile of the band
+      const int64_t tw = gx - full * kTx, u = r - full * tile_cells;
+      cyi = u / tw;
+      cxi = full * kTx + u % tw;
+    }
+    return ((band * kTy + cyi) * 8 + w) * gx + cxi;
+  }
+};
+
 // Every SELL entry word is loaded exactly once per pass (one 128-bit load per
 // pair or quad), so those loads carry the streaming (evict-first) hint and
 // leave L2 to the gathered operand vector, which the whole pass reuses.  (The
@@ -235,16 +355,16 @@ struct Lanes {
 
 // kNC: gather X through the read-only path (X unchanged during the launch);
 // false for the persistent kernel, whose vectors change between phases.
-template <int B, class Epi, bool kNC = true>
+template <int B, class Epi, bool kNC = true, class Map = IdentityMap>
 __device__ __forceinline__ void sell_rowgroups(const int64_t *__restrict__ cp, const int32_t *__restrict__ rl,
                                                const int2 *__restrict__ ent, int64_t rows,
                                                const float *__restrict__ X, const Epi &epi, int64_t rg_begin,
-                                               int64_t rg_step, int64_t rg_end, double *ss) {
+                                               int64_t rg_step, int64_t rg_end, double *ss, Map map = Map()) {
   constexpr int V = Lanes<B>::V, L = Lanes<B>::L, G = Lanes<B>::G;
   const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
   const float *Xl = X + l * V;
-  for (int64_t rg = rg_begin; rg < rg_end; rg += rg_step) {
-    const int64_t row = rg * G + g;
+  for (int64_t t = rg_begin; t < rg_end; t += rg_step) {
+    const int64_t row = map(t) * G + g;
     if (row >= rows) continue;
     Vec<V> acc;
 #pragma unroll
@@ -324,15 +444,18 @@ struct Sell16View {
   float inv_np;
 };
 
-template <int B, bool kBf16, bool kTrans, class Epi, bool kNC = true>
+// kPre (A^T only): the gathered operand already carries the per-angle factor
+// 1/a(theta) of its rows (the solvers write it that way), so the entries need
+// no per-entry scale lookup.
+template <int B, bool kBf16, bool kTrans, class Epi, bool kNC = true, bool kPre = false, class Map = IdentityMap>
 __device__ __forceinline__ void sell16_rowgroups(const Sell16View &M, int64_t rows, const float *__restrict__ X,
                                                  const Epi &epi, int64_t rg_begin, int64_t rg_step, int64_t rg_end,
-                                                 double *ss) {
+                                                 double *ss, Map map = Map()) {
   constexpr int V = Lanes<B>::V, L = Lanes<B>::L, G = Lanes<B>::G;
   const int lane = threadIdx.x & 31, l = lane % L, g = lane / L;
   const float *Xl = X + l * V;
-  for (int64_t rg = rg_begin; rg < rg_end; rg += rg_step) {
-    const int64_t row = rg * G + g;
+  for (int64_t t = rg_begin; t < rg_end; t += rg_step) {
+    const int64_t row = map(t) * G + g;
     if (row >= rows) continue;
     Vec<V> acc;
 #pragma unroll
@@ -359,7 +482,7 @@ __device__ __forceinline__ void sell16_rowgroups(const Sell16View &M, int64_t ro
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           float w = w16<kBf16>(pk[u]);
-          if constexpr (kTrans) w *= __ldg(M.scale + div_exact(cc[u], M.np, M.inv_np));
+          if constexpr (kTrans && !kPre) w *= __ldg(M.scale + div_exact(cc[u], M.np, M.inv_np));
 #pragma unroll
           for (int t = 0; t < V; ++t) acc.v[t] = fmaf(w, xv[u].v[t], acc.v[t]);
         }

@@ -237,6 +237,12 @@ WORKLOADS["fubini_512x360_b64"] = Workload("fubini_512x360_b64", 512, 360, 64, "
 WORKLOADS["fubini_normal_512x360_b64"] = Workload("fubini_normal_512x360_b64", 512, 360, 64, "fubini_normal", 30,
                                                  "poisson", 1e4, "ellipsoids3d", seed=12677 + 2)
 
+# a profiling stand-in for cgls_2048x1024_b16: the same image, detector, slices
+# and 16-bit values on 128 of the angles (one eighth of the matrix, a few GB),
+# for hardware-counter captures that replay each launch many times
+WORKLOADS["cgls_2048x128_b16"] = Workload("cgls_2048x128_b16", 2048, 128, 16, "cgls", 50,
+                                         "gaussian", 0.05, "ellipsoids3d", values="bf16", seed=12677 + 3)
+
 WORKLOADS["uneven_256"] = Workload("uneven_256", 2048, 1024, 0, "cgls", 30, "poisson", 1e5, "ellipses2d",
                                   values="bf16", seed=12677 + 5)
 

@@ -60,20 +60,26 @@ def textbook_cgls(S, ST, b, iters, dtype, recompute=0, S_rec=None):
 
 
 def _bf16(v):
-    u = np.ascontiguousarray(v, np.float32).view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32)
+    """FP64 -> bf16 (8 significand bits), round to nearest even, as float64."""
+    m, e = np.frexp(np.asarray(v, np.float64))
+    return np.ldexp(np.round(m * 256.0), e - 8)
 
 
-def lowprec_values(A, g, kind):
-    """FP32 values of the 16-bit form: round(L a) to `kind`, times fl32(1/a)."""
+def lowprec_weights(A, g, kind):
+    """(16-bit weights round(L a) as float64, fl32(1/a) of every entry)."""
     cs, sn = g.trig()
     a = np.maximum(np.abs(cs), np.abs(sn))
     ang = np.repeat(np.arange(g.n_theta), g.n_p)                     # angle of every row
     row_a = np.repeat(a[ang], np.diff(A.row_ptr))                     # a of every entry
-    scaled = (A.val * row_a).astype(np.float32)
-    w = _bf16(scaled) if kind == "bf16" else scaled.astype(np.float16).astype(np.float32)
-    return (w * (1.0 / row_a).astype(np.float32)).astype(np.float32)
+    scaled = A.val * row_a
+    w = _bf16(scaled) if kind == "bf16" else scaled.astype(np.float16).astype(np.float64)
+    return w, (1.0 / row_a).astype(np.float32).astype(np.float64)
+
+
+def lowprec_values(A, g, kind):
+    """FP32 values of the 16-bit form: round(L a) to `kind`, times fl32(1/a)."""
+    w, sc = lowprec_weights(A, g, kind)
+    return (w * sc).astype(np.float32)
 
 
 def data_fit(S64, b, xs):

@@ -15,16 +15,19 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_reference_arm_line():
+@pytest.mark.parametrize("workload", [None, "sirt_512x360_b64"])
+def test_reference_arm_line(workload):
+    """The default (CGLS, 2048^2 x 1024) and the SIRT workload."""
+    extra = [] if workload is None else ["--workload", workload]
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, timeout=600)
+                        "--warmup", "0"] + extra, capture_output=True, text=True, cwd=ROOT, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
-    assert line["config"]["workload"] == "sirt_512x360_b64"
+    assert line["config"]["workload"] == (workload or "cgls_2048x1024_b16")
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]

@@ -17,7 +17,9 @@ import pytest
 import oracle
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-FILES = sorted(glob.glob(os.path.join(HERE, "*.json")))
+# the small fixtures of make_golden.py (cgls_*_slice0.json are data-fit histories of large
+# workloads, written by make_cgls_2048.py and checked below)
+FILES = sorted(f for f in glob.glob(os.path.join(HERE, "*.json")) if not os.path.basename(f).startswith("cgls_"))
 
 
 def load(path):
@@ -93,3 +95,18 @@ def test_gpu_matches_golden(path):
         for k in range(nz):
             assert np.linalg.norm(x[k] - d["cgls"][k]) <= 1e-4 * np.linalg.norm(d["cgls"][k])
     M.close()
+
+
+def test_stored_cgls_data_fit_history():
+    """The stored 2048^2 x 1024 CGLS history: the FP64 recurrence residual
+    equals the true residual ||b - A x_k|| (recomputed by the oracle when it was
+    written) to 1e-12 at the checked iterations, and never increases (CGLS
+    minimises it over growing Krylov spaces)."""
+    with open(os.path.join(HERE, "cgls_2048x1024_slice0.json")) as f:
+        d = json.load(f)
+    res = np.array(d["resnorm"])
+    assert len(res) == d["iters"] >= 50
+    for k, v in d["true_resnorm"].items():
+        assert abs(res[int(k) - 1] - v) <= 1e-12 * v
+    assert np.all(np.diff(res) <= 0) and res[0] < d["b_norm"]
+    assert len(d["sample_index"]) == len(d["samples"]["1"]) == 1024

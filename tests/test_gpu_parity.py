@@ -359,16 +359,30 @@ def test_lowprec_corner_gaps(values):
 
 
 def test_autotune_choice_is_used_by_default():
+    """The tuner searches width x format x A^T row-group order, then fewer
+    resident blocks per SM for the best shape; calls with the defaults use its
+    choice and give the bits of the explicit choice; every order and block
+    count gives the same bits (the order of rows changes no sum)."""
     g, A, AT, M = pair(nx=128, nt=180)
     res = M.autotune(6)
     assert res["batch_width"] in (1, 2, 4, 8) and res["format"] in ("sell", "csr")
-    assert len(res["table"]) == 2 * 4 and res["slice_iters_per_s"] > 0
-    assert max(t["slice_iters_per_s"] for t in res["table"]) == res["slice_iters_per_s"]
+    t = res["table"]
+    assert len(t) >= 12 and res["slice_iters_per_s"] > 0
+    assert {e["order"] for e in t if e["format"] == "sell"} == {"rows", "tiles"}
+    assert any(e["blocks_per_sm"] > 0 for e in t)
+    assert max(e["slice_iters_per_s"] for e in t) == res["slice_iters_per_s"]
     c = inputs.make_case(128, 180, 6, seed=9, phantom="ellipsoids3d", noise="poisson", level=1e4)
     sino = torch.from_numpy(c.sino).cuda()
     auto = tomo.sirt(M, sino, 10, batch_width=0, fmt="auto")
-    expl = tomo.sirt(M, sino, 10, batch_width=res["batch_width"], fmt=res["format"])
-    assert torch.equal(auto, expl)   # same kernels, same order: bit-identical
+    try:
+        tomo.set_launch(order=res["order"], blocks_per_sm=res["blocks_per_sm"])
+        expl = tomo.sirt(M, sino, 10, batch_width=res["batch_width"], fmt=res["format"])
+        tomo.set_launch(order="rows", blocks_per_sm=3)
+        other = tomo.sirt(M, sino, 10, batch_width=res["batch_width"], fmt=res["format"])
+    finally:
+        tomo.set_launch()
+    assert torch.equal(auto, expl)   # same kernels, same sums: bit-identical
+    assert torch.equal(auto, other)
     ref = oracle.sirt(A, AT, c.sino.reshape(6, -1), 10)
     assert per_slice_rel(auto.cpu().numpy(), ref).max() < 1e-4
 
@@ -394,3 +408,53 @@ def test_errors_are_reported():
         tomo.project(M, torch.zeros((3, 64, 64), device="cuda"), batch_width=3)
     with pytest.raises(_lib.TomoError):
         tomo.project(M, torch.zeros((1, 64, 64), device="cuda"), fmt="sell16")
+
+
+def _oracle16(g, A, values):
+    """The oracle's CSR pair with the 16-bit form's values (weights round(L a)
+    times fl32(1/a), exact in FP64), so that the GPU's 16-bit kernels are held
+    to their arithmetic alone."""
+    import cgls_reference as cr
+    v = cr.lowprec_values(A, g, values).astype(np.float64)
+    A16 = oracle.CSR(A.rows, A.cols, A.row_ptr, A.col, v)
+    return A16, A16.transpose()
+
+
+@pytest.mark.parametrize("values", ["bf16", "f16"])
+@pytest.mark.parametrize("geom,bands", [(dict(nx=96, nt=120), 3), (dict(nx=37, nt=23, n_p=41, center=19.7), 5),
+                                        (dict(nx=40, nt=7, ny=29, n_p=50), 29)])
+def test_banded_16bit_operator(values, geom, bands):
+    """The 16-bit A stored as column bands (bands of image rows, one pass each,
+    partial sums added in a workspace buffer): y = A x at widths 1, 4, 16
+    (slice-major) and 8 (interleaved) equals the FP64 oracle applied to the same
+    16-bit values within 1e-5, as does the unbanded form; x = A^T y too; CGLS
+    over 3 iterations agrees with the unbanded form within 1e-4; the persistent
+    batched solver rejects banded matrices."""
+    g, A, AT, _ = pair(values=values, **geom)
+    nx, ny, nt = geom["nx"], geom.get("ny", geom["nx"]), geom["nt"]
+    kw = dict(n_p=geom.get("n_p"), n_y=geom.get("ny"), center=geom.get("center"), values=values)
+    Mb = tomo.Matrix(nx, nt, col_blocks=bands, **kw)
+    Mu = tomo.Matrix(nx, nt, **kw)
+    A16, AT16 = _oracle16(g, A, values)
+    x = inputs.random_slices((8, ny, nx), seed=61)
+    y = inputs.random_slices((8, nt, g.n_p), seed=62)
+    ref_y, ref_x = A16.apply(x), AT16.apply(y)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    for M in (Mb, Mu):
+        for B in (1, 4, 16):
+            yd = tomo.project(M, xt, batch_width=B, fmt="sell16").cpu().numpy()
+            assert per_slice_rel(yd, ref_y).max() < 1e-5, (B, M is Mb)
+            xd = tomo.backproject(M, yt, batch_width=B, fmt="sell16").cpu().numpy()
+            assert per_slice_rel(xd, ref_x).max() < 1e-5, (B, M is Mb)
+        xi = xt.reshape(8, -1).t().contiguous()
+        yi = tomo.project(M, xi, fmt="sell16", interleaved=True).t().cpu().numpy()
+        assert per_slice_rel(yi, ref_y).max() < 1e-5
+    sino = torch.from_numpy(np.ascontiguousarray(ref_y.astype(np.float32))).cuda()
+    # the bands only change the order of FP32 sums, which CGLS amplifies (its
+    # iterates part like two FP64 runs with different summation orders)
+    cb = tomo.cgls(Mb, sino, 3, batch_width=4, fmt="sell16")
+    cu = tomo.cgls(Mu, sino, 3, batch_width=4, fmt="sell16")
+    assert per_slice_rel(cb.cpu().numpy(), cu.cpu().numpy()).max() < 1e-4
+    with pytest.raises(_lib.TomoError) as ei:
+        tomo.cgls_batched([(Mb, sino)], 1, batch_width=4, fmt="sell16")
+    assert ei.value.code == 5

@@ -68,3 +68,16 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     assert lib.tomo_build_matrix(ctypes.byref(g), None, None, ctypes.byref(h)) == 1
     assert lib.tomo_project(None, None, None, 1, 0, None, None, 0, None) == 1
     assert lib.tomo_sirt(None, None, None, 1, 1, ctypes.c_float(1.0), None, None, 0, None) == 1
+
+
+def test_more_arguments_rejected_without_gpu(lib_path):
+    """TV's eps must have a normal FP32 square; the data-fit call needs its buffers."""
+    import numpy as np
+    from paper_2003_12677_b300 import _lib
+    lib = _lib.load(lib_path)
+    buf = np.zeros(64, np.float64)        # host memory, 16-byte aligned; never dereferenced here
+    p = ctypes.c_void_p(buf.ctypes.data)
+    assert buf.ctypes.data % 16 == 0
+    assert lib.tomo_tv(p, 1, 2, 2, ctypes.c_float(1e-20), p, p, None) == 1
+    assert b"eps" in lib.tomo_last_error()
+    assert lib.tomo_residual_norm(None, p, p, 1, p, None, 0, None) == 1
