@@ -13,7 +13,7 @@ build is deterministic, so every replica is bit-identical.
 """
 from __future__ import annotations
 
-from typing import List, Optional, Tuple
+from typing import Callable, List, Optional, Tuple
 
 import torch
 import torch.distributed as dist
@@ -69,3 +69,29 @@ def gather_slices(local: torch.Tensor, n_z: int, chunk: Optional[int] = None, ds
         for i, s in enumerate(owned[k]):
             out[s] = bufs[k][i]
     return out
+
+
+def solve_sharded(solve: Callable[[torch.Tensor], torch.Tensor], sino: torch.Tensor, chunk: Optional[int] = None,
+                  dst: int = 0, out_shape: Optional[Tuple[int, ...]] = None) -> Optional[torch.Tensor]:
+    """One slice stack solved by all ranks (Sec. 3.1): every rank takes its own
+    slices of `sino` (n_z, ...) by slice_plan -- loops of at most `chunk`
+    slices, the last loop split unevenly -- and runs `solve` on each loop's
+    consecutive slices (a callable mapping sinograms (k, ...) to tomograms
+    (k, ...), e.g. a CGLS solve with the library's kernels on this rank's GPU);
+    rank `dst` gathers the tomograms in stack order and returns them, the other
+    ranks return None.  No data moves between ranks while they iterate; the
+    gather at the end is the only collective.  out_shape: the shape of one
+    tomogram, needed only by a rank that owns no slice (else it solves one
+    slice to learn it)."""
+    world, rank = dist.get_world_size(), dist.get_rank()
+    n_z = sino.shape[0]
+    outs = [solve(sino[b:e].contiguous()) for b, e in slice_plan(n_z, world, chunk)[rank]]
+    if outs:
+        local = torch.cat(outs)
+    elif out_shape is not None:  # more ranks than slices: this rank contributes nothing
+        local = torch.empty((0,) + tuple(out_shape), dtype=sino.dtype, device=sino.device)
+    else:
+        probe = solve(sino[:1].contiguous()) if n_z else None
+        tail = tuple(probe.shape[1:]) if probe is not None else ()
+        local = torch.empty((0,) + tail, dtype=probe.dtype if probe is not None else sino.dtype, device=sino.device)
+    return gather_slices(local, n_z, chunk, dst)
