@@ -360,6 +360,25 @@ def test_cgls_resume_continues_the_same_recurrence():
     np.testing.assert_array_equal(hr, h12[5:])
 
 
+@pytest.mark.parametrize("n,nt,n_p,center", [(16, 20, 16, None), (13, 8, 17, 7.3), (24, 6, 30, None)])
+def test_quarter_turn_symmetry(n, nt, n_p, center):
+    """The ray of angle theta + pi/2 meets pixel (ix, iy) exactly as the ray of
+    theta with the same bin meets pixel (iy, n - 1 - ix): the square grid and
+    the detector line are symmetric under a quarter turn.  So with the default
+    angles and an even n_theta, row (m + n_theta/2, k) of A is row (m, k) with
+    its columns turned; the FP64 evaluation of the two angles' cosines and
+    sines differs in the last bits, which moves the values by ~1e-13 and can
+    flip only entries of length ~0 (a line through a pixel corner)."""
+    g = oracle.Geometry(n, n, n_p, nt, None, center)
+    D = oracle.build_matrix(g).dense()
+    half = nt // 2 * n_p
+    rho = np.array([(n - 1 - (j % n)) * n + (j // n) for j in range(n * n)])
+    turned = D[:half][:, rho]
+    assert np.abs(D[half:] - turned).max() < 1e-12
+    flipped = (D[half:] != 0) != (turned != 0)
+    assert np.all(np.maximum(D[half:], turned)[flipped] < 1e-12)
+
+
 def test_cgls_matrix_free_equals_stored():
     """The matrix-free CGLS (products generated on the fly) takes the same
     steps in the same summation order as the stored form: bit for bit, from
