@@ -66,7 +66,7 @@ def parse():
     p.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                    help="N > 1: weak = every rank solves its own copy of the batch; strong = the batch's slices "
                         "are split over the ranks (Sec. 3.1's plan) and gathered on rank 0 inside the timed step")
-    p.add_argument("--order", default="auto", choices=["auto", "rows", "tiles"],
+    p.add_argument("--order", default="auto", choices=["auto", "rows", "tiles", "staged"],
                    help="row-group order of the A^T passes (same bits, different speed)")
     p.add_argument("--no-csr", action="store_true",
                    help="CGLS: build without the FP32 CSR pair (implies --no-extras: the comparators and the "
@@ -320,7 +320,7 @@ def spmm_roofline(M, B, fmt, tm, kinds, torch, local, clk):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = (clk or {}).get("sm_mhz") or 2032.0
     gathered = nnz * B * 4
-    roof = {"bound": "hbm", "kernel": name % (KERNEL[fmt], B), "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roof = {"bound": "hbm", "kernel": name % ((KERNEL[fmt], B) if "%s" in name else (B,)), "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None, "peak_source": src + " (burst copy)",
             "alg_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
             "kernel_share": tm.ms[kind] / max(sum(tm.ms[k] for k in range(3)), 1e-12)}
@@ -744,15 +744,17 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_names(solver, fmt, B):
+def kernel_names(solver, fmt, B, staged=False):
     """(name template, output vectors read or written per output row and slice) of the
-    A pass (kind 0) and the A^T pass (kind 1) of a solver's iteration."""
+    A pass (kind 0) and the A^T pass (kind 1) of a solver's iteration; staged: the
+    A^T pass is the tiled 16-bit one (detector windows staged in shared memory)."""
+    at = "k_spmm_tile16<%d, %s> (A^T pass, staged tiles" if staged else "k_spmm_%s<%d, %s> (A^T pass"
     if solver == "sirt":   # r = R o (b - A x): b read, r written; x += lam C o A^T r: x read + written
         return [("k_spmm_%s<%d, EpiSirtResidual> (A pass)", 2),
-                ("k_spmm_%s<%d, EpiSirtUpdate> (A^T pass)", 2)]
+                (at.replace("%s>", "EpiSirtUpdate>", 1) + ")", 2)]
     # CGLS: q = A p and s = A^T r, each written once with its squared norm
     return [("k_spmm_%s<%d, EpiStoreNorm> (A pass, q = A p)", 1),
-            ("k_spmm_%s<%d, EpiStoreNorm> (A^T pass, s = A^T r)", 1)]
+            (at.replace("%s>", "EpiStoreNorm>", 1) + ", s = A^T r)", 1)]
 
 
 def golden_fit(w):
@@ -946,7 +948,11 @@ def run_main(args, w):
     line["gpu_launches"] = launches * args.steps
     tot = sum(tm.ms[k] for k in range(3))
     line["time_split"] = {"A": tm.ms[0] / tot, "A^T": tm.ms[1] / tot, "vector+scalar": tm.ms[2] / tot}
-    kinds = kernel_names(w.solver, fmt, B)
+    # the A^T pass streams the tiled 16-bit A^T when the resolved order is "staged"
+    staged = (fmt == "sell16" and B == 16 and M.has_at_tiles and
+              (args.order == "staged" or (args.order == "auto" and (tune is None or tune["order"] in ("staged", "auto")))))
+    line["config"]["at_order"] = "staged" if staged else (tune["order"] if tune and args.order == "auto" else args.order)
+    kinds = kernel_names(w.solver, fmt, B, staged)
     roof, ceil = spmm_roofline(M, B, fmt, tm, kinds, torch, local, clk)
     kind = 0 if tm.ms[0] >= tm.ms[1] else 1
     tpath = os.path.join(ROOT, "profiles", "traffic.json")

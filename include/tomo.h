@@ -101,7 +101,11 @@ typedef struct {
                             in a workspace buffer, so that each pass gathers only its band of the image
                             (which can stay in L2 when the whole image stack cannot).  0 or 1: one band;
                             at most min(64, n_y).  tomo_cgls_batched rejects banded matrices. */
-  int32_t reserved[3];
+  int32_t no_at_tiles;   /* 16-bit values only.  0 (default): also store the 16-bit A^T in image tiles of
+                            16 x 16 pixels (about 4.7 B/nnz more), for the SIRT / CGLS passes at batch
+                            width 16 that stage each tile's detector window, 8 angles at a time, in
+                            shared memory (order 3 of tomo_exec_opts).  Non-zero: do not build it. */
+  int32_t reserved[2];
 } tomo_matrix_opts;
 
 /* Device time of the kernels one call launched, filled when a call is given
@@ -142,11 +146,16 @@ typedef struct {
                           the periodic residual r = b - A x with the FP32 values of A (the FP32
                           SELL form when built, else CSR) instead of the 16-bit ones */
   int32_t order;       /* order in which the SELL A^T passes visit their rows (pixels): 0 = auto
-                          (image tiles when the gathered sinogram batch exceeds 64 MB, else row
-                          order), 1 = row order, 2 = image tiles (blocks of 8 image rows, tiles of
-                          128 rows, so a block's rays share sinogram rows in L1 and a tile's stay
-                          in L2).  The results are the same bits either way.  After
-                          tomo_autotune for this slice count, 0 selects the tuned order. */
+                          (3 where it applies, else image tiles when the gathered sinogram batch
+                          exceeds 64 MB, else row order), 1 = row order, 2 = image tiles (blocks of
+                          8 image rows, tiles of 128 rows, so a block's rays share sinogram rows in
+                          L1 and a tile's stay in L2), 3 = staged tiles: the SIRT / CGLS A^T passes
+                          with TOMO_FMT_SELL16 at batch width 16 on a matrix with the tiled 16-bit
+                          A^T (tomo_matrix_opts.no_at_tiles = 0) stream it, one block per 16 x 16
+                          pixel tile, gathering from the tile's detector window staged in shared
+                          memory (other passes keep order 2).  The results are the same bits
+                          either way.  After tomo_autotune for this slice count, 0 selects the
+                          tuned order. */
   int32_t blocks_per_sm; /* resident blocks per SM the SpMM launches use: 0 = all that fit (or the
                           tuned count after tomo_autotune for this slice count), else at most this
                           many.  The results are the same bits either way. */
@@ -161,7 +170,7 @@ typedef struct {
   int64_t bytes_lp;    /* device bytes of the 16-bit pair (0 if not built) */
   int64_t max_row_len, max_col_len;
   int32_t lp_dtype;    /* tomo_dtype of the 16-bit values (TOMO_F32 if none) */
-  int32_t reserved;
+  int32_t at_tiles;    /* non-zero when the 16-bit A^T is also stored in image tiles (order 3) */
 } tomo_matrix_info_t;
 
 /* Operations that need scratch memory; see tomo_workspace_size. */
@@ -379,7 +388,7 @@ TOMO_API tomo_status tomo_cgls_batched_workspace(const tomo_request *reqs, int32
 /* One timed candidate of tomo_autotune. */
 typedef struct {
   int32_t batch_width, format;
-  int32_t order;             /* row-group order of the A^T pass (1 rows, 2 image tiles) */
+  int32_t order;             /* row-group order of the A^T pass (1 rows, 2 image tiles, 3 staged tiles) */
   int32_t blocks_per_sm;     /* resident blocks per SM (0 = all that fit) */
   double ms_per_iter;        /* one SIRT iteration (A pass + A^T pass) over one batch of batch_width slices */
   double slice_iters_per_s;  /* for n_z slices: n_z / (ceil(n_z / batch_width) * ms_per_iter) */

@@ -38,7 +38,8 @@ class Geometry(ctypes.Structure):
 
 class MatrixOpts(ctypes.Structure):
     _fields_ = [("values", ctypes.c_int32), ("no_fp32_sell", ctypes.c_int32), ("drop_csr", ctypes.c_int32),
-                ("model", ctypes.c_int32), ("col_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("model", ctypes.c_int32), ("col_blocks", ctypes.c_int32), ("no_at_tiles", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Timing(ctypes.Structure):
@@ -78,7 +79,7 @@ class MatrixInfo(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("bytes_f32", ctypes.c_int64), ("bytes_lp", ctypes.c_int64),
                 ("max_row_len", ctypes.c_int64), ("max_col_len", ctypes.c_int64),
-                ("lp_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lp_dtype", ctypes.c_int32), ("at_tiles", ctypes.c_int32)]
 
 
 _lib = None

@@ -47,14 +47,15 @@ def _fmt(fmt) -> int:
     return FORMATS[fmt]
 
 
-ORDERS = {"auto": 0, "rows": 1, "tiles": 2}
+ORDERS = {"auto": 0, "rows": 1, "tiles": 2, "staged": 3}
 _launch = {"order": "auto", "blocks_per_sm": 0}
 
 
 def set_launch(order: str = "auto", blocks_per_sm: int = 0):
     """Launch shape of the SpMM passes of later calls: the row-group order of
-    the A^T passes ("auto", "rows" or "tiles") and the resident blocks per SM
-    (0: all that fit).  "auto" / 0 take tomo_autotune's choice for the slice
+    the A^T passes ("auto", "rows", "tiles" or "staged": the 16-bit passes at
+    batch width 16 stream the tiled A^T and stage each tile's detector window
+    in shared memory) and the resident blocks per SM (0: all that fit).  "auto" / 0 take tomo_autotune's choice for the slice
     count when there is one.  The results are the same bits either way."""
     if order not in ORDERS:
         raise ValueError("order must be one of %s" % sorted(ORDERS))
@@ -94,12 +95,13 @@ class Matrix:
     skips the FP32 SELL-32 copy and keep_csr=False frees the CSR pair after
     the SELL forms are built (memory for very large geometries).  col_blocks
     > 1 stores the 16-bit A as that many bands of image rows, so that each
-    projection pass gathers one band (which can stay in L2).
+    projection pass gathers one band (which can stay in L2).  at_tiles=False
+    skips the tiled copy of the 16-bit A^T (the "staged" order's operand).
     """
 
     def __init__(self, n: int, n_theta: int, n_p: Optional[int] = None, n_y: Optional[int] = None,
                  angles=None, center: Optional[float] = None, values: str = "f32", fp32_sell: bool = True,
-                 keep_csr: bool = True, model: str = "line", col_blocks: int = 0):
+                 keep_csr: bool = True, model: str = "line", col_blocks: int = 0, at_tiles: bool = True):
         self._h = None
         lib = _lib.load()
         if not torch.cuda.is_available():
@@ -125,6 +127,7 @@ class Matrix:
         o.drop_csr = 0 if keep_csr else 1
         o.model = MODELS[model]
         o.col_blocks = int(col_blocks)
+        o.no_at_tiles = 0 if at_tiles else 1
         h = ctypes.c_void_p()
         _lib.check(lib.tomo_build_matrix(ctypes.byref(g), ctypes.byref(o), _stream(), ctypes.byref(h)),
                    "tomo_build_matrix")
@@ -136,6 +139,7 @@ class Matrix:
         self.rows, self.cols, self.nnz = info.rows, info.cols, info.nnz
         self.bytes_f32, self.bytes_lp = info.bytes_f32, info.bytes_lp
         self.max_row_len, self.max_col_len = info.max_row_len, info.max_col_len
+        self.has_at_tiles = bool(info.at_tiles)
 
     @property
     def handle(self) -> ctypes.c_void_p:
@@ -201,7 +205,7 @@ class Matrix:
         n = ctypes.c_int32()
         _lib.call("tomo_autotune", self.handle, n_z, mode, ctypes.byref(best), ctypes.byref(rate),
                   table, 64, ctypes.byref(n), _stream())
-        names = {1: "rows", 2: "tiles"}
+        names = {1: "rows", 2: "tiles", 3: "staged"}
         rows = [{"batch_width": t.batch_width, "format": FORMAT_NAMES[t.format], "order": names.get(t.order, "auto"),
                  "blocks_per_sm": t.blocks_per_sm, "ms_per_iter": t.ms_per_iter,
                  "slice_iters_per_s": t.slice_iters_per_s} for t in table[:min(n.value, 64)]]

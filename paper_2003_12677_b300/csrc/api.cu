@@ -80,6 +80,7 @@ tomo_status tomo_matrix_info(const tomo_matrix *A, tomo_matrix_info_t *info) {
   info->max_row_len = A->A.max_len;
   info->max_col_len = A->AT.max_len;
   info->lp_dtype = A->lp_dtype;
+  info->at_tiles = A->lpATt.ent != nullptr ? 1 : 0;
   return TOMO_OK;
 }
 

@@ -17,6 +17,7 @@
 // Two discretisations share the enumeration: the line model (chord lengths)
 // and the strip model (the area of the pixel inside the unit-width strip of
 // bin k), which differ only in the support half width hs and the weight.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -546,6 +547,234 @@ tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_
   return TOMO_OK;
 }
 
+// ---------------------------------------------------------------------------
+// 16-bit A^T in image tiles (TileLp): one block of 256 threads per tile, one
+// thread per pixel (thread j: tile row j / 16, column j % 16), each walking its
+// pixel's row of the A^T CSR (columns ascending: angle-major, bins ascending).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool tile_pixel(int64_t t, int tiles_x, int nx, int ny, int &ix, int &iy) {
+  const int ty = (int)(t / tiles_x), tx = (int)(t - (int64_t)ty * tiles_x);
+  iy = ty * kTileSide + (int)(threadIdx.x >> 4);
+  ix = tx * kTileSide + (int)(threadIdx.x & 15);
+  return ix < nx && iy < ny;
+}
+
+// pass 1: per (tile, angle) the lowest bin any pixel meets (INT32_MAX if
+// none) into win, and the widest span of bins over all (tile, angle) into *wmax
+__global__ void __launch_bounds__(256) k_tile_window(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                     int nx, int ny, int np, int nt, int tiles_x,
+                                                     int32_t *__restrict__ win, int *__restrict__ wmax) {
+  extern __shared__ int tw_sm[];
+  int *lo = tw_sm, *hi = tw_sm + nt;
+  const int64_t t = blockIdx.x;
+  for (int m = threadIdx.x; m < nt; m += blockDim.x) {
+    lo[m] = INT32_MAX;
+    hi[m] = -1;
+  }
+  __syncthreads();
+  int ix, iy;
+  if (tile_pixel(t, tiles_x, nx, ny, ix, iy)) {
+    const int64_t row = (int64_t)iy * nx + ix;
+    for (int64_t e = rp[row], end = rp[row + 1]; e < end; ++e) {
+      const int col = ci[e], m = col / np, k = col - m * np;
+      atomicMin(lo + m, k);
+      atomicMax(hi + m, k);
+    }
+  }
+  __syncthreads();
+  int w = 0;
+  for (int m = threadIdx.x; m < nt; m += blockDim.x) {
+    win[t * nt + m] = lo[m];
+    if (hi[m] >= 0) w = max(w, hi[m] - lo[m] + 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+  if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(wmax, w);
+}
+
+__global__ void k_tile_clamp(int32_t *__restrict__ win, int64_t n, int32_t hi) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    win[j] = min(win[j], hi);
+}
+
+// pass 2: slot pairs of each (tile, chunk, group): the group's longest pixel
+__global__ void __launch_bounds__(256) k_tile_count(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                    int nx, int ny, int np, int nt, int tiles_x, int nch,
+                                                    int32_t *__restrict__ cnt) {
+  const int64_t t = blockIdx.x;
+  int ix, iy;
+  int64_t e = 0, end = 0;
+  if (tile_pixel(t, tiles_x, nx, ny, ix, iy)) {
+    const int64_t row = (int64_t)iy * nx + ix;
+    e = rp[row];
+    end = rp[row + 1];
+  }
+  const int h = (int)(threadIdx.x >> 4) * 2 + (int)((threadIdx.x >> 3) & 1);
+  for (int k = 0; k < nch; ++k) {
+    const int64_t lim = (int64_t)min((k + 1) * kTileChunk, nt) * np;
+    int n = 0;
+    while (e < end && ci[e] < lim) {
+      ++n;
+      ++e;
+    }
+    // the 8 pixels of a group are 8 consecutive threads
+    n = max(n, __shfl_xor_sync(0xffffffffu, n, 1));
+    n = max(n, __shfl_xor_sync(0xffffffffu, n, 2));
+    n = max(n, __shfl_xor_sync(0xffffffffu, n, 4));
+    if ((threadIdx.x & 7) == 0) cnt[(t * nch + k) * 32 + h] = (n + 1) >> 1;
+  }
+}
+
+__global__ void k_tile_offsets(const int64_t *__restrict__ off, int64_t n, uint32_t *__restrict__ qoff) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += (int64_t)gridDim.x * blockDim.x)
+    qoff[j] = (uint32_t)off[j];
+}
+
+// most pairs of one (tile, chunk): the size of the pass's staged entry buffer
+__global__ void k_tile_max_pairs(const int64_t *__restrict__ off, int64_t chunks, int *__restrict__ mx) {
+  int m = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < chunks; j += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)(off[(j + 1) * 32] - off[j * 32]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+}
+
+// pass 3: the words, with the weights of k_sell16_fill (same FP64 rule, same rounding)
+template <typename W>
+__global__ void __launch_bounds__(256) k_tile_fill(const AngleC *__restrict__ ang, int model, double c,
+                                                   const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                   int nx, int ny, int np, int nt, int tiles_x, int nch, int wlen,
+                                                   const uint32_t *__restrict__ qoff, const int32_t *__restrict__ win,
+                                                   uint32_t *__restrict__ ent) {
+  const int64_t t = blockIdx.x;
+  int ix, iy;
+  if (!tile_pixel(t, tiles_x, nx, ny, ix, iy)) return;
+  const int64_t row = (int64_t)iy * nx + ix;
+  const int h = (int)(threadIdx.x >> 4) * 2 + (int)((threadIdx.x >> 3) & 1), i = (int)(threadIdx.x & 7);
+  const double x = coord(ix, nx), y = coord(iy, ny);
+  int kc = -1, s = 0;
+  uint32_t q0 = 0;
+  for (int64_t e = rp[row], end = rp[row + 1]; e < end; ++e) {
+    const int col = ci[e], m = col / np, k = col - m * np, ch = m / kTileChunk;
+    if (ch != kc) {
+      kc = ch;
+      s = 0;
+      q0 = qoff[(t * nch + ch) * 32 + h];
+    }
+    // byte offset of the entry's row in the staged window
+    const uint32_t off = (uint32_t)((m - ch * kTileChunk) * wlen + (k - win[t * nt + m])) * (uint32_t)kTileRow;
+    const AngleC A = ang[m];
+    const double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
+    const double w = __dmul_rn(chord_len(A, model, pk, x, y), A.a);
+    uint16_t wbits;
+    if constexpr (std::is_same<W, __nv_bfloat16>::value)
+      wbits = __bfloat16_as_ushort(__double2bfloat16(w));
+    else
+      wbits = __half_as_ushort(__double2half(w));
+    ent[((size_t)q0 + (s >> 1)) * 16 + 2 * i + (s & 1)] = (off << 16) | (uint32_t)wbits;
+    ++s;
+  }
+}
+
+// Padding words read the row of the other pixel of their shared-memory phase
+// (pixel i ^ 1, same slot) with weight 0: the phase then loads one row (a
+// broadcast) instead of two that may share banks.  Where both are padding the
+// word stays 0 (row 0).
+__global__ void k_tile_pad_partner(uint32_t *__restrict__ ent, int64_t words) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < words; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = ent[j], o = ent[j ^ 2];
+    // one thread per word pair (j, j ^ 2): the lower index writes both
+    if ((j & 2) == 0) {
+      if (w == 0 && o != 0) ent[j] = o & 0xffff0000u;
+      if (o == 0 && w != 0) ent[j ^ 2] = w & 0xffff0000u;
+    }
+  }
+}
+
+// The tiled form of the 16-bit A^T (TileLp) from the A^T CSR.  Leaves it
+// unbuilt (ent == nullptr) where the geometry does not suit it: more angles
+// than the window pass's shared arrays hold, or windows too wide for the
+// 16-bit row field.
+tomo_status build_tile16(tomo_matrix *h, cudaStream_t st) {
+  TileLp &T = h->lpATt;
+  const int nt = h->nt, np = h->np;
+  const size_t win_smem = (size_t)2 * nt * sizeof(int);
+  if (win_smem > (size_t)(160 << 10)) return TOMO_OK;
+  T.tiles_x = (h->nx + kTileSide - 1) / kTileSide;
+  T.tiles_y = (h->ny + kTileSide - 1) / kTileSide;
+  T.tiles = (int64_t)T.tiles_x * T.tiles_y;
+  T.nch = (nt + kTileChunk - 1) / kTileChunk;
+  int *small = nullptr;  // [0] widest window, [1] most pairs of a chunk
+  TOMO_TRY(dmalloc(&small, 2));
+  DevBuf small_guard{small};
+  TOMO_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(int), st));
+  TOMO_TRY(dmalloc(&T.win, (size_t)T.tiles * nt));
+  if (win_smem > (size_t)(48 << 10))
+    TOMO_CUDA(cudaFuncSetAttribute(k_tile_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem));
+  k_tile_window<<<(unsigned)T.tiles, 256, win_smem, st>>>(h->AT.rp, h->AT.ci, h->nx, h->ny, np, nt, T.tiles_x,
+                                                          T.win, small);
+  TOMO_CUDA(cudaGetLastError());
+  int wmax = 0;
+  TOMO_CUDA(cudaMemcpyAsync(&wmax, small, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  T.W = std::max(wmax, 1);
+  if (T.W > 32) {  // wider than the pass stages (a unit-spaced detector needs at most 26): leave it unbuilt
+    cudaFree(T.win);
+    T = TileLp{};
+    return TOMO_OK;
+  }
+  const int64_t nwin = T.tiles * nt;
+  k_tile_clamp<<<(unsigned)std::min<int64_t>((nwin + 255) / 256, 4096), 256, 0, st>>>(T.win, nwin,
+                                                                                      std::max(np - T.W, 0));
+  const int64_t n = T.tiles * T.nch * 32;
+  int32_t *cnt = nullptr;
+  int64_t *off = nullptr, *part = nullptr;
+  int *maxv = nullptr;
+  TOMO_TRY(dmalloc(&cnt, n));
+  DevBuf cnt_guard{cnt};
+  TOMO_TRY(dmalloc(&off, n + 1));
+  DevBuf off_guard{off};
+  TOMO_TRY(dmalloc(&part, n / kScanTile + 2));
+  DevBuf part_guard{part};
+  TOMO_TRY(dmalloc(&maxv, 1));
+  DevBuf maxv_guard{maxv};
+  k_tile_count<<<(unsigned)T.tiles, 256, 0, st>>>(h->AT.rp, h->AT.ci, h->nx, h->ny, np, nt, T.tiles_x, T.nch, cnt);
+  TOMO_CUDA(cudaGetLastError());
+  TOMO_TRY(scan_counts(cnt, n, off, part, maxv, st));
+  k_tile_max_pairs<<<(unsigned)std::min<int64_t>((T.tiles * T.nch + 255) / 256, 4096), 256, 0, st>>>(
+      off, T.tiles * T.nch, small + 1);
+  TOMO_CUDA(cudaGetLastError());
+  int mp = 0;
+  TOMO_CUDA(cudaMemcpyAsync(&T.pairs, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaMemcpyAsync(&mp, small + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaStreamSynchronize(st));
+  T.max_pairs = std::max(mp, 1);
+  if (T.pairs >= ((int64_t)1 << 32)) {  // pair offsets are 32-bit
+    cudaFree(T.win);
+    T = TileLp{};
+    return TOMO_OK;
+  }
+  TOMO_TRY(dmalloc(&T.qoff, n + 4));  // the pass copies 36 offsets per chunk (16-byte pieces)
+  TOMO_CUDA(cudaMemsetAsync(T.qoff, 0, sizeof(uint32_t) * (n + 4), st));
+  k_tile_offsets<<<(unsigned)std::min<int64_t>((n + 256) / 256, 4096), 256, 0, st>>>(off, n, T.qoff);
+  TOMO_TRY(dmalloc(&T.ent, (size_t)std::max<int64_t>(T.pairs, 1) * 16));
+  TOMO_CUDA(cudaMemsetAsync(T.ent, 0, sizeof(uint32_t) * 16 * (size_t)std::max<int64_t>(T.pairs, 1), st));
+#define TOMO_TFILL(WT)                                                                                        \
+  k_tile_fill<WT><<<(unsigned)T.tiles, 256, 0, st>>>(h->ang, h->model, h->center, h->AT.rp, h->AT.ci, h->nx, h->ny, \
+                                                    np, nt, T.tiles_x, T.nch, T.W, T.qoff, T.win, T.ent)
+  if (h->lp_dtype == TOMO_BF16) TOMO_TFILL(__nv_bfloat16);
+  else TOMO_TFILL(__half);
+#undef TOMO_TFILL
+  TOMO_CUDA(cudaGetLastError());
+  const int64_t words = std::max<int64_t>(T.pairs, 1) * 16;
+  k_tile_pad_partner<<<(unsigned)std::min<int64_t>((words + 255) / 256, 8192), 256, 0, st>>>(T.ent, words);
+  TOMO_CUDA(cudaGetLastError());
+  TOMO_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed on return
+  h->bytes_lp += (n + 4) * 4 + nwin * 4 + T.pairs * 64;
+  return TOMO_OK;
+}
+
 }  // namespace
 
 // Exclusive scan of n int32 counts into n+1 int64 offsets (other translation
@@ -626,7 +855,7 @@ void free_matrix(tomo_matrix *h) {
                   h->AT.ci,    h->AT.v,      h->R,        h->C,        h->sA.cp,     h->sA.rl,
                   h->sA.ent,   h->sAT.cp,    h->sAT.rl,   h->sAT.ent,  h->lpA.cpw,   h->lpA.cpb,
                   h->lpA.ow,   h->lpA.base,  h->lpAT.cpw, h->lpAT.cpb, h->lpAT.ow,   h->lpAT.base,
-                  h->lpA.rl,   h->lpAT.rl,   h->ramp};
+                  h->lpA.rl,   h->lpAT.rl,   h->ramp,     h->lpATt.qoff, h->lpATt.win, h->lpATt.ent};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -745,10 +974,12 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
 
   size_t freeb = 0, totalb = 0;
   TOMO_CUDA(cudaMemGetInfo(&freeb, &totalb));
-  // CSR pair (16 B/nnz) [+ SELL pair (~17 B/nnz)] [+ 16-bit pair (~9.5 B/nnz)]
+  // CSR pair (16 B/nnz) [+ SELL pair (~17 B/nnz)] [+ 16-bit pair (~9.5 B/nnz)] [+ tiled 16-bit A^T (~5 B/nnz)]
   const bool sell32 = !(o && o->no_fp32_sell);
+  const bool at_tiles = lp != TOMO_F32 && !(o && o->no_at_tiles);
   size_t need = (size_t)nnz_a * (16 + (sell32 ? 18 : 0)) +
-                (size_t)(lp != TOMO_F32 ? nnz_a * 10 + (rows + cols) * 64 : 0);
+                (size_t)(lp != TOMO_F32 ? nnz_a * 10 + (rows + cols) * 64 : 0) +
+                (size_t)(at_tiles ? nnz_a * 5 + (int64_t)nt * cols / 3 : 0);
   if (need + (size_t)(1ull << 30) > freeb)
     return fail(TOMO_ERR_OOM, "matrix needs " + std::to_string(need) + " bytes, device has " +
                                   std::to_string(freeb) + " free");
@@ -780,6 +1011,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
       TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch, h->lpA, 0, INT32_MAX));
     }
     TOMO_TRY(build_sell16(h, true, st, cnt, part, scratch, h->lpAT, 0, INT32_MAX));
+    if (!(o && o->no_at_tiles)) TOMO_TRY(build_tile16(h, st));
   }
   TOMO_CUDA(cudaMemcpyAsync(hs, scratch, sizeof(hs), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));

@@ -68,6 +68,34 @@ struct SellLp {
   int32_t *base = nullptr;  // [bases]
 };
 
+// 16-bit A^T in image tiles, for a pass that stages each tile's detector
+// window in shared memory (k_spmm_tile16).  The image is cut into tiles of
+// kTileSide x kTileSide pixels (t = ty * tiles_x + tx; the last column and row
+// of tiles may be ragged) and the angles into chunks of kTileChunk.  For tile t
+// and angle m, win[t * n_theta + m] is the first bin of a window of W bins that
+// holds every bin the tile's pixels meet at m (clamped into [0, n_p - W] when
+// n_p >= W).  The tile's pixels form 32 groups of 8 (group h: tile row h / 2,
+// columns 8 (h % 2) .. 8 (h % 2) + 7).  The entries of group h's pixel i at
+// the angles of chunk k, in the pixel's CSR order, occupy slot pairs:
+//   word(t, k, h, i, s) = ent[(qoff[(t * nch + k) * 32 + h] + s / 2) * 16 + 2 i + s % 2]
+// where the group has qoff[.. + 1] - qoff[..] pairs (its longest pixel, rounded
+// up to even; the offsets run over (t, k, h) in that order).  A word packs the
+// byte offset 64 ((m - k kTileChunk) W + bin - win) of the entry's row in the
+// staged window (rows of 64 bytes: 16 slices) in its high half and the 16-bit
+// weight of the SellLp form in its low half; padding words are 0 (row 0,
+// weight 0).  W <= 32.
+constexpr int kTileSide = 16;
+constexpr int kTileChunk = 8;
+constexpr int kTileRow = 64;  // bytes of a staged window row (16 slices)
+struct TileLp {
+  int64_t tiles = 0, pairs = 0;
+  int32_t tiles_x = 0, tiles_y = 0, nch = 0, W = 0;
+  int32_t max_pairs = 0;      // most pairs of one (tile, chunk)
+  uint32_t *qoff = nullptr;   // [tiles * nch * 32 + 4] (3 zero words of padding)
+  int32_t *win = nullptr;     // [tiles * n_theta]
+  uint32_t *ent = nullptr;    // [pairs * 16]
+};
+
 }  // namespace tomo
 
 struct tomo_matrix {
@@ -87,6 +115,8 @@ struct tomo_matrix {
   // SELL-32 matrix over all rows of A) when built with col_blocks > 1; lpA is
   // then empty
   std::vector<tomo::SellLp> lpAb;
+  // the 16-bit A^T also in image tiles (ent == nullptr when not built)
+  tomo::TileLp lpATt;
   int64_t bytes_f32 = 0, bytes_lp = 0;
   // tomo_autotune's choice per slice count (most recent first)
   struct Tuned {
@@ -137,7 +167,7 @@ struct Exec {
   int format = TOMO_FMT_SELL;
   tomo_timing *timing = nullptr;
   bool recompute_fp32 = false;  // CGLS on 16-bit values: residual recompute with the FP32 values
-  int order = 0;                // A^T row-group order: 0 auto, 1 rows, 2 image tiles
+  int order = 0;                // A^T row-group order: 0 auto, 1 rows, 2 image tiles, 3 staged tiles
   int blocks = 0;               // SpMM blocks per SM (0: all that fit)
 };
 tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t nz, Exec *ex);

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "spmm.cuh"
@@ -60,6 +61,189 @@ __global__ void __launch_bounds__(kThreads) k_spmm_sell16(Sell16View M, int64_t 
   else
     sell16_rowgroups<B, kBf16, kTrans, Epi, true, kPre>(M, rows, X, epi, warp, nwarps, (rows + G - 1) / G, ss);
   if constexpr (Epi::kNorm) block_norms<V>(ss, ((threadIdx.x & 31) % L) * V, B, part);
+}
+
+// ---------------------------------------------------------------------------
+// 16-bit A^T in image tiles (TileLp), B = 16, pre-scaled operand.  A
+// persistent block walks the (tile, angle chunk) stream of its tiles
+// (t = blockIdx.x, + gridDim.x, ...).  For every chunk it copies into shared
+// memory, with cp.async and one chunk ahead of the chunk it computes (two
+// buffers): the tile's detector window at the chunk's 8 angles (rows of the
+// gathered operand, 64 B each), the chunk's entry words and its 33 group
+// offsets.  The gathers of an entry then read shared memory instead of L2:
+// the window holds each operand row once per tile, where the SELL pass
+// fetches it once per pixel that meets it.  The global reads a copy needs
+// (window bases, entry span) are loaded one chunk earlier still, so no thread
+// waits on them.  Warp w accumulates the pixel groups w, w + 8, w + 16,
+// w + 24 of the tile; lane 4 i + l holds slices 4 l .. 4 l + 3 of pixel i of
+// a group.  A shared-memory phase of a 128-bit load serves pixels 2p and
+// 2p + 1, horizontal neighbours whose rows are mostly the same or adjacent
+// bins (conflict-free); about 1 pair in 5 conflicts (storing every row twice,
+// so that the two pixels read opposite bank halves, measured slower: the
+// doubled window leaves room for 2 blocks per SM instead of 3).  Padding words
+// read the row of the phase's other pixel.  Every pixel adds its
+// entries in its CSR order, the order of the SELL passes, and a padding word
+// adds 0 * (row 0), as a SELL padding slot adds 0 * (a real column): the
+// output is the same bits.
+// ---------------------------------------------------------------------------
+struct Tile16View {
+  const uint32_t *qoff;
+  const int32_t *win;
+  const uint32_t *ent;
+  int64_t tiles;
+  int tiles_x, nch, W, max_pairs, nx, ny, np, nt;
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+constexpr int kTileQo = 36;   // group offsets copied per chunk (33 used, 16-byte pieces)
+constexpr int kTilePieces = 4;  // window pieces (16 B) per thread and chunk: C W 4 <= 4 * 256, W <= 32
+
+// shared bytes of one launch: two buffers of (window rows, entry pairs, offsets)
+inline size_t tile16_buf_bytes(const TileLp &T) {
+  return (size_t)kTileChunk * T.W * kTileRow + (size_t)T.max_pairs * 64 + kTileQo * 4;
+}
+inline size_t tile16_smem(const TileLp &T) { return 2 * tile16_buf_bytes(T); }
+
+template <bool kBf16>
+__device__ __forceinline__ float tile_w(uint32_t wd) {
+  if constexpr (kBf16)
+    return __uint_as_float(wd << 16);
+  else
+    return __half2float(__ushort_as_half((unsigned short)(wd & 0xffffu)));
+}
+
+template <bool kBf16>
+__device__ __forceinline__ void tile_fma(Vec<4> &a, uint32_t wd, const char *wrow) {
+  const float4 x = *reinterpret_cast<const float4 *>(wrow + (wd >> 16));
+  const float w = tile_w<kBf16>(wd);
+  a.v[0] = fmaf(w, x.x, a.v[0]);
+  a.v[1] = fmaf(w, x.y, a.v[1]);
+  a.v[2] = fmaf(w, x.z, a.v[2]);
+  a.v[3] = fmaf(w, x.w, a.v[3]);
+}
+
+template <bool kBf16, class Epi>
+__global__ void __launch_bounds__(kThreads, 3) k_spmm_tile16(Tile16View M, const float *__restrict__ X, Epi epi,
+                                                             double *__restrict__ part) {
+  constexpr int B = 16, V = 4, C = kTileChunk;
+  extern __shared__ float4 tile_sm[];
+  double *ss = norm_slots<V, Epi>();
+  const int W = M.W, Weff = min(M.W, M.np), W4 = W * 4;
+  constexpr int RF4 = kTileRow / 16;  // float4 per window row slot
+  const int buf_f4 = (C * W * kTileRow + M.max_pairs * 64 + kTileQo * 4 + 15) / 16;  // float4 per buffer
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, i = lane >> 2, l = lane & 3;
+  const int64_t my_tiles = (int64_t)blockIdx.x < M.tiles ? (M.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * M.nch;
+  // buffer b: window rows at f4 [0, C W 4), entry pairs next, then the offsets
+  auto win_of = [&](int b) { return tile_sm + b * buf_f4; };
+  auto ent_of = [&](int b) { return tile_sm + b * buf_f4 + C * W * RF4; };
+  auto qo_of = [&](int b) {
+    return reinterpret_cast<uint32_t *>(tile_sm + b * buf_f4 + C * W * RF4 + M.max_pairs * 4);
+  };
+  // this thread's window pieces: (angle in chunk << 16) | (row in window * 4 + 16-byte quarter), -1 if none
+  int pk[kTilePieces];
+#pragma unroll
+  for (int j = 0; j < kTilePieces; ++j) {
+    const int p = threadIdx.x + j * kThreads;
+    pk[j] = p < C * W4 ? ((p / W4) << 16) | (p % W4) : -1;
+  }
+  // global reads of the next copy, loaded one chunk ahead
+  int wnext[kTilePieces];
+  uint32_t p0n = 0, p1n = 0;
+  auto load_next = [&](int64_t s) {  // the reads of chunk s's copy
+    if (s >= total) return;
+    const int64_t t = blockIdx.x + (s / M.nch) * gridDim.x;
+    const int k = (int)(s % M.nch);
+#pragma unroll
+    for (int j = 0; j < kTilePieces; ++j) {
+      const int m = k * C + (pk[j] >> 16);
+      wnext[j] = (pk[j] >= 0 && m < M.nt) ? __ldg(M.win + t * M.nt + m) : 0;
+    }
+    const int64_t g0 = (t * M.nch + k) * 32;
+    p0n = __ldg(M.qoff + g0);
+    p1n = __ldg(M.qoff + g0 + 32);
+  };
+  auto stage = [&](int64_t s, int b) {  // copies of chunk s into buffer b (its reads are loaded)
+    const int64_t t = blockIdx.x + (s / M.nch) * gridDim.x;
+    const int k = (int)(s % M.nch);
+    float4 *wb = win_of(b);
+#pragma unroll
+    for (int j = 0; j < kTilePieces; ++j) {
+      if (pk[j] < 0) continue;
+      const int a = pk[j] >> 16, rem = pk[j] & 0xffff, w = rem >> 2, m = k * C + a;
+      if (m < M.nt && w < Weff) {
+        const float *src = X + ((int64_t)m * M.np + wnext[j] + w) * B + (rem & 3) * 4;
+        float4 *dst = wb + (a * W + w) * RF4 + (rem & 3);
+        cp_async16(dst, src);
+      }
+    }
+    const int n16 = (int)(p1n - p0n) * 4;
+    const float4 *esrc = reinterpret_cast<const float4 *>(M.ent) + (size_t)p0n * 4;
+    float4 *edst = ent_of(b);
+    for (int p = threadIdx.x; p < n16; p += kThreads) cp_async16(edst + p, esrc + p);
+    if (threadIdx.x < kTileQo / 4)
+      cp_async16(qo_of(b) + 4 * threadIdx.x, M.qoff + (t * M.nch + k) * 32 + 4 * threadIdx.x);
+  };
+
+  Vec<V> acc[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[j].v[u] = 0.f;
+  load_next(0);
+  if (total > 0) stage(0, 0);
+  cp_async_commit();
+  load_next(1);
+  for (int64_t s = 0; s < total; ++s) {
+    if (s + 1 < total) stage(s + 1, (int)((s + 1) & 1));
+    cp_async_commit();
+    load_next(s + 2);  // in flight while chunk s is computed
+    cp_async_wait1();  // this thread's copies of chunk s have landed
+    __syncthreads();   // ... and every thread's
+    const int b = (int)(s & 1);
+    const uint32_t *qo = qo_of(b);
+    const char *wrow = reinterpret_cast<const char *>(win_of(b)) + l * 16;
+    const uint2 *ev = reinterpret_cast<const uint2 *>(ent_of(b)) + i;
+    const uint32_t q0 = qo[0];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int h = warp + 8 * j;
+      const int pa = (int)(qo[h] - q0), pb = (int)(qo[h + 1] - q0);
+      int p = pa;
+      for (; p + 2 <= pb; p += 2) {
+        const uint2 e0 = ev[p * 8], e1 = ev[(p + 1) * 8];
+        tile_fma<kBf16>(acc[j], e0.x, wrow);
+        tile_fma<kBf16>(acc[j], e0.y, wrow);
+        tile_fma<kBf16>(acc[j], e1.x, wrow);
+        tile_fma<kBf16>(acc[j], e1.y, wrow);
+      }
+      if (p < pb) {
+        const uint2 e0 = ev[p * 8];
+        tile_fma<kBf16>(acc[j], e0.x, wrow);
+        tile_fma<kBf16>(acc[j], e0.y, wrow);
+      }
+    }
+    const int64_t t = blockIdx.x + (s / M.nch) * gridDim.x;
+    if ((int)(s % M.nch) == M.nch - 1) {  // the tile is complete
+      const int ty = (int)(t / M.tiles_x), tx = (int)(t - (int64_t)ty * M.tiles_x);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int h = warp + 8 * j;
+        const int iy = ty * kTileSide + (h >> 1), ix = tx * kTileSide + (h & 1) * 8 + i;
+        if (ix < M.nx && iy < M.ny) epi.template operator()<V>((int64_t)iy * M.nx + ix, l * V, acc[j], ss);
+#pragma unroll
+        for (int u = 0; u < V; ++u) acc[j].v[u] = 0.f;
+      }
+    }
+    __syncthreads();  // buffer b is refilled by the next iteration's copies
+  }
+  if constexpr (Epi::kNorm) block_norms<V>(ss, l * V, B, part);
 }
 
 // ---------------------------------------------------------------------------
@@ -637,6 +821,8 @@ struct Op {  // one SpMM operand (A or A^T) in the selected storage
   float *partial = nullptr;                     // (rows, B) sums of the bands before the last
   int order = 0;                                // A^T row-group order (Exec::order)
   int blocks = 0;                               // resident blocks per SM to launch (0: all that fit)
+  const TileLp *tl = nullptr;                   // 16-bit A^T in tiles, when the order allows it
+  int nt = 0;
 };
 
 // blocks per SM a launch of the op uses: all that fit, or fewer when asked
@@ -679,6 +865,68 @@ int resident_blocks(K kernel) {
 }
 
 inline int max_spmm_grid() { return num_sms() * 8; }
+
+// The tiled 16-bit A^T pass serves the pre-scaled passes at B = 16 (op.tl is
+// set only when the order allows it).
+// (epilogues of the A^T passes: backprojection, SIRT update, CGLS s = A^T r)
+template <class Epi>
+constexpr bool kTile16Epi =
+    std::is_same<Epi, EpiStore>::value || std::is_same<Epi, EpiStoreNorm>::value || std::is_same<Epi, EpiSirtUpdate>::value;
+template <class Epi>
+inline bool use_tile16(const Op &op, int B) {
+  return kTile16Epi<Epi> && B == 16 && op.trans && op.pre && op.tl != nullptr && op.tl->W <= 32;
+}
+
+// Its kernels take more than the default 48 KB of dynamic shared memory: raise
+// each instantiation's limit once, before any launch or occupancy query (the
+// operators call this when they set op.tl, ahead of any graph capture).
+template <class K>
+void allow_tile16_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && optin > (int)fa.sharedSizeBytes)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  cudaGetLastError();
+}
+
+void prepare_tile16() {
+  static const bool done = [] {
+    allow_tile16_smem(k_spmm_tile16<true, EpiStore>);
+    allow_tile16_smem(k_spmm_tile16<false, EpiStore>);
+    allow_tile16_smem(k_spmm_tile16<true, EpiStoreNorm>);
+    allow_tile16_smem(k_spmm_tile16<false, EpiStoreNorm>);
+    allow_tile16_smem(k_spmm_tile16<true, EpiSirtUpdate>);
+    allow_tile16_smem(k_spmm_tile16<false, EpiSirtUpdate>);
+    return true;
+  }();
+  (void)done;
+}
+
+// persistent grid of the tiled pass: the blocks that fit at once, at most one per tile
+template <bool kBf16, class Epi>
+int tile16_grid(const Op &op) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spmm_tile16<kBf16, Epi>, kThreads,
+                                                    tile16_smem(*op.tl)) != cudaSuccess ||
+      n <= 0) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>(op.tl->tiles, (int64_t)num_sms() * op_res(op, n)));
+}
+
+template <class Epi>
+void launch_tile16(const Op &op, const float *X, Epi epi, double *part, cudaStream_t st) {
+  const TileLp &T = *op.tl;
+  const Tile16View v{T.qoff, T.win, T.ent, T.tiles, T.tiles_x, T.nch, T.W, T.max_pairs, op.nx, op.ny, op.np, op.nt};
+  const size_t smem = tile16_smem(T);
+  if (op.bf16)
+    k_spmm_tile16<true, Epi><<<tile16_grid<true, Epi>(op), kThreads, smem, st>>>(v, X, epi, part);
+  else
+    k_spmm_tile16<false, Epi><<<tile16_grid<false, Epi>(op), kThreads, smem, st>>>(v, X, epi, part);
+}
 
 // The CSR gather kernels keep at most 6 blocks (48 warps) per SM: the
 // 32-register norm variants would fit 8, and measured 20-30% slower there
@@ -732,6 +980,8 @@ void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream
         }
       }
     }
+  } else if (op.format == TOMO_FMT_SELL16 && use_tile16<Epi>(op, B)) {
+    if constexpr (kTile16Epi<Epi>) launch_tile16(op, X, epi, part, st);
   } else if (op.format == TOMO_FMT_SELL16) {
     const SellLp &L = *op.lp;
     const float inv_np = 1.0f / (float)op.np;
@@ -779,6 +1029,9 @@ int spmm_grid_of(const Op &op) {
   const int G = rows_per_warp(op.format, B);
   const bool tile = tile_map(op, G, B).gx != 0;
   int res = kMinBlocks;
+  if constexpr (kTile16Epi<Epi>)
+    if (op.format == TOMO_FMT_SELL16 && use_tile16<Epi>(op, B))
+      return op.bf16 ? tile16_grid<true, Epi>(op) : tile16_grid<false, Epi>(op);
   if (op.format == TOMO_FMT_SELL) {
     res = tile ? resident_blocks(k_spmm_sell<B, Epi, true>) : resident_blocks(k_spmm_sell<B, Epi>);
   } else if (op.format == TOMO_FMT_SELL16 && op.bands) {  // the last band's pass reduces the norms
@@ -917,7 +1170,12 @@ Op make_op(const tomo_matrix *h, bool trans, const Exec &ex) {
   op.ny = h->ny;
   op.order = ex.order;
   op.blocks = ex.blocks;
+  op.nt = h->nt;
   if (!trans && ex.format == TOMO_FMT_SELL16 && !h->lpAb.empty()) op.bands = &h->lpAb;
+  if (trans && ex.format == TOMO_FMT_SELL16 && h->lpATt.ent && (ex.order == 0 || ex.order == 3)) {
+    op.tl = &h->lpATt;
+    prepare_tile16();
+  }
   return op;
 }
 
@@ -1368,7 +1626,7 @@ tomo_status resolve_exec(const tomo_matrix *h, const tomo_exec_opts *o, int32_t 
     return fail(TOMO_ERR_UNSUPPORTED, "matrix was built with drop_csr");
   e.recompute_fp32 = o ? o->recompute_fp32 != 0 : false;
   e.order = o ? o->order : 0;
-  if (e.order < 0 || e.order > 2) return fail(TOMO_ERR_INVALID_ARG, "order must be 0, 1 or 2");
+  if (e.order < 0 || e.order > 3) return fail(TOMO_ERR_INVALID_ARG, "order must be 0, 1, 2 or 3");
   if (e.order == 0 && tuned) e.order = tc->order;
   e.blocks = o ? o->blocks_per_sm : 0;
   if (e.blocks < 0) return fail(TOMO_ERR_INVALID_ARG, "blocks_per_sm must be >= 0");
@@ -1637,6 +1895,7 @@ tomo_status run_autotune(tomo_matrix *h, int32_t nz, int allow16, tomo_exec_opts
       const bool tileable = f != TOMO_FMT_CSR && h->nx % G == 0 && h->ny % 8 == 0;
       TOMO_TRY(run(B, f, 1, 0));
       if (tileable) TOMO_TRY(run(B, f, 2, 0));
+      if (f == TOMO_FMT_SELL16 && B == 16 && h->lpATt.ent) TOMO_TRY(run(B, f, 3, 0));
     }
   }
   // stage 2: the best shape with fewer resident blocks per SM

@@ -40,7 +40,8 @@ def test_stored_traffic_matches_the_spmm_sources():
     they are captured again (skipped here, not failed)."""
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         tj = json.load(f)
-    for k in ("sirt_512x360_b64/B64/sell/k0", "sirt_512x360_b64/B64/sell/k1"):
+    for k in ("sirt_512x360_b64/B64/sell/k0", "sirt_512x360_b64/B64/sell/k1",
+              "cgls_2048x1024_b16/B16/sell16/k0", "cgls_2048x1024_b16/B16/sell16/k1"):
         assert tj["per_launch_bytes"][k] > 1e9
     if tj["kernel_hash"] != bench.kernel_hash():
         pytest.skip("SpMM sources changed since the DRAM counters were taken: capture them again")

@@ -410,6 +410,77 @@ def test_errors_are_reported():
         tomo.project(M, torch.zeros((1, 64, 64), device="cuda"), fmt="sell16")
 
 
+TILE_GEOMS = [
+    dict(nx=128, nt=180),                        # whole tiles, 180 angles (22.5 chunks of 8)
+    dict(nx=37, nt=23, n_p=41, center=19.7),     # ragged tiles, shifted axis, 23 angles
+    dict(nx=40, nt=7, ny=29, n_p=50),            # rectangular image, fewer angles than a chunk
+    dict(nx=20, nt=9, ny=18, n_p=5),             # detector narrower than a tile's window
+]
+
+
+@pytest.mark.parametrize("values", ["bf16", "f16"])
+@pytest.mark.parametrize("geom", TILE_GEOMS)
+def test_tiled_at_same_bits(values, geom):
+    """The 16-bit A^T in image tiles with each tile's detector window staged in
+    shared memory (order "staged") adds every pixel's entries in the SELL
+    pass's order: backprojection (19 slices: a full batch of 16 and a ragged
+    one) and 10 SIRT iterations at width 16 give the bits of the row-order
+    SELL pass; CGLS agrees within 1e-5 over 3 iterations (its FP64 norms are
+    summed per block of another partition); backprojection equals the oracle
+    applied to the same 16-bit values within 1e-5; a matrix built without the
+    tiled copy runs order "staged" as the SELL pass."""
+    g, A, AT, M = pair(values=values, **geom)
+    assert M.has_at_tiles
+    nx, ny, nt = geom["nx"], geom.get("ny", geom["nx"]), geom["nt"]
+    _, AT16 = _oracle16(g, A, values)
+    y = inputs.random_slices((19, nt, g.n_p), seed=71)
+    yt = torch.from_numpy(y).cuda()
+    x = inputs.random_slices((16, ny, nx), seed=72)
+    sino = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=16, fmt="sell16")
+    out = {}
+    try:
+        for order in ("rows", "staged"):
+            tomo.set_launch(order=order)
+            out[order] = (tomo.backproject(M, yt, batch_width=16, fmt="sell16"),
+                          tomo.sirt(M, sino, 10, batch_width=16, fmt="sell16"),
+                          tomo.cgls(M, sino, 3, batch_width=16, fmt="sell16"))
+        Mn = tomo.Matrix(nx, nt, n_p=geom.get("n_p"), n_y=geom.get("ny"), center=geom.get("center"),
+                         values=values, at_tiles=False)
+        assert not Mn.has_at_tiles
+        tomo.set_launch(order="staged")
+        xn = tomo.backproject(Mn, yt, batch_width=16, fmt="sell16")
+    finally:
+        tomo.set_launch()
+    (br, sr, cr_), (bs, ss_, cs) = out["rows"], out["staged"]
+    assert torch.equal(bs, br)
+    assert torch.equal(ss_, sr)
+    assert per_slice_rel(cs.cpu().numpy(), cr_.cpu().numpy()).max() < 1e-5
+    assert torch.equal(xn, br)
+    assert per_slice_rel(bs.cpu().numpy(), AT16.apply(y)).max() < 1e-5
+
+
+def test_tiled_at_strip_model_and_auto_order():
+    """The strip model (up to 3 bins per pixel and angle, wider windows) in
+    the tiled form gives the row-order bits, and so does the default order
+    (which takes the tiled form where it applies), one A^T launch per
+    iteration."""
+    M = tomo.Matrix(48, 30, n_p=56, values="bf16", model="strip")
+    assert M.has_at_tiles
+    x = inputs.random_slices((16, 48, 48), seed=73)
+    sino = tomo.project(M, torch.from_numpy(x).cuda(), batch_width=16, fmt="sell16")
+    try:
+        tomo.set_launch(order="rows")
+        ref = tomo.sirt(M, sino, 6, batch_width=16, fmt="sell16")
+        tomo.set_launch(order="staged")
+        st = tomo.sirt(M, sino, 6, batch_width=16, fmt="sell16")
+    finally:
+        tomo.set_launch()
+    tm = tomo.new_timing()
+    auto = tomo.sirt(M, sino, 6, batch_width=16, fmt="sell16", timing=tm)
+    assert torch.equal(st, ref) and torch.equal(auto, ref)
+    assert tm.launches[1] == 6
+
+
 def _oracle16(g, A, values):
     """The oracle's CSR pair with the 16-bit form's values (weights round(L a)
     times fl32(1/a), exact in FP64), so that the GPU's 16-bit kernels are held
