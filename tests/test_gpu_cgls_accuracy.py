@@ -160,3 +160,52 @@ def test_residual_norm_is_the_fp64_data_fit_of_the_fp32_operator():
     got = tomo.residual_norm(M, torch.from_numpy(b).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
     exact = np.linalg.norm(b - A32.apply(x), axis=1)
     np.testing.assert_allclose(got, exact, rtol=1e-12)
+
+
+def _batched_walk(pairs, fmt, fit_mats, iters):
+    """Data fits ||b - A x_k|| (k = 1 .. iters) of every request's slices, and
+    its first iterate: the persistent batched solver, one launch per
+    iteration, resumed from the previous state."""
+    xs, states = tomo.cgls_batched(pairs, 0, batch_width=4, fmt=fmt, return_state=True)
+    fits, first = [], None
+    for k in range(1, iters + 1):
+        xs, states = tomo.cgls_batched(pairs, 1, batch_width=4, fmt=fmt, resume=states, return_state=True)
+        fits.append([tomo.residual_norm(fit_mats[i], s, x).cpu().numpy() for i, ((_, s), x) in enumerate(zip(pairs, xs))])
+        if k == 1:
+            first = [x.cpu().numpy().reshape(x.shape[0], -1) for x in xs]
+    return fits, first
+
+
+def test_batched_precisions_at_equal_data_fit():
+    """The uneven batch (one persistent launch per iteration for requests of
+    three geometries and 1-3 slices) with FP32 and with BF16 values: every
+    slice reaches the FP64 oracle's 30-iteration data fit (to 1e-4) within 40
+    iterations in both precisions, BF16 within 3 iterations of FP32; the FP32
+    form's first iterate is within 1e-4 of the oracle's."""
+    geos = [(64, 90, 1, 31), (96, 60, 3, 32), (128, 180, 2, 33)]
+    reqs32, reqs16, fit_mats, refs = [], [], [], []
+    for n, nt, nz, seed in geos:
+        g = oracle.Geometry(n, n, n, nt)
+        A = oracle.build_matrix(g)
+        AT = A.transpose()
+        c = inputs.make_case(n, nt, nz, seed=seed, phantom="ellipsoids3d", noise="poisson", level=1e5)
+        b = c.sino.reshape(nz, -1)
+        walk = _oracle_walk(A, AT, b, 30)
+        S64, _ = cr.csr_pair(A)
+        refs.append((np.array([np.linalg.norm(b[z] - S64 @ walk[29, z]) for z in range(nz)]), walk[0]))
+        sino = torch.from_numpy(np.ascontiguousarray(c.sino)).cuda()
+        M32, M16 = tomo.Matrix(n, nt), tomo.Matrix(n, nt, values="bf16")
+        reqs32.append((M32, sino))
+        reqs16.append((M16, sino))
+        fit_mats.append(M32)
+    f32, first32 = _batched_walk(reqs32, "sell", fit_mats, 40)
+    f16, _ = _batched_walk(reqs16, "sell16", fit_mats, 40)
+    for i, (target, x1) in enumerate(refs):
+        for z in range(len(target)):
+            k32 = cr.iters_to_fit(np.array([f[i][z] for f in f32]), target[z] * (1 + 1e-4))
+            k16 = cr.iters_to_fit(np.array([f[i][z] for f in f16]), target[z] * (1 + 1e-4))
+            print("  request %d slice %d (%dx%d, %d angles): FP32 %s, BF16 %s iterations" %
+                  (i, z, geos[i][0], geos[i][0], geos[i][1], k32, k16))
+            assert k32 is not None and k16 is not None and k32 <= 40 and k16 <= 40
+            assert abs(k16 - k32) <= 3
+            assert _rel(first32[i][z], x1[z]) < 1e-4
