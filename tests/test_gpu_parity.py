@@ -415,6 +415,8 @@ TILE_GEOMS = [
     dict(nx=37, nt=23, n_p=41, center=19.7),     # ragged tiles, shifted axis, 23 angles
     dict(nx=40, nt=7, ny=29, n_p=50),            # rectangular image, fewer angles than a chunk
     dict(nx=20, nt=9, ny=18, n_p=5),             # detector narrower than a tile's window
+    GEOMS[3],                                    # given angles, two of them 1e-9 from 0 and pi
+    GEOMS[4],                                    # one pixel, one ray
 ]
 
 
@@ -444,8 +446,8 @@ def test_tiled_at_same_bits(values, geom):
             out[order] = (tomo.backproject(M, yt, batch_width=16, fmt="sell16"),
                           tomo.sirt(M, sino, 10, batch_width=16, fmt="sell16"),
                           tomo.cgls(M, sino, 3, batch_width=16, fmt="sell16"))
-        Mn = tomo.Matrix(nx, nt, n_p=geom.get("n_p"), n_y=geom.get("ny"), center=geom.get("center"),
-                         values=values, at_tiles=False)
+        Mn = tomo.Matrix(nx, nt, n_p=geom.get("n_p"), n_y=geom.get("ny"), angles=geom.get("angles"),
+                         center=geom.get("center"), values=values, at_tiles=False)
         assert not Mn.has_at_tiles
         tomo.set_launch(order="staged")
         xn = tomo.backproject(Mn, yt, batch_width=16, fmt="sell16")
