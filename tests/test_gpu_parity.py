@@ -250,18 +250,22 @@ def test_cgls_batched_every_step_matches_an_oracle_step():
         st = st1
 
 
-@pytest.mark.parametrize("values,tol", [("bf16", 1e-2), ("f16", 2e-3)])
-def test_cgls_batched_16bit(values, tol):
+@pytest.mark.parametrize("values", ["bf16", "f16"])
+def test_cgls_batched_16bit(values):
+    """The persistent batched CGLS on 16-bit values: 4 iterations within 1e-4
+    of the FP64 oracle run on the same 16-bit values (the FP32 arithmetic's
+    bar; the value rounding's effect on accuracy is measured at equal data fit
+    in test_gpu_cgls_accuracy.py)."""
     reqs, refs = [], []
     for k, (n, nt, nz) in enumerate([(64, 90, 3), (96, 120, 2)]):
         g, A, AT, M = pair(nx=n, nt=nt, values=values)
         c = inputs.make_case(n, nt, nz, seed=400 + k, phantom="ellipses2d", noise="poisson", level=1e5)
         reqs.append((M, torch.from_numpy(c.sino).cuda()))
-        refs.append((A, AT, c.sino.reshape(nz, -1)))
+        refs.append((_oracle16(g, A, values), c.sino.reshape(nz, -1)))
     xs = tomo.cgls_batched(reqs, 4, batch_width=4, fmt="sell16")
-    for x, (A, AT, b) in zip(xs, refs):
-        ref, _ = oracle.cgls(A, AT, b, 4)
-        assert per_slice_rel(x.cpu().numpy(), ref).max() < tol
+    for x, ((A16, AT16), b) in zip(xs, refs):
+        ref, _ = oracle.cgls(A16, AT16, b, 4)
+        assert per_slice_rel(x.cpu().numpy(), ref).max() < 1e-4
 
 
 def test_cgls_batched_barrier_timeout_is_reported():

@@ -144,13 +144,18 @@ def test_zero_data_freezes_and_x0_is_used():
     assert per_slice_rel(x.cpu().numpy(), ref).max() < 1e-4
 
 
-@pytest.mark.parametrize("values,tol", [("bf16", 1e-2), ("f16", 2e-3)])
-def test_16bit_values(values, tol):
+@pytest.mark.parametrize("values", ["bf16", "f16"])
+def test_16bit_values(values):
+    """BB-SIRT on 16-bit values: 5 iterations within 1e-4 of the FP64 oracle
+    run on the same 16-bit values (weights round(L a) times fl32(1/a))."""
+    import cgls_reference as cr
     g, A, AT, M = pair(nx=128, nt=180, values=values)
+    v = cr.lowprec_values(A, g, values).astype(np.float64)
+    A16 = oracle.CSR(A.rows, A.cols, A.row_ptr, A.col, v)
     sino = case_128(4)
     x = tomo.sirt_bb(M, torch.from_numpy(sino).cuda(), 5, batch_width=4, fmt="sell16")
-    ref, _ = oracle.sirt_bb(A, AT, 128, sino.reshape(4, -1), 5)
-    assert per_slice_rel(x.cpu().numpy(), ref).max() < tol
+    ref, _ = oracle.sirt_bb(A16, A16.transpose(), 128, sino.reshape(4, -1), 5)
+    assert per_slice_rel(x.cpu().numpy(), ref).max() < 1e-4
 
 
 def test_converges_faster_than_classical_sirt():
