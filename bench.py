@@ -995,6 +995,9 @@ def run_main(args, w):
     line["gpu_launches"] = launches * args.steps
     tot = sum(tm.ms[k] for k in range(3))
     line["time_split"] = {"A": tm.ms[0] / tot, "A^T": tm.ms[1] / tot, "vector+scalar": tm.ms[2] / tot}
+    # average device time of one pass of each kind (CUDA events around every launch)
+    line["pass_ms"] = {"A": tm.ms[0] / max(tm.launches[0], 1), "A^T": tm.ms[1] / max(tm.launches[1], 1),
+                       "passes_per_solve": {"A": int(tm.launches[0]), "A^T": int(tm.launches[1])}}
     # the A^T pass streams the tiled 16-bit A^T when the resolved order is "staged"
     staged = (fmt == "sell16" and B == 16 and M.has_at_tiles and
               (args.order == "staged" or (args.order == "auto" and (tune is None or tune["order"] in ("staged", "auto")))))
