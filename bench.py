@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -780,14 +781,18 @@ def cusparse_leg(M, B, torch):
 
 
 def kernel_hash():
-    """Hash of the sources the SpMM kernels compile from (the solver kernels
-    and their device building blocks): stored DRAM counters are used only
-    while it is unchanged."""
+    """Hash of the code the SpMM passes and their matrix layouts compile from
+    (the solver kernels, their device building blocks, the handle's layout
+    constants and the matrix build), with comments and blank space removed:
+    stored DRAM counters are used only while it is unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2003_12677_b300", "csrc")
-    for f in ("ops.cu", "spmm.cuh"):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+    for f in ("ops.cu", "spmm.cuh", "internal.cuh", "build.cu"):
+        with open(os.path.join(d, f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

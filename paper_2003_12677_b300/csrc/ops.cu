@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(kThreads) k_spmm_sell16(Sell16View M, int64_t 
 // doubled window leaves room for 2 blocks per SM instead of 3).  Padding words
 // read the row of the phase's other pixel.  Every pixel adds its
 // entries in its CSR order, the order of the SELL passes, and a padding word
-// adds 0 * (row 0), as a SELL padding slot adds 0 * (a real column): the
-// output is the same bits.
+// adds 0 times a staged row, as a SELL padding slot adds 0 times a real
+// column: the output is the same bits.
 // ---------------------------------------------------------------------------
 struct Tile16View {
   const uint32_t *qoff;
