@@ -50,6 +50,9 @@ struct PBatch {
   Sell16View lA, lT;
   int64_t rows, cols;
   float *x, *r, *q, *p, *s;
+  float *rs;                         // 16-bit values: r times 1/a(theta) of its row (the A^T operand)
+  const float *scale;                // per angle 1/a(theta) (16-bit values)
+  int32_t np;
   double *scal;                      // B x 8
   double *part_q, *part_r, *part_s;  // items x B
   int32_t itemA0, nitemA, itemT0, nitemT;
@@ -134,8 +137,8 @@ __device__ void spmm_item(const PBatch &bt, const PItem &it, const float *X, con
       sell_rowgroups<B, Epi, false>(bt.cpA, bt.rlA, bt.entA, bt.rows, X, epi, it.rg0 + w, kWarps, it.rg1, ss);
   } else {
     constexpr bool kBf16 = kFmt == 1;
-    if (kTrans)
-      sell16_rowgroups<B, kBf16, true, Epi, false>(bt.lT, bt.cols, X, epi, it.rg0 + w, kWarps, it.rg1, ss);
+    if (kTrans)  // X is the pre-scaled operand rs: no per-entry scale
+      sell16_rowgroups<B, kBf16, true, Epi, false, true>(bt.lT, bt.cols, X, epi, it.rg0 + w, kWarps, it.rg1, ss);
     else
       sell16_rowgroups<B, kBf16, false, Epi, false>(bt.lA, bt.rows, X, epi, it.rg0 + w, kWarps, it.rg1, ss);
   }
@@ -173,7 +176,9 @@ __device__ __noinline__ void ph_layout_in(const PPlan &P) {
     for (int64_t e = gtid; e < bt.rows * B; e += gthreads) {
       const int64_t i = e / B;
       const int s = (int)(e % B);
-      bt.r[e] = sl[s].resume ? sl[s].r_in[i] : (sl[s].sino ? sl[s].sino[i] : 0.f);
+      const float v = sl[s].resume ? sl[s].r_in[i] : (sl[s].sino ? sl[s].sino[i] : 0.f);
+      bt.r[e] = v;
+      if (bt.rs) bt.rs[e] = v * bt.scale[i / bt.np];
     }
     for (int64_t e = gtid; e < bt.cols * B; e += gthreads) {
       const int64_t j = e / B;
@@ -198,7 +203,7 @@ __device__ __noinline__ void ph_spmm(const PPlan &P) {
 #pragma unroll
     for (int t = 0; t < V; ++t) ss[t] = 0.0;
     if constexpr (kTrans) {
-      spmm_item<B, kFmt, true>(bt, item, bt.r, EpiStoreNorm{bt.s, B}, ss);
+      spmm_item<B, kFmt, true>(bt, item, kFmt == 0 ? bt.r : bt.rs, EpiStoreNorm{bt.s, B}, ss);
       block_norms_to<V>(ss, lane_s0, B, bt.part_s + (int64_t)(it - bt.itemT0) * B);
     } else {
       spmm_item<B, kFmt, false>(bt, item, bt.p, EpiStoreNorm{bt.q, B}, ss);
@@ -275,6 +280,12 @@ __device__ __noinline__ void ph_step(const PPlan &P) {
           ss[t] += (double)rv.v[t] * (double)rv.v[t];
         }
         st_vec<V>(bt.r + i * V, rv);
+        if (bt.rs) {  // the A^T operand: row i / PER, angle (i / PER) / np
+          const float sc = bt.scale[(i / PER) / bt.np];
+#pragma unroll
+          for (int t = 0; t < V; ++t) rv.v[t] *= sc;
+          st_vec<V>(bt.rs + i * V, rv);
+        }
       } else {
         Vec<V> xv = ld_vec<V>(bt.x + i * V), pv = ld_vec<V>(bt.p + i * V);
 #pragma unroll
@@ -399,7 +410,7 @@ struct Layout {
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-tomo_status plan_layout(const tomo_request *reqs, int32_t n, int B, Layout *L) {
+tomo_status plan_layout(const tomo_request *reqs, int32_t n, int B, bool pre, Layout *L) {
   // group requests by geometry handle, in order of first appearance
   std::vector<const tomo_matrix *> order;
   std::map<const tomo_matrix *, std::vector<int>> groups;
@@ -460,7 +471,7 @@ tomo_status plan_layout(const tomo_request *reqs, int32_t n, int B, Layout *L) {
     for (int64_t rg = 0; rg < rgT; rg += kItemRowGroups)
       L->itemsT.push_back(PItem{(int32_t)bi, 0, rg, std::min<int64_t>(rg + kItemRowGroups, rgT)});
     const int64_t nA = L->itemsA.size() - L->itemA0.back(), nT = L->itemsT.size() - L->itemT0.back();
-    bytes += 2 * align256(sizeof(float) * rows * B) + 3 * align256(sizeof(float) * cols * B) +
+    bytes += (pre ? 3 : 2) * align256(sizeof(float) * rows * B) + 3 * align256(sizeof(float) * cols * B) +
              align256(sizeof(double) * B * 8) + 2 * align256(sizeof(double) * nA * B) +
              align256(sizeof(double) * nT * B);
   }
@@ -530,7 +541,7 @@ tomo_status batched_workspace(const tomo_request *reqs, int32_t n, const tomo_ex
   const int fmt = o ? o->format : TOMO_FMT_SELL;
   TOMO_TRY(check_requests(reqs, n, B, fmt));
   Layout L;
-  TOMO_TRY(plan_layout(reqs, n, B, &L));
+  TOMO_TRY(plan_layout(reqs, n, B, fmt == TOMO_FMT_SELL16, &L));
   *bytes = L.bytes;
   return TOMO_OK;
 }
@@ -542,7 +553,7 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
   TOMO_TRY(check_requests(reqs, n, B, fmt));
   if (iters < 0) return fail(TOMO_ERR_INVALID_ARG, "iters must be >= 0");
   Layout L;
-  TOMO_TRY(plan_layout(reqs, n, B, &L));
+  TOMO_TRY(plan_layout(reqs, n, B, fmt == TOMO_FMT_SELL16, &L));
   void *own = nullptr;
   if (!ws) {
     cudaError_t e = cudaMallocAsync(&own, L.bytes, st);
@@ -595,6 +606,11 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
     b.x = (float *)take(sizeof(float) * b.cols * B);
     b.p = (float *)take(sizeof(float) * b.cols * B);
     b.s = (float *)take(sizeof(float) * b.cols * B);
+    if (fmt == TOMO_FMT_SELL16) {
+      b.rs = (float *)take(sizeof(float) * b.rows * B);
+      b.scale = h->ang_scale;
+    }
+    b.np = h->np;
     b.scal = (double *)take(sizeof(double) * B * 8);
     b.part_q = (double *)take(sizeof(double) * b.nitemA * B);
     b.part_r = (double *)take(sizeof(double) * b.nitemA * B);
