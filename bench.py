@@ -454,9 +454,12 @@ def run_alternate(args, w):
         reqs = inputs.uneven_requests()
         geos = sorted({(r.n, r.n_theta) for r in reqs}, key=lambda g: -g[0] * g[0] * g[1])
         t0 = time.perf_counter()
-        # the persistent solver streams the 16-bit SELL pair: no tiled A^T copy
-        mats = {g: tomo.Matrix(g[0], g[1], values="bf16", fp32_sell=False, keep_csr=False, at_tiles=False)
-                for g in geos}
+        # the persistent solver streams the 16-bit SELL pair (no tiled A^T copy); A in
+        # column bands where a 16-slice image batch exceeds 48 MB (the default line's rule)
+        def nbands(nn):
+            return args.col_blocks if args.col_blocks >= 0 else max(1, math.ceil(nn * nn * 16 * 4 / (48 << 20)))
+        mats = {g: tomo.Matrix(g[0], g[1], values="bf16", fp32_sell=False, keep_csr=False, at_tiles=False,
+                               col_blocks=min(nbands(g[0]), 64, g[0])) for g in geos}
         torch.cuda.synchronize()
         build_s = time.perf_counter() - t0
         pairs = []

@@ -100,7 +100,8 @@ typedef struct {
                             a projection then runs one pass per band and adds the bands' partial sums
                             in a workspace buffer, so that each pass gathers only its band of the image
                             (which can stay in L2 when the whole image stack cannot).  0 or 1: one band;
-                            at most min(64, n_y).  tomo_cgls_batched rejects banded matrices. */
+                            at most min(64, n_y).  tomo_cgls_batched runs a banded A one band at a
+                            time (a grid barrier between bands). */
   int32_t no_at_tiles;   /* 16-bit values only.  0 (default): also store the 16-bit A^T in image tiles of
                             16 x 16 pixels (about 4.7 B/nnz more), for the SIRT / CGLS passes at batch
                             width 16 that stage each tile's detector window, 8 angles at a time, in

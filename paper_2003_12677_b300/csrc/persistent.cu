@@ -27,7 +27,7 @@ namespace tomo {
 
 namespace {
 
-constexpr int kItemRowGroups = 64;  // row groups per work item (8 warps x 8)
+constexpr int kItemRowGroups = 8;  // row groups per work item: one per warp (finer items balance better)
 
 struct PSlot {        // one lane of a batch
   const float *sino;  // start of the slice's sinogram (nullptr: padding)
@@ -53,6 +53,9 @@ struct PBatch {
   float *rs;                         // 16-bit values: r times 1/a(theta) of its row (the A^T operand)
   const float *scale;                // per angle 1/a(theta) (16-bit values)
   int32_t np;
+  int32_t nbands;                    // 16-bit A stored as column bands: their number, else 0
+  const Sell16View *bandv;           // [nbands] the bands' views
+  float *partial;                    // (rows, B) sums of the bands before the last
   double *scal;                      // B x 8
   double *part_q, *part_r, *part_s;  // items x B
   int32_t itemA0, nitemA, itemT0, nitemT;
@@ -75,6 +78,7 @@ struct PPlan {
   const PSlot *slots;
   const PItem *itemsA, *itemsT;
   int32_t nbatch, nitemA, nitemT, iters;
+  int32_t maxbands;  // A-phase steps: the most column bands of any batch (1 when none is banded)
   GridBar *bar;
   unsigned long long timeout_ns;
   int32_t skip_block;  // test hook: this block never arrives at a barrier (-1: none)
@@ -209,6 +213,47 @@ __device__ __noinline__ void ph_spmm(const PPlan &P) {
       spmm_item<B, kFmt, false>(bt, item, bt.p, EpiStoreNorm{bt.q, B}, ss);
       block_norms_to<V>(ss, lane_s0, B, bt.part_q + (int64_t)(it - bt.itemA0) * B);
     }
+  }
+}
+
+// q = A p with ||q||^2, step `band` of the A phase.  A batch whose 16-bit A is
+// stored as column bands runs band `band` (each step is separated by a grid
+// barrier, so that every block works on the same band of the images, which
+// can stay in L2): the bands before the last add their sums into the batch's
+// partial buffer, the last adds it and stores q with the norm partials.  Other
+// batches run whole at step 0.
+template <int B, int kFmt>
+__device__ __noinline__ void ph_spmm_a(const PPlan &P, int band) {
+  constexpr int V = Lanes<B>::V, L = Lanes<B>::L;
+  const int lane_s0 = ((threadIdx.x & 31) % L) * V;
+  for (int it = blockIdx.x; it < P.nitemA; it += gridDim.x) {
+    const PItem &item = P.itemsA[it];
+    const PBatch &bt = P.batches[item.batch];
+    const int nb = bt.nbands;
+    if (nb == 0 ? band != 0 : band >= nb) continue;  // uniform over the block (one item per block)
+    double ss[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) ss[t] = 0.0;
+    if constexpr (kFmt != 0) {
+      if (nb > 0) {
+        constexpr bool kBf16 = kFmt == 1;
+        const Sell16View v = bt.bandv[band];
+        const int64_t w = threadIdx.x >> 5;
+        if (band < nb - 1) {
+          sell16_rowgroups<B, kBf16, false, EpiBandPartial, false>(v, bt.rows, bt.p,
+                                                                   EpiBandPartial{bt.partial, B, band == 0},
+                                                                   item.rg0 + w, kWarps, item.rg1, ss);
+          continue;
+        }
+        sell16_rowgroups<B, kBf16, false, EpiBandLast<EpiStoreNorm>, false>(
+            v, bt.rows, bt.p, EpiBandLast<EpiStoreNorm>{bt.partial, B, EpiStoreNorm{bt.q, B}}, item.rg0 + w, kWarps,
+            item.rg1, ss);
+        block_norms_to<V>(ss, lane_s0, B, bt.part_q + (int64_t)(it - bt.itemA0) * B);
+        continue;
+      }
+    }
+    spmm_item<B, kFmt, false>(bt, item, bt.p, EpiStoreNorm{bt.q, B}, ss);
+    block_norms_to<V>(ss, lane_s0, B, bt.part_q + (int64_t)(it - bt.itemA0) * B);
   }
 }
 
@@ -377,8 +422,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_cgls_persistent(PPlan P) {
   ph_init_scalars<B>(P);  // gamma, p = s
   if (!grid_barrier(P)) return;
   for (int iter = 0; iter < P.iters; ++iter) {
-    ph_spmm<B, kFmt, false>(P);  // q = A p, ||q||^2
-    if (!grid_barrier(P)) return;
+    for (int band = 0; band < P.maxbands; ++band) {  // q = A p, ||q||^2
+      ph_spmm_a<B, kFmt>(P, band);
+      if (!grid_barrier(P)) return;
+    }
     ph_alpha<B>(P);
     if (!grid_barrier(P)) return;
     ph_step<B>(P);  // r -= alpha q, x += alpha p
@@ -471,6 +518,8 @@ tomo_status plan_layout(const tomo_request *reqs, int32_t n, int B, bool pre, La
     for (int64_t rg = 0; rg < rgT; rg += kItemRowGroups)
       L->itemsT.push_back(PItem{(int32_t)bi, 0, rg, std::min<int64_t>(rg + kItemRowGroups, rgT)});
     const int64_t nA = L->itemsA.size() - L->itemA0.back(), nT = L->itemsT.size() - L->itemT0.back();
+    if (pre && !h->lpAb.empty())  // band views and the bands' partial sums
+      bytes += align256(sizeof(Sell16View) * h->lpAb.size()) + align256(sizeof(float) * rows * B);
     bytes += (pre ? 3 : 2) * align256(sizeof(float) * rows * B) + 3 * align256(sizeof(float) * cols * B) +
              align256(sizeof(double) * B * 8) + 2 * align256(sizeof(double) * nA * B) +
              align256(sizeof(double) * nT * B);
@@ -504,8 +553,6 @@ tomo_status check_requests(const tomo_request *reqs, int32_t n, int B, int fmt) 
       if (q.A->lp_dtype == TOMO_F32) return fail(TOMO_ERR_UNSUPPORTED, "a matrix was built without 16-bit values");
       if (lp == -2) lp = q.A->lp_dtype;
       if (q.A->lp_dtype != lp) return fail(TOMO_ERR_UNSUPPORTED, "requests mix bf16 and f16 matrices");
-      if (!q.A->lpAb.empty())
-        return fail(TOMO_ERR_UNSUPPORTED, "a matrix stores its 16-bit A as column bands (col_blocks > 1)");
     }
   }
   return TOMO_OK;
@@ -582,6 +629,7 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
   };
   std::vector<PBatch> hb(L.batches.size());
   std::vector<PSlot> hs;
+  int32_t maxbands = 1;
   for (size_t bi = 0; bi < L.batches.size(); ++bi) {
     const tomo_matrix *h = L.batches[bi].h;
     PBatch &b = hb[bi];
@@ -609,6 +657,17 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
     if (fmt == TOMO_FMT_SELL16) {
       b.rs = (float *)take(sizeof(float) * b.rows * B);
       b.scale = h->ang_scale;
+      if (!h->lpAb.empty()) {
+        std::vector<Sell16View> views;
+        for (const SellLp &Lb : h->lpAb)
+          views.push_back(Sell16View{Lb.cpw, Lb.cpb, Lb.rl, Lb.ow, Lb.base, h->ang_scale, h->np, inv_np});
+        Sell16View *dv = (Sell16View *)take(sizeof(Sell16View) * views.size());
+        TOMO_CUDA(cudaMemcpyAsync(dv, views.data(), sizeof(Sell16View) * views.size(), cudaMemcpyHostToDevice, st));
+        b.nbands = (int32_t)views.size();
+        b.bandv = dv;
+        b.partial = (float *)take(sizeof(float) * b.rows * B);
+        maxbands = std::max(maxbands, b.nbands);
+      }
     }
     b.np = h->np;
     b.scal = (double *)take(sizeof(double) * B * 8);
@@ -637,6 +696,7 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
   plan.nitemA = (int32_t)L.itemsA.size();
   plan.nitemT = (int32_t)L.itemsT.size();
   plan.iters = iters;
+  plan.maxbands = maxbands;
   plan.bar = bar;
   const double tsec = o && o->timeout_s > 0 ? o->timeout_s : 10.0;
   plan.timeout_ns = (unsigned long long)(tsec * 1e9);
