@@ -99,8 +99,9 @@ typedef struct {
                             consecutive image rows, each its own 16-bit SELL-32 matrix) instead of one;
                             a projection then runs one pass per band and adds the bands' partial sums
                             in a workspace buffer, so that each pass gathers only its band of the image
-                            (which can stay in L2 when the whole image stack cannot).  0 or 1: one band;
-                            at most min(64, n_y).  tomo_cgls_batched runs a banded A one band at a
+                            (which can stay in L2 when the whole image stack cannot).  0 (default):
+                            enough bands that one band of a 16-slice FP32 image batch fits in 48 MB
+                            (1 up to about 886 x 886 pixels); 1: one band; at most min(64, n_y).  tomo_cgls_batched runs a banded A one band at a
                             time (a grid barrier between bands). */
   int32_t no_at_tiles;   /* 16-bit values only.  0 (default): also store the 16-bit A^T in image tiles of
                             16 x 16 pixels (about 4.7 B/nnz more), for the SIRT / CGLS passes at batch

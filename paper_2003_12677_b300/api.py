@@ -95,7 +95,9 @@ class Matrix:
     skips the FP32 SELL-32 copy and keep_csr=False frees the CSR pair after
     the SELL forms are built (memory for very large geometries).  col_blocks
     > 1 stores the 16-bit A as that many bands of image rows, so that each
-    projection pass gathers one band (which can stay in L2).  at_tiles=False
+    projection pass gathers one band (which can stay in L2); 0 (default)
+    chooses enough bands that a band of a 16-slice image batch fits in 48 MB,
+    1 keeps one matrix.  at_tiles=False
     skips the tiled copy of the 16-bit A^T (the "staged" order's operand).
     """
 

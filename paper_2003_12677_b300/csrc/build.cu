@@ -879,11 +879,16 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   const int32_t model = o ? o->model : TOMO_MODEL_LINE;
   if (model != TOMO_MODEL_LINE && model != TOMO_MODEL_STRIP)
     return fail(TOMO_ERR_INVALID_ARG, "opts.model must be TOMO_MODEL_LINE or TOMO_MODEL_STRIP");
-  const int32_t bands = o ? o->col_blocks : 0;
+  int32_t bands = o ? o->col_blocks : 0;
   if (bands < 0 || bands > 64 || bands > g->n_y)
     return fail(TOMO_ERR_INVALID_ARG, "opts.col_blocks must be in [0, min(64, n_y)]");
   if (bands > 1 && lp == TOMO_F32)
     return fail(TOMO_ERR_INVALID_ARG, "opts.col_blocks > 1 needs 16-bit values (TOMO_BF16 or TOMO_F16)");
+  if (bands == 0 && lp != TOMO_F32) {
+    // auto: enough bands that one band of a 16-slice FP32 image batch fits in 48 MB of L2
+    const int64_t batch_bytes = (int64_t)g->n_x * g->n_y * 16 * 4;
+    bands = (int32_t)std::min<int64_t>({(batch_bytes + (48 << 20) - 1) / (48 << 20), 64, (int64_t)g->n_y});
+  }
   const int nt = g->n_theta;
   std::vector<AngleC> ang(nt);
   std::vector<float> scale(nt);

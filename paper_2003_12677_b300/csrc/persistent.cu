@@ -71,6 +71,7 @@ struct GridBar {
   unsigned int count, gen;
   int status;
   int pad;
+  unsigned int work[2];  // item counters of the SpMM phases (alternating; see ph_spmm)
 };
 
 struct PPlan {
@@ -91,7 +92,9 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 // Grid barrier with a time limit.  Returns false when the launch must stop.
-__device__ bool grid_barrier(const PPlan &P) {
+// The last block to arrive resets item counter `reset` (>= 0) before it
+// releases the others.
+__device__ bool grid_barrier(const PPlan &P, int reset = -1) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -103,6 +106,7 @@ __device__ bool grid_barrier(const PPlan &P) {
       __threadfence();
       const unsigned int arrived = atomicAdd(&bar->count, 1u);
       if (arrived == gridDim.x - 1) {
+        if (reset >= 0) atomicExch(&bar->work[reset], 0u);
         atomicExch(&bar->count, 0u);
         __threadfence();
         atomicAdd(&bar->gen, 1u);
@@ -193,14 +197,27 @@ __device__ __noinline__ void ph_layout_in(const PPlan &P) {
   }
 }
 
+// Next item of an SpMM phase, taken in order from counter `slot`: the blocks
+// then stay together in the item list, so the images that the items in flight
+// gather belong to one or two batches and stay in L2 (with a fixed stride, a
+// block slowed by longer items falls behind and the items in flight spread
+// over many batches).
+__device__ __forceinline__ int next_item(const PPlan &P, int slot) {
+  __shared__ int s_it;
+  __syncthreads();  // every thread has read the previous item's index
+  if (threadIdx.x == 0) s_it = (int)atomicAdd(&P.bar->work[slot], 1u);
+  __syncthreads();
+  return s_it;
+}
+
 // SpMM over every batch's items: out = M X with per-item norm partials;
 // kTrans: A^T (T items, X = r, out = s) else A (A items, X = p, out = q)
 template <int B, int kFmt, bool kTrans>
-__device__ __noinline__ void ph_spmm(const PPlan &P) {
+__device__ __noinline__ void ph_spmm(const PPlan &P, int slot) {
   constexpr int V = Lanes<B>::V, L = Lanes<B>::L;
   const int lane_s0 = ((threadIdx.x & 31) % L) * V;
   const int nitem = kTrans ? P.nitemT : P.nitemA;
-  for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+  for (int it = next_item(P, slot); it < nitem; it = next_item(P, slot)) {
     const PItem &item = kTrans ? P.itemsT[it] : P.itemsA[it];
     const PBatch &bt = P.batches[item.batch];
     double ss[V];
@@ -223,10 +240,10 @@ __device__ __noinline__ void ph_spmm(const PPlan &P) {
 // partial buffer, the last adds it and stores q with the norm partials.  Other
 // batches run whole at step 0.
 template <int B, int kFmt>
-__device__ __noinline__ void ph_spmm_a(const PPlan &P, int band) {
+__device__ __noinline__ void ph_spmm_a(const PPlan &P, int band, int slot) {
   constexpr int V = Lanes<B>::V, L = Lanes<B>::L;
   const int lane_s0 = ((threadIdx.x & 31) % L) * V;
-  for (int it = blockIdx.x; it < P.nitemA; it += gridDim.x) {
+  for (int it = next_item(P, slot); it < P.nitemA; it = next_item(P, slot)) {
     const PItem &item = P.itemsA[it];
     const PBatch &bt = P.batches[item.batch];
     const int nb = bt.nbands;
@@ -415,23 +432,27 @@ __device__ __noinline__ void ph_layout_out(const PPlan &P) {
 template <int B, int kFmt>
 __global__ void __launch_bounds__(kThreads, 5) k_cgls_persistent(PPlan P) {
   if ((int)blockIdx.x == P.skip_block) return;  // test hook: a block that never arrives
+  int slot = 0;  // item counter of the next SpMM phase; the barrier after it resets the other
   ph_layout_in<B>(P);
   if (!grid_barrier(P)) return;
-  ph_spmm<B, kFmt, true>(P);  // s = A^T r, ||s||^2
-  if (!grid_barrier(P)) return;
+  ph_spmm<B, kFmt, true>(P, slot);  // s = A^T r, ||s||^2
+  if (!grid_barrier(P, slot ^ 1)) return;
+  slot ^= 1;
   ph_init_scalars<B>(P);  // gamma, p = s
   if (!grid_barrier(P)) return;
   for (int iter = 0; iter < P.iters; ++iter) {
     for (int band = 0; band < P.maxbands; ++band) {  // q = A p, ||q||^2
-      ph_spmm_a<B, kFmt>(P, band);
-      if (!grid_barrier(P)) return;
+      ph_spmm_a<B, kFmt>(P, band, slot);
+      if (!grid_barrier(P, slot ^ 1)) return;
+      slot ^= 1;
     }
     ph_alpha<B>(P);
     if (!grid_barrier(P)) return;
     ph_step<B>(P);  // r -= alpha q, x += alpha p
     if (!grid_barrier(P)) return;
-    ph_spmm<B, kFmt, true>(P);  // s = A^T r, ||s||^2
-    if (!grid_barrier(P)) return;
+    ph_spmm<B, kFmt, true>(P, slot);  // s = A^T r, ||s||^2
+    if (!grid_barrier(P, slot ^ 1)) return;
+    slot ^= 1;
     ph_beta<B>(P, iter);
     if (!grid_barrier(P)) return;
     ph_direction<B>(P);  // p = s + beta p
