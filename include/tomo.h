@@ -101,8 +101,9 @@ typedef struct {
                             in a workspace buffer, so that each pass gathers only its band of the image
                             (which can stay in L2 when the whole image stack cannot).  0 (default):
                             enough bands that one band of a 16-slice FP32 image batch fits in 48 MB
-                            (1 up to about 886 x 886 pixels); 1: one band; at most min(64, n_y).  tomo_cgls_batched runs a banded A one band at a
-                            time (a grid barrier between bands). */
+                            (1 up to about 886 x 886 pixels); 1: one band; at most min(64, n_y).
+                            tomo_cgls_batched runs a banded A one band at a time (a grid barrier
+                            between bands). */
   int32_t no_at_tiles;   /* 16-bit values only.  0 (default): also store the 16-bit A^T in image tiles of
                             16 x 16 pixels (about 4.7 B/nnz more), for the SIRT / CGLS passes at batch
                             width 16 that stage each tile's detector window, 8 angles at a time, in
@@ -372,8 +373,12 @@ typedef struct {
  * `iters` iterations from x0 = 0 as in tomo_cgls (no residual recompute).
  * opts: batch_width 4, 8, 16 (default) or 32; format TOMO_FMT_SELL (default)
  * or TOMO_FMT_SELL16 (every matrix built with the same 16-bit type);
- * timeout_s bounds each grid-barrier wait.  All matrices on one device.  The
- * launch is cooperative (every block resident), the barriers are bounded: a
+ * timeout_s bounds each grid-barrier wait.  All matrices on one device.  With
+ * 16-bit values the A^T phases gather the residual pre-scaled by 1/a(theta),
+ * and a matrix whose 16-bit A is stored as column bands runs its A phase band
+ * by band.  Inside a phase the blocks take (batch, 8 row groups) work items in
+ * list order.  The launch is cooperative (every block resident), the barriers
+ * are bounded: a
  * wait that runs out stops every block and the call returns TOMO_ERR_TIMEOUT.
  * Workspace as tomo_cgls_batched_workspace reports (NULL: allocated by the
  * call, stream-ordered).  Synchronises `stream` and returns the launch's
