@@ -7,8 +7,8 @@
 // kernel runs every phase of every batch: layout in, initialisation, `iters`
 // iterations, layout out.  Inside a phase the work is a flat list of
 // (batch, block of row groups) items spread over all resident blocks, so
-// large and small requests load-balance together; phases are separated by a
-// grid barrier.
+// large and small requests load-balance together (the SpMM phases hand them
+// out in list order from a counter); phases are separated by a grid barrier.
 //
 // The barrier is the library's own: it spins on a generation counter with a
 // time limit read from %globaltimer.  When the limit passes (or another block
