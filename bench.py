@@ -792,11 +792,15 @@ def kernel_hash():
     d = os.path.join(ROOT, "paper_2003_12677_b300", "csrc")
     for f in ("ops.cu", "spmm.cuh", "internal.cuh", "build.cu"):
         with open(os.path.join(d, f)) as fh:
-            src = fh.read()
-        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
-        src = re.sub(r"//[^\n]*", " ", src)
-        h.update(" ".join(src.split()).encode())
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
+
+
+def code_only(src):
+    """C / CUDA source without its comments, blank space collapsed."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
 
 
 def kernel_names(solver, fmt, B, staged=False):

@@ -53,3 +53,12 @@ def test_peaks_come_from_the_measured_file():
         assert src == "measured" and peak > 1000
     else:
         assert src == "fallback" and peak == 6400.0
+
+
+def test_counter_key_ignores_comments_not_code():
+    """The stored DRAM counters stay valid across comment edits, not code edits."""
+    a = "int f(int x) {  // doubles\n  return 2 * x; /* the\n  factor */\n}\n"
+    b = "int f(int x) {\n  // twice x\n  return 2 * x;\n}"
+    c = "int f(int x) {\n  return 3 * x;\n}"
+    assert bench.code_only(a) == bench.code_only(b) == "int f(int x) { return 2 * x; }"
+    assert bench.code_only(c) != bench.code_only(a)
