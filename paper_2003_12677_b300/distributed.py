@@ -51,10 +51,21 @@ def rank_slices(n_z: int, world: int, rank: int, chunk: Optional[int] = None) ->
     return [s for b, e in slice_plan(n_z, world, chunk)[rank] for s in range(b, e)]
 
 
+def world_rank() -> Tuple[int, int]:
+    """(world size, rank) of the default process group; (1, 0) when there is
+    none (a single process)."""
+    if dist.is_available() and dist.is_initialized():
+        return dist.get_world_size(), dist.get_rank()
+    return 1, 0
+
+
 def gather_slices(local: torch.Tensor, n_z: int, chunk: Optional[int] = None, dst: int = 0) -> Optional[torch.Tensor]:
     """Assemble (n_z, ...) on rank `dst` from each rank's (n_local, ...) results
-    (ordered like rank_slices).  Other ranks return None."""
-    world, rank = dist.get_world_size(), dist.get_rank()
+    (ordered like rank_slices).  Other ranks return None.  A single process
+    (no process group) owns every slice in order: `local` is the stack."""
+    world, rank = world_rank()
+    if world == 1:
+        return local
     owned = [rank_slices(n_z, world, k, chunk) for k in range(world)]
     tail = tuple(local.shape[1:])
     maxn = max(len(o) for o in owned)
@@ -83,7 +94,7 @@ def solve_sharded(solve: Callable[[torch.Tensor], torch.Tensor], sino: torch.Ten
     gather at the end is the only collective.  out_shape: the shape of one
     tomogram, needed only by a rank that owns no slice (else it solves one
     slice to learn it)."""
-    world, rank = dist.get_world_size(), dist.get_rank()
+    world, rank = world_rank()
     n_z = sino.shape[0]
     outs = [solve(sino[b:e].contiguous()) for b, e in slice_plan(n_z, world, chunk)[rank]]
     if outs:

@@ -131,3 +131,21 @@ def test_solve_sharded_equals_single_rank(tmp_path, world, n_z, chunk):
     case = inputs.make_case(24, 30, n_z, seed=9, phantom="ellipsoids3d", noise="poisson", level=1e4)
     ref, _ = oracle.cgls(A, A.transpose(), case.sino.reshape(n_z, -1), 6)
     np.testing.assert_array_equal(got.reshape(n_z, -1), ref)
+
+
+def test_solve_sharded_single_process():
+    """Without a process group (one process) the sharded solve is the plain
+    solve over the plan's loops, in stack order."""
+    import torch
+    from paper_2003_12677_b300 import distributed as dd
+    assert not torch.distributed.is_initialized()
+    sino = torch.arange(7 * 3, dtype=torch.float32).reshape(7, 3)
+    calls = []
+
+    def solve(s):
+        calls.append(s.shape[0])
+        return 2 * s
+    out = dd.solve_sharded(solve, sino, chunk=3)
+    assert torch.equal(out, 2 * sino)
+    assert calls == [3, 3, 1]
+    assert dd.world_rank() == (1, 0)
