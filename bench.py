@@ -559,19 +559,22 @@ def run_alternate(args, w):
         line.update({"value": w.n_z * iters / (ms / 1000.0), "ms_per_step": ms, "dtype": "f32 (complex64 FFTs)",
                      "data": DATA, "config": {"workload": w.name, "n": w.n, "n_theta": w.n_theta, "slices": w.n_z,
                                               "iters": iters, "operator": "Fubini-Radon: 2D FFT, Kaiser-Bessel "
-                                              "gridding SpMM (kw = 6), 1D FFTs; one forward + one adjoint per "
-                                              "slice-iteration"},
+                                              "gridding SpMM (kw = 6), 1D FFTs (register FFTs at this size); "
+                                              "one forward + one adjoint per slice-iteration"},
                      "clocks": clk, "build_s": build_s, "fbp": {"ms_per_64_slices": fbp_ms,
                                                                "slices_per_s": w.n_z / (fbp_ms / 1000.0)},
-                     "gpu_launches": args.steps * iters * 2 * 7 * math.ceil(w.n_z / 16)})
-        # whole-pair roofline over modelled bytes: every kernel's compulsory reads
-        # and writes per slice, each cuFFT 2D transform as two passes over the
-        # complex G x G grid, 1D transforms as one pass, S / S^T read once per
-        # 16-slice group
+                     # per 16-slice group: forward rows, columns, S, radial; adjoint
+                     # radial, short and long rows of S^T, columns, rows
+                     "gpu_launches": args.steps * iters * 9 * math.ceil(w.n_z / 16)})
+        # whole-pair roofline over modelled bytes: the compulsory reads and writes
+        # per slice of each kernel that runs at this size (power-of-two grid and
+        # n_p: register-FFT passes), S / S^T read once per 16-slice group.
+        # Forward: rows (image in, n x G complex out), columns (those in, the
+        # G x G spectrum out), S (spectrum in, polar samples out), radial
+        # (samples in, sinogram out); the adjoint the same in reverse.
         G, rows_p = 2 * w.n, w.n_theta * w.n
-        grid_c, pol_c = G * G * 8, rows_p * 8
-        per_slice_dir = (w.n * w.n * 4 + grid_c) + 4 * grid_c + 2 * grid_c + grid_c + pol_c \
-            + 2 * pol_c + 2 * pol_c + (pol_c + rows_p * 4)
+        img, mid, grid_c, pol_c, sino_b = w.n * w.n * 4, w.n * G * 8, G * G * 8, rows_p * 8, rows_p * 4
+        per_slice_dir = (img + mid) + (mid + grid_c) + (grid_c + pol_c) + (pol_c + sino_b)
         mat = 2 * (rows_p * 36 * 8) / 16
         bytes_step = iters * w.n_z * (2 * per_slice_dir + mat)
         peak, src = measured_peaks()

@@ -498,7 +498,7 @@ void free_fubini(tomo_fubini *F) {
   free_normal(F);
   void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->STs.rp, F->STs.ci, F->STs.v, F->STl.rp, F->STl.ci, F->STl.v,
                   F->rows_l, F->faT, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
-                  F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin, F->cs, F->sn};
+                  F->polI, F->pol, F->ph_grid, F->ph_rad, F->ph_bin, F->cs, F->sn, F->twP};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete F;
@@ -574,6 +574,132 @@ tomo_status fa_dispatch(tomo_fubini *F, int cnt, float *x, cudaStream_t st) {
     case 2048: return fa_run<64, 32>(F, cnt, x, st);
   }
   return fail(TOMO_ERR_INVALID_ARG, "no register-FFT adjoint for this grid");
+}
+
+// ---- the radial 1D transforms by register FFTs (n_p a power of two, 32..1024) ----
+// A block takes angle m and SB = 256 / R2 consecutive slices, one FFT of
+// length L = n_p per group of R2 lanes.  The slice-interleaved rows of polI
+// (SB slices of one row are 8 SB contiguous bytes) pass through a shared
+// staging area of SB rows of L + 1 (the pad spreads a row's slices over the
+// banks); the FFT tiles of regfft.cuh reuse the same memory afterwards.
+inline bool radial_ok(int np) { return np >= 32 && np <= 1024 && (np & (np - 1)) == 0; }
+
+template <int R1, int R2>
+constexpr int rad_smem() {
+  constexpr int L = R1 * R2, SB = 256 / R2;
+  constexpr int stage = SB * (L + 1) * (int)sizeof(float2);
+  constexpr int tiles = SB * (R1 * (R2 + 1) + 1) * (int)sizeof(float2);
+  return stage > tiles ? stage : tiles;
+}
+
+// forward, after the gridding SpMM (steps 5-7): z[q] = polI[m np + q][s]
+// ph_rad[q], Z = its unnormalised inverse DFT, y[s][m][k] = Re(Z[k]
+// conj(ph_bin[k])) / np -- the transpose, the inverse 1D FFT and k_fub_out
+template <int R1, int R2>
+__global__ void __launch_bounds__(256) k_fub_rad_fwd(const float2 *__restrict__ polI, float *__restrict__ y, int cnt,
+                                                     int Bf, int nt, const float2 *__restrict__ ph_rad,
+                                                     const float2 *__restrict__ ph_bin, const float2 *twP,
+                                                     const __grid_constant__ Tw64 tw) {
+  constexpr int L = R1 * R2, G = R2, SB = 256 / G, T = R1 / G;
+  extern __shared__ float2 rad_sm[];
+  const int m = blockIdx.x, s0 = blockIdx.y * SB;
+  if (s0 >= cnt) return;  // the whole block: no slice of it is written
+  for (int e = threadIdx.x; e < L * SB; e += 256) {
+    const int q = e / SB, sl = e % SB;
+    const float2 z = s0 + sl < Bf ? polI[((int64_t)m * L + q) * Bf + s0 + sl] : make_float2(0.f, 0.f);
+    rad_sm[sl * (L + 1) + q] = cmulf(z, __ldg(ph_rad + q));
+  }
+  __syncthreads();
+  const int g = threadIdx.x / G, l = threadIdx.x % G;
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) v[j1] = rad_sm[g * (L + 1) + j1 * R2 + l];
+  __syncthreads();  // the FFT tiles overwrite the staging area
+  fft_fwd<R1, R2, true>(v, w, rad_sm + g * (R1 * (R2 + 1) + 1), l, twP, tw);
+  const int s = s0 + g;
+  if (s < cnt) {
+    float *yr = y + ((int64_t)s * nt + m) * L;
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) {
+        const int k = (l + G * t) + R1 * k2;
+        const float2 z = w[t * R2 + k2], pb = __ldg(ph_bin + k);
+        yr[k] = (z.x * pb.x + z.y * pb.y) / (float)L;
+      }
+  }
+}
+
+// adjoint (steps 1-3): u[k] = y[s][m][k] ph_bin[k] (0 for slices >= cnt),
+// P = its forward DFT, polI[m np + q][s] = P[q] conj(ph_rad[q] f[q]) with
+// f = (w ? w[q] : 1) scale -- k_fub_adj_in, the forward 1D FFT and the
+// transpose; every slice of the batch is written (zeros past cnt)
+template <int R1, int R2>
+__global__ void __launch_bounds__(256) k_fub_rad_adj(const float *__restrict__ y, float2 *__restrict__ polI, int cnt,
+                                                     int Bf, int nt, const float2 *__restrict__ ph_rad,
+                                                     const float2 *__restrict__ ph_bin, const float *__restrict__ wq,
+                                                     float scale, const float2 *twP, const __grid_constant__ Tw64 tw) {
+  constexpr int L = R1 * R2, G = R2, SB = 256 / G, T = R1 / G;
+  extern __shared__ float2 rad_sm[];
+  const int m = blockIdx.x, s0 = blockIdx.y * SB;
+  const int g = threadIdx.x / G, l = threadIdx.x % G, s = s0 + g;
+  float2 v[R1], w[R1];
+#pragma unroll
+  for (int j1 = 0; j1 < R1; ++j1) {
+    const int k = j1 * R2 + l;
+    const float val = s < cnt ? y[((int64_t)s * nt + m) * L + k] : 0.f;
+    const float2 pb = __ldg(ph_bin + k);
+    v[j1] = make_float2(val * pb.x, val * pb.y);
+  }
+  fft_fwd<R1, R2, false>(v, w, rad_sm + g * (R1 * (R2 + 1) + 1), l, twP, tw);
+  __syncthreads();  // every group is done with its tile: the staging area takes the spectra
+#pragma unroll
+  for (int t = 0; t < T; ++t)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int q = (l + G * t) + R1 * k2;
+      float2 f = __ldg(ph_rad + q);
+      const float sc = wq ? __ldg(wq + q) * scale : scale;
+      f = make_float2(f.x * sc, -f.y * sc);
+      rad_sm[g * (L + 1) + q] = cmulf(w[t * R2 + k2], f);
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < L * SB; e += 256) {
+    const int q = e / SB, sl = e % SB;
+    if (s0 + sl < Bf) polI[((int64_t)m * L + q) * Bf + s0 + sl] = rad_sm[sl * (L + 1) + q];
+  }
+}
+
+template <int R1, int R2>
+tomo_status rad_run(tomo_fubini *F, bool adj, int cnt, const float *y_in, float *y_out, const float *wq, float scale,
+                    cudaStream_t st) {
+  constexpr int sm = rad_smem<R1, R2>(), SB = 256 / R2;
+  const Tw64 tw = tw64();
+  const dim3 grid(F->nt, (F->Bf + SB - 1) / SB);
+  if (adj) {
+    TOMO_CUDA(cudaFuncSetAttribute(k_fub_rad_adj<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    k_fub_rad_adj<R1, R2><<<grid, 256, sm, st>>>(y_in, (float2 *)F->polI, cnt, F->Bf, F->nt, F->ph_rad, F->ph_bin,
+                                                 wq, scale, F->twP, tw);
+  } else {
+    TOMO_CUDA(cudaFuncSetAttribute(k_fub_rad_fwd<R1, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    k_fub_rad_fwd<R1, R2><<<grid, 256, sm, st>>>((const float2 *)F->polI, y_out, cnt, F->Bf, F->nt, F->ph_rad,
+                                                 F->ph_bin, F->twP, tw);
+  }
+  TOMO_CUDA(cudaGetLastError());
+  return TOMO_OK;
+}
+
+tomo_status rad_dispatch(tomo_fubini *F, bool adj, int cnt, const float *y_in, float *y_out, const float *wq,
+                         float scale, cudaStream_t st) {
+  switch (F->np) {
+    case 32: return rad_run<8, 4>(F, adj, cnt, y_in, y_out, wq, scale, st);
+    case 64: return rad_run<8, 8>(F, adj, cnt, y_in, y_out, wq, scale, st);
+    case 128: return rad_run<16, 8>(F, adj, cnt, y_in, y_out, wq, scale, st);
+    case 256: return rad_run<16, 16>(F, adj, cnt, y_in, y_out, wq, scale, st);
+    case 512: return rad_run<32, 16>(F, adj, cnt, y_in, y_out, wq, scale, st);
+    case 1024: return rad_run<32, 32>(F, adj, cnt, y_in, y_out, wq, scale, st);
+  }
+  return fail(TOMO_ERR_INVALID_ARG, "no register-FFT radial transform for this n_p");
 }
 
 }  // namespace
@@ -723,6 +849,12 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
     TOMO_TRY(ensure_twiddles(F, st));
     TOMO_TRY(dalloc(&F->faT, (size_t)F->Bf * F->G * F->n));
   }
+  if (radial_ok(F->np)) {  // the radial 1D transforms by register FFTs
+    const int R2 = fft_r2(F->np), R1 = F->np / R2;
+    TOMO_TRY(dalloc(&F->twP, (size_t)2 * F->np));
+    k_fft_twiddles<<<(2 * F->np + kT - 1) / kT, kT, 0, st>>>(R1, R2, F->twP);
+    TOMO_CUDA(cudaGetLastError());
+  }
   // cuFFT plans: G x G 2D transforms and length-np 1D transforms, contiguous batches
   int dims2[2] = {F->G, F->G};
   TOMO_TRY(cufft_check(cufftPlanMany(&F->plan2, 2, dims2, nullptr, 1, F->G * F->G, nullptr, 1, F->G * F->G,
@@ -759,6 +891,10 @@ tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz,
           F->grid, (float2 *)F->gridI, (int64_t)G * G, Bf, F->ph_grid, G, np, nullptr, 1.f);
     }
     TOMO_TRY(spmm_csr_store(F->S, 2 * Bf, F->gridI, F->polI, st));
+    if (F->twP) {  // steps 5-7 in one pass of register FFTs
+      TOMO_TRY(rad_dispatch(F, false, cnt, nullptr, y + (int64_t)s0 * rows, nullptr, 1.f, st));
+      continue;
+    }
     k_fub_transpose<false, false, false><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad,
                                                                G, np, nullptr, 1.f);
     TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_INVERSE), "1D inverse"));
@@ -777,10 +913,14 @@ tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t
   const float *dens = filter == 1 ? F->dens : (filter == 2 ? F->dens_h : nullptr);
   for (int32_t s0 = 0; s0 < nz; s0 += Bf) {
     const int cnt = std::min<int32_t>(Bf, nz - s0);
-    k_fub_adj_in<<<egrid(rows * Bf), kT, 0, st>>>(y + (int64_t)s0 * rows, F->pol, cnt, Bf, nt, np, F->ph_bin);
-    TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_FORWARD), "1D forward"));
-    k_fub_transpose<true, false, true><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad, G,
-                                                              np, dens, scale);
+    if (F->twP) {  // steps 1-3 in one pass of register FFTs
+      TOMO_TRY(rad_dispatch(F, true, cnt, y + (int64_t)s0 * rows, nullptr, dens, scale, st));
+    } else {
+      k_fub_adj_in<<<egrid(rows * Bf), kT, 0, st>>>(y + (int64_t)s0 * rows, F->pol, cnt, Bf, nt, np, F->ph_bin);
+      TOMO_TRY(cufft_check(cufftExecC2C(F->plan1, F->pol, F->pol, CUFFT_FORWARD), "1D forward"));
+      k_fub_transpose<true, false, true><<<tgrid(rows), 256, 0, st>>>(F->pol, (float2 *)F->polI, rows, Bf, F->ph_rad,
+                                                                G, np, dens, scale);
+    }
     TOMO_TRY(spmm_csr_store(F->STs, 2 * Bf, F->polI, F->gridI, st));  // long rows come out 0 ...
     TOMO_TRY(long_rows(F, F->polI, F->gridI, st));                    // ... and are written here
     if (F->faT) {

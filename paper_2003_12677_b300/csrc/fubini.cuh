@@ -44,6 +44,7 @@ struct tomo_fubini {
   float *polI = nullptr;          // [nt*np][2 Bf]
   cufftComplex *pol = nullptr;    // [Bf][nt][np]
   float2 *faT = nullptr;          // [Bf][G][n] the adjoint's column-transformed grid (register-FFT path)
+  float2 *twP = nullptr;          // [2 np] W_np^{j2 k1} in both orders (register-FFT radial transforms)
   cufftHandle plan2 = 0, plan1 = 0;
   bool plans = false;
   // normal operator (normal.cu), built on first use per filter

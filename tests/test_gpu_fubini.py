@@ -44,7 +44,8 @@ def pair(n, nt, n_p=None, center=None, angles=None, kw=6):
 
 
 GEOS = [dict(n=24, nt=13, n_p=26, center=12.7), dict(n=128, nt=180), dict(n=64, nt=30, kw=8),
-        dict(n=40, nt=7, angles=[0.0, 0.3, 1.1, math.pi / 2, 2.0, 2.9, 3.1])]
+        dict(n=40, nt=7, angles=[0.0, 0.3, 1.1, math.pi / 2, 2.0, 2.9, 3.1]),
+        dict(n=40, nt=11, n_p=64, center=30.2)]  # radial register FFTs (n_p = 64) beside a cuFFT grid (G = 80)
 
 
 @pytest.mark.parametrize("geo", GEOS)
@@ -122,7 +123,8 @@ def test_sirt_bb_matches_oracle():
 @pytest.mark.parametrize("n,nt", [(16, 12), (32, 20), (256, 40), (1024, 30)])
 def test_register_fft_grids_match_oracle(n, nt):
     """Every power-of-two grid split of the register-FFT passes (G = 2n = 32 ..
-    2048): forward, adjoint and the Hamming iRadon against the oracle."""
+    2048) and, with n_p = n, the radial ones (n_p = 32 .. 1024; 16 takes
+    cuFFT): forward, adjoint and the Hamming iRadon against the oracle."""
     fg, S, F = pair(n=n, nt=nt)
     x = inputs.random_slices((3, n, n), 60 + n)
     y = inputs.random_slices((3, nt, n), 61 + n)
