@@ -597,10 +597,46 @@ __global__ void k_tile_clamp(int32_t *__restrict__ win, int64_t n, int32_t hi) {
     win[j] = min(win[j], hi);
 }
 
-// pass 2: slot pairs of each (tile, chunk, group): the group's longest pixel
+// The quad of thread j's pixel (q = 8 g + i) and its place a = 2 dy + dx in it
+__device__ __forceinline__ int tile_quad(int j) { return (j >> 5) * 8 + ((j & 15) >> 1); }
+__device__ __forceinline__ int tile_quad_pixel(int j) { return ((j >> 4) & 1) * 2 + (j & 1); }
+
+// Per (quad, angle of chunk k) the lowest and highest bin its pixels meet
+// (INT32_MAX / -1 where none), from this thread's CSR cursor e, which it
+// advances past the chunk.  Every thread of the block calls it.
+__device__ __forceinline__ void quad_runs(const int32_t *__restrict__ ci, int64_t &e, int64_t end, int np, int nt,
+                                          int k, int *lo, int *hi) {
+  for (int j = threadIdx.x; j < 64 * kTileChunk; j += blockDim.x) {
+    lo[j] = INT32_MAX;
+    hi[j] = -1;
+  }
+  __syncthreads();
+  const int q = tile_quad(threadIdx.x);
+  const int64_t lim = (int64_t)min((k + 1) * kTileChunk, nt) * np;
+  for (; e < end && ci[e] < lim; ++e) {
+    const int col = ci[e], m = col / np, b = col - m * np, s = q * kTileChunk + m - k * kTileChunk;
+    atomicMin(lo + s, b);
+    atomicMax(hi + s, b);
+  }
+  __syncthreads();
+}
+
+// slots of quad q in the chunk: its angles' runs
+__device__ __forceinline__ int quad_slots(const int *lo, const int *hi, int q) {
+  int n = 0;
+#pragma unroll
+  for (int a = 0; a < kTileChunk; ++a) {
+    const int j = q * kTileChunk + a;
+    if (hi[j] >= 0) n += hi[j] - lo[j] + 1;
+  }
+  return n;
+}
+
+// pass 2: blocks of each (tile, chunk, group): the group's longest quad
 __global__ void __launch_bounds__(256) k_tile_count(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                     int nx, int ny, int np, int nt, int tiles_x, int nch,
                                                     int32_t *__restrict__ cnt) {
+  __shared__ int lo[64 * kTileChunk], hi[64 * kTileChunk];
   const int64_t t = blockIdx.x;
   int ix, iy;
   int64_t e = 0, end = 0;
@@ -609,19 +645,17 @@ __global__ void __launch_bounds__(256) k_tile_count(const int64_t *__restrict__ 
     e = rp[row];
     end = rp[row + 1];
   }
-  const int h = (int)(threadIdx.x >> 4) * 2 + (int)((threadIdx.x >> 3) & 1);
   for (int k = 0; k < nch; ++k) {
-    const int64_t lim = (int64_t)min((k + 1) * kTileChunk, nt) * np;
-    int n = 0;
-    while (e < end && ci[e] < lim) {
-      ++n;
-      ++e;
+    quad_runs(ci, e, end, np, nt, k, lo, hi);
+    if (threadIdx.x < 64) {  // thread q: quad q; a group's 8 quads are 8 consecutive threads
+      int n = quad_slots(lo, hi, (int)threadIdx.x);
+      n = max(n, __shfl_xor_sync(0xffffffffu, n, 1));
+      n = max(n, __shfl_xor_sync(0xffffffffu, n, 2));
+      n = max(n, __shfl_xor_sync(0xffffffffu, n, 4));
+      if ((threadIdx.x & 7) == 0)
+        cnt[(t * nch + k) * 8 + (threadIdx.x >> 3)] = (n + kTileBlockSlots - 1) / kTileBlockSlots;
     }
-    // the 8 pixels of a group are 8 consecutive threads
-    n = max(n, __shfl_xor_sync(0xffffffffu, n, 1));
-    n = max(n, __shfl_xor_sync(0xffffffffu, n, 2));
-    n = max(n, __shfl_xor_sync(0xffffffffu, n, 4));
-    if ((threadIdx.x & 7) == 0) cnt[(t * nch + k) * 32 + h] = (n + 1) >> 1;
+    __syncthreads();  // lo / hi are reset for the next chunk
   }
 }
 
@@ -630,72 +664,93 @@ __global__ void k_tile_offsets(const int64_t *__restrict__ off, int64_t n, uint3
     qoff[j] = (uint32_t)off[j];
 }
 
-// most pairs of one (tile, chunk): the size of the pass's staged entry buffer
-__global__ void k_tile_max_pairs(const int64_t *__restrict__ off, int64_t chunks, int *__restrict__ mx) {
+// most blocks of one (tile, chunk): the size of the pass's staged entry buffer
+__global__ void k_tile_max_blocks(const int64_t *__restrict__ off, int64_t chunks, int *__restrict__ mx) {
   int m = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < chunks; j += (int64_t)gridDim.x * blockDim.x)
-    m = max(m, (int)(off[(j + 1) * 32] - off[j * 32]));
+    m = max(m, (int)(off[(j + 1) * 8] - off[j * 8]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
 }
 
-// pass 3: the words, with the weights of k_sell16_fill (same FP64 rule, same rounding)
+// pass 3: weights (the FP64 rule and rounding of k_sell16_fill) and staged row
+// positions of every slot
 template <typename W>
 __global__ void __launch_bounds__(256) k_tile_fill(const AngleC *__restrict__ ang, int model, double c,
                                                    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                    int nx, int ny, int np, int nt, int tiles_x, int nch, int wlen,
                                                    const uint32_t *__restrict__ qoff, const int32_t *__restrict__ win,
                                                    uint32_t *__restrict__ ent) {
+  constexpr int C = kTileChunk;
+  __shared__ int lo[64 * C], hi[64 * C], st[64 * (C + 1)];
   const int64_t t = blockIdx.x;
   int ix, iy;
-  if (!tile_pixel(t, tiles_x, nx, ny, ix, iy)) return;
-  const int64_t row = (int64_t)iy * nx + ix;
-  const int h = (int)(threadIdx.x >> 4) * 2 + (int)((threadIdx.x >> 3) & 1), i = (int)(threadIdx.x & 7);
-  const double x = coord(ix, nx), y = coord(iy, ny);
-  int kc = -1, s = 0;
-  uint32_t q0 = 0;
-  for (int64_t e = rp[row], end = rp[row + 1]; e < end; ++e) {
-    const int col = ci[e], m = col / np, k = col - m * np, ch = m / kTileChunk;
-    if (ch != kc) {
-      kc = ch;
-      s = 0;
-      q0 = qoff[(t * nch + ch) * 32 + h];
-    }
-    // byte offset of the entry's row in the staged window
-    const uint32_t off = (uint32_t)((m - ch * kTileChunk) * wlen + (k - win[t * nt + m])) * (uint32_t)kTileRow;
-    const AngleC A = ang[m];
-    const double pk = __dsub_rn(__dadd_rn((double)k, 0.5), c);
-    const double w = __dmul_rn(chord_len(A, model, pk, x, y), A.a);
-    uint16_t wbits;
-    if constexpr (std::is_same<W, __nv_bfloat16>::value)
-      wbits = __bfloat16_as_ushort(__double2bfloat16(w));
-    else
-      wbits = __half_as_ushort(__double2half(w));
-    ent[((size_t)q0 + (s >> 1)) * 16 + 2 * i + (s & 1)] = (off << 16) | (uint32_t)wbits;
-    ++s;
+  int64_t e = 0, end = 0;
+  const bool mine = tile_pixel(t, tiles_x, nx, ny, ix, iy);
+  if (mine) {
+    const int64_t row = (int64_t)iy * nx + ix;
+    e = rp[row];
+    end = rp[row + 1];
   }
-}
-
-// Padding words read the row of the other pixel of their shared-memory phase
-// (pixel i ^ 1, same slot) with weight 0: the phase then loads one row (a
-// broadcast) instead of two that may share banks.  Where both are padding the
-// word stays 0 (row 0).
-__global__ void k_tile_pad_partner(uint32_t *__restrict__ ent, int64_t words) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < words; j += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t w = ent[j], o = ent[j ^ 2];
-    // one thread per word pair (j, j ^ 2): the lower index writes both
-    if ((j & 2) == 0) {
-      if (w == 0 && o != 0) ent[j] = o & 0xffff0000u;
-      if (o == 0 && w != 0) ent[j ^ 2] = w & 0xffff0000u;
+  const double x = coord(ix, nx), y = coord(iy, ny);
+  const int q = tile_quad(threadIdx.x), pa = tile_quad_pixel(threadIdx.x), i = q & 7;
+  unsigned char *ent8 = reinterpret_cast<unsigned char *>(ent);
+  for (int k = 0; k < nch; ++k) {
+    const int64_t e0 = e;
+    quad_runs(ci, e, end, np, nt, k, lo, hi);
+    if (threadIdx.x < 64) {  // each quad's first slot per angle
+      int n = 0;
+      for (int a = 0; a < C; ++a) {
+        const int j = threadIdx.x * C + a;
+        st[threadIdx.x * (C + 1) + a] = n;
+        if (hi[j] >= 0) n += hi[j] - lo[j] + 1;
+      }
+      st[threadIdx.x * (C + 1) + C] = n;
     }
+    __syncthreads();
+    const uint32_t *qg = qoff + (t * nch + k) * 8;
+    for (int64_t f = e0; f < e; ++f) {  // this pixel's weights
+      const int col = ci[f], m = col / np, b = col - m * np, a = m - k * C;
+      const int s = st[q * (C + 1) + a] + (b - lo[q * C + a]);
+      const AngleC A = ang[m];
+      const double pk = __dsub_rn(__dadd_rn((double)b, 0.5), c);
+      const double w = __dmul_rn(chord_len(A, model, pk, x, y), A.a);
+      uint16_t wbits;
+      if constexpr (std::is_same<W, __nv_bfloat16>::value)
+        wbits = __bfloat16_as_ushort(__double2bfloat16(w));
+      else
+        wbits = __half_as_ushort(__double2half(w));
+      const size_t blk = (size_t)qg[q >> 3] + (size_t)(s >> 2);
+      reinterpret_cast<uint16_t *>(ent8 + blk * kTileBlockBytes)[((s & 3) >> 1) * 64 + i * 8 + (s & 1) * 4 + pa] =
+          wbits;
+    }
+    if (threadIdx.x < 64) {  // the row positions of the quad's slots, padding included
+      const int qq = (int)threadIdx.x, g = qq >> 3, qi = qq & 7, partner = qq ^ 1;
+      const int S = (int)(qg[g + 1] - qg[g]) * kTileBlockSlots;
+      // staged row of quad Q's slot s (s below its slot count)
+      auto row_of = [&](int Q, int s) {
+        int a = 0;
+        while (s >= st[Q * (C + 1) + a + 1]) ++a;
+        const int b = lo[Q * C + a] + (s - st[Q * (C + 1) + a]);
+        return a * wlen + b - win[t * nt + k * C + a];
+      };
+      const int nq = st[qq * (C + 1) + C], npart = st[partner * (C + 1) + C];
+      for (int s = 0; s < S; ++s) {
+        const int r = s < nq ? row_of(qq, s) : (s < npart ? row_of(partner, s) : 0);
+        const size_t blk = (size_t)qg[g] + (size_t)(s >> 2);
+        ent8[blk * kTileBlockBytes + 256 + qi * 4 + (s & 3)] = (unsigned char)tile_swz(r);
+      }
+    }
+    __syncthreads();  // lo / hi / st are reset for the next chunk
   }
 }
 
 // The tiled form of the 16-bit A^T (TileLp) from the A^T CSR.  Leaves it
 // unbuilt (ent == nullptr) where the geometry does not suit it: more angles
-// than the window pass's shared arrays hold, or windows too wide for the
-// 16-bit row field.
+// than the window pass's shared arrays hold, windows wider than 32 bins (a
+// staged row position is one byte), or chunks whose staged entries would not
+// leave room for two blocks of the pass per SM.
 tomo_status build_tile16(tomo_matrix *h, cudaStream_t st) {
   TileLp &T = h->lpATt;
   const int nt = h->nt, np = h->np;
@@ -705,7 +760,7 @@ tomo_status build_tile16(tomo_matrix *h, cudaStream_t st) {
   T.tiles_y = (h->ny + kTileSide - 1) / kTileSide;
   T.tiles = (int64_t)T.tiles_x * T.tiles_y;
   T.nch = (nt + kTileChunk - 1) / kTileChunk;
-  int *small = nullptr;  // [0] widest window, [1] most pairs of a chunk
+  int *small = nullptr;  // [0] widest window, [1] most blocks of a chunk
   TOMO_TRY(dmalloc(&small, 2));
   DevBuf small_guard{small};
   TOMO_CUDA(cudaMemsetAsync(small, 0, 2 * sizeof(int), st));
@@ -727,7 +782,7 @@ tomo_status build_tile16(tomo_matrix *h, cudaStream_t st) {
   const int64_t nwin = T.tiles * nt;
   k_tile_clamp<<<(unsigned)std::min<int64_t>((nwin + 255) / 256, 4096), 256, 0, st>>>(T.win, nwin,
                                                                                       std::max(np - T.W, 0));
-  const int64_t n = T.tiles * T.nch * 32;
+  const int64_t n = T.tiles * T.nch * 8;
   int32_t *cnt = nullptr;
   int64_t *off = nullptr, *part = nullptr;
   int *maxv = nullptr;
@@ -742,24 +797,27 @@ tomo_status build_tile16(tomo_matrix *h, cudaStream_t st) {
   k_tile_count<<<(unsigned)T.tiles, 256, 0, st>>>(h->AT.rp, h->AT.ci, h->nx, h->ny, np, nt, T.tiles_x, T.nch, cnt);
   TOMO_CUDA(cudaGetLastError());
   TOMO_TRY(scan_counts(cnt, n, off, part, maxv, st));
-  k_tile_max_pairs<<<(unsigned)std::min<int64_t>((T.tiles * T.nch + 255) / 256, 4096), 256, 0, st>>>(
+  k_tile_max_blocks<<<(unsigned)std::min<int64_t>((T.tiles * T.nch + 255) / 256, 4096), 256, 0, st>>>(
       off, T.tiles * T.nch, small + 1);
   TOMO_CUDA(cudaGetLastError());
-  int mp = 0;
-  TOMO_CUDA(cudaMemcpyAsync(&T.pairs, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  TOMO_CUDA(cudaMemcpyAsync(&mp, small + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int mb = 0;
+  TOMO_CUDA(cudaMemcpyAsync(&T.blocks, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TOMO_CUDA(cudaMemcpyAsync(&mb, small + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   TOMO_CUDA(cudaStreamSynchronize(st));
-  T.max_pairs = std::max(mp, 1);
-  if (T.pairs >= ((int64_t)1 << 32)) {  // pair offsets are 32-bit
+  T.max_blocks = std::max(mb, 1);
+  // block offsets are 32-bit; the pass's two staging buffers must leave room for 2 blocks per SM
+  const int64_t buf = (int64_t)kTileChunk * T.W * kTileRow + (int64_t)T.max_blocks * kTileBlockBytes + 48;
+  if (T.blocks >= ((int64_t)1 << 32) || 2 * buf > (100 << 10)) {
     cudaFree(T.win);
     T = TileLp{};
     return TOMO_OK;
   }
-  TOMO_TRY(dmalloc(&T.qoff, n + 4));  // the pass copies 36 offsets per chunk (16-byte pieces)
+  TOMO_TRY(dmalloc(&T.qoff, n + 4));  // the pass copies 12 offsets per chunk (16-byte pieces)
   TOMO_CUDA(cudaMemsetAsync(T.qoff, 0, sizeof(uint32_t) * (n + 4), st));
   k_tile_offsets<<<(unsigned)std::min<int64_t>((n + 256) / 256, 4096), 256, 0, st>>>(off, n, T.qoff);
-  TOMO_TRY(dmalloc(&T.ent, (size_t)std::max<int64_t>(T.pairs, 1) * 16));
-  TOMO_CUDA(cudaMemsetAsync(T.ent, 0, sizeof(uint32_t) * 16 * (size_t)std::max<int64_t>(T.pairs, 1), st));
+  const size_t ent_bytes = (size_t)std::max<int64_t>(T.blocks, 1) * kTileBlockBytes;
+  TOMO_TRY(dmalloc(&T.ent, ent_bytes / 4));
+  TOMO_CUDA(cudaMemsetAsync(T.ent, 0, ent_bytes, st));
 #define TOMO_TFILL(WT)                                                                                        \
   k_tile_fill<WT><<<(unsigned)T.tiles, 256, 0, st>>>(h->ang, h->model, h->center, h->AT.rp, h->AT.ci, h->nx, h->ny, \
                                                     np, nt, T.tiles_x, T.nch, T.W, T.qoff, T.win, T.ent)
@@ -767,11 +825,8 @@ tomo_status build_tile16(tomo_matrix *h, cudaStream_t st) {
   else TOMO_TFILL(__half);
 #undef TOMO_TFILL
   TOMO_CUDA(cudaGetLastError());
-  const int64_t words = std::max<int64_t>(T.pairs, 1) * 16;
-  k_tile_pad_partner<<<(unsigned)std::min<int64_t>((words + 255) / 256, 8192), 256, 0, st>>>(T.ent, words);
-  TOMO_CUDA(cudaGetLastError());
   TOMO_CUDA(cudaStreamSynchronize(st));  // the temporaries are freed on return
-  h->bytes_lp += (n + 4) * 4 + nwin * 4 + T.pairs * 64;
+  h->bytes_lp += (n + 4) * 4 + nwin * 4 + T.blocks * kTileBlockBytes;
   return TOMO_OK;
 }
 

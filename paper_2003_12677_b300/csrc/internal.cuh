@@ -74,26 +74,40 @@ struct SellLp {
 // of tiles may be ragged) and the angles into chunks of kTileChunk.  For tile t
 // and angle m, win[t * n_theta + m] is the first bin of a window of W bins that
 // holds every bin the tile's pixels meet at m (clamped into [0, n_p - W] when
-// n_p >= W).  The tile's pixels form 32 groups of 8 (group h: tile row h / 2,
-// columns 8 (h % 2) .. 8 (h % 2) + 7).  The entries of group h's pixel i at
-// the angles of chunk k, in the pixel's CSR order, occupy slot pairs:
-//   word(t, k, h, i, s) = ent[(qoff[(t * nch + k) * 32 + h] + s / 2) * 16 + 2 i + s % 2]
-// where the group has qoff[.. + 1] - qoff[..] pairs (its longest pixel, rounded
-// up to even; the offsets run over (t, k, h) in that order).  A word packs the
-// byte offset 64 ((m - k kTileChunk) W + bin - win) of the entry's row in the
-// staged window (rows of 64 bytes: 16 slices) in its high half and the 16-bit
-// weight of the SellLp form in its low half; padding words are 0 (row 0,
-// weight 0).  W <= 32.
+// n_p >= W); window row r = (m - k kTileChunk) W + bin - win of chunk k is
+// staged at position swz(r) (bits 0 and 1 of r swapped).  W <= 32.
+//
+// The pixels form 2 x 2 quads: group g (0..7) is the tile's pixel rows 2g and
+// 2g + 1, quad i (0..7) of a group its pixel columns 2i and 2i + 1, pixel
+// a = 2 dy + dx of a quad.  At angle m a quad walks the bins from the lowest
+// to the highest that any of its pixels meets, in that order, one slot per
+// bin: a slot carries the staged row of its bin and the 16-bit weights of the
+// four pixels there (0 where a pixel has no entry).  A quad's slots for chunk
+// k are its angles' runs in angle order; each pixel meets its entries in its
+// CSR order.  The group's quads are padded with weight-0 slots to its longest
+// quad, rounded up to blocks of kTileBlockSlots slots.  Block j of group g of
+// (t, k) is ent + 72 (qoff[(t * nch + k) * 8 + g] + j) words:
+//   bytes   0..127  slots 0, 1: quad i at 16 i (slot 0: 8 bytes, then slot 1)
+//   bytes 128..255  slots 2, 3: the same
+//   bytes 256..287  staged row positions: quad i at 4 i, slot s in byte s
+// where a slot's 8 bytes hold the weights of pixels 0..3 (2 bytes each, in
+// order).  A padding slot reads the row of the other quad of its
+// shared-memory phase (quad i ^ 1) at that slot, or row 0.  The offsets run
+// over (t, k, g) in that order; qoff[.. + 1] - qoff[..] is the group's block
+// count.
 constexpr int kTileSide = 16;
 constexpr int kTileChunk = 8;
-constexpr int kTileRow = 64;  // bytes of a staged window row (16 slices)
+constexpr int kTileRow = 64;          // bytes of a staged window row (16 slices)
+constexpr int kTileBlockSlots = 4;    // slots of one entry block
+constexpr int kTileBlockBytes = 288;  // bytes of one entry block
+__host__ __device__ constexpr int tile_swz(int r) { return (r & ~3) | ((r & 1) << 1) | ((r >> 1) & 1); }
 struct TileLp {
-  int64_t tiles = 0, pairs = 0;
+  int64_t tiles = 0, blocks = 0;
   int32_t tiles_x = 0, tiles_y = 0, nch = 0, W = 0;
-  int32_t max_pairs = 0;      // most pairs of one (tile, chunk)
-  uint32_t *qoff = nullptr;   // [tiles * nch * 32 + 4] (3 zero words of padding)
+  int32_t max_blocks = 0;     // most blocks of one (tile, chunk)
+  uint32_t *qoff = nullptr;   // [tiles * nch * 8 + 4] (3 zero words of padding)
   int32_t *win = nullptr;     // [tiles * n_theta]
-  uint32_t *ent = nullptr;    // [pairs * 16]
+  uint32_t *ent = nullptr;    // [blocks * 72]
 };
 
 }  // namespace tomo

@@ -69,29 +69,29 @@ __global__ void __launch_bounds__(kThreads) k_spmm_sell16(Sell16View M, int64_t 
 // (t = blockIdx.x, + gridDim.x, ...).  For every chunk it copies into shared
 // memory, with cp.async and one chunk ahead of the chunk it computes (two
 // buffers): the tile's detector window at the chunk's 8 angles (rows of the
-// gathered operand, 64 B each), the chunk's entry words and its 33 group
-// offsets.  The gathers of an entry then read shared memory instead of L2:
-// the window holds each operand row once per tile, where the SELL pass
-// fetches it once per pixel that meets it.  The global reads a copy needs
-// (window bases, entry span) are loaded one chunk earlier still, so no thread
-// waits on them.  Warp w accumulates the pixel groups w, w + 8, w + 16,
-// w + 24 of the tile; lane 4 i + l holds slices 4 l .. 4 l + 3 of pixel i of
-// a group.  A shared-memory phase of a 128-bit load serves pixels 2p and
-// 2p + 1, horizontal neighbours whose rows are mostly the same or adjacent
-// bins (conflict-free); about 1 pair in 5 conflicts (storing every row twice,
-// so that the two pixels read opposite bank halves, measured slower: the
-// doubled window leaves room for 2 blocks per SM instead of 3).  Padding words
-// read the row of the phase's other pixel.  Every pixel adds its
-// entries in its CSR order, the order of the SELL passes, and a padding word
-// adds 0 times a staged row, as a SELL padding slot adds 0 times a real
-// column: the output is the same bits.
+// gathered operand, 64 B each), the chunk's entry blocks and its 9 group
+// offsets.  The gathers then read shared memory instead of L2: the window
+// holds each operand row once per tile, where the SELL pass fetches it once
+// per pixel that meets it.  The global reads a copy needs (window bases,
+// entry span) are loaded one chunk earlier still, so no thread waits on them.
+// Warp w accumulates group w (tile rows 2w, 2w + 1); lane 4 i + l holds slices
+// 4 l .. 4 l + 3 of the four pixels of quad i.  A slot's row load serves all
+// four: the pixels of a 2 x 2 quad meet overlapping bins, so a quad walks
+// about 0.55 rows per entry where a pixel walks one.  A shared-memory phase of
+// a 128-bit load serves quads 2p and 2p + 1; rows are staged with bits 0 and
+// 1 of their index swapped, so that rows 2 apart (the usual step between
+// neighbouring quads) fall in opposite bank halves, and a padding slot reads
+// its partner's row (a broadcast).  Every pixel adds its entries in its CSR
+// order, the order of the SELL passes, with 0 times a staged row between them
+// where its quad walks a bin it does not meet, as a SELL padding slot adds 0
+// times a real column: the output is the same bits.
 // ---------------------------------------------------------------------------
 struct Tile16View {
   const uint32_t *qoff;
   const int32_t *win;
   const uint32_t *ent;
   int64_t tiles;
-  int tiles_x, nch, W, max_pairs, nx, ny, np, nt;
+  int tiles_x, nch, W, max_blocks, nx, ny, np, nt;
 };
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -101,31 +101,48 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-constexpr int kTileQo = 36;   // group offsets copied per chunk (33 used, 16-byte pieces)
+constexpr int kTileQo = 12;     // group offsets copied per chunk (9 used, 16-byte pieces)
 constexpr int kTilePieces = 4;  // window pieces (16 B) per thread and chunk: C W 4 <= 4 * 256, W <= 32
+constexpr int kTileBlockF4 = kTileBlockBytes / 16;
 
-// shared bytes of one launch: two buffers of (window rows, entry pairs, offsets)
+// shared bytes of one launch: two buffers of (window rows, entry blocks, offsets)
 inline size_t tile16_buf_bytes(const TileLp &T) {
-  return (size_t)kTileChunk * T.W * kTileRow + (size_t)T.max_pairs * 64 + kTileQo * 4;
+  return (size_t)kTileChunk * T.W * kTileRow + (size_t)T.max_blocks * kTileBlockBytes + kTileQo * 4;
 }
 inline size_t tile16_smem(const TileLp &T) { return 2 * tile16_buf_bytes(T); }
 
+// the four pixels' weights of a slot (2 bytes each, pixel 0 lowest) as FP32
 template <bool kBf16>
-__device__ __forceinline__ float tile_w(uint32_t wd) {
+__device__ __forceinline__ float tile_w(uint32_t wd, int half) {
   if constexpr (kBf16)
-    return __uint_as_float(wd << 16);
+    return __uint_as_float(half ? (wd & 0xffff0000u) : (wd << 16));
   else
-    return __half2float(__ushort_as_half((unsigned short)(wd & 0xffffu)));
+    return __half2float(__ushort_as_half((unsigned short)(half ? (wd >> 16) : (wd & 0xffffu))));
 }
 
+// Two FP32 lanes per instruction (a 64-bit register pair): d = a b + d, each
+// lane rounded as one fmaf, so the sums keep the bits of the scalar form.
+__device__ __forceinline__ void fma_x2(unsigned long long &d, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ unsigned long long pack_x2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+// one slot of a quad: acc[2 p] holds slices (0, 1) of pixel p, acc[2 p + 1] slices (2, 3)
 template <bool kBf16>
-__device__ __forceinline__ void tile_fma(Vec<4> &a, uint32_t wd, const char *wrow) {
-  const float4 x = *reinterpret_cast<const float4 *>(wrow + (wd >> 16));
-  const float w = tile_w<kBf16>(wd);
-  a.v[0] = fmaf(w, x.x, a.v[0]);
-  a.v[1] = fmaf(w, x.y, a.v[1]);
-  a.v[2] = fmaf(w, x.z, a.v[2]);
-  a.v[3] = fmaf(w, x.w, a.v[3]);
+__device__ __forceinline__ void quad_fma(unsigned long long (&acc)[8], uint32_t w01, uint32_t w23, const char *row) {
+  const float4 x = *reinterpret_cast<const float4 *>(row);
+  const unsigned long long xa = pack_x2(x.x, x.y), xb = pack_x2(x.z, x.w);
+  const float w[4] = {tile_w<kBf16>(w01, 0), tile_w<kBf16>(w01, 1), tile_w<kBf16>(w23, 0), tile_w<kBf16>(w23, 1)};
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const unsigned long long ww = pack_x2(w[p], w[p]);
+    fma_x2(acc[2 * p], ww, xa);
+    fma_x2(acc[2 * p + 1], ww, xb);
+  }
 }
 
 template <bool kBf16, class Epi>
@@ -136,111 +153,113 @@ __global__ void __launch_bounds__(kThreads, 3) k_spmm_tile16(Tile16View M, const
   double *ss = norm_slots<V, Epi>();
   const int W = M.W, Weff = min(M.W, M.np), W4 = W * 4;
   constexpr int RF4 = kTileRow / 16;  // float4 per window row slot
-  const int buf_f4 = (C * W * kTileRow + M.max_pairs * 64 + kTileQo * 4 + 15) / 16;  // float4 per buffer
+  const int buf_f4 = C * W * RF4 + M.max_blocks * kTileBlockF4 + kTileQo / 4;  // float4 per buffer
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, i = lane >> 2, l = lane & 3;
   const int64_t my_tiles = (int64_t)blockIdx.x < M.tiles ? (M.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t total = my_tiles * M.nch;
-  // buffer b: window rows at f4 [0, C W 4), entry pairs next, then the offsets
+  // buffer b: window rows at f4 [0, C W 4), entry blocks next, then the offsets
   auto win_of = [&](int b) { return tile_sm + b * buf_f4; };
   auto ent_of = [&](int b) { return tile_sm + b * buf_f4 + C * W * RF4; };
   auto qo_of = [&](int b) {
-    return reinterpret_cast<uint32_t *>(tile_sm + b * buf_f4 + C * W * RF4 + M.max_pairs * 4);
+    return reinterpret_cast<uint32_t *>(tile_sm + b * buf_f4 + C * W * RF4 + M.max_blocks * kTileBlockF4);
   };
-  // this thread's window pieces: (angle in chunk << 16) | (row in window * 4 + 16-byte quarter), -1 if none
-  int pk[kTilePieces];
+  // this thread's window pieces (16 B each): (angle in chunk << 16) | float offset
+  // of the piece in its operand row run, -1 if none; and its staged position
+  int pk[kTilePieces], pd[kTilePieces];
 #pragma unroll
   for (int j = 0; j < kTilePieces; ++j) {
-    const int p = threadIdx.x + j * kThreads;
-    pk[j] = p < C * W4 ? ((p / W4) << 16) | (p % W4) : -1;
+    const int p = threadIdx.x + j * kThreads, a = p / W4, rem = p % W4, w = rem >> 2;
+    const bool on = p < C * W4 && w < Weff;
+    pk[j] = on ? (a << 16) | (w * B + (rem & 3) * 4) : -1;
+    pd[j] = on ? tile_swz(a * W + w) * RF4 + (rem & 3) : 0;
   }
+  // (tile, chunk) of a step, advanced one step at a time
+  struct Cursor {
+    int64_t t;
+    int k;
+  };
+  auto advance = [&](Cursor &c) {
+    if (++c.k == M.nch) {
+      c.k = 0;
+      c.t += gridDim.x;
+    }
+  };
   // global reads of the next copy, loaded one chunk ahead
   int wnext[kTilePieces];
   uint32_t p0n = 0, p1n = 0;
-  auto load_next = [&](int64_t s) {  // the reads of chunk s's copy
-    if (s >= total) return;
-    const int64_t t = blockIdx.x + (s / M.nch) * gridDim.x;
-    const int k = (int)(s % M.nch);
+  auto load_next = [&](const Cursor &c) {  // the reads of chunk c's copy
 #pragma unroll
     for (int j = 0; j < kTilePieces; ++j) {
-      const int m = k * C + (pk[j] >> 16);
-      wnext[j] = (pk[j] >= 0 && m < M.nt) ? __ldg(M.win + t * M.nt + m) : 0;
+      const int m = c.k * C + (pk[j] >> 16);
+      wnext[j] = (pk[j] >= 0 && m < M.nt) ? __ldg(M.win + c.t * M.nt + m) : 0;
     }
-    const int64_t g0 = (t * M.nch + k) * 32;
+    const int64_t g0 = (c.t * M.nch + c.k) * 8;
     p0n = __ldg(M.qoff + g0);
-    p1n = __ldg(M.qoff + g0 + 32);
+    p1n = __ldg(M.qoff + g0 + 8);
   };
-  auto stage = [&](int64_t s, int b) {  // copies of chunk s into buffer b (its reads are loaded)
-    const int64_t t = blockIdx.x + (s / M.nch) * gridDim.x;
-    const int k = (int)(s % M.nch);
+  auto stage = [&](const Cursor &c, int b) {  // copies of chunk c into buffer b (its reads are loaded)
     float4 *wb = win_of(b);
 #pragma unroll
     for (int j = 0; j < kTilePieces; ++j) {
-      if (pk[j] < 0) continue;
-      const int a = pk[j] >> 16, rem = pk[j] & 0xffff, w = rem >> 2, m = k * C + a;
-      if (m < M.nt && w < Weff) {
-        const float *src = X + ((int64_t)m * M.np + wnext[j] + w) * B + (rem & 3) * 4;
-        float4 *dst = wb + (a * W + w) * RF4 + (rem & 3);
-        cp_async16(dst, src);
-      }
+      const int m = c.k * C + (pk[j] >> 16);
+      if (pk[j] >= 0 && m < M.nt)
+        cp_async16(wb + pd[j], X + ((int64_t)m * M.np + wnext[j]) * B + (pk[j] & 0xffff));
     }
-    const int n16 = (int)(p1n - p0n) * 4;
-    const float4 *esrc = reinterpret_cast<const float4 *>(M.ent) + (size_t)p0n * 4;
+    const int n16 = (int)(p1n - p0n) * kTileBlockF4;
+    const float4 *esrc = reinterpret_cast<const float4 *>(M.ent) + (size_t)p0n * kTileBlockF4;
     float4 *edst = ent_of(b);
     for (int p = threadIdx.x; p < n16; p += kThreads) cp_async16(edst + p, esrc + p);
     if (threadIdx.x < kTileQo / 4)
-      cp_async16(qo_of(b) + 4 * threadIdx.x, M.qoff + (t * M.nch + k) * 32 + 4 * threadIdx.x);
+      cp_async16(qo_of(b) + 4 * threadIdx.x, M.qoff + (c.t * M.nch + c.k) * 8 + 4 * threadIdx.x);
   };
 
-  Vec<V> acc[4];
+  unsigned long long acc[8];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int u = 0; u < V; ++u) acc[j].v[u] = 0.f;
-  load_next(0);
-  if (total > 0) stage(0, 0);
+  for (int j = 0; j < 8; ++j) acc[j] = 0ull;  // +0.0f in both lanes
+  Cursor cc{(int64_t)blockIdx.x, 0}, cn = cc;  // the chunk computed; the next chunk to copy
+  if (total > 0) {
+    load_next(cn);
+    stage(cn, 0);
+  }
   cp_async_commit();
-  load_next(1);
+  advance(cn);
+  if (total > 1) load_next(cn);
   for (int64_t s = 0; s < total; ++s) {
-    if (s + 1 < total) stage(s + 1, (int)((s + 1) & 1));
+    if (s + 1 < total) stage(cn, (int)((s + 1) & 1));
     cp_async_commit();
-    load_next(s + 2);  // in flight while chunk s is computed
-    cp_async_wait1();  // this thread's copies of chunk s have landed
-    __syncthreads();   // ... and every thread's
+    advance(cn);
+    if (s + 2 < total) load_next(cn);  // in flight while chunk s is computed
+    cp_async_wait1();                  // this thread's copies of chunk s have landed
+    __syncthreads();                   // ... and every thread's
     const int b = (int)(s & 1);
     const uint32_t *qo = qo_of(b);
     const char *wrow = reinterpret_cast<const char *>(win_of(b)) + l * 16;
-    const uint2 *ev = reinterpret_cast<const uint2 *>(ent_of(b)) + i;
+    const char *eb = reinterpret_cast<const char *>(ent_of(b));
     const uint32_t q0 = qo[0];
+    const int ba = (int)(qo[warp] - q0), bb = (int)(qo[warp + 1] - q0);
+    for (int j = ba; j < bb; ++j) {
+      const char *blk = eb + j * kTileBlockBytes;
+      const uint4 w01 = *reinterpret_cast<const uint4 *>(blk + i * 16);
+      const uint4 w23 = *reinterpret_cast<const uint4 *>(blk + 128 + i * 16);
+      const uint32_t r = *reinterpret_cast<const uint32_t *>(blk + 256 + i * 4);
+      quad_fma<kBf16>(acc, w01.x, w01.y, wrow + (r & 0xffu) * kTileRow);
+      quad_fma<kBf16>(acc, w01.z, w01.w, wrow + ((r >> 8) & 0xffu) * kTileRow);
+      quad_fma<kBf16>(acc, w23.x, w23.y, wrow + ((r >> 16) & 0xffu) * kTileRow);
+      quad_fma<kBf16>(acc, w23.z, w23.w, wrow + (r >> 24) * kTileRow);
+    }
+    if (cc.k == M.nch - 1) {  // the tile is complete
+      const int ty = (int)(cc.t / M.tiles_x), tx = (int)(cc.t - (int64_t)ty * M.tiles_x);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int h = warp + 8 * j;
-      const int pa = (int)(qo[h] - q0), pb = (int)(qo[h + 1] - q0);
-      int p = pa;
-      for (; p + 2 <= pb; p += 2) {
-        const uint2 e0 = ev[p * 8], e1 = ev[(p + 1) * 8];
-        tile_fma<kBf16>(acc[j], e0.x, wrow);
-        tile_fma<kBf16>(acc[j], e0.y, wrow);
-        tile_fma<kBf16>(acc[j], e1.x, wrow);
-        tile_fma<kBf16>(acc[j], e1.y, wrow);
-      }
-      if (p < pb) {
-        const uint2 e0 = ev[p * 8];
-        tile_fma<kBf16>(acc[j], e0.x, wrow);
-        tile_fma<kBf16>(acc[j], e0.y, wrow);
+      for (int p = 0; p < 4; ++p) {
+        const int iy = ty * kTileSide + 2 * warp + (p >> 1), ix = tx * kTileSide + 2 * i + (p & 1);
+        Vec<V> v;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(v.v[0]), "=f"(v.v[1]) : "l"(acc[2 * p]));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(v.v[2]), "=f"(v.v[3]) : "l"(acc[2 * p + 1]));
+        if (ix < M.nx && iy < M.ny) epi.template operator()<V>((int64_t)iy * M.nx + ix, l * V, v, ss);
+        acc[2 * p] = acc[2 * p + 1] = 0ull;
       }
     }
-    const int64_t t = blockIdx.x + (s / M.nch) * gridDim.x;
-    if ((int)(s % M.nch) == M.nch - 1) {  // the tile is complete
-      const int ty = (int)(t / M.tiles_x), tx = (int)(t - (int64_t)ty * M.tiles_x);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int h = warp + 8 * j;
-        const int iy = ty * kTileSide + (h >> 1), ix = tx * kTileSide + (h & 1) * 8 + i;
-        if (ix < M.nx && iy < M.ny) epi.template operator()<V>((int64_t)iy * M.nx + ix, l * V, acc[j], ss);
-#pragma unroll
-        for (int u = 0; u < V; ++u) acc[j].v[u] = 0.f;
-      }
-    }
+    advance(cc);
     __syncthreads();  // buffer b is refilled by the next iteration's copies
   }
   if constexpr (Epi::kNorm) block_norms<V>(ss, l * V, B, part);
@@ -920,7 +939,7 @@ int tile16_grid(const Op &op) {
 template <class Epi>
 void launch_tile16(const Op &op, const float *X, Epi epi, double *part, cudaStream_t st) {
   const TileLp &T = *op.tl;
-  const Tile16View v{T.qoff, T.win, T.ent, T.tiles, T.tiles_x, T.nch, T.W, T.max_pairs, op.nx, op.ny, op.np, op.nt};
+  const Tile16View v{T.qoff, T.win, T.ent, T.tiles, T.tiles_x, T.nch, T.W, T.max_blocks, op.nx, op.ny, op.np, op.nt};
   const size_t smem = tile16_smem(T);
   if (op.bf16)
     k_spmm_tile16<true, Epi><<<tile16_grid<true, Epi>(op), kThreads, smem, st>>>(v, X, epi, part);
