@@ -108,7 +108,13 @@ typedef struct {
                             16 x 16 pixels (about 4.7 B/nnz more), for the SIRT / CGLS passes at batch
                             width 16 that stage each tile's detector window, 8 angles at a time, in
                             shared memory (order 3 of tomo_exec_opts).  Non-zero: do not build it. */
-  int32_t reserved[2];
+  int32_t a_ray_order;   /* 16-bit values only.  0 (default): when n_theta is even and n_p a multiple of 4,
+                            store the 16-bit A's rows in pair order: each 8 consecutive rows are the
+                            rays of 2 adjacent angles x 4 adjacent bins, which one warp gathers together
+                            at batch width 16 (their image rows coincide more often in L1 than those of
+                            8 bins at one angle).  Same results, bit for bit.  Non-zero: rays in their
+                            natural order. */
+  int32_t reserved[1];
 } tomo_matrix_opts;
 
 /* Device time of the kernels one call launched, filled when a call is given

@@ -39,7 +39,7 @@ class Geometry(ctypes.Structure):
 class MatrixOpts(ctypes.Structure):
     _fields_ = [("values", ctypes.c_int32), ("no_fp32_sell", ctypes.c_int32), ("drop_csr", ctypes.c_int32),
                 ("model", ctypes.c_int32), ("col_blocks", ctypes.c_int32), ("no_at_tiles", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("a_ray_order", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class Timing(ctypes.Structure):

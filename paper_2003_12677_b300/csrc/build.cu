@@ -381,10 +381,11 @@ __global__ void __launch_bounds__(kThreads) k_sell_fill(const int64_t *__restric
 // ranges of angles (image corners).
 // Only the entries with column in [c0, c1) are taken (one band of a banded A).
 __global__ void k_sell16_len(const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t rows,
-                             int32_t *__restrict__ rl16, int32_t c0, int32_t c1) {
+                             int32_t *__restrict__ rl16, int32_t c0, int32_t c1, int nb4, int np) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  int64_t b = rp[r], len = rp[r + 1] - b;
+  const int64_t src = ray_of(r, nb4, np);  // the CSR row that row r holds
+  int64_t b = rp[src], len = rp[src + 1] - b;
   int64_t slot = 0;
   int32_t cb = 0;
   for (int64_t e = 0; e < len; ++e) {
@@ -405,10 +406,11 @@ __global__ void k_sell16_fill(const AngleC *__restrict__ ang, int model, int nx,
                               const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, int64_t rows,
                               const int64_t *__restrict__ cpw, const int64_t *__restrict__ cpb,
                               uint32_t *__restrict__ ow, int32_t *__restrict__ base, int *__restrict__ err,
-                              int32_t c0, int32_t c1) {
+                              int32_t c0, int32_t c1, int nb4) {
   int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  int64_t b = rp[r], len = rp[r + 1] - b;
+  const int64_t src = ray_of(r, nb4, np);  // the CSR row that row r holds
+  int64_t b = rp[src], len = rp[src + 1] - b;
   int64_t w0 = cpw[r >> 5], b0 = cpb[r >> 5];
   int q = (int)(r & 31);
   int64_t slot = 0;
@@ -423,8 +425,8 @@ __global__ void k_sell16_fill(const AngleC *__restrict__ ang, int model, int nx,
     }
     int64_t d = (int64_t)col - cb;
     if (d < 0 || d > 65535) atomicExch(err, 2);  // impossible after the early cut; reported
-    int ray = kTranspose ? col : (int)r;
-    int pix = kTranspose ? (int)r : col;
+    int ray = kTranspose ? col : (int)src;
+    int pix = kTranspose ? (int)src : col;
     int m = ray / np, k = ray % np;
     int ix = pix % nx, iy = pix / nx;
     AngleC A = ang[m];
@@ -510,15 +512,16 @@ tomo_status build_sell(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t 
 
 // The 16-bit SELL-32 form of A (or A^T) restricted to columns [c0, c1), into L.
 tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_t *cnt, int64_t *part,
-                         int *scratch, SellLp &L, int32_t c0, int32_t c1) {
+                         int *scratch, SellLp &L, int32_t c0, int32_t c1, bool pair_order = false) {
   const Csr &M = transpose ? h->AT : h->A;
   L.rows = M.rows;
+  L.nb4 = (!transpose && pair_order && h->nt % 2 == 0 && h->np % 4 == 0) ? h->np / 4 : 0;
   L.chunks = (M.rows + 31) / 32;
   TOMO_TRY(dmalloc(&L.rl, M.rows));
   TOMO_TRY(dmalloc(&L.cpw, L.chunks + 1));
   TOMO_TRY(dmalloc(&L.cpb, L.chunks + 1));
   const unsigned gr = (unsigned)((M.rows + 255) / 256), gc = (unsigned)((L.chunks + 255) / 256);
-  k_sell16_len<<<gr, 256, 0, st>>>(M.rp, M.ci, M.rows, L.rl, c0, c1);
+  k_sell16_len<<<gr, 256, 0, st>>>(M.rp, M.ci, M.rows, L.rl, c0, c1, L.nb4, h->np);
   int32_t *cntb = cnt + L.chunks;  // cnt holds enough entries for two per-chunk arrays
   k_chunk_sizes_rl<<<gc, 256, 0, st>>>(L.rl, M.rows, cnt, cntb);
   TOMO_TRY(scan_counts(cnt, L.chunks, L.cpw, part, scratch + 3, st));
@@ -533,7 +536,7 @@ tomo_status build_sell16(tomo_matrix *h, bool transpose, cudaStream_t st, int32_
   const double c = h->center;
 #define TOMO_FILL16(TR, W)                                                                                      \
   k_sell16_fill<TR, W><<<gr, 256, 0, st>>>(h->ang, h->model, h->nx, h->ny, h->np, c, M.rp, M.ci, M.rows, L.cpw,  \
-                                           L.cpb, L.ow, L.base, scratch, c0, c1)
+                                           L.cpb, L.ow, L.base, scratch, c0, c1, L.nb4)
   if (h->lp_dtype == TOMO_BF16) {
     if (transpose) TOMO_FILL16(true, __nv_bfloat16);
     else TOMO_FILL16(false, __nv_bfloat16);
@@ -1037,6 +1040,7 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
   // CSR pair (16 B/nnz) [+ SELL pair (~17 B/nnz)] [+ 16-bit pair (~9.5 B/nnz)] [+ tiled 16-bit A^T (~5 B/nnz)]
   const bool sell32 = !(o && o->no_fp32_sell);
   const bool at_tiles = lp != TOMO_F32 && !(o && o->no_at_tiles);
+  const bool pair_order = !(o && o->a_ray_order);
   size_t need = (size_t)nnz_a * (16 + (sell32 ? 18 : 0)) +
                 (size_t)(lp != TOMO_F32 ? nnz_a * 10 + (rows + cols) * 64 : 0) +
                 (size_t)(at_tiles ? nnz_a * 5 + (int64_t)nt * cols / 3 : 0);
@@ -1065,10 +1069,10 @@ tomo_status build_matrix(const tomo_geometry *g, const tomo_matrix_opts *o, cuda
       h->lpAb.resize(bands);
       for (int b = 0; b < bands; ++b) {
         const int32_t y0 = (int32_t)((int64_t)g->n_y * b / bands), y1 = (int32_t)((int64_t)g->n_y * (b + 1) / bands);
-        TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch, h->lpAb[b], y0 * g->n_x, y1 * g->n_x));
+        TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch, h->lpAb[b], y0 * g->n_x, y1 * g->n_x, pair_order));
       }
     } else {
-      TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch, h->lpA, 0, INT32_MAX));
+      TOMO_TRY(build_sell16(h, false, st, cnt, part, scratch, h->lpA, 0, INT32_MAX, pair_order));
     }
     TOMO_TRY(build_sell16(h, true, st, cnt, part, scratch, h->lpAT, 0, INT32_MAX));
     if (!(o && o->no_at_tiles)) TOMO_TRY(build_tile16(h, st));

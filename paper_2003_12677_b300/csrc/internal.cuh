@@ -59,14 +59,28 @@ struct Sell {
 // factor 1/a(theta) of the angle is applied by the kernels (per output row
 // for A, per gathered entry for A^T).  Padding slots carry weight 0 and
 // offset 0 (column = the segment base).
+// The 16-bit A may store its rows in pair order (nb4 > 0, n_theta even and n_p
+// a multiple of 4): row rho holds ray ray_of(rho), so that each group of 8
+// consecutive rows (the rows one warp takes at batch width 16) is 2 adjacent
+// angles x 4 adjacent bins, whose gathers meet the same image rows more often
+// than 8 bins of one angle do.
 struct SellLp {
   int64_t rows = 0, chunks = 0, slots = 0, bases = 0;
+  int32_t nb4 = 0;          // n_p / 4 when the rows are in pair order, else 0
   int64_t *cpw = nullptr;   // [chunks+1]
   int64_t *cpb = nullptr;   // [chunks+1]
   int32_t *rl = nullptr;    // [rows] padded slot count per row
   uint32_t *ow = nullptr;   // [slots]
   int32_t *base = nullptr;  // [bases]
 };
+
+// the ray (row of A) that row rho of a 16-bit A in pair order holds
+__host__ __device__ __forceinline__ int64_t ray_of(int64_t rho, int nb4, int np) {
+  if (nb4 == 0) return rho;
+  const int64_t grp = rho >> 3, m2 = grp / nb4;
+  const int j = (int)(rho & 7), b4 = (int)(grp - m2 * nb4);
+  return (2 * m2 + (j >> 2)) * np + 4 * b4 + (j & 3);
+}
 
 // 16-bit A^T in image tiles, for a pass that stages each tile's detector
 // window in shared memory (k_spmm_tile16).  The image is cut into tiles of

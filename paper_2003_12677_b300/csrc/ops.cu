@@ -974,7 +974,7 @@ void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream
     const int K = (int)op.bands->size();
     for (int b = 0; b < K; ++b) {
       const SellLp &L = (*op.bands)[b];
-      const Sell16View view{L.cpw, L.cpb, L.rl, L.ow, L.base, op.scale, op.np, inv_np};
+      const Sell16View view{L.cpw, L.cpb, L.rl, L.ow, L.base, op.scale, op.np, inv_np, L.nb4};
       if (b < K - 1) {
         const EpiBandPartial ep{op.partial, B, b == 0};
         if (op.bf16) {
@@ -1004,7 +1004,7 @@ void launch_spmm(const Op &op, const float *X, Epi epi, double *part, cudaStream
   } else if (op.format == TOMO_FMT_SELL16) {
     const SellLp &L = *op.lp;
     const float inv_np = 1.0f / (float)op.np;
-    const Sell16View view{L.cpw, L.cpb, L.rl, L.ow, L.base, op.scale, op.np, inv_np};
+    const Sell16View view{L.cpw, L.cpb, L.rl, L.ow, L.base, op.scale, op.np, inv_np, L.nb4};
     const TileMap map = tile_map(op, G, B);
 #define TOMO_SELL16(BF, TR, PRE)                                                                               \
   do {                                                                                                         \

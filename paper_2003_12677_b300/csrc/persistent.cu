@@ -662,7 +662,8 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
     b.rlT = h->sAT.rl;
     b.entT = h->sAT.ent;
     const float inv_np = 1.0f / (float)h->np;
-    b.lA = Sell16View{h->lpA.cpw, h->lpA.cpb, h->lpA.rl, h->lpA.ow, h->lpA.base, h->ang_scale, h->np, inv_np};
+    b.lA = Sell16View{h->lpA.cpw, h->lpA.cpb, h->lpA.rl, h->lpA.ow, h->lpA.base, h->ang_scale, h->np, inv_np,
+                      h->lpA.nb4};
     b.lT = Sell16View{h->lpAT.cpw, h->lpAT.cpb, h->lpAT.rl, h->lpAT.ow, h->lpAT.base, h->ang_scale, h->np, inv_np};
     b.rows = h->A.rows;
     b.cols = h->A.cols;
@@ -681,7 +682,7 @@ tomo_status run_cgls_batched(const tomo_request *reqs, int32_t n, int32_t iters,
       if (!h->lpAb.empty()) {
         std::vector<Sell16View> views;
         for (const SellLp &Lb : h->lpAb)
-          views.push_back(Sell16View{Lb.cpw, Lb.cpb, Lb.rl, Lb.ow, Lb.base, h->ang_scale, h->np, inv_np});
+          views.push_back(Sell16View{Lb.cpw, Lb.cpb, Lb.rl, Lb.ow, Lb.base, h->ang_scale, h->np, inv_np, Lb.nb4});
         Sell16View *dv = (Sell16View *)take(sizeof(Sell16View) * views.size());
         TOMO_CUDA(cudaMemcpyAsync(dv, views.data(), sizeof(Sell16View) * views.size(), cudaMemcpyHostToDevice, st));
         b.nbands = (int32_t)views.size();

@@ -442,6 +442,7 @@ struct Sell16View {
   const float *scale;
   int np;
   float inv_np;
+  int nb4 = 0;  // A in pair order (SellLp::nb4)
 };
 
 // kPre (A^T only): the gathered operand already carries the per-angle factor
@@ -488,12 +489,14 @@ __device__ __forceinline__ void sell16_rowgroups(const Sell16View &M, int64_t ro
         }
       }
     }
+    int64_t out = row;
     if constexpr (!kTrans) {
-      const float sc = __ldg(M.scale + div_exact((int)row, M.np, M.inv_np));
+      out = ray_of(row, M.nb4, M.np);
+      const float sc = __ldg(M.scale + div_exact((int)out, M.np, M.inv_np));
 #pragma unroll
       for (int t = 0; t < V; ++t) acc.v[t] *= sc;
     }
-    epi.template operator()<V>(row, l * V, acc, ss);
+    epi.template operator()<V>(out, l * V, acc, ss);
   }
 }
 
