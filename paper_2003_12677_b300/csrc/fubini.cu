@@ -491,10 +491,8 @@ tomo_status dalloc(T **p, size_t count) {
 
 void free_fubini(tomo_fubini *F) {
   if (!F) return;
-  if (F->plans) {
-    cufftDestroy(F->plan2);
-    cufftDestroy(F->plan1);
-  }
+  if (F->has_plan2) cufftDestroy(F->plan2);
+  if (F->has_plan1) cufftDestroy(F->plan1);
   free_normal(F);
   void *ptrs[] = {F->S.rp, F->S.ci, F->S.v, F->STs.rp, F->STs.ci, F->STs.v, F->STl.rp, F->STl.ci, F->STl.v,
                   F->rows_l, F->faT, F->deapod, F->dens, F->dens_h, F->grid, F->gridI,
@@ -841,10 +839,8 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
   k_fub_tables<<<(std::max(F->G, F->np) + kT - 1) / kT, kT, 0, st>>>(F->G, F->np, c, F->ph_grid, F->ph_rad,
                                                                       F->ph_bin);
   TOMO_CUDA(cudaGetLastError());
-  TOMO_TRY(dalloc(&F->grid, (size_t)G * G * F->Bf));
   TOMO_TRY(dalloc(&F->gridI, (size_t)G * G * F->Bf * 2));
   TOMO_TRY(dalloc(&F->polI, (size_t)rows * F->Bf * 2));
-  TOMO_TRY(dalloc(&F->pol, (size_t)rows * F->Bf));
   if (fused_ok(F->G)) {  // the adjoint's inverse 2D transform by register FFTs
     TOMO_TRY(ensure_twiddles(F, st));
     TOMO_TRY(dalloc(&F->faT, (size_t)F->Bf * F->G * F->n));
@@ -855,17 +851,22 @@ tomo_status fubini_create(const tomo_geometry *g, int32_t kw, cudaStream_t st, t
     k_fft_twiddles<<<(2 * F->np + kT - 1) / kT, kT, 0, st>>>(R1, R2, F->twP);
     TOMO_CUDA(cudaGetLastError());
   }
-  // cuFFT plans: G x G 2D transforms and length-np 1D transforms, contiguous batches
-  int dims2[2] = {F->G, F->G};
-  TOMO_TRY(cufft_check(cufftPlanMany(&F->plan2, 2, dims2, nullptr, 1, F->G * F->G, nullptr, 1, F->G * F->G,
-                                     CUFFT_C2C, F->Bf), "plan 2D"));
-  int dims1[1] = {F->np};
-  cufftResult r1 = cufftPlanMany(&F->plan1, 1, dims1, nullptr, 1, F->np, nullptr, 1, F->np, CUFFT_C2C, F->nt * F->Bf);
-  if (r1 != CUFFT_SUCCESS) {
-    cufftDestroy(F->plan2);
-    return cufft_check(r1, "plan 1D");
+  // cuFFT plans and their buffers, only for the sizes the register-FFT passes
+  // do not take: G x G 2D transforms and length-np 1D transforms, contiguous batches
+  if (!F->faT) {
+    TOMO_TRY(dalloc(&F->grid, (size_t)G * G * F->Bf));
+    int dims2[2] = {F->G, F->G};
+    TOMO_TRY(cufft_check(cufftPlanMany(&F->plan2, 2, dims2, nullptr, 1, F->G * F->G, nullptr, 1, F->G * F->G,
+                                       CUFFT_C2C, F->Bf), "plan 2D"));
+    F->has_plan2 = true;
   }
-  F->plans = true;
+  if (!F->twP) {
+    TOMO_TRY(dalloc(&F->pol, (size_t)rows * F->Bf));
+    int dims1[1] = {F->np};
+    TOMO_TRY(cufft_check(cufftPlanMany(&F->plan1, 1, dims1, nullptr, 1, F->np, nullptr, 1, F->np, CUFFT_C2C,
+                                       F->nt * F->Bf), "plan 1D"));
+    F->has_plan1 = true;
+  }
   TOMO_CUDA(cudaStreamSynchronize(st));
   guard.keep = true;
   *out = F;
@@ -877,8 +878,8 @@ void fubini_destroy(tomo_fubini *F) { free_fubini(F); }
 tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz, cudaStream_t st) {
   const int G = F->G, n = F->n, nt = F->nt, np = F->np, Bf = F->Bf;
   const int64_t rows = (int64_t)nt * np;
-  TOMO_TRY(cufft_check(cufftSetStream(F->plan2, st), "set stream"));
-  TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
+  if (F->has_plan2) TOMO_TRY(cufft_check(cufftSetStream(F->plan2, st), "set stream"));
+  if (F->has_plan1) TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
   for (int32_t s0 = 0; s0 < nz; s0 += Bf) {
     const int cnt = std::min<int32_t>(Bf, nz - s0);
     if (F->faT) {
@@ -907,8 +908,8 @@ tomo_status fubini_project(tomo_fubini *F, const float *x, float *y, int32_t nz,
 tomo_status fubini_backproject(tomo_fubini *F, const float *y, float *x, int32_t nz, int filter, cudaStream_t st) {
   const int G = F->G, n = F->n, nt = F->nt, np = F->np, Bf = F->Bf;
   const int64_t rows = (int64_t)nt * np;
-  TOMO_TRY(cufft_check(cufftSetStream(F->plan2, st), "set stream"));
-  TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
+  if (F->has_plan2) TOMO_TRY(cufft_check(cufftSetStream(F->plan2, st), "set stream"));
+  if (F->has_plan1) TOMO_TRY(cufft_check(cufftSetStream(F->plan1, st), "set stream"));
   const float scale = filter ? (float)(M_PI / ((double)np * nt)) : (float)(1.0 / np);
   const float *dens = filter == 1 ? F->dens : (filter == 2 ? F->dens_h : nullptr);
   for (int32_t s0 = 0; s0 < nz; s0 += Bf) {

@@ -45,8 +45,8 @@ struct tomo_fubini {
   cufftComplex *pol = nullptr;    // [Bf][nt][np]
   float2 *faT = nullptr;          // [Bf][G][n] the adjoint's column-transformed grid (register-FFT path)
   float2 *twP = nullptr;          // [2 np] W_np^{j2 k1} in both orders (register-FFT radial transforms)
-  cufftHandle plan2 = 0, plan1 = 0;
-  bool plans = false;
+  cufftHandle plan2 = 0, plan1 = 0;  // only for sizes the register-FFT passes do not take
+  bool has_plan2 = false, has_plan1 = false;
   // normal operator (normal.cu), built on first use per filter
   tomo::NormalKernel nk[3];
   int32_t Bn = 0;                 // slices per convolution pass
