@@ -115,9 +115,6 @@ constexpr int kTileRow = 64;          // bytes of a staged window row (16 slices
 constexpr int kTileBlockSlots = 4;    // slots of one entry block
 constexpr int kTileBlockBytes = 288;  // bytes of one entry block
 __host__ __device__ constexpr int tile_swz(int r) { return (r & ~3) | ((r & 1) << 1) | ((r >> 1) & 1); }
-static_assert(tile_swz(1) == 2 && tile_swz(2) == 1 && tile_swz(7) == 7 && tile_swz(tile_swz(13)) == 13 &&
-                  tile_swz(255) == 255,
-              "the staged row swap is a permutation of each aligned group of 4 rows");
 struct TileLp {
   int64_t tiles = 0, blocks = 0;
   int32_t tiles_x = 0, tiles_y = 0, nch = 0, W = 0;
